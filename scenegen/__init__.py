@@ -1,0 +1,267 @@
+"""Seeded inputs: scenes of disjoint segments on the 2^20 integer grid, their
+constrained Delaunay triangulation, a flip annealer (the paper's polishing
+step with edge flips, Sec. 3.2.7 and 3.3), and ray batches with start cells.
+
+This module only produces inputs.  Both the CUDA path (``paper_2112_05570_gb300``)
+and the CPU oracle (``oracle``) consume what it returns; it holds none of the
+walk / closest-hit arithmetic of Sec. 5.1.
+
+Domain: integer points of [0, D]^2 with D = 2^20; the square's four corners are
+vertices and its boundary is the triangulation hull.  Triangles are CCW and
+edge i is the edge opposite vertex i.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+D = 1 << 20
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "scenegen.cpp")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "libscenegen.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the generator library in-tree with g++ (host code, any arch)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(_LIBDIR, exist_ok=True)
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    L = ctypes.CDLL(_LIB)
+    i64, i32, u64, dbl, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
+    P = ctypes.POINTER
+    L.sg_gen_random_segments.restype = i64
+    L.sg_gen_random_segments.argtypes = [i64, u64, i32, dbl, dbl, dbl, dbl, vp, i64]
+    L.sg_gen_clustered.restype = i64
+    L.sg_gen_clustered.argtypes = [i64, u64, i32, dbl, dbl, dbl, i32, dbl, vp, i64]
+    L.sg_gen_circles.restype = i64
+    L.sg_gen_circles.argtypes = [i64, u64, i32, i32, i32, vp, i64]
+    L.sg_gen_dash_grid.restype = i64
+    L.sg_gen_dash_grid.argtypes = [i64, dbl, i32, vp, i64]
+    L.sg_gen_ring_of_circles.restype = i64
+    L.sg_gen_ring_of_circles.argtypes = [i64, i32, vp, i64]
+    L.sg_cdt_build.restype = vp
+    L.sg_cdt_build.argtypes = [i64, vp, i32, P(i32)]
+    L.sg_tri_import.restype = vp
+    L.sg_tri_import.argtypes = [i32, i64, vp, vp, i64, vp, vp, vp]
+    L.sg_tri_copy.restype = vp
+    L.sg_tri_copy.argtypes = [vp]
+    L.sg_tri_free.restype = None
+    L.sg_tri_free.argtypes = [vp]
+    L.sg_tri_status.restype = i32
+    L.sg_tri_status.argtypes = [vp]
+    L.sg_tri_sizes.restype = None
+    L.sg_tri_sizes.argtypes = [vp, P(i64), P(i64)]
+    L.sg_tri_export.restype = None
+    L.sg_tri_export.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.sg_tri_length.restype = ctypes.c_float
+    L.sg_tri_length.argtypes = [vp, i32]
+    L.sg_anneal.restype = i64
+    L.sg_anneal.argtypes = [vp, u64, dbl, dbl, dbl]
+    L.sg_rays_isotropic.restype = i64
+    L.sg_rays_isotropic.argtypes = [vp, i64, u64, vp, vp, vp, vp, vp, i32]
+    L.sg_rays_pinhole.restype = i64
+    L.sg_rays_pinhole.argtypes = [vp, i64, i64, dbl, u64, vp, vp, vp, vp, vp, i32]
+    _lib = L
+    return L
+
+
+def _ptr(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def _threads() -> int:
+    return max(1, min(os.cpu_count() or 1, 64))
+
+
+# ----------------------------------------------------------------------------- scenes
+def length_scale(n: int) -> float:
+    """Segment lengths shrink as sqrt(200/N) above 200 segments, as the paper's
+    line scenes scale their length with 1/sqrt(N) (Sec. 4.2)."""
+    return 1.0 if n <= 200 else float(np.sqrt(200.0 / n))
+
+
+def random_segments(n: int, seed: int, len_lo=0.005, len_hi=0.03, margin=0.01, scale=None) -> np.ndarray:
+    """n pairwise-disjoint random segments, lengths U[len_lo, len_hi] of the
+    domain side (times ``length_scale(n)``), endpoints >= margin from the border."""
+    L = _load()
+    out = np.zeros((n, 4), np.int32)
+    s = length_scale(n) if scale is None else scale
+    m = L.sg_gen_random_segments(n, seed, D, len_lo, len_hi, s, margin, _ptr(out), n)
+    return out[:m].copy()
+
+
+def clustered(n: int, seed: int, n_clusters=32, sigma=0.02, len_lo=0.005, len_hi=0.03) -> np.ndarray:
+    L = _load()
+    out = np.zeros((n, 4), np.int32)
+    m = L.sg_gen_clustered(n, seed, D, len_lo, len_hi, length_scale(n), n_clusters, sigma, _ptr(out), n)
+    return out[:m].copy()
+
+
+def circles(n_target: int, seed: int, min_sides=64, max_sides=1024) -> np.ndarray:
+    L = _load()
+    cap = n_target + max_sides + 8
+    out = np.zeros((cap, 4), np.int32)
+    m = L.sg_gen_circles(n_target, seed, D, min_sides, max_sides, _ptr(out), cap)
+    return out[:m].copy()
+
+
+def dash_grid(n_target: int, theta_deg: float) -> np.ndarray:
+    L = _load()
+    cap = 2 * n_target + 1024
+    out = np.zeros((cap, 4), np.int32)
+    m = L.sg_gen_dash_grid(n_target, theta_deg, D, _ptr(out), cap)
+    return out[:m].copy()
+
+
+def ring_of_circles(n_target: int) -> np.ndarray:
+    L = _load()
+    cap = n_target + 4096
+    out = np.zeros((cap, 4), np.int32)
+    m = L.sg_gen_ring_of_circles(n_target, D, _ptr(out), cap)
+    if m < 0:
+        raise RuntimeError("ring_of_circles: polygon rounding failed")
+    return out[:m].copy()
+
+
+# ----------------------------------------------------------------------------- triangulations
+@dataclass
+class Triangulation:
+    """A triangulation of [0,D]^2 whose constrained edges cover the segments.
+
+    vx, vy: int32 vertex coordinates; tri_v: (T,3) CCW vertex ids; tri_nb: (T,3)
+    neighbour across edge i (opposite vertex i) or -1 on the hull; tri_seg: (T,3)
+    scene segment id of a constrained edge or -1."""
+
+    vx: np.ndarray
+    vy: np.ndarray
+    tri_v: np.ndarray
+    tri_nb: np.ndarray
+    tri_seg: np.ndarray
+    segs: np.ndarray
+    kind: str = "cdt"
+    _h: int = field(default=0, repr=False)
+
+    @property
+    def n_tri(self) -> int:
+        return int(self.tri_v.shape[0])
+
+    @property
+    def n_vert(self) -> int:
+        return int(self.vx.shape[0])
+
+    def length(self, interior_only=False) -> float:
+        return float(_load().sg_tri_length(self._h, 1 if interior_only else 0))
+
+    def __del__(self):
+        if self._h and _lib is not None:
+            _lib.sg_tri_free(self._h)
+            self._h = 0
+
+
+def _export(h: int, segs: np.ndarray, kind: str) -> Triangulation:
+    L = _load()
+    nv, nt = ctypes.c_int64(), ctypes.c_int64()
+    L.sg_tri_sizes(h, ctypes.byref(nv), ctypes.byref(nt))
+    vx = np.zeros(nv.value, np.int32)
+    vy = np.zeros(nv.value, np.int32)
+    tv = np.zeros((nt.value, 3), np.int32)
+    tn = np.zeros((nt.value, 3), np.int32)
+    ts = np.zeros((nt.value, 3), np.int32)
+    L.sg_tri_export(h, _ptr(vx), _ptr(vy), _ptr(tv), _ptr(tn), _ptr(ts))
+    return Triangulation(vx, vy, tv, tn, ts, segs, kind, h)
+
+
+def cdt(segs: np.ndarray) -> Triangulation:
+    """Constrained Delaunay triangulation of the segments inside [0,D]^2."""
+    L = _load()
+    segs = np.ascontiguousarray(segs, np.int32).reshape(-1, 4)
+    st = ctypes.c_int32(0)
+    h = L.sg_cdt_build(segs.shape[0], _ptr(segs), D, ctypes.byref(st))
+    if st.value < 0:
+        L.sg_tri_free(h)
+        raise RuntimeError(f"CDT construction failed with status {st.value}")
+    return _export(h, segs, "cdt")
+
+
+def anneal(tri: Triangulation, seed: int, sweeps=20.0, T0=0.02, T1=1e-4) -> Triangulation:
+    """A copy of ``tri`` annealed over edge flips: greedy flips to shorter
+    diagonals, then simulated annealing with temperature T0 -> T1 (units of the
+    domain side, as the paper's unit-square schedule, Sec. 3.3), then greedy
+    flips again; the shorter of (greedy only, annealed) is kept."""
+    L = _load()
+    h = L.sg_tri_copy(tri._h)
+    L.sg_anneal(h, seed, float(sweeps), float(T0) * D, float(T1) * D)
+    return _export(h, tri.segs, "annealed")
+
+
+def from_arrays(vx, vy, tri_v, tri_nb, tri_seg, segs, kind="given") -> Triangulation:
+    """Wrap caller-made arrays (e.g. hand-written test triangulations)."""
+    L = _load()
+    vx = np.ascontiguousarray(vx, np.int32)
+    vy = np.ascontiguousarray(vy, np.int32)
+    tv = np.ascontiguousarray(tri_v, np.int32).reshape(-1, 3)
+    tn = np.ascontiguousarray(tri_nb, np.int32).reshape(-1, 3)
+    ts = np.ascontiguousarray(tri_seg, np.int32).reshape(-1, 3)
+    h = L.sg_tri_import(D, vx.size, _ptr(vx), _ptr(vy), tv.shape[0], _ptr(tv), _ptr(tn), _ptr(ts))
+    return Triangulation(vx, vy, tv, tn, ts, np.ascontiguousarray(segs, np.int32).reshape(-1, 4), kind, h)
+
+
+# ----------------------------------------------------------------------------- rays
+@dataclass
+class Rays:
+    """Ray batch: int32 origins, fp32 directions on the 2^-22 grid, and the
+    triangle (export numbering) whose interior holds each origin."""
+
+    ox: np.ndarray
+    oy: np.ndarray
+    dx: np.ndarray
+    dy: np.ndarray
+    start: np.ndarray
+
+    def __len__(self):
+        return int(self.ox.shape[0])
+
+    def take(self, idx) -> "Rays":
+        return Rays(self.ox[idx], self.oy[idx], self.dx[idx], self.dy[idx], self.start[idx])
+
+
+def _alloc_rays(n):
+    return Rays(np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.float32),
+                np.zeros(n, np.float32), np.zeros(n, np.int32))
+
+
+def rays_isotropic(tri: Triangulation, n: int, seed: int, threads: int | None = None) -> Rays:
+    """Uniform, isotropic rays inside the domain (Sec. 5.4)."""
+    L = _load()
+    r = _alloc_rays(n)
+    L.sg_rays_isotropic(tri._h, n, seed, _ptr(r.ox), _ptr(r.oy), _ptr(r.dx), _ptr(r.dy), _ptr(r.start),
+                        threads or _threads())
+    return r
+
+
+def rays_pinhole(tri: Triangulation, n_eyes: int, rays_per_eye: int, seed: int, fov_deg=90.0,
+                 threads: int | None = None) -> Rays:
+    """Coherent pinhole fans: n_eyes eyes, rays_per_eye rays over fov_deg each."""
+    L = _load()
+    r = _alloc_rays(n_eyes * rays_per_eye)
+    L.sg_rays_pinhole(tri._h, n_eyes, rays_per_eye, fov_deg, seed, _ptr(r.ox), _ptr(r.oy), _ptr(r.dx),
+                      _ptr(r.dy), _ptr(r.start), threads or _threads())
+    return r

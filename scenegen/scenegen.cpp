@@ -1,0 +1,1096 @@
+// Seeded inputs for the constrained-triangulation ray walk: scene segments on the
+// integer grid, the constrained Delaunay triangulation (CDT) that contains them,
+// a flip-based annealer that lowers its total edge length, and ray batches with
+// their start triangles.
+//
+// This module is the offline CPU prerequisite of the method (Sec. 3.5: an initial
+// CDT, Sec. 3.2.7 / 3.3: annealing with edge flips).  It is the ONE module that
+// both the CUDA path and the CPU oracle consume, and it contains none of the
+// ray-walk / closest-hit arithmetic (Sec. 5.1): it only produces inputs.
+//
+// Conventions (the domain): vertices are integer points of [0, D]^2 with
+// D = 2^20; the four corners of that square are vertices and its boundary is the
+// hull of every triangulation.  Triangles are CCW; edge i of a triangle is the
+// edge opposite its vertex i.  Neighbour -1 = hull.  tri_seg[3t+i] = scene
+// segment id carried by edge i (a constrained edge) or -1.
+//
+// Exactness: all geometric predicates here are exact (int64 orientation,
+// int128 in-circle), so the CDT is built without tolerances.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+namespace {
+
+typedef __int128 i128;
+
+struct Pt {
+  int32_t x, y;
+};
+static inline bool operator==(const Pt& a, const Pt& b) { return a.x == b.x && a.y == b.y; }
+
+// ---------------------------------------------------------------- random numbers
+// SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014).  One counter-based stream per (seed, stream id).
+struct Rng {
+  uint64_t s;
+  explicit Rng(uint64_t seed, uint64_t stream = 0) {
+    s = seed;
+    uint64_t t = stream * 0xD1B54A32D192ED03ull + 0x8CB92BA72F3D8DD7ull;
+    s ^= mix(t);
+    (void)next();
+  }
+  static uint64_t mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  uint64_t next() { return mix(s += 0x9E3779B97F4A7C15ull); }
+  double uni() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }  // [0,1)
+  uint32_t below(uint32_t n) { return (uint32_t)(((next() >> 32) * (uint64_t)n) >> 32); }
+  double normal() {  // Box-Muller
+    double u1 = uni(), u2 = uni();
+    if (u1 < 1e-300) u1 = 1e-300;
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+  }
+};
+
+// ---------------------------------------------------------------- exact predicates
+static inline int64_t orient(const Pt& a, const Pt& b, const Pt& c) {
+  return (int64_t)(b.x - a.x) * (int64_t)(c.y - a.y) - (int64_t)(b.y - a.y) * (int64_t)(c.x - a.x);
+}
+static inline int sgn(int64_t v) { return (v > 0) - (v < 0); }
+static inline int sgn128(i128 v) { return (v > 0) - (v < 0); }
+
+// > 0 iff d lies strictly inside the circumcircle of the CCW triangle (a, b, c).
+static inline int incircle(const Pt& a, const Pt& b, const Pt& c, const Pt& d) {
+  int64_t adx = a.x - d.x, ady = a.y - d.y;
+  int64_t bdx = b.x - d.x, bdy = b.y - d.y;
+  int64_t cdx = c.x - d.x, cdy = c.y - d.y;
+  i128 al = (i128)adx * adx + (i128)ady * ady;
+  i128 bl = (i128)bdx * bdx + (i128)bdy * bdy;
+  i128 cl = (i128)cdx * cdx + (i128)cdy * cdy;
+  i128 det = al * ((i128)bdx * cdy - (i128)bdy * cdx) + bl * ((i128)cdx * ady - (i128)cdy * adx) +
+             cl * ((i128)adx * bdy - (i128)ady * bdx);
+  return sgn128(det);
+}
+
+static inline bool on_closed_box(const Pt& a, const Pt& b, const Pt& p) {
+  return std::min(a.x, b.x) <= p.x && p.x <= std::max(a.x, b.x) && std::min(a.y, b.y) <= p.y &&
+         p.y <= std::max(a.y, b.y);
+}
+
+// Closed segments [a,b] and [c,d] share at least one point.
+static bool seg_touch(const Pt& a, const Pt& b, const Pt& c, const Pt& d) {
+  int o1 = sgn(orient(a, b, c)), o2 = sgn(orient(a, b, d));
+  int o3 = sgn(orient(c, d, a)), o4 = sgn(orient(c, d, b));
+  if (o1 * o2 < 0 && o3 * o4 < 0) return true;
+  if (o1 == 0 && on_closed_box(a, b, c)) return true;
+  if (o2 == 0 && on_closed_box(a, b, d)) return true;
+  if (o3 == 0 && on_closed_box(c, d, a)) return true;
+  if (o4 == 0 && on_closed_box(c, d, b)) return true;
+  return false;
+}
+
+static inline int64_t len2(const Pt& a, const Pt& b) {
+  int64_t dx = a.x - b.x, dy = a.y - b.y;
+  return dx * dx + dy * dy;
+}
+
+// ---------------------------------------------------------------- segment soup with a hash grid
+struct SegGrid {
+  int32_t D;
+  int G;
+  double cell;
+  std::vector<std::vector<int32_t>> cells;
+  std::vector<Pt> A, B;
+  SegGrid(int32_t D_, double cell_size) : D(D_) {
+    G = (int)std::ceil((double)D / cell_size);
+    G = std::max(1, std::min(G, 4096));
+    cell = (double)D / G + 1e-9;
+    cells.assign((size_t)G * G, {});
+  }
+  void range(const Pt& a, const Pt& b, int& i0, int& i1, int& j0, int& j1) const {
+    i0 = std::clamp((int)(std::min(a.x, b.x) / cell), 0, G - 1);
+    i1 = std::clamp((int)(std::max(a.x, b.x) / cell), 0, G - 1);
+    j0 = std::clamp((int)(std::min(a.y, b.y) / cell), 0, G - 1);
+    j1 = std::clamp((int)(std::max(a.y, b.y) / cell), 0, G - 1);
+  }
+  // true if the closed segment [a,b] shares a point with any stored segment
+  bool touches(const Pt& a, const Pt& b) const {
+    int i0, i1, j0, j1;
+    range(a, b, i0, i1, j0, j1);
+    for (int j = j0; j <= j1; ++j)
+      for (int i = i0; i <= i1; ++i)
+        for (int32_t s : cells[(size_t)j * G + i])
+          if (seg_touch(a, b, A[s], B[s])) return true;
+    return false;
+  }
+  void add(const Pt& a, const Pt& b) {
+    int id = (int)A.size();
+    A.push_back(a);
+    B.push_back(b);
+    int i0, i1, j0, j1;
+    range(a, b, i0, i1, j0, j1);
+    for (int j = j0; j <= j1; ++j)
+      for (int i = i0; i <= i1; ++i) cells[(size_t)j * G + i].push_back(id);
+  }
+};
+
+static inline int32_t rnd_coord(double v) { return (int32_t)std::llround(v); }
+
+// Random, pairwise disjoint segments (no shared points), lengths uniform in
+// [len_lo, len_hi] * D * scale, centres uniform (or from Gaussian clusters),
+// endpoints at least `margin`*D from the border.
+static int64_t gen_segments(int64_t n, uint64_t seed, int32_t D, double len_lo, double len_hi, double scale,
+                            double margin, int n_clusters, double sigma, int32_t* out, int64_t cap) {
+  Rng rng(seed, 0x5E6);
+  double lmax = len_hi * D * scale;
+  SegGrid grid(D, std::max(lmax, (double)D / 4096.0));
+  double lo = margin * D, hi = (1.0 - margin) * D;
+  std::vector<double> ccx, ccy;
+  for (int c = 0; c < n_clusters; ++c) {
+    ccx.push_back((0.1 + 0.8 * rng.uni()) * D);
+    ccy.push_back((0.1 + 0.8 * rng.uni()) * D);
+  }
+  int64_t cnt = 0, tries = 0, max_tries = std::max<int64_t>(1000 * n, 100000);
+  while (cnt < n && cnt < cap && tries < max_tries) {
+    ++tries;
+    double cx, cy;
+    if (n_clusters > 0) {
+      int c = (int)rng.below((uint32_t)n_clusters);
+      cx = ccx[c] + sigma * D * rng.normal();
+      cy = ccy[c] + sigma * D * rng.normal();
+    } else {
+      cx = lo + (hi - lo) * rng.uni();
+      cy = lo + (hi - lo) * rng.uni();
+    }
+    double L = D * scale * (len_lo + (len_hi - len_lo) * rng.uni());
+    double th = 6.283185307179586 * rng.uni();
+    double hx = 0.5 * L * std::cos(th), hy = 0.5 * L * std::sin(th);
+    Pt a{rnd_coord(cx - hx), rnd_coord(cy - hy)}, b{rnd_coord(cx + hx), rnd_coord(cy + hy)};
+    if (a == b) continue;
+    if (a.x < lo || a.x > hi || a.y < lo || a.y > hi || b.x < lo || b.x > hi || b.y < lo || b.y > hi) continue;
+    if (grid.touches(a, b)) continue;
+    grid.add(a, b);
+    out[4 * cnt + 0] = a.x;
+    out[4 * cnt + 1] = a.y;
+    out[4 * cnt + 2] = b.x;
+    out[4 * cnt + 3] = b.y;
+    ++cnt;
+  }
+  return cnt;
+}
+
+// Closed regular polygon with m sides around (cx, cy), radius r, phase phi,
+// vertices rounded to the grid.  Returns false if rounding collapsed a side.
+static bool polygon(double cx, double cy, double r, int m, double phi, std::vector<Pt>& v) {
+  v.clear();
+  for (int k = 0; k < m; ++k) {
+    double a = phi + 6.283185307179586 * k / m;
+    v.push_back(Pt{rnd_coord(cx + r * std::cos(a)), rnd_coord(cy + r * std::sin(a))});
+  }
+  for (int k = 0; k < m; ++k)
+    if (v[k] == v[(k + 1) % m]) return false;
+  // reject a fold-back from rounding: consecutive sides must not turn by more
+  // than 90 degrees (slight clockwise turns from rounding are harmless)
+  for (int k = 0; k < m; ++k) {
+    const Pt &a = v[k], &b = v[(k + 1) % m], &c = v[(k + 2) % m];
+    int64_t dot = (int64_t)(b.x - a.x) * (c.x - b.x) + (int64_t)(b.y - a.y) * (c.y - b.y);
+    if (dot <= 0) return false;
+  }
+  return true;
+}
+
+static int64_t emit_polygon(const std::vector<Pt>& v, int32_t* out, int64_t cnt, int64_t cap) {
+  int m = (int)v.size();
+  for (int k = 0; k < m && cnt < cap; ++k) {
+    out[4 * cnt + 0] = v[k].x;
+    out[4 * cnt + 1] = v[k].y;
+    out[4 * cnt + 2] = v[(k + 1) % m].x;
+    out[4 * cnt + 3] = v[(k + 1) % m].y;
+    ++cnt;
+  }
+  return cnt;
+}
+
+// ---------------------------------------------------------------- triangulation
+struct Tri {
+  int32_t v[3];
+  int32_t n[3];
+  int32_t c[3];
+};
+
+struct Triangulation {
+  int32_t D = 0;
+  std::vector<Pt> P;
+  std::vector<Tri> T;
+  std::vector<int32_t> vtri;
+  int32_t last = 0;
+  Rng rng{12345, 7};
+  int status = 0;  // 0 ok, <0 error
+
+  static int idx_of(const Tri& t, int v) { return t.v[0] == v ? 0 : (t.v[1] == v ? 1 : (t.v[2] == v ? 2 : -1)); }
+  int nb_edge(int u, int t) const {
+    const Tri& x = T[u];
+    return x.n[0] == t ? 0 : (x.n[1] == t ? 1 : (x.n[2] == t ? 2 : -1));
+  }
+  void replace_nb(int x, int old_t, int new_t) {
+    if (x < 0) return;
+    for (int k = 0; k < 3; ++k)
+      if (T[x].n[k] == old_t) {
+        T[x].n[k] = new_t;
+        return;
+      }
+  }
+
+  void init_square(int32_t D_) {
+    D = D_;
+    P = {{0, 0}, {D, 0}, {D, D}, {0, D}};
+    vtri = {0, 0, 0, 1};
+    T.clear();
+    T.push_back(Tri{{0, 1, 2}, {-1, 1, -1}, {-1, -1, -1}});
+    T.push_back(Tri{{0, 2, 3}, {-1, -1, 0}, {-1, -1, -1}});
+    last = 0;
+  }
+
+  // Visibility walk with a random first edge (Devillers, Pion & Teillaud,
+  // "Walking in a triangulation", 2002); terminates with probability one.
+  int locate(const Pt& p, int start, Rng& r) const {
+    int t = start;
+    for (int64_t guard = 0; guard < 50000000; ++guard) {
+      const Tri& tr = T[t];
+      int s = (int)r.below(3);
+      bool moved = false;
+      for (int k = 0; k < 3; ++k) {
+        int i = (s + k) % 3;
+        if (orient(P[tr.v[(i + 1) % 3]], P[tr.v[(i + 2) % 3]], p) < 0) {
+          if (tr.n[i] < 0) return -1;
+          t = tr.n[i];
+          moved = true;
+          break;
+        }
+      }
+      if (!moved) return t;
+    }
+    return -1;
+  }
+
+  void legalize(std::vector<std::pair<int, int>>& st) {
+    while (!st.empty()) {
+      auto [t, i] = st.back();
+      st.pop_back();
+      int u = T[t].n[i];
+      if (u < 0 || T[t].c[i] >= 0) continue;
+      int j = nb_edge(u, t);
+      int s = T[u].v[j];
+      if (incircle(P[T[t].v[0]], P[T[t].v[1]], P[T[t].v[2]], P[s]) > 0) {
+        flip(t, i);
+        st.push_back({t, 0});
+        st.push_back({u, 0});
+      }
+    }
+  }
+
+  // Flip the edge i of t.  Before: t = (p, q, r), u = (s, r, q) across edge i.
+  // After: t = (p, q, s), u = (p, s, r).
+  void flip(int t, int i) {
+    Tri ot = T[t];
+    int p = ot.v[i], q = ot.v[(i + 1) % 3], r = ot.v[(i + 2) % 3];
+    int u = ot.n[i];
+    Tri ou = T[u];
+    int j = nb_edge(u, t);
+    int s = ou.v[j];
+    int nA = ot.n[(i + 1) % 3], nB = ot.n[(i + 2) % 3];
+    int cA = ot.c[(i + 1) % 3], cB = ot.c[(i + 2) % 3];
+    int nC = ou.n[(j + 1) % 3], nD = ou.n[(j + 2) % 3];
+    int cC = ou.c[(j + 1) % 3], cD = ou.c[(j + 2) % 3];
+    T[t] = Tri{{p, q, s}, {nC, u, nB}, {cC, -1, cB}};
+    T[u] = Tri{{p, s, r}, {nD, nA, t}, {cD, cA, -1}};
+    replace_nb(nA, t, u);
+    replace_nb(nC, u, t);
+    vtri[p] = t;
+    vtri[q] = t;
+    vtri[s] = t;
+    vtri[r] = u;
+  }
+
+  void split_tri(int t, int pi, std::vector<std::pair<int, int>>& st) {
+    Tri o = T[t];
+    int a = o.v[0], b = o.v[1], c = o.v[2];
+    int t1 = (int)T.size(), t2 = t1 + 1;
+    T.resize(T.size() + 2);
+    T[t] = Tri{{pi, b, c}, {o.n[0], t1, t2}, {o.c[0], -1, -1}};
+    T[t1] = Tri{{pi, c, a}, {o.n[1], t2, t}, {o.c[1], -1, -1}};
+    T[t2] = Tri{{pi, a, b}, {o.n[2], t, t1}, {o.c[2], -1, -1}};
+    replace_nb(o.n[1], t, t1);
+    replace_nb(o.n[2], t, t2);
+    vtri[pi] = t;
+    vtri[b] = t;
+    vtri[c] = t;
+    vtri[a] = t1;
+    st.push_back({t, 0});
+    st.push_back({t1, 0});
+    st.push_back({t2, 0});
+    last = t;
+  }
+
+  // p lies on edge i of t (between q and r, apex a); split both sides.
+  void split_edge(int t, int i, int pi, std::vector<std::pair<int, int>>& st) {
+    Tri ot = T[t];
+    int a = ot.v[i], q = ot.v[(i + 1) % 3], r = ot.v[(i + 2) % 3];
+    int nq = ot.n[(i + 1) % 3], nr = ot.n[(i + 2) % 3];
+    int cs = ot.c[i], cq = ot.c[(i + 1) % 3], cr = ot.c[(i + 2) % 3];
+    int u = ot.n[i];
+    int t2 = (int)T.size();
+    T.push_back(Tri{});
+    int u2 = -1;
+    if (u >= 0) {
+      u2 = (int)T.size();
+      T.push_back(Tri{});
+    }
+    T[t] = Tri{{a, q, pi}, {u2, t2, nr}, {cs, -1, cr}};
+    T[t2] = Tri{{a, pi, r}, {u, nq, t}, {cs, cq, -1}};
+    replace_nb(nq, t, t2);
+    vtri[a] = t;
+    vtri[q] = t;
+    vtri[pi] = t;
+    vtri[r] = t2;
+    st.push_back({t, 2});
+    st.push_back({t2, 1});
+    if (u >= 0) {
+      Tri ou = T[u];
+      int j = nb_edge(u, t);
+      int s = ou.v[j];
+      int nur = ou.n[(j + 1) % 3], nuq = ou.n[(j + 2) % 3];
+      int cur = ou.c[(j + 1) % 3], cuq = ou.c[(j + 2) % 3];
+      T[u] = Tri{{s, r, pi}, {t2, u2, nuq}, {cs, -1, cuq}};
+      T[u2] = Tri{{s, pi, q}, {t, nur, u}, {cs, cur, -1}};
+      replace_nb(nur, u, u2);
+      vtri[s] = u;
+      st.push_back({u, 2});
+      st.push_back({u2, 1});
+    }
+    last = t;
+  }
+
+  // Insert a point; returns its vertex index (existing index for a duplicate).
+  int insert_point(const Pt& p) {
+    int t = locate(p, last, rng);
+    if (t < 0) {
+      status = -2;
+      return -1;
+    }
+    const Tri& tr = T[t];
+    int64_t o[3];
+    int zeros = 0, zi = -1;
+    for (int i = 0; i < 3; ++i) {
+      o[i] = orient(P[tr.v[(i + 1) % 3]], P[tr.v[(i + 2) % 3]], p);
+      if (o[i] == 0) {
+        ++zeros;
+        zi = i;
+      }
+    }
+    if (zeros >= 2) {
+      for (int k = 0; k < 3; ++k)
+        if (P[tr.v[k]] == p) return tr.v[k];
+      status = -3;
+      return -1;
+    }
+    int pi = (int)P.size();
+    P.push_back(p);
+    vtri.push_back(t);
+    std::vector<std::pair<int, int>> st;
+    if (zeros == 1)
+      split_edge(t, zi, pi, st);
+    else
+      split_tri(t, pi, st);
+    legalize(st);
+    last = vtri[pi];
+    return pi;
+  }
+
+  template <class F>
+  bool for_fan(int a, F f) const {
+    int t0 = vtri[a], t = t0;
+    do {
+      int k = idx_of(T[t], a);
+      if (f(t, k)) return true;
+      t = T[t].n[(k + 1) % 3];
+    } while (t != t0 && t >= 0);
+    if (t < 0) {
+      int k0 = idx_of(T[t0], a);
+      t = T[t0].n[(k0 + 2) % 3];
+      while (t >= 0) {
+        int k = idx_of(T[t], a);
+        if (f(t, k)) return true;
+        t = T[t].n[(k + 2) % 3];
+      }
+    }
+    return false;
+  }
+
+  // Edge (a,b): triangle t and its edge index i (edge opposite the third vertex).
+  bool find_edge(int a, int b, int& to, int& io) const {
+    return for_fan(a, [&](int t, int k) {
+      const Tri& x = T[t];
+      if (x.v[(k + 1) % 3] == b) {
+        to = t;
+        io = (k + 2) % 3;
+        return true;
+      }
+      if (x.v[(k + 2) % 3] == b) {
+        to = t;
+        io = (k + 1) % 3;
+        return true;
+      }
+      return false;
+    });
+  }
+
+  void mark(int t, int i, int seg) {
+    T[t].c[i] = seg;
+    int u = T[t].n[i];
+    if (u >= 0) T[u].c[nb_edge(u, t)] = seg;
+  }
+
+  bool strictly_convex(int t, int i, int& x, int& y) const {
+    int u = T[t].n[i];
+    if (u < 0) return false;
+    x = T[t].v[i];
+    y = T[u].v[nb_edge(u, t)];
+    int q = T[t].v[(i + 1) % 3], r = T[t].v[(i + 2) % 3];
+    return sgn(orient(P[x], P[y], P[q])) * sgn(orient(P[x], P[y], P[r])) < 0;
+  }
+
+  // Sloan's edge-flip constraint insertion (Sloan, "A fast algorithm for
+  // generating constrained Delaunay triangulations", 1993).
+  void insert_segment(int a0, int b0, int seg) {
+    std::vector<std::pair<int, int>> work{{a0, b0}};
+    int guard = 0;
+    while (!work.empty()) {
+      if (++guard > 1000000) {
+        status = -4;
+        return;
+      }
+      auto [a, b] = work.back();
+      work.pop_back();
+      int t, i;
+      if (a == b) continue;
+      if (find_edge(a, b, t, i)) {
+        if (T[t].c[i] >= 0 && T[t].c[i] != seg) status = -5;  // overlapping segments
+        mark(t, i, seg);
+        continue;
+      }
+      const Pt A = P[a], B = P[b];
+      // first triangle of the fan of a that the segment enters
+      int ft = -1, fe = -1, onv = -1;
+      for_fan(a, [&](int tt, int k) {
+        int u = T[tt].v[(k + 1) % 3], w = T[tt].v[(k + 2) % 3];
+        int64_t ou = orient(A, B, P[u]), ow = orient(A, B, P[w]);
+        for (int z : {u, w}) {
+          int64_t oz = (z == u) ? ou : ow;
+          if (oz == 0 && z >= 0) {
+            int64_t dot = (int64_t)(P[z].x - A.x) * (B.x - A.x) + (int64_t)(P[z].y - A.y) * (B.y - A.y);
+            if (dot > 0 && len2(A, P[z]) < len2(A, B)) {
+              onv = z;
+              return true;
+            }
+          }
+        }
+        if (ou < 0 && ow > 0) {
+          ft = tt;
+          fe = k;
+          return true;
+        }
+        return false;
+      });
+      if (onv >= 0) {
+        work.push_back({onv, b});
+        work.push_back({a, onv});
+        continue;
+      }
+      if (ft < 0) {
+        status = -6;
+        return;
+      }
+      // walk across the triangles pierced by (a,b), collecting crossed edges
+      std::vector<std::pair<int, int>> cross;
+      int t_cur = ft, e = fe;
+      int u = T[ft].v[(fe + 1) % 3], w = T[ft].v[(fe + 2) % 3];
+      bool split = false;
+      while (true) {
+        if (T[t_cur].c[e] >= 0) {
+          status = -7;  // crossing constraints
+          return;
+        }
+        cross.push_back({u, w});
+        int nt = T[t_cur].n[e];
+        if (nt < 0) {
+          status = -8;
+          return;
+        }
+        int j = nb_edge(nt, t_cur);
+        int z = T[nt].v[j];
+        if (z == b) break;
+        int64_t oz = orient(A, B, P[z]);
+        if (oz == 0) {
+          work.push_back({z, b});
+          work.push_back({a, z});
+          split = true;
+          break;
+        }
+        // nt = (z, w, u) CCW starting at j
+        if (oz < 0) {
+          e = (j + 2) % 3;  // exits through (z, w)
+          u = z;
+        } else {
+          e = (j + 1) % 3;  // exits through (u, z)
+          w = z;
+        }
+        t_cur = nt;
+      }
+      if (split) continue;
+      // remove crossings by flips
+      std::vector<std::pair<int, int>> fresh;
+      size_t head = 0;
+      int64_t fguard = 0;
+      while (head < cross.size()) {
+        if (++fguard > 50000000) {
+          status = -9;
+          return;
+        }
+        auto [p, q] = cross[head++];
+        int tt, ii;
+        if (!find_edge(p, q, tt, ii)) {
+          status = -10;
+          return;
+        }
+        int x, y;
+        if (strictly_convex(tt, ii, x, y)) {
+          flip(tt, ii);
+          int64_t sx = sgn(orient(A, B, P[x])), sy = sgn(orient(A, B, P[y]));
+          if (sx * sy < 0)
+            cross.push_back({x, y});
+          else
+            fresh.push_back({x, y});
+        } else {
+          cross.push_back({p, q});
+        }
+        if (head > 4096 && head * 2 > cross.size()) {
+          cross.erase(cross.begin(), cross.begin() + head);
+          head = 0;
+        }
+      }
+      // restore the Delaunay property among the new edges
+      bool swapped = true;
+      int rounds = 0;
+      while (swapped && ++rounds < 10000) {
+        swapped = false;
+        for (auto& ed : fresh) {
+          if ((ed.first == a && ed.second == b) || (ed.first == b && ed.second == a)) continue;
+          int tt, ii;
+          if (!find_edge(ed.first, ed.second, tt, ii)) continue;
+          if (T[tt].c[ii] >= 0) continue;
+          int uu = T[tt].n[ii];
+          if (uu < 0) continue;
+          int s = T[uu].v[nb_edge(uu, tt)];
+          if (incircle(P[T[tt].v[0]], P[T[tt].v[1]], P[T[tt].v[2]], P[s]) > 0) {
+            int x, y;
+            if (!strictly_convex(tt, ii, x, y)) continue;
+            flip(tt, ii);
+            ed = {x, y};
+            swapped = true;
+          }
+        }
+      }
+      if (find_edge(a, b, t, i))
+        mark(t, i, seg);
+      else
+        status = -11;
+    }
+  }
+
+  // Lawson flips on every unconstrained interior edge until all are locally
+  // (constrained-)Delaunay.
+  void make_delaunay() {
+    std::vector<std::pair<int, int>> st;
+    for (int t = 0; t < (int)T.size(); ++t)
+      for (int i = 0; i < 3; ++i)
+        if (T[t].n[i] > t) st.push_back({t, i});
+    while (!st.empty()) {
+      auto [t, i] = st.back();
+      st.pop_back();
+      int u = T[t].n[i];
+      if (u < 0 || T[t].c[i] >= 0) continue;
+      int j = nb_edge(u, t);
+      if (j < 0) continue;
+      int s = T[u].v[j];
+      if (incircle(P[T[t].v[0]], P[T[t].v[1]], P[T[t].v[2]], P[s]) > 0) {
+        int x, y;
+        if (!strictly_convex(t, i, x, y)) continue;
+        flip(t, i);
+        for (int k = 0; k < 3; ++k) {
+          st.push_back({t, k});
+          st.push_back({u, k});
+        }
+      }
+    }
+  }
+
+  double total_length(bool interior_only) const;
+};
+
+// Hilbert index of (x, y) on a 2^order grid (the classic rotate-and-flip form).
+static uint64_t hilbert_d(int order, uint32_t x, uint32_t y) {
+  uint64_t d = 0;
+  for (uint32_t s = 1u << (order - 1); s > 0; s >>= 1) {
+    uint32_t rx = (x & s) > 0, ry = (y & s) > 0;
+    d += (uint64_t)s * s * ((3 * rx) ^ ry);
+    if (ry == 0) {
+      if (rx == 1) {
+        x = s - 1 - x;
+        y = s - 1 - y;
+      }
+      std::swap(x, y);
+    }
+  }
+  return d;
+}
+
+// Compensated (Kahan) fp32 sum of edge lengths.
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  void add(float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+static inline float edge_len(const Pt& a, const Pt& b) { return std::sqrt((float)len2(a, b)); }
+
+double Triangulation::total_length(bool interior_only) const {
+  KahanF k;
+  for (int t = 0; t < (int)T.size(); ++t)
+    for (int i = 0; i < 3; ++i) {
+      int u = T[t].n[i];
+      if (u >= 0 && u < t) continue;
+      if (u < 0 && interior_only) continue;
+      k.add(edge_len(P[T[t].v[(i + 1) % 3]], P[T[t].v[(i + 2) % 3]]));
+    }
+  return (double)k.s;
+}
+
+static Triangulation* build_cdt(int64_t n_seg, const int32_t* seg, int32_t D) {
+  auto* tr = new Triangulation();
+  tr->init_square(D);
+  // unique endpoints, inserted in Hilbert order
+  std::vector<Pt> pts;
+  pts.reserve(2 * n_seg);
+  for (int64_t s = 0; s < n_seg; ++s) {
+    pts.push_back(Pt{seg[4 * s + 0], seg[4 * s + 1]});
+    pts.push_back(Pt{seg[4 * s + 2], seg[4 * s + 3]});
+  }
+  for (const Pt& p : pts)
+    if (p.x < 0 || p.y < 0 || p.x > D || p.y > D) {
+      tr->status = -1;
+      return tr;
+    }
+  std::vector<std::pair<uint64_t, int64_t>> key(pts.size());
+  for (size_t k = 0; k < pts.size(); ++k) key[k] = {hilbert_d(21, (uint32_t)pts[k].x, (uint32_t)pts[k].y), (int64_t)k};
+  std::sort(key.begin(), key.end());
+  std::vector<int32_t> vid(pts.size(), -1);
+  std::unordered_map<uint64_t, int32_t> seen;
+  seen.reserve(pts.size() * 2);
+  tr->P.reserve(pts.size() + 4);
+  tr->T.reserve(2 * pts.size() + 8);
+  for (auto& kv : key) {
+    const Pt& p = pts[kv.second];
+    uint64_t h = ((uint64_t)(uint32_t)p.x << 32) | (uint32_t)p.y;
+    auto it = seen.find(h);
+    if (it != seen.end()) {
+      vid[kv.second] = it->second;
+      continue;
+    }
+    int v = tr->insert_point(p);
+    if (v < 0) return tr;
+    seen[h] = v;
+    vid[kv.second] = v;
+  }
+  for (int64_t s = 0; s < n_seg; ++s) {
+    tr->insert_segment(vid[2 * s], vid[2 * s + 1], (int)s);
+    if (tr->status < 0) return tr;
+  }
+  tr->make_delaunay();
+  return tr;
+}
+
+// ---------------------------------------------------------------- annealing
+// Greedy flips to a shorter diagonal until none is left (each flip strictly
+// lowers the total length, so this terminates).  Squared lengths are exact.
+static int64_t greedy_flips(Triangulation& tr) {
+  std::vector<std::pair<int, int>> st;
+  for (int t = 0; t < (int)tr.T.size(); ++t)
+    for (int i = 0; i < 3; ++i)
+      if (tr.T[t].n[i] > t) st.push_back({t, i});
+  int64_t flips = 0;
+  while (!st.empty()) {
+    auto [t, i] = st.back();
+    st.pop_back();
+    if (tr.T[t].c[i] >= 0 || tr.T[t].n[i] < 0) continue;
+    int x, y;
+    if (!tr.strictly_convex(t, i, x, y)) continue;
+    const Pt& q = tr.P[tr.T[t].v[(i + 1) % 3]];
+    const Pt& r = tr.P[tr.T[t].v[(i + 2) % 3]];
+    if (len2(tr.P[x], tr.P[y]) < len2(q, r)) {
+      int u = tr.T[t].n[i];
+      tr.flip(t, i);
+      ++flips;
+      for (int k = 0; k < 3; ++k) {
+        st.push_back({t, k});
+        st.push_back({u, k});
+      }
+    }
+  }
+  return flips;
+}
+
+// Simulated annealing over edge flips (Sec. 3.2.7) with Metropolis acceptance
+// (Sec. 3.1) and an exponential temperature schedule (Sec. 3.3).  The energy is
+// the total edge length; lengths and differences are fp32.
+static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double T0, double T1) {
+  Rng rng(seed, 0xA77);
+  int64_t n_half = (int64_t)tr.T.size() * 3;
+  int64_t K = (int64_t)(sweeps * (double)n_half);
+  if (K <= 0) return;
+  double lt0 = std::log(T0), lt1 = std::log(T1);
+  for (int64_t k = 0; k < K; ++k) {
+    float temp = (float)std::exp(lt0 + (lt1 - lt0) * ((double)k / (double)K));
+    int t = (int)rng.below((uint32_t)tr.T.size());
+    int i = (int)rng.below(3);
+    if (tr.T[t].c[i] >= 0 || tr.T[t].n[i] < 0) continue;
+    int x, y;
+    if (!tr.strictly_convex(t, i, x, y)) continue;
+    const Pt& q = tr.P[tr.T[t].v[(i + 1) % 3]];
+    const Pt& r = tr.P[tr.T[t].v[(i + 2) % 3]];
+    float delta = edge_len(tr.P[x], tr.P[y]) - edge_len(q, r);
+    if (delta <= 0.f || (float)rng.uni() < std::exp(-delta / temp)) tr.flip(t, i);
+  }
+}
+
+// ---------------------------------------------------------------- rays
+struct SeedGrid {
+  int G = 1;
+  double cell = 1;
+  std::vector<int32_t> tri;
+};
+
+static void build_seed_grid(const Triangulation& tr, SeedGrid& sg) {
+  int64_t nt = (int64_t)tr.T.size();
+  sg.G = std::max(1, std::min(1024, (int)std::sqrt((double)nt / 4.0)));
+  sg.cell = (double)tr.D / sg.G;
+  sg.tri.assign((size_t)sg.G * sg.G, 0);
+  Rng r(99, 1);
+  int last = 0;
+  for (int j = 0; j < sg.G; ++j)
+    for (int ii = 0; ii < sg.G; ++ii) {
+      int i = (j & 1) ? sg.G - 1 - ii : ii;  // boustrophedon keeps walks short
+      Pt c{(int32_t)((i + 0.5) * sg.cell), (int32_t)((j + 0.5) * sg.cell)};
+      int t = tr.locate(c, last, r);
+      if (t < 0) t = last;
+      sg.tri[(size_t)j * sg.G + i] = t;
+      last = t;
+    }
+}
+
+// Locate p; returns the triangle containing p strictly inside, or -1 if p lies
+// on an edge or a vertex.
+static int locate_strict(const Triangulation& tr, const SeedGrid& sg, const Pt& p, Rng& r) {
+  int i = std::clamp((int)(p.x / sg.cell), 0, sg.G - 1), j = std::clamp((int)(p.y / sg.cell), 0, sg.G - 1);
+  int t = tr.locate(p, sg.tri[(size_t)j * sg.G + i], r);
+  if (t < 0) return -1;
+  const Tri& x = tr.T[t];
+  for (int e = 0; e < 3; ++e)
+    if (orient(tr.P[x.v[(e + 1) % 3]], tr.P[x.v[(e + 2) % 3]], p) == 0) return -1;
+  return t;
+}
+
+static inline float dir_on_grid(double c) {
+  // round to a multiple of 2^-22 (exact in fp32)
+  return (float)(std::nearbyint(c * 4194304.0) / 4194304.0);
+}
+
+template <class F>
+static void parallel_for(int64_t n, int n_threads, F f) {
+  if (n_threads <= 1 || n < 4096) {
+    f(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  int64_t chunk = (n + n_threads - 1) / n_threads;
+  for (int k = 0; k < n_threads; ++k) {
+    int64_t lo = k * chunk, hi = std::min(n, lo + chunk);
+    if (lo >= hi) break;
+    th.emplace_back([=]() { f(lo, hi); });
+  }
+  for (auto& x : th) x.join();
+}
+
+}  // namespace
+
+// =============================================================== C ABI
+extern "C" {
+
+// Config-1 style random disjoint segments.  Lengths are uniform in
+// [len_lo, len_hi]*D*scale; returns the number written (<= n).
+int64_t sg_gen_random_segments(int64_t n, uint64_t seed, int32_t D, double len_lo, double len_hi, double scale,
+                               double margin, int32_t* out, int64_t cap) {
+  return gen_segments(n, seed, D, len_lo, len_hi, scale, margin, 0, 0.0, out, cap);
+}
+
+// Random disjoint segments whose centres come from n_clusters Gaussian clusters
+// of standard deviation sigma*D.
+int64_t sg_gen_clustered(int64_t n, uint64_t seed, int32_t D, double len_lo, double len_hi, double scale,
+                         int32_t n_clusters, double sigma, int32_t* out, int64_t cap) {
+  return gen_segments(n, seed, D, len_lo, len_hi, scale, 0.01, n_clusters, sigma, out, cap);
+}
+
+// Disjoint polygonal circles with sides uniform in [min_sides, max_sides],
+// until about n_target segments.  Fill: the discs cover about 30% of the domain.
+int64_t sg_gen_circles(int64_t n_target, uint64_t seed, int32_t D, int32_t min_sides, int32_t max_sides,
+                       int32_t* out, int64_t cap) {
+  Rng rng(seed, 0xC1C);
+  double mean_sides = 0.5 * (min_sides + max_sides);
+  double k_est = std::max(1.0, (double)n_target / mean_sides);
+  double r_mean = D * std::sqrt(0.30 / (3.141592653589793 * k_est));
+  std::vector<double> cx, cy, cr;
+  std::vector<Pt> poly;
+  int64_t cnt = 0;
+  int64_t tries = 0;
+  while (cnt < n_target && tries < 2000000) {
+    ++tries;
+    int m = min_sides + (int)rng.below((uint32_t)(max_sides - min_sides + 1));
+    if (cnt + m > cap) break;
+    double r = r_mean * (0.6 + 0.8 * rng.uni());
+    double minr = 16.0 * m / 6.283185307179586;  // side >= 16 grid units
+    if (tries > 200000) r *= 0.5;
+    if (r < minr) r = minr;
+    double x = r + 0.01 * D + (D - 2 * r - 0.02 * D) * rng.uni();
+    double y = r + 0.01 * D + (D - 2 * r - 0.02 * D) * rng.uni();
+    if (x - r < 0.01 * D || y - r < 0.01 * D || x + r > 0.99 * D || y + r > 0.99 * D) continue;
+    bool ok = true;
+    for (size_t k = 0; k < cx.size() && ok; ++k) {
+      double dd = std::hypot(x - cx[k], y - cy[k]);
+      if (dd < (r + cr[k]) * 1.02 + 4.0) ok = false;
+    }
+    if (!ok) continue;
+    if (!polygon(x, y, r, m, 6.283185307179586 * rng.uni(), poly)) continue;
+    cx.push_back(x);
+    cy.push_back(y);
+    cr.push_back(r);
+    cnt = emit_polygon(poly, out, cnt, cap);
+  }
+  return cnt;
+}
+
+// Regular lattice of disjoint dashes (length 0.7 * pitch), horizontal and
+// vertical in a checkerboard, rotated by theta_deg about the domain centre and
+// clipped to the domain; about n_target dashes.
+int64_t sg_gen_dash_grid(int64_t n_target, double theta_deg, int32_t D, int32_t* out, int64_t cap) {
+  double side = std::sqrt((double)n_target);
+  double pitch = 0.96 * D / side;
+  double th = theta_deg * 3.141592653589793 / 180.0;
+  double c = std::cos(th), s = std::sin(th);
+  double h = 0.35 * pitch, lo = 0.01 * D, hi = 0.99 * D;
+  int64_t cnt = 0;
+  int R = (int)std::ceil(side * 0.75) + 2;
+  for (int j = -R; j <= R; ++j)
+    for (int i = -R; i <= R; ++i) {
+      double lx = (i + 0.5) * pitch, ly = (j + 0.5) * pitch;
+      bool horiz = ((i + j) & 1) == 0;
+      double ax = lx - (horiz ? h : 0), ay = ly - (horiz ? 0 : h);
+      double bx = lx + (horiz ? h : 0), by = ly + (horiz ? 0 : h);
+      double X0 = 0.5 * D + c * ax - s * ay, Y0 = 0.5 * D + s * ax + c * ay;
+      double X1 = 0.5 * D + c * bx - s * by, Y1 = 0.5 * D + s * bx + c * by;
+      if (X0 < lo || X0 > hi || Y0 < lo || Y0 > hi || X1 < lo || X1 > hi || Y1 < lo || Y1 > hi) continue;
+      if (cnt >= cap) return cnt;
+      out[4 * cnt + 0] = rnd_coord(X0);
+      out[4 * cnt + 1] = rnd_coord(Y0);
+      out[4 * cnt + 2] = rnd_coord(X1);
+      out[4 * cnt + 3] = rnd_coord(Y1);
+      ++cnt;
+    }
+  return cnt;
+}
+
+// A ring of M polygonal circles in a fixed domain, n_target sides in total.
+int64_t sg_gen_ring_of_circles(int64_t n_target, int32_t D, int32_t* out, int64_t cap) {
+  int M = std::max(8, (int)std::lround(std::sqrt((double)n_target) / 4.0));
+  int m = (int)std::max<int64_t>(3, n_target / M);
+  // ring radius R and circle radius rc = 0.95 pi R / M (neighbours never touch),
+  // with R + rc = 0.49 D so every circle stays inside the domain
+  double R = 0.49 * D / (1.0 + 0.95 * 3.141592653589793 / M);
+  double rc = 0.95 * 3.141592653589793 * R / M;
+  std::vector<Pt> poly;
+  int64_t cnt = 0;
+  for (int k = 0; k < M; ++k) {
+    double a = 6.283185307179586 * k / M;
+    if (!polygon(0.5 * D + R * std::cos(a), 0.5 * D + R * std::sin(a), rc, m, 0.1 * k, poly)) return -1;
+    cnt = emit_polygon(poly, out, cnt, cap);
+  }
+  return cnt;
+}
+
+// Constrained Delaunay triangulation of the segments (4 int32 per segment:
+// x0 y0 x1 y1) inside the square [0,D]^2.  Segment s becomes constrained edges
+// labelled s.  *status < 0 on failure (crossing or overlapping segments, point
+// outside the domain).
+void* sg_cdt_build(int64_t n_seg, const int32_t* seg, int32_t D, int32_t* status) {
+  Triangulation* t = build_cdt(n_seg, seg, D);
+  *status = t->status;
+  return t;
+}
+
+// Import an arbitrary triangulation (same array conventions as the export).
+void* sg_tri_import(int32_t D, int64_t n_vert, const int32_t* vx, const int32_t* vy, int64_t n_tri,
+                    const int32_t* tri_v, const int32_t* tri_nb, const int32_t* tri_seg) {
+  auto* tr = new Triangulation();
+  tr->D = D;
+  tr->P.resize(n_vert);
+  tr->vtri.assign(n_vert, 0);
+  for (int64_t v = 0; v < n_vert; ++v) tr->P[v] = Pt{vx[v], vy[v]};
+  tr->T.resize(n_tri);
+  for (int64_t t = 0; t < n_tri; ++t)
+    for (int k = 0; k < 3; ++k) {
+      tr->T[t].v[k] = tri_v[3 * t + k];
+      tr->T[t].n[k] = tri_nb[3 * t + k];
+      tr->T[t].c[k] = tri_seg[3 * t + k];
+      tr->vtri[tri_v[3 * t + k]] = (int32_t)t;
+    }
+  return tr;
+}
+
+void* sg_tri_copy(void* h) { return new Triangulation(*(Triangulation*)h); }
+
+void sg_tri_free(void* h) { delete (Triangulation*)h; }
+
+int32_t sg_tri_status(void* h) { return ((Triangulation*)h)->status; }
+
+void sg_tri_sizes(void* h, int64_t* n_vert, int64_t* n_tri) {
+  auto* t = (Triangulation*)h;
+  *n_vert = (int64_t)t->P.size();
+  *n_tri = (int64_t)t->T.size();
+}
+
+void sg_tri_export(void* h, int32_t* vx, int32_t* vy, int32_t* tri_v, int32_t* tri_nb, int32_t* tri_seg) {
+  auto* t = (Triangulation*)h;
+  for (size_t v = 0; v < t->P.size(); ++v) {
+    vx[v] = t->P[v].x;
+    vy[v] = t->P[v].y;
+  }
+  for (size_t k = 0; k < t->T.size(); ++k)
+    for (int i = 0; i < 3; ++i) {
+      tri_v[3 * k + i] = t->T[k].v[i];
+      tri_nb[3 * k + i] = t->T[k].n[i];
+      tri_seg[3 * k + i] = t->T[k].c[i];
+    }
+}
+
+// Total edge length (fp32, compensated sum); interior_only skips hull edges.
+float sg_tri_length(void* h, int32_t interior_only) {
+  return (float)((Triangulation*)h)->total_length(interior_only != 0);
+}
+
+// Anneal in place: greedy flips, then simulated annealing over flips from
+// temperature T0 to T1 (grid units) for `sweeps` proposals per half-edge, then
+// greedy flips again.  Keeps whichever of (greedy-only, annealed) is shorter.
+// Returns the number of greedy flips of the kept result.
+int64_t sg_anneal(void* h, uint64_t seed, double sweeps, double T0, double T1) {
+  auto* tr = (Triangulation*)h;
+  Triangulation g = *tr;
+  int64_t f0 = greedy_flips(g);
+  float lg = (float)g.total_length(false);
+  anneal_flips(*tr, seed, sweeps, T0, T1);
+  int64_t f1 = greedy_flips(*tr);
+  float la = (float)tr->total_length(false);
+  if (la > lg) {
+    *tr = g;
+    return f0;
+  }
+  return f1;
+}
+
+// n isotropic rays: origins uniform on the integer grid strictly inside a
+// triangle (rejection of points on edges and vertices), directions uniform in
+// angle with components rounded to multiples of 2^-22; start = the triangle
+// containing the origin (export numbering).  Ray k depends only on (seed, k).
+int64_t sg_rays_isotropic(void* h, int64_t n, uint64_t seed, int32_t* ox, int32_t* oy, float* dx, float* dy,
+                          int32_t* start, int32_t n_threads) {
+  auto* tr = (Triangulation*)h;
+  SeedGrid sg;
+  build_seed_grid(*tr, sg);
+  int32_t D = tr->D;
+  parallel_for(n, n_threads, [&](int64_t lo, int64_t hi) {
+    for (int64_t k = lo; k < hi; ++k) {
+      Rng r(seed, (uint64_t)k);
+      while (true) {
+        Pt p{1 + (int32_t)r.below((uint32_t)(D - 1)), 1 + (int32_t)r.below((uint32_t)(D - 1))};
+        int t = locate_strict(*tr, sg, p, r);
+        if (t < 0) continue;
+        double th = 6.283185307179586 * r.uni();
+        ox[k] = p.x;
+        oy[k] = p.y;
+        dx[k] = dir_on_grid(std::cos(th));
+        dy[k] = dir_on_grid(std::sin(th));
+        start[k] = t;
+        break;
+      }
+    }
+  });
+  return n;
+}
+
+// Pinhole fans: n_eyes eye points (uniform, strictly inside a triangle), each
+// with rays_per_eye rays evenly spaced over fov_deg around a uniform central
+// direction.  Ray k belongs to eye k / rays_per_eye.
+int64_t sg_rays_pinhole(void* h, int64_t n_eyes, int64_t rays_per_eye, double fov_deg, uint64_t seed,
+                        int32_t* ox, int32_t* oy, float* dx, float* dy, int32_t* start, int32_t n_threads) {
+  auto* tr = (Triangulation*)h;
+  SeedGrid sg;
+  build_seed_grid(*tr, sg);
+  int32_t D = tr->D;
+  double fov = fov_deg * 3.141592653589793 / 180.0;
+  parallel_for(n_eyes, n_threads, [&](int64_t lo, int64_t hi) {
+    for (int64_t e = lo; e < hi; ++e) {
+      Rng r(seed, (uint64_t)e);
+      Pt p;
+      int t;
+      while (true) {
+        p = Pt{1 + (int32_t)r.below((uint32_t)(D - 1)), 1 + (int32_t)r.below((uint32_t)(D - 1))};
+        t = locate_strict(*tr, sg, p, r);
+        if (t >= 0) break;
+      }
+      double phi = 6.283185307179586 * r.uni();
+      for (int64_t j = 0; j < rays_per_eye; ++j) {
+        int64_t k = e * rays_per_eye + j;
+        double th = phi - 0.5 * fov + fov * ((double)j + 0.5) / (double)rays_per_eye;
+        ox[k] = p.x;
+        oy[k] = p.y;
+        dx[k] = dir_on_grid(std::cos(th));
+        dy[k] = dir_on_grid(std::sin(th));
+        start[k] = t;
+      }
+    }
+  });
+  return n_eyes * rays_per_eye;
+}
+
+}  // extern "C"
