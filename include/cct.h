@@ -1,0 +1,165 @@
+/* cct.h -- C ABI of libcct: closest-hit queries of 2D rays against a scene of
+ * line segments, answered by a stackless walk through a constrained
+ * triangulation whose edges contain every segment, on one GB300 (sm_103a).
+ *
+ * Method: Frederickx & Dutre, "Stackless Ray-Object Intersections Using
+ * Approximate Minimum Weight Triangulations" (arXiv 2112.05570).
+ *   Sec. 5.1  ray traversal: in the triangle that holds the ray, find the edge
+ *             the ray leaves through; an edge of the original geometry is the
+ *             closest hit, an edge with no neighbour (the hull) is a miss,
+ *             otherwise continue in the neighbour across that edge.
+ *   Sec. 5.2  the start triangle: known a priori, or found by walking from a
+ *             point with a known triangle; seed points on a regular grid.
+ *   Sec. 5.4  one traversal operation = one exit-edge determination in one
+ *             visited triangle; start cells known a priori for the count.
+ *
+ * Geometry and exactness.  Vertices are integer points of [0, D]^2 with
+ * D <= 2^20; the hull of the triangulation is that square.  Ray origins are
+ * integer points; a direction d = (dx, dy) is fp32 with each component a
+ * multiple of 2^-22 and |dx|, |dy| <= 1, so k = 2^22 d is an exact integer
+ * vector.  The side of a point v is L iff k.x (v.y - o.y) - k.y (v.x - o.x) >= 0
+ * (a point on the ray's line counts as left: the ray is shifted infinitesimally
+ * to its right), which makes the walk consistent across neighbouring triangles
+ * (Sec. 5.1 requires consistency).  Sides are decided in fp32 under a static
+ * error bound and, only where that is inconclusive, in exact int64 arithmetic:
+ * hit ids and step counts are exact; t is fp32 (within 4 ulp of the exact
+ * rational parameter of the hit).
+ *
+ * Conventions for every function:
+ *   - returns CCT_OK (0) or a negative CCT_ERR_* code; no function aborts,
+ *     throws or traps the GPU;
+ *   - pointers named d_* are device memory owned by the caller; cct_tri_desc
+ *     arrays are host memory owned by the caller, only read during the call;
+ *   - work is enqueued on `stream` (a cudaStream_t, NULL = legacy default) and
+ *     the call returns without waiting, except cct_scene_load (waits for its
+ *     upload), cct_get_stats (waits for `stream`) and cct_scene_free;
+ *   - a scene is immutable after loading and may be used from several streams
+ *     at once; free it only after all work using it has completed.
+ */
+#ifndef CCT_H
+#define CCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define CCT_OK 0
+#define CCT_ERR_INVALID_ARGUMENT -1    /* null pointer, negative count, size out of range */
+#define CCT_ERR_BAD_TRIANGULATION -2   /* cct_scene_load validation failed */
+#define CCT_ERR_OUT_OF_MEMORY -3       /* a device or host allocation failed */
+#define CCT_ERR_CUDA -4                /* a CUDA runtime call failed */
+#define CCT_ERR_WALK_LIMIT -5          /* reported by cct_get_stats' counters only */
+#define CCT_ERR_NO_DEVICE -6           /* no usable CUDA device */
+
+/* Per-ray status, written to d_steps instead of a step count. */
+#define CCT_RAY_INVALID -1    /* direction off the 2^-22 grid, |component| > 1, zero, or the
+                                 start triangle does not strictly contain the origin */
+#define CCT_RAY_WALK_LIMIT -2 /* more than n_tri + 8 steps (only on a corrupt triangulation) */
+
+/* ------------------------------------------------------------------ flags */
+/* cct_scene_load */
+#define CCT_LOAD_NO_REORDER 1u  /* keep the caller's triangle order (default: Hilbert order) */
+#define CCT_LOAD_NO_VALIDATE 2u /* skip the geometric checks of cct_scene_load (fault-injection tests);
+                                   index ranges are always checked */
+/* cct_trace */
+#define CCT_TRACE_EXACT_ONLY 1u /* decide every side in int64 (no fp32 filter) */
+#define CCT_TRACE_BIN 2u        /* sort rays by start cell before walking (ray binning) */
+
+/* ------------------------------------------------------------------ types */
+typedef struct cct_scene_s* cct_scene; /* opaque; the library owns all device memory of a scene */
+
+/* A triangulation of [0, D]^2 whose constrained edges cover the scene
+ * segments (Sec. 1.3: the primitives lie on cell boundaries).  Host arrays:
+ *   vx, vy   [n_vert]   integer coordinates in [0, D]
+ *   tri_v    [3*n_tri]  vertex ids of triangle t, counter-clockwise
+ *   tri_nb   [3*n_tri]  triangle across edge i of t (the edge opposite
+ *                       vertex i), or -1 on the hull
+ *   tri_seg  [3*n_tri]  scene segment id carried by edge i (a constrained edge)
+ *                       or -1; equal on both sides of an edge
+ * Triangle ids used by cct_trace / cct_locate are indices into this array. */
+typedef struct {
+  int32_t n_vert;
+  int32_t n_tri;
+  int32_t n_seg;  /* segment ids in tri_seg lie in [0, n_seg) */
+  int32_t domain; /* D, 1 <= D <= 2^20 */
+  const int32_t* vx;
+  const int32_t* vy;
+  const int32_t* tri_v;
+  const int32_t* tri_nb;
+  const int32_t* tri_seg;
+} cct_tri_desc;
+
+/* Device-side counters of a scene, accumulated by every call that uses it. */
+typedef struct {
+  uint64_t rays;           /* rays walked by cct_trace */
+  uint64_t steps;          /* sum of step counts of valid rays (Sec. 5.4 operations) */
+  uint64_t side_tests;     /* side-of-line decisions taken by the walk */
+  uint64_t exact_fallbacks;/* of those, decided in int64 because the fp32 filter was inconclusive */
+  uint64_t invalid_rays;   /* rays reported CCT_RAY_INVALID */
+  uint64_t walk_limit_rays;/* rays reported CCT_RAY_WALK_LIMIT */
+  uint64_t located;        /* origins located by cct_locate or cct_trace(start = NULL) */
+  uint64_t locate_steps;   /* triangles visited by those locate walks (not part of `steps`) */
+} cct_stats;
+
+/* ------------------------------------------------------------------ scene */
+/* Validates and uploads a triangulation (Sec. 5.1's structure).  Checks: index
+ * ranges, strictly CCW triangles, neighbour symmetry, equal labels on both
+ * sides, hull edges on the square's sides, sum of areas = D^2.  Reorders the
+ * triangles along a Hilbert curve (unless CCT_LOAD_NO_REORDER), packs one
+ * 32-byte record per triangle and builds the locate seed grid (Sec. 5.2).
+ * Waits for its upload on `stream`.  *out receives the handle.
+ * Errors: CCT_ERR_INVALID_ARGUMENT, CCT_ERR_BAD_TRIANGULATION,
+ * CCT_ERR_OUT_OF_MEMORY, CCT_ERR_CUDA, CCT_ERR_NO_DEVICE. */
+int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* stream, cct_scene* out);
+
+/* Releases a scene's device memory.  The caller guarantees no work using it
+ * is pending.  NULL is accepted. */
+int cct_scene_free(cct_scene scene);
+
+/* Device bytes held by the scene and its number of triangles (either output
+ * pointer may be NULL). */
+int cct_scene_info(cct_scene scene, size_t* device_bytes, int32_t* n_tri);
+
+/* Start triangles (Sec. 5.2): for each of n origins (d_ox, d_oy, device int32),
+ * walks from the seed point of its grid cell to the origin and writes the id
+ * (caller numbering) of the triangle whose interior holds it to
+ * d_start_tri[i], or -1 if the origin lies on an edge or a vertex or outside
+ * the domain.  n = 0 is a no-op.  Errors: CCT_ERR_INVALID_ARGUMENT,
+ * CCT_ERR_CUDA. */
+int cct_locate(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy, int64_t n, int32_t* d_start_tri,
+               void* stream);
+
+/* Closest hit of n rays (Sec. 5.1).  Inputs (device): origins d_ox, d_oy
+ * (int32), directions d_dx, d_dy (fp32 on the 2^-22 grid), and d_start_tri,
+ * the triangle (caller numbering) that holds each origin -- or NULL, in which
+ * case the origins are located first as by cct_locate.  Outputs (device, all
+ * n entries written): d_hit_seg = segment id of the closest hit or -1 (miss
+ * or invalid ray); d_t = hit parameter (o + t d), +inf on a miss, NaN on an
+ * invalid ray; d_steps = triangles visited including the start triangle
+ * (Sec. 5.4), or CCT_RAY_INVALID / CCT_RAY_WALK_LIMIT.  flags: CCT_TRACE_*.
+ * Scratch memory (ray binning, start cells) is taken from the stream-ordered
+ * allocator on `stream` and released on it.  n = 0 is a no-op.
+ * Errors: CCT_ERR_INVALID_ARGUMENT, CCT_ERR_OUT_OF_MEMORY, CCT_ERR_CUDA. */
+int cct_trace(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy, const float* d_dx, const float* d_dy,
+              const int32_t* d_start_tri, int64_t n, int32_t* d_hit_seg, float* d_t, int32_t* d_steps,
+              uint32_t flags, void* stream);
+
+/* Copies the scene's counters to *out after waiting for `stream`; reset != 0
+ * zeroes them afterwards.  Errors: CCT_ERR_INVALID_ARGUMENT, CCT_ERR_CUDA. */
+int cct_get_stats(cct_scene scene, cct_stats* out, int reset, void* stream);
+
+/* Static text for a status code. */
+const char* cct_error_string(int code);
+
+/* Library version, (major << 16) | minor. */
+int cct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCT_H */

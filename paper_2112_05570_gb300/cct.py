@@ -1,0 +1,227 @@
+"""Thin Python binding of libcct (include/cct.h): the same entry points, with
+torch CUDA tensors for device buffers and torch streams.  Argument marshalling
+only -- every step of the ray query runs in the library's CUDA kernels.  There
+is no CPU fallback: if libcct.so is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+CCT_OK = 0
+CCT_ERR_INVALID_ARGUMENT = -1
+CCT_ERR_BAD_TRIANGULATION = -2
+CCT_ERR_OUT_OF_MEMORY = -3
+CCT_ERR_CUDA = -4
+CCT_ERR_WALK_LIMIT = -5
+CCT_ERR_NO_DEVICE = -6
+CCT_RAY_INVALID = -1
+CCT_RAY_WALK_LIMIT = -2
+CCT_LOAD_NO_REORDER = 1
+CCT_LOAD_NO_VALIDATE = 2
+CCT_TRACE_EXACT_ONLY = 1
+CCT_TRACE_BIN = 2
+
+
+class CctError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {cct_error_string(code)} ({code})")
+        self.code = code
+
+
+class _TriDesc(ctypes.Structure):
+    _fields_ = [("n_vert", ctypes.c_int32), ("n_tri", ctypes.c_int32), ("n_seg", ctypes.c_int32),
+                ("domain", ctypes.c_int32), ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p),
+                ("tri_v", ctypes.c_void_p), ("tri_nb", ctypes.c_void_p), ("tri_seg", ctypes.c_void_p)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("rays", "steps", "side_tests", "exact_fallbacks", "invalid_rays",
+                                               "walk_limit_rays", "located", "locate_steps")]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libcct.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libcct.so not built at {_build.LIB}: call __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    L.cct_scene_load.restype = ctypes.c_int
+    L.cct_scene_load.argtypes = [ctypes.POINTER(_TriDesc), u32, vp, ctypes.POINTER(vp)]
+    L.cct_scene_free.restype = ctypes.c_int
+    L.cct_scene_free.argtypes = [vp]
+    L.cct_scene_info.restype = ctypes.c_int
+    L.cct_scene_info.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i32)]
+    L.cct_locate.restype = ctypes.c_int
+    L.cct_locate.argtypes = [vp, vp, vp, i64, vp, vp]
+    L.cct_trace.restype = ctypes.c_int
+    L.cct_trace.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, u32, vp]
+    L.cct_get_stats.restype = ctypes.c_int
+    L.cct_get_stats.argtypes = [vp, ctypes.POINTER(_Stats), ctypes.c_int, vp]
+    L.cct_error_string.restype = ctypes.c_char_p
+    L.cct_error_string.argtypes = [ctypes.c_int]
+    L.cct_version.restype = ctypes.c_int
+    L.cct_measure_gather.restype = ctypes.c_int
+    L.cct_measure_gather.argtypes = [ctypes.c_size_t, i64, i32, vp, ctypes.POINTER(ctypes.c_float),
+                                     ctypes.POINTER(ctypes.c_double)]
+    _lib = L
+    return L
+
+
+def cct_error_string(code: int) -> str:
+    return lib().cct_error_string(int(code)).decode()
+
+
+def _check(code: int, what: str):
+    if code != CCT_OK:
+        raise CctError(code, what)
+
+
+def _stream_ptr(stream):
+    """A cudaStream_t: an int handle, a torch stream, or None for torch's
+    current stream (the legacy default stream when CUDA is unavailable)."""
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    import torch
+
+    if stream is None:
+        if not torch.cuda.is_available():
+            return ctypes.c_void_p(0)
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    import torch
+
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ----------------------------------------------------------------------------- entry points
+def cct_scene_load(vx, vy, tri_v, tri_nb, tri_seg, n_seg: int, domain: int, flags: int = 0, stream=None) -> int:
+    """Validate and upload a triangulation (host arrays); returns the scene handle."""
+    arrs = [np.ascontiguousarray(a, np.int32).ravel() for a in (vx, vy, tri_v, tri_nb, tri_seg)]
+    d = _TriDesc(arrs[0].size, arrs[2].size // 3, int(n_seg), int(domain),
+                 *[ctypes.c_void_p(a.ctypes.data) for a in arrs])
+    h = ctypes.c_void_p()
+    _check(lib().cct_scene_load(ctypes.byref(d), flags, _stream_ptr(stream), ctypes.byref(h)), "cct_scene_load")
+    return h.value
+
+
+def cct_scene_free(scene: int) -> None:
+    _check(lib().cct_scene_free(ctypes.c_void_p(scene)), "cct_scene_free")
+
+
+def cct_scene_info(scene: int):
+    b, n = ctypes.c_size_t(), ctypes.c_int32()
+    _check(lib().cct_scene_info(ctypes.c_void_p(scene), ctypes.byref(b), ctypes.byref(n)), "cct_scene_info")
+    return int(b.value), int(n.value)
+
+
+def cct_locate(scene: int, ox, oy, start, stream=None) -> None:
+    import torch
+
+    n = ox.numel()
+    _check(lib().cct_locate(ctypes.c_void_p(scene), _dev(ox, torch.int32, "ox"), _dev(oy, torch.int32, "oy"), n,
+                            _dev(start, torch.int32, "start"), _stream_ptr(stream)), "cct_locate")
+
+
+def cct_trace(scene: int, ox, oy, dx, dy, start, hit, t, steps, flags: int = 0, stream=None) -> None:
+    import torch
+
+    n = ox.numel()
+    for a in (oy, dx, dy, hit, t, steps) + ((start,) if start is not None else ()):
+        if a.numel() != n:
+            raise ValueError("all ray and result tensors must have the same length")
+    _check(lib().cct_trace(ctypes.c_void_p(scene), _dev(ox, torch.int32, "ox"), _dev(oy, torch.int32, "oy"),
+                           _dev(dx, torch.float32, "dx"), _dev(dy, torch.float32, "dy"),
+                           _dev(start, torch.int32, "start"), n, _dev(hit, torch.int32, "hit"),
+                           _dev(t, torch.float32, "t"), _dev(steps, torch.int32, "steps"), flags,
+                           _stream_ptr(stream)), "cct_trace")
+
+
+def cct_get_stats(scene: int, reset: bool = False, stream=None) -> dict:
+    s = _Stats()
+    _check(lib().cct_get_stats(ctypes.c_void_p(scene), ctypes.byref(s), 1 if reset else 0, _stream_ptr(stream)),
+           "cct_get_stats")
+    return {k: int(getattr(s, k)) for k, _ in _Stats._fields_}
+
+
+def cct_version() -> int:
+    return int(lib().cct_version())
+
+
+def cct_measure_gather(table_bytes: int, loads: int, reps: int = 5, stream=None):
+    """Random 32-byte sector gather rate over a table of table_bytes
+    (include/cct_measure.h): (ms per launch, bytes per second)."""
+    ms, bps = ctypes.c_float(), ctypes.c_double()
+    _check(lib().cct_measure_gather(int(table_bytes), int(loads), int(reps), _stream_ptr(stream), ctypes.byref(ms),
+                                    ctypes.byref(bps)), "cct_measure_gather")
+    return float(ms.value), float(bps.value)
+
+
+# ----------------------------------------------------------------------------- convenience
+class Scene:
+    """A device-resident triangulation (owns its handle)."""
+
+    def __init__(self, vx, vy, tri_v, tri_nb, tri_seg, n_seg: int, domain: int, flags: int = 0, stream=None):
+        self.handle = cct_scene_load(vx, vy, tri_v, tri_nb, tri_seg, n_seg, domain, flags, stream)
+        self.n_tri = int(np.asarray(tri_v).size // 3)
+
+    @classmethod
+    def from_triangulation(cls, tri, domain: int, flags: int = 0, stream=None) -> "Scene":
+        n_seg = int(np.asarray(tri.segs).reshape(-1, 4).shape[0])
+        return cls(tri.vx, tri.vy, tri.tri_v, tri.tri_nb, tri.tri_seg, n_seg, domain, flags, stream)
+
+    def trace(self, ox, oy, dx, dy, start=None, flags: int = 0, stream=None, out=None):
+        """Closest hits of the rays (device tensors): (hit, t, steps) tensors."""
+        import torch
+
+        n = ox.numel()
+        if out is None:
+            out = (torch.empty(n, dtype=torch.int32, device=ox.device),
+                   torch.empty(n, dtype=torch.float32, device=ox.device),
+                   torch.empty(n, dtype=torch.int32, device=ox.device))
+        cct_trace(self.handle, ox, oy, dx, dy, start, out[0], out[1], out[2], flags, stream)
+        return out
+
+    def locate(self, ox, oy, stream=None):
+        import torch
+
+        start = torch.empty(ox.numel(), dtype=torch.int32, device=ox.device)
+        cct_locate(self.handle, ox, oy, start, stream)
+        return start
+
+    def stats(self, reset: bool = False, stream=None) -> dict:
+        return cct_get_stats(self.handle, reset, stream)
+
+    def info(self):
+        return cct_scene_info(self.handle)
+
+    def free(self):
+        if self.handle:
+            cct_scene_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,188 @@
+// Internal layout and device helpers of libcct (see include/cct.h for the ABI).
+//
+// Device scene layout (one allocation per scene, 256-byte aligned pieces):
+//   rec       TriRec[n_tri]     32-byte triangle records in Hilbert order of the
+//                               triangle centroids: one L2 sector per walk step
+//   cnb       int32[3*n_tri]    neighbour word across constrained edges (read
+//                               only by the locate walk, which crosses them)
+//   user2dev  int32[n_tri]      caller triangle id -> record index
+//   dev2user  int32[n_tri]      record index -> caller triangle id
+//   seeds     SeedCell[G*G]     locate seed grid (Sec. 5.2): per cell a point
+//                               with a known triangle (a triangle centroid)
+//   stats     DevStats          counters (cct_stats)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cct.h"
+
+namespace cct {
+
+constexpr int kCoordBits = 21;  // coordinates lie in [0, 2^20]
+constexpr uint64_t kCoordMask = (1ull << kCoordBits) - 1;
+constexpr float kDirScale = 4194304.0f;  // 2^22
+
+// One triangle.  X / Y hold the coordinates of vertex i at bits [21 i, 21 i + 21).
+// nb[i] describes the edge opposite vertex i (vertices CCW):
+//   nb >= 0 : interior edge; (neighbour record index << 2) | (index of the same
+//             edge in the neighbour)
+//   nb == -1: hull edge (the ray leaves the domain: a miss)
+//   nb <= -2: constrained edge carrying scene segment -2 - nb (a hit)
+struct __align__(32) TriRec {
+  uint64_t X;
+  uint64_t Y;
+  int32_t nb[3];
+  int32_t pad;
+};
+static_assert(sizeof(TriRec) == 32, "TriRec must be one 32-byte sector");
+
+struct __align__(16) SeedCell {
+  int32_t px3, py3;  // 3 x seed point (the centroid of `tri`, exact in thirds)
+  int32_t tri;       // record index of the triangle that holds the seed point
+  int32_t pad;
+};
+
+struct DevStats {
+  unsigned long long rays, steps, side_tests, exact_fallbacks, invalid_rays, walk_limit_rays, located,
+      locate_steps;
+};
+
+struct SceneDev {
+  const TriRec* rec;
+  const int32_t* cnb;
+  const int32_t* user2dev;
+  const int32_t* dev2user;
+  const SeedCell* seeds;
+  DevStats* stats;
+  int32_t n_tri;
+  int32_t G;
+  int32_t D;
+  int32_t max_steps;
+};
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ TriRec load_rec(const TriRec* p) {
+  TriRec r;
+  unsigned long long a, b, c, d;
+  asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+  r.X = a;
+  r.Y = b;
+  r.nb[0] = (int32_t)(uint32_t)c;
+  r.nb[1] = (int32_t)(uint32_t)(c >> 32);
+  r.nb[2] = (int32_t)(uint32_t)d;
+  r.pad = (int32_t)(uint32_t)(d >> 32);
+  return r;
+}
+
+__device__ __forceinline__ int vx_of(const TriRec& r, int i) { return (int)((r.X >> (kCoordBits * i)) & kCoordMask); }
+__device__ __forceinline__ int vy_of(const TriRec& r, int i) { return (int)((r.Y >> (kCoordBits * i)) & kCoordMask); }
+
+__device__ __forceinline__ int32_t nb_of(const TriRec& r, int e) { return e == 0 ? r.nb[0] : (e == 1 ? r.nb[1] : r.nb[2]); }
+
+// Direction component -> exact integer k = 2^22 d; false if off the grid or |d| > 1.
+__device__ __forceinline__ bool dir_to_k(float d, int& k) {
+  float s = d * kDirScale;  // exact: power-of-two scaling
+  if (!(fabsf(s) <= kDirScale) || s != rintf(s)) return false;
+  k = (int)s;
+  return true;
+}
+
+// Static error bound of the fp32 side test r = fma(dx, dy_v, -(dy * dx_v)) for
+// |d| <= 1 and |v - o| <= 2^20: |r - E| <= 2^-24 (|r| + 2^20) (1 + 2^-23), so
+// |r| >= 2^-4 (1 + 2^-10) fixes the sign of the exact E = dx dy_v - dy dx_v.
+constexpr float kFilterBound = 0.0625f * (1.0f + 1.0f / 1024.0f);
+
+// Side of v relative to the ray (o, d): true = L (exact E >= 0).
+template <bool kExactOnly>
+__device__ __forceinline__ bool side_L(float fdx, float fdy, int kx, int ky, int ox, int oy, int vx, int vy,
+                                       unsigned& fallbacks) {
+  const int ddx = vx - ox, ddy = vy - oy;
+  if (!kExactOnly) {
+    const float p = __fmul_rn(fdy, (float)ddx);
+    const float r = __fmaf_rn(fdx, (float)ddy, -p);
+    if (fabsf(r) >= kFilterBound) return r > 0.0f;
+    ++fallbacks;
+  }
+  const long long e = (long long)kx * ddy - (long long)ky * ddx;
+  return e >= 0;
+}
+
+__device__ __forceinline__ long long orient_ll(long long ax, long long ay, long long bx, long long by, long long cx,
+                                               long long cy) {
+  return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+}
+
+// t of the crossing of the ray (o, k / 2^22) with the line of edge (a, b):
+// t = 2^22 num / den, num = cross(b - a, a - o), den = cross(b - a, k); fp32.
+__device__ __forceinline__ float hit_param(int ax, int ay, int bx, int by, int ox, int oy, int kx, int ky) {
+  const long long ex = bx - ax, ey = by - ay;
+  long long num = ex * (long long)(ay - oy) - ey * (long long)(ax - ox);
+  long long den = ex * (long long)ky - ey * (long long)kx;
+  if (den < 0) {
+    num = -num;
+    den = -den;
+  }
+  return __fmul_rn(__fdiv_rn(__ll2float_rn(num), __ll2float_rn(den)), kDirScale);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- host helpers
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int sm_count(int dev);
+
+// Stream-ordered scratch for one call: one cudaMallocAsync, released with
+// cudaFreeAsync on the same stream.
+struct Scratch {
+  char* base = nullptr;
+  cudaStream_t stream = nullptr;
+  ~Scratch() {
+    if (base) cudaFreeAsync(base, stream);
+  }
+};
+
+// Launchers shared between translation units (all enqueue on `stream`).
+cudaError_t launch_locate(const SceneDev& S, const int32_t* ox, const int32_t* oy, int64_t n, int32_t* out,
+                          bool to_user, cudaStream_t stream);
+
+struct BinOut {
+  int4* rays;      // {ox, oy, dx bits, dy bits} sorted by start cell
+  int32_t* start;  // record index, sorted
+  int32_t* orig;   // original ray index, sorted
+};
+size_t bin_scratch_bytes(int64_t n, int32_t n_tri, int shift);
+cudaError_t launch_bin(const SceneDev& S, const int32_t* ox, const int32_t* oy, const float* dx, const float* dy,
+                       const int32_t* start, bool start_is_user, int64_t n, int shift, char* scratch, BinOut& out,
+                       cudaStream_t stream);
+
+}  // namespace cct
+
+struct cct_scene_s {
+  cct::SceneDev dev;
+  void* d_base;
+  size_t bytes;
+  int device;
+};

@@ -1,0 +1,106 @@
+// Start-triangle location (Sec. 5.2) and cct_locate.
+//
+// The paper's option without an extra data structure: from a point p whose
+// triangle is known, follow the traversal towards the origin o until the
+// current triangle holds o.  Seeds sit on a regular grid (one per cell, found
+// at load time): p is a triangle centroid, kept as 3p so all arithmetic stays
+// exact in int64.  The locate walk crosses constrained edges (it is a point
+// location, not a ray query), reading their neighbours from `cnb`.
+#include <algorithm>
+
+#include "cct_internal.cuh"
+
+namespace cct {
+
+constexpr int kLocateThreads = 256;
+
+__global__ void __launch_bounds__(kLocateThreads) locate_kernel(SceneDev S, const int32_t* __restrict__ ox,
+                                                                const int32_t* __restrict__ oy, int64_t n,
+                                                                int32_t* __restrict__ out, bool to_user) {
+  unsigned long long c_loc = 0, c_steps = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int qx = ox[i], qy = oy[i];
+    int32_t res = -1;
+    if (qx >= 0 && qy >= 0 && qx <= S.D && qy <= S.D) {
+      const int G = S.G;
+      const int ix = (int)min((long long)G - 1, (long long)qx * G / S.D);
+      const int iy = (int)min((long long)G - 1, (long long)qy * G / S.D);
+      const SeedCell sd = S.seeds[(long long)iy * G + ix];
+      const long long px3 = sd.px3, py3 = sd.py3;
+      const long long kx = 3ll * qx - px3, ky = 3ll * qy - py3;  // direction p -> o, in thirds
+      int T = sd.tri;
+      int steps = 0;
+      while (true) {
+        if (++steps > S.max_steps) {
+          res = -1;
+          break;
+        }
+        const TriRec r = load_rec(S.rec + T);
+        const long long x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
+        const long long x2 = vx_of(r, 2), y2 = vy_of(r, 2);
+        const long long o0 = orient_ll(x1, y1, x2, y2, qx, qy);
+        const long long o1 = orient_ll(x2, y2, x0, y0, qx, qy);
+        const long long o2 = orient_ll(x0, y0, x1, y1, qx, qy);
+        if (o0 > 0 && o1 > 0 && o2 > 0) {
+          res = T;
+          break;
+        }
+        if (o0 >= 0 && o1 >= 0 && o2 >= 0) {  // on an edge or a vertex of T
+          res = -1;
+          break;
+        }
+        // leave along p -> o through the CCW edge (a -> b) with s(a) = R, s(b) = L
+        const bool s0 = kx * (3 * y0 - py3) - ky * (3 * x0 - px3) >= 0;
+        const bool s1 = kx * (3 * y1 - py3) - ky * (3 * x1 - px3) >= 0;
+        const bool s2 = kx * (3 * y2 - py3) - ky * (3 * x2 - px3) >= 0;
+        const int e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
+        int32_t w = nb_of(r, e);
+        if (w <= -2) w = S.cnb[3ll * T + e];
+        if (w < 0) {
+          res = -1;
+          break;
+        }
+        T = w >> 2;
+      }
+      ++c_loc;
+      c_steps += (unsigned)steps;
+    }
+    out[i] = (res >= 0 && to_user) ? S.dev2user[res] : res;
+  }
+  c_loc = warp_sum(c_loc);
+  c_steps = warp_sum(c_steps);
+  if ((threadIdx.x & 31) == 0 && c_loc) {
+    atomicAdd(&S.stats->located, c_loc);
+    atomicAdd(&S.stats->locate_steps, c_steps);
+  }
+}
+
+cudaError_t launch_locate(const SceneDev& S, const int32_t* ox, const int32_t* oy, int64_t n, int32_t* out,
+                          bool to_user, cudaStream_t stream) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, locate_kernel, kLocateThreads, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  long long want = (n + kLocateThreads - 1) / kLocateThreads;
+  long long grid = std::min<long long>((long long)sm_count(dev) * per_sm * 4, want);
+  if (grid < 1) grid = 1;
+  locate_kernel<<<(unsigned)grid, kLocateThreads, 0, stream>>>(S, ox, oy, n, out, to_user);
+  return cudaGetLastError();
+}
+
+}  // namespace cct
+
+using namespace cct;
+
+extern "C" int cct_locate(cct_scene scene, const int32_t* ox, const int32_t* oy, int64_t n, int32_t* start,
+                          void* stream_v) {
+  if (!scene || n < 0) return CCT_ERR_INVALID_ARGUMENT;
+  if (n == 0) return CCT_OK;
+  if (!ox || !oy || !start) return CCT_ERR_INVALID_ARGUMENT;
+  DeviceGuard g(scene->device);
+  if (launch_locate(scene->dev, ox, oy, n, start, true, (cudaStream_t)stream_v) != cudaSuccess) return CCT_ERR_CUDA;
+  return CCT_OK;
+}

@@ -1,0 +1,312 @@
+// Scene load / free / info / stats of libcct (include/cct.h).
+//
+// cct_scene_load turns the caller's triangulation (Sec. 5.1: triangles with
+// neighbours, some edges belonging to the original geometry) into the device
+// layout described in cct_internal.cuh:
+//   1. validation (exact integer checks, host);
+//   2. Hilbert order of the triangle centroids, so that triangles adjacent in
+//      space are adjacent in memory (walk and locate locality);
+//   3. one 32-byte record per triangle (coordinates + neighbour words);
+//   4. the locate seed grid of Sec. 5.2: G x G cells, each with a seed point
+//      whose triangle is known -- a triangle centroid inside the cell, or the
+//      nearest filled cell's seed for cells that hold no centroid.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <vector>
+
+#include "cct_internal.cuh"
+
+namespace cct {
+
+int sm_count(int dev) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  return n;
+}
+
+static uint64_t hilbert_d(int order, uint32_t x, uint32_t y) {
+  uint64_t d = 0;
+  for (uint32_t s = 1u << (order - 1); s > 0; s >>= 1) {
+    uint32_t rx = (x & s) > 0, ry = (y & s) > 0;
+    d += (uint64_t)s * s * ((3 * rx) ^ ry);
+    if (ry == 0) {
+      if (rx == 1) {
+        x = s - 1 - x;
+        y = s - 1 - y;
+      }
+      uint32_t t = x;
+      x = y;
+      y = t;
+    }
+  }
+  return d;
+}
+
+static inline long long orient_h(long long ax, long long ay, long long bx, long long by, long long cx, long long cy) {
+  return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+}
+
+// Index ranges and coordinates: always checked (even with CCT_LOAD_NO_VALIDATE),
+// so every record and neighbour word the kernels can reach is in bounds.
+static int check_ranges(const cct_tri_desc& d) {
+  const long long D = d.domain;
+  for (int v = 0; v < d.n_vert; ++v)
+    if (d.vx[v] < 0 || d.vy[v] < 0 || d.vx[v] > D || d.vy[v] > D) return CCT_ERR_BAD_TRIANGULATION;
+  for (long long k = 0; k < 3ll * d.n_tri; ++k) {
+    int32_t v = d.tri_v[k], nb = d.tri_nb[k], s = d.tri_seg[k];
+    if (v < 0 || v >= d.n_vert || nb < -1 || nb >= d.n_tri || s < -1 || s >= d.n_seg)
+      return CCT_ERR_BAD_TRIANGULATION;
+  }
+  return CCT_OK;
+}
+
+static int validate(const cct_tri_desc& d) {
+  const long long D = d.domain;
+  const int nt = d.n_tri;
+  long long area2 = 0;
+  for (int t = 0; t < nt; ++t) {
+    const int32_t* tv = d.tri_v + 3 * t;
+    long long o = orient_h(d.vx[tv[0]], d.vy[tv[0]], d.vx[tv[1]], d.vy[tv[1]], d.vx[tv[2]], d.vy[tv[2]]);
+    if (o <= 0) return CCT_ERR_BAD_TRIANGULATION;
+    area2 += o;
+  }
+  if (area2 != 2 * D * D) return CCT_ERR_BAD_TRIANGULATION;
+  for (int t = 0; t < nt; ++t)
+    for (int i = 0; i < 3; ++i) {
+      int32_t a = d.tri_v[3 * t + (i + 1) % 3], b = d.tri_v[3 * t + (i + 2) % 3];
+      int32_t u = d.tri_nb[3 * t + i];
+      if (u < 0) {
+        long long ax = d.vx[a], ay = d.vy[a], bx = d.vx[b], by = d.vy[b];
+        bool on_side = (ax == 0 && bx == 0) || (ay == 0 && by == 0) || (ax == D && bx == D) || (ay == D && by == D);
+        if (!on_side) return CCT_ERR_BAD_TRIANGULATION;
+        continue;
+      }
+      int j = -1;
+      for (int k = 0; k < 3; ++k)
+        if (d.tri_v[3 * u + (k + 1) % 3] == b && d.tri_v[3 * u + (k + 2) % 3] == a) j = k;
+      if (j < 0 || d.tri_nb[3 * u + j] != t || d.tri_seg[3 * u + j] != d.tri_seg[3 * t + i])
+        return CCT_ERR_BAD_TRIANGULATION;
+    }
+  return CCT_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace cct
+
+using namespace cct;
+
+extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* stream_v, cct_scene* out) {
+  if (!desc || !out) return CCT_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  const cct_tri_desc& d = *desc;
+  if (d.n_tri < 1 || d.n_vert < 3 || d.n_seg < 0 || d.domain < 1 || d.domain > (1 << 20) || !d.vx || !d.vy ||
+      !d.tri_v || !d.tri_nb || !d.tri_seg)
+    return CCT_ERR_INVALID_ARGUMENT;
+  if ((int64_t)d.n_tri >= (1ll << 29)) return CCT_ERR_INVALID_ARGUMENT;
+  {
+    int v = check_ranges(d);
+    if (v == CCT_OK && !(flags & CCT_LOAD_NO_VALIDATE)) v = validate(d);
+    if (v != CCT_OK) return v;
+  }
+  int dev = 0, ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return CCT_ERR_NO_DEVICE;
+  }
+  if (cudaGetDevice(&dev) != cudaSuccess) return CCT_ERR_CUDA;
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  const int nt = d.n_tri;
+  try {
+    // ---- order
+    std::vector<int32_t> dev2user(nt), user2dev(nt);
+    if (flags & CCT_LOAD_NO_REORDER) {
+      for (int t = 0; t < nt; ++t) dev2user[t] = t;
+    } else {
+      std::vector<std::pair<uint64_t, int32_t>> key(nt);
+      for (int t = 0; t < nt; ++t) {
+        const int32_t* tv = d.tri_v + 3 * t;
+        uint32_t cx = (uint32_t)(d.vx[tv[0]] + d.vx[tv[1]] + d.vx[tv[2]]);
+        uint32_t cy = (uint32_t)(d.vy[tv[0]] + d.vy[tv[1]] + d.vy[tv[2]]);
+        key[t] = {hilbert_d(22, cx, cy), t};
+      }
+      std::sort(key.begin(), key.end());
+      for (int t = 0; t < nt; ++t) dev2user[t] = key[t].second;
+    }
+    for (int t = 0; t < nt; ++t) user2dev[dev2user[t]] = t;
+    // ---- records
+    std::vector<TriRec> rec(nt);
+    std::vector<int32_t> cnb(3 * (size_t)nt, -1);
+    for (int T = 0; T < nt; ++T) {
+      const int u = dev2user[T];
+      const int32_t* tv = d.tri_v + 3 * u;
+      TriRec r{};
+      for (int i = 0; i < 3; ++i) {
+        r.X |= (uint64_t)(uint32_t)d.vx[tv[i]] << (kCoordBits * i);
+        r.Y |= (uint64_t)(uint32_t)d.vy[tv[i]] << (kCoordBits * i);
+      }
+      for (int i = 0; i < 3; ++i) {
+        int32_t nbu = d.tri_nb[3 * u + i], seg = d.tri_seg[3 * u + i];
+        int32_t word = -1;
+        if (nbu >= 0) {
+          int32_t a = tv[(i + 1) % 3], b = tv[(i + 2) % 3];
+          int j = 0;
+          for (int k = 0; k < 3; ++k)
+            if (d.tri_v[3 * nbu + (k + 1) % 3] == b && d.tri_v[3 * nbu + (k + 2) % 3] == a) j = k;
+          word = (user2dev[nbu] << 2) | j;
+        }
+        if (seg >= 0) {
+          cnb[3 * (size_t)T + i] = word;
+          r.nb[i] = -2 - seg;
+        } else {
+          r.nb[i] = word;
+        }
+      }
+      rec[T] = r;
+    }
+    // ---- seed grid (Sec. 5.2): a centroid per cell, empty cells copy the nearest
+    long long D = d.domain;
+    int G = (int)std::max(1.0, std::min(2048.0, std::sqrt((double)nt / 2.0)));
+    std::vector<SeedCell> seeds((size_t)G * G, SeedCell{0, 0, -1, 0});
+    std::vector<long long> best((size_t)G * G, -1);
+    for (int T = 0; T < nt; ++T) {
+      const int u = dev2user[T];
+      const int32_t* tv = d.tri_v + 3 * u;
+      long long px3 = (long long)d.vx[tv[0]] + d.vx[tv[1]] + d.vx[tv[2]];
+      long long py3 = (long long)d.vy[tv[0]] + d.vy[tv[1]] + d.vy[tv[2]];
+      int ix = (int)std::min<long long>(G - 1, px3 * G / (3 * D));
+      int iy = (int)std::min<long long>(G - 1, py3 * G / (3 * D));
+      // distance (x9) of the centroid to the cell centre, in thirds
+      long long ccx = (3 * D * (2 * ix + 1)) / (2 * G), ccy = (3 * D * (2 * iy + 1)) / (2 * G);
+      long long dist = (px3 - ccx) * (px3 - ccx) + (py3 - ccy) * (py3 - ccy);
+      size_t c = (size_t)iy * G + ix;
+      if (best[c] < 0 || dist < best[c]) {
+        best[c] = dist;
+        seeds[c] = SeedCell{(int32_t)px3, (int32_t)py3, T, 0};
+      }
+    }
+    {
+      std::deque<int> q;
+      for (int c = 0; c < G * G; ++c)
+        if (seeds[c].tri >= 0) q.push_back(c);
+      while (!q.empty()) {
+        int c = q.front();
+        q.pop_front();
+        int ix = c % G, iy = c / G;
+        const int nbx[4] = {ix - 1, ix + 1, ix, ix}, nby[4] = {iy, iy, iy - 1, iy + 1};
+        for (int k = 0; k < 4; ++k) {
+          if (nbx[k] < 0 || nby[k] < 0 || nbx[k] >= G || nby[k] >= G) continue;
+          int c2 = nby[k] * G + nbx[k];
+          if (seeds[c2].tri >= 0) continue;
+          seeds[c2] = seeds[c];
+          q.push_back(c2);
+        }
+      }
+    }
+    // ---- device allocation and upload
+    size_t o_rec = 0;
+    size_t o_cnb = o_rec + align256(sizeof(TriRec) * (size_t)nt);
+    size_t o_u2d = o_cnb + align256(sizeof(int32_t) * 3 * (size_t)nt);
+    size_t o_d2u = o_u2d + align256(sizeof(int32_t) * (size_t)nt);
+    size_t o_seed = o_d2u + align256(sizeof(int32_t) * (size_t)nt);
+    size_t o_stats = o_seed + align256(sizeof(SeedCell) * (size_t)G * G);
+    size_t total = o_stats + align256(sizeof(DevStats));
+    char* base = nullptr;
+    if (cudaMalloc(&base, total) != cudaSuccess) {
+      cudaGetLastError();
+      return CCT_ERR_OUT_OF_MEMORY;
+    }
+    cudaError_t e = cudaSuccess;
+    auto up = [&](size_t off, const void* src, size_t n) {
+      if (e == cudaSuccess) e = cudaMemcpyAsync(base + off, src, n, cudaMemcpyHostToDevice, stream);
+    };
+    up(o_rec, rec.data(), sizeof(TriRec) * (size_t)nt);
+    up(o_cnb, cnb.data(), sizeof(int32_t) * 3 * (size_t)nt);
+    up(o_u2d, user2dev.data(), sizeof(int32_t) * (size_t)nt);
+    up(o_d2u, dev2user.data(), sizeof(int32_t) * (size_t)nt);
+    up(o_seed, seeds.data(), sizeof(SeedCell) * (size_t)G * G);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_stats, 0, sizeof(DevStats), stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+      cudaFree(base);
+      return CCT_ERR_CUDA;
+    }
+    auto* s = new cct_scene_s;
+    s->d_base = base;
+    s->bytes = total;
+    s->device = dev;
+    s->dev.rec = (const TriRec*)(base + o_rec);
+    s->dev.cnb = (const int32_t*)(base + o_cnb);
+    s->dev.user2dev = (const int32_t*)(base + o_u2d);
+    s->dev.dev2user = (const int32_t*)(base + o_d2u);
+    s->dev.seeds = (const SeedCell*)(base + o_seed);
+    s->dev.stats = (DevStats*)(base + o_stats);
+    s->dev.n_tri = nt;
+    s->dev.G = G;
+    s->dev.D = d.domain;
+    s->dev.max_steps = nt + 8;
+    *out = s;
+    return CCT_OK;
+  } catch (const std::bad_alloc&) {
+    return CCT_ERR_OUT_OF_MEMORY;
+  }
+}
+
+extern "C" int cct_scene_free(cct_scene s) {
+  if (!s) return CCT_OK;
+  int rc = CCT_OK;
+  {
+    DeviceGuard g(s->device);
+    if (cudaFree(s->d_base) != cudaSuccess) rc = CCT_ERR_CUDA;
+  }
+  delete s;
+  return rc;
+}
+
+extern "C" int cct_scene_info(cct_scene s, size_t* device_bytes, int32_t* n_tri) {
+  if (!s) return CCT_ERR_INVALID_ARGUMENT;
+  if (device_bytes) *device_bytes = s->bytes;
+  if (n_tri) *n_tri = s->dev.n_tri;
+  return CCT_OK;
+}
+
+extern "C" int cct_get_stats(cct_scene s, cct_stats* out, int reset, void* stream_v) {
+  if (!s || !out) return CCT_ERR_INVALID_ARGUMENT;
+  DeviceGuard g(s->device);
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  DevStats h{};
+  if (cudaMemcpyAsync(&h, s->dev.stats, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+    return CCT_ERR_CUDA;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return CCT_ERR_CUDA;
+  if (reset) {
+    if (cudaMemsetAsync(s->dev.stats, 0, sizeof(DevStats), stream) != cudaSuccess) return CCT_ERR_CUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return CCT_ERR_CUDA;
+  }
+  out->rays = h.rays;
+  out->steps = h.steps;
+  out->side_tests = h.side_tests;
+  out->exact_fallbacks = h.exact_fallbacks;
+  out->invalid_rays = h.invalid_rays;
+  out->walk_limit_rays = h.walk_limit_rays;
+  out->located = h.located;
+  out->locate_steps = h.locate_steps;
+  return CCT_OK;
+}
+
+extern "C" const char* cct_error_string(int code) {
+  switch (code) {
+    case CCT_OK: return "ok";
+    case CCT_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case CCT_ERR_BAD_TRIANGULATION: return "triangulation failed validation";
+    case CCT_ERR_OUT_OF_MEMORY: return "out of memory";
+    case CCT_ERR_CUDA: return "CUDA runtime error";
+    case CCT_ERR_WALK_LIMIT: return "walk step limit exceeded";
+    case CCT_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int cct_version(void) { return (0 << 16) | 1; }

@@ -1,0 +1,104 @@
+"""C-ABI library checks that need no GPU: libcct.so loads, exports every symbol
+include/cct.h declares, and its host-side validation returns status codes."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import scenegen as sg
+from paper_2112_05570_gb300 import _build, cct
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"^\s*(?:int|const char\s*\*)\s+(cct_\w+)\s*\(", txt, re.M))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return ctypes.CDLL(_build.LIB)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "cct_trace" in names and "cct_scene_load" in names and len(names) >= 8
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_status_strings_and_version():
+    assert cct.cct_error_string(cct.CCT_OK) == "ok"
+    assert "validation" in cct.cct_error_string(cct.CCT_ERR_BAD_TRIANGULATION)
+    assert cct.cct_version() >= 1
+
+
+def _tri(n=60, seed=3):
+    return sg.cdt(sg.random_segments(n, seed))
+
+
+@pytest.mark.parametrize("corrupt", ["orientation", "neighbour", "label", "index", "area", "hull"])
+def test_load_rejects_corrupt_triangulations(corrupt):
+    t = _tri()
+    vx, vy, tv, tn, ts = t.vx.copy(), t.vy.copy(), t.tri_v.copy(), t.tri_nb.copy(), t.tri_seg.copy()
+    n_seg = t.segs.shape[0]
+    if corrupt == "orientation":
+        tv[4] = tv[4][[0, 2, 1]]
+    elif corrupt == "neighbour":
+        i = np.argwhere(tn[5] >= 0)[0, 0]
+        tn[5, i] = (tn[5, i] + 1) % t.n_tri
+    elif corrupt == "label":
+        tt, ti = np.argwhere(ts >= 0)[0]
+        ts[tt, ti] = -1
+    elif corrupt == "index":
+        tv[2, 1] = t.n_vert + 5
+    elif corrupt == "area":
+        vx = vx.copy()
+        vx[vx == sg.D] = sg.D - 1  # the hull no longer spans the domain
+    elif corrupt == "hull":
+        i = np.argwhere(tn[0] >= 0)[0, 0]
+        tn = tn.copy()
+        u = tn[0, i]
+        j = np.argwhere(tn[u] == 0)[0, 0]
+        tn[0, i] = -1
+        tn[u, j] = -1
+    with pytest.raises(cct.CctError) as e:
+        cct.cct_scene_load(vx, vy, tv, tn, ts, n_seg, sg.D)
+    assert e.value.code == cct.CCT_ERR_BAD_TRIANGULATION
+
+
+def test_load_argument_errors():
+    t = _tri()
+    with pytest.raises(cct.CctError) as e:
+        cct.cct_scene_load(t.vx, t.vy, t.tri_v, t.tri_nb, t.tri_seg, t.segs.shape[0], (1 << 20) + 1)
+    assert e.value.code == cct.CCT_ERR_INVALID_ARGUMENT
+    with pytest.raises(cct.CctError) as e:
+        cct.cct_scene_load(t.vx, t.vy, t.tri_v[:0], t.tri_nb[:0], t.tri_seg[:0], 0, sg.D)
+    assert e.value.code == cct.CCT_ERR_INVALID_ARGUMENT
+    L = cct.lib()
+    assert L.cct_trace(None, None, None, None, None, None, 0, None, None, None, 0, None) == cct.CCT_ERR_INVALID_ARGUMENT
+    assert L.cct_locate(None, None, None, 0, None, None) == cct.CCT_ERR_INVALID_ARGUMENT
+    assert L.cct_scene_free(None) == cct.CCT_OK
+
+
+def test_valid_triangulation_passes_validation_without_gpu():
+    """Without a GPU a valid triangulation gets past validation and stops at the
+    device check; with a GPU it loads."""
+    import torch
+
+    t = _tri()
+    if torch.cuda.is_available():
+        s = cct.Scene.from_triangulation(t, sg.D)
+        s.free()
+        return
+    with pytest.raises(cct.CctError) as e:
+        cct.Scene.from_triangulation(t, sg.D)
+    assert e.value.code == cct.CCT_ERR_NO_DEVICE
