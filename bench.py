@@ -1,12 +1,15 @@
 """Closest-hit ray throughput on one GB300 (and N replicas under torchrun).
 
-Workload (the paper-shaped scenes, Sec. 4 / 6): 30,000-segment scenes of
-polygonal circles with 64-1024 sides, annealed triangulation, 2^24 isotropic
-rays (origins uniform on the integer grid, angles uniform), start cells found
-on the GPU.  One step = the whole query path on one batch: locate (Sec. 5.2)
-+ walk (Sec. 5.1) of all 2^24 rays through ``cct_trace``.  Inputs (2^24 rays,
-320 MB with results) are larger than L2; the 2 MB triangle table stays
-L2-resident across steps as an acceleration structure would.
+Workload: the paper-shaped scene families (the lines / floor-plan shapes of
+Sec. 4 and 6, rendered as synthetic scenes): polygonal circles with 64-1024
+sides, a regular dash grid rotated by 0, 1, 22.5 and 45 degrees (kd-tree
+misalignment stress), and Gaussian-clustered random segments -- six scenes of
+about 30,000 segments, each with its annealed triangulation and 2^24 isotropic
+rays (origins uniform on the integer grid, angles uniform).  One step = the
+whole query path on one batch: for every scene, locate (Sec. 5.2) + walk
+(Sec. 5.1) of its 2^24 rays through ``cct_trace``, start cells found on the
+GPU.  Inputs (6 x 2^24 rays, 2 GB with results) are larger than L2; the
+2-4 MB triangle tables stay L2-resident as acceleration structures do.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
 bounded sample of the same workload instead (the baseline arm).
@@ -29,18 +32,32 @@ sys.path.insert(0, ROOT)
 N_SEGMENTS = 30000
 N_RAYS = 1 << 24
 SCENE_SEED = 2
-RAY_SEED = 7
-WORKLOAD = "config2-circles-30k-annealed-2^24-isotropic"
+WORKLOAD = "config2-families-30k-annealed-6x2^24-isotropic"
+FAMILIES = ("circles", "dash0", "dash1", "dash22.5", "dash45", "clustered")
 
 
-def build_workload(n_rays=N_RAYS):
+def family_segments(name):
     import scenegen as sg
 
-    segs = sg.circles(N_SEGMENTS, SCENE_SEED)
-    cdt = sg.cdt(segs)
-    tri = sg.anneal(cdt, SCENE_SEED, sweeps=4)
-    rays = sg.rays_isotropic(tri, n_rays, RAY_SEED)
-    return segs, cdt, tri, rays
+    if name == "circles":
+        return sg.circles(N_SEGMENTS, SCENE_SEED)
+    if name == "clustered":
+        return sg.clustered(N_SEGMENTS, SCENE_SEED)
+    return sg.dash_grid(N_SEGMENTS, float(name[4:]))
+
+
+def build_workload(n_rays=N_RAYS, families=FAMILIES):
+    """[(name, segs, cdt, annealed, rays)] for the scene families."""
+    import scenegen as sg
+
+    out = []
+    for k, name in enumerate(families):
+        segs = family_segments(name)
+        cdt = sg.cdt(segs)
+        tri = sg.anneal(cdt, SCENE_SEED + k, sweeps=4)
+        rays = sg.rays_isotropic(tri, n_rays, 100 + k)
+        out.append((name, segs, cdt, tri, rays))
+    return out
 
 
 class ClockSampler:
@@ -100,53 +117,70 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(tri, rays, seconds_target=4.0, max_rays=1 << 22):
-    """Oracle walk (given start cells) on the host cores: rays/s over a bounded sample."""
+def cpu_oracle_rate(work, seconds_target=4.0):
+    """Oracle walk (given start cells) on all host cores over a bounded sample:
+    the first rays of every scene, sized to take about seconds_target."""
     import oracle
 
     threads = os.cpu_count() or 1
-    n = 1 << 16
+    n = 1 << 14
     t0 = time.perf_counter()
-    oracle.walk(tri, rays.ox[:n], rays.oy[:n], rays.dx[:n], rays.dy[:n], rays.start[:n], n_threads=threads)
+    for name, segs, cdt, tri, r in work:
+        oracle.walk(tri, r.ox[:n], r.oy[:n], r.dx[:n], r.dy[:n], r.start[:n], n_threads=threads)
     dt = time.perf_counter() - t0
-    n2 = int(min(max_rays, len(rays), max(n, n * seconds_target / max(dt, 1e-6))))
+    n2 = int(min(N_RAYS, max(n, n * seconds_target / max(dt, 1e-6))))
     t0 = time.perf_counter()
-    oracle.walk(tri, rays.ox[:n2], rays.oy[:n2], rays.dx[:n2], rays.dy[:n2], rays.start[:n2], n_threads=threads)
+    for name, segs, cdt, tri, r in work:
+        oracle.walk(tri, r.ox[:n2], r.oy[:n2], r.dx[:n2], r.dy[:n2], r.start[:n2], n_threads=threads)
     dt = time.perf_counter() - t0
-    return n2 / dt, threads, n2, dt
+    return n2 * len(work) / dt, threads, n2, dt
 
 
 def run_reference(args):
+    """The baseline arm: the CPU oracle, as it stands, on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    segs, cdt, tri, rays = build_workload()
     import oracle
 
+    sample = 1 << 18
+    work = build_workload(n_rays=sample * max(1, min(args.steps, 4)))
     threads = os.cpu_count() or 1
-    sample = 1 << 20
     for _ in range(args.warmup):
-        oracle.walk(tri, rays.ox[:4096], rays.oy[:4096], rays.dx[:4096], rays.dy[:4096], rays.start[:4096],
-                    n_threads=threads)
+        for name, segs, cdt, tri, r in work:
+            oracle.walk(tri, r.ox[:4096], r.oy[:4096], r.dx[:4096], r.dy[:4096], r.start[:4096], n_threads=threads)
     times = []
     for k in range(args.steps):
-        lo = (k * sample) % (len(rays) - sample + 1)
+        lo = (k * sample) % (len(work[0][4]) - sample + 1)
         sl = slice(lo, lo + sample)
         t0 = time.perf_counter()
-        oracle.walk(tri, rays.ox[sl], rays.oy[sl], rays.dx[sl], rays.dy[sl], rays.start[sl], n_threads=threads)
+        for name, segs, cdt, tri, r in work:
+            oracle.walk(tri, r.ox[sl], r.oy[sl], r.dx[sl], r.dy[sl], r.start[sl], n_threads=threads)
         times.append(time.perf_counter() - t0)
-    value = sample * len(times) / sum(times)
+    rays_per_step = sample * len(work)
+    value = rays_per_step * len(times) / sum(times)
     line = {"impl": "reference", "metric": "closest-hit rays/s", "value": value, "unit": "rays/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rays_per_step": sample, "segments": int(segs.shape[0]),
-                       "triangles": tri.n_tri},
+            "config": {"workload": WORKLOAD, "rays_per_step": rays_per_step, "families": list(FAMILIES)},
             "cpu_baseline": {"value": value, "unit": "rays/s", "cores": threads, "kind": "oracle",
-                             "sample": f"oracle walk from given start cells, {sample} rays per step"},
+                             "sample": f"oracle walk from given start cells, {sample} rays of each of the "
+                                       f"{len(work)} scenes per step"},
             "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def _time_loop(torch, dev, stream, fn, k):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(k):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / k
 
 
 def main():
@@ -157,6 +191,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--flags", default="auto", help="auto | plain | bin")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling mode: per scene, 2 warm-up walk launches then 1 walk launch (start cells "
+                         "given); no timing, no JSON")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -180,46 +217,51 @@ def main():
     _build.build()
     import scenegen as sg
 
-    segs, cdt, tri, rays = build_workload()
-    scene = cct.Scene.from_triangulation(tri, sg.D)
-    n = len(rays)
-    ox, oy = torch.from_numpy(rays.ox).to(dev), torch.from_numpy(rays.oy).to(dev)
-    dx, dy = torch.from_numpy(rays.dx).to(dev), torch.from_numpy(rays.dy).to(dev)
-    start = torch.from_numpy(rays.start).to(dev)
+    work = build_workload()
+    stream = torch.cuda.current_stream(dev)
+    n = N_RAYS
     hit = torch.empty(n, dtype=torch.int32, device=dev)
     t = torch.empty(n, dtype=torch.float32, device=dev)
     steps = torch.empty(n, dtype=torch.int32, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    scenes = []
+    for name, segs, cdt, tri, r in work:
+        d = {k: torch.from_numpy(getattr(r, k)).to(dev) for k in ("ox", "oy", "dx", "dy", "start")}
+        scenes.append(dict(name=name, segs=segs, cdt=cdt, tri=tri, rays=r, d=d,
+                           scene=cct.Scene.from_triangulation(tri, sg.D)))
+
+    def trace(sc, start, flags, s=None):
+        d = sc["d"]
+        cct.cct_trace(sc["scene"].handle, d["ox"], d["oy"], d["dx"], d["dy"], start, hit, t, steps, flags,
+                      stream if s is None else s)
+
+    if args.profile:
+        for sc in scenes:
+            for _ in range(3):
+                trace(sc, sc["d"]["start"], 0)
+        torch.cuda.synchronize(dev)
+        return 0
 
     def step(flags):
-        cct.cct_trace(scene.handle, ox, oy, dx, dy, None, hit, t, steps, flags, stream)
+        for sc in scenes:
+            trace(sc, None, flags)
 
-    # path choice: plain vs binned (a short measurement; "auto" keeps the faster)
-    def time_loop(fn, k):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for _ in range(k):
-            fn()
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1) / k
-
+    # path: plain vs binned, kept per run ("auto" times both briefly and keeps the faster)
     choice = {"plain": 0, "bin": cct.CCT_TRACE_BIN}
     if args.flags == "auto":
         for f in choice.values():
             step(f)
-        tried = {k: time_loop(lambda f=f: step(f), 3) for k, f in choice.items()}
+        tried = {k: _time_loop(torch, dev, stream, lambda f=f: step(f), 2) for k, f in choice.items()}
         path = min(tried, key=tried.get)
     else:
         path, tried = args.flags, {}
     flags = choice[path]
-    kernels_per_step = 2 + (5 if flags & cct.CCT_TRACE_BIN else 0)
+    kernels_per_trace = 2 + (5 if flags & cct.CCT_TRACE_BIN else 0)
 
     for _ in range(max(3, args.warmup)):
         step(flags)
     torch.cuda.synchronize(dev)
-    scene.stats(reset=True)
+    for sc in scenes:
+        sc["scene"].stats(reset=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -237,84 +279,106 @@ def main():
         m = torch.tensor([ms], device=dev)
         dist.all_reduce(m, op=dist.ReduceOp.MAX)
         ms = float(m.item())
-    stats = scene.stats(reset=True)
-    value = n * world / (ms * 1e-3)
-    steps_per_ray = stats["steps"] / max(1, stats["rays"])
+    rays_per_step = n * len(scenes)
+    value = rays_per_step * world / (ms * 1e-3)
+    tot = {"rays": 0, "steps": 0, "side_tests": 0, "exact_fallbacks": 0, "located": 0, "locate_steps": 0}
+    for sc in scenes:
+        st = sc["scene"].stats(reset=True)
+        for k in tot:
+            tot[k] += st[k]
 
-    # ---- roofline of the dominant kernel (the walk), start cells given
-    torch.cuda.synchronize(dev)
-    for _ in range(3):
-        cct.cct_trace(scene.handle, ox, oy, dx, dy, start, hit, t, steps, 0, stream)
-    k_rep = max(5, args.steps // 2)
-    walk_ms = time_loop(lambda: cct.cct_trace(scene.handle, ox, oy, dx, dy, start, hit, t, steps, 0, stream), k_rep)
-    st_walk = scene.stats(reset=True)
-    walk_steps = st_walk["steps"] / (k_rep + 3)  # steps per launch (warm-up launches included in the counters)
-    alg_bytes = walk_steps * 32.0 + n * 32.0
-    achieved_gbs = alg_bytes / (walk_ms * 1e-3) / 1e9
-    table_bytes = tri.n_tri * 32
-    _, l2_bps = cct.cct_measure_gather(table_bytes, 1 << 27, 5, stream)
+    # ---- per scene: the walk kernel alone (start cells given) -> roofline; CDT vs annealed steps
+    per = {}
+    walk_ms_tot, alg_bytes_tot, alg_over_peak = 0.0, 0.0, 0.0
+    for sc in scenes:
+        for _ in range(2):
+            trace(sc, sc["d"]["start"], 0)
+        sc["scene"].stats(reset=True)
+        k_rep = max(3, args.steps // 4)
+        wms = _time_loop(torch, dev, stream, lambda sc=sc: trace(sc, sc["d"]["start"], 0), k_rep)
+        st = sc["scene"].stats(reset=True)
+        wsteps = st["steps"] / k_rep
+        alg = wsteps * 32.0 + n * 32.0
+        table_bytes = sc["tri"].n_tri * 32
+        _, bps = cct.cct_measure_gather(table_bytes, 1 << 27, 5, stream)
+        walk_ms_tot += wms
+        alg_bytes_tot += alg
+        alg_over_peak += alg / bps
+        cdt_scene = cct.Scene.from_triangulation(sc["cdt"], sg.D)
+        d = sc["d"]
+        cct.cct_trace(cdt_scene.handle, d["ox"], d["oy"], d["dx"], d["dy"], None, hit, t, steps, 0, stream)
+        cst = cdt_scene.stats()
+        cdt_scene.free()
+        per[sc["name"]] = {"segments": int(sc["segs"].shape[0]), "triangles": sc["tri"].n_tri,
+                           "walk_rays_per_s": n / (wms * 1e-3), "steps_per_ray": wsteps / n,
+                           "steps_per_ray_cdt": cst["steps"] / max(1, cst["rays"]),
+                           "length_annealed_over_cdt": sc["tri"].length(True) / sc["cdt"].length(True),
+                           "walk_l2_frac": (alg / (wms * 1e-3)) / bps, "gather_peak_gbs": bps / 1e9}
+    achieved = alg_bytes_tot / (walk_ms_tot * 1e-3) / 1e9
+    l2_peak = alg_bytes_tot / alg_over_peak / 1e9  # time-weighted gather peak over the scenes' table sizes
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    hbm_peak = None
-    if os.path.exists(peaks_path):
-        hbm_peak = json.load(open(peaks_path)).get("hbm_gbs")
-    hbm_src = "MEASURED_PEAKS.json" if hbm_peak else "fallback"
+    hbm_peak = json.load(open(peaks_path)).get("hbm_gbs") if os.path.exists(peaks_path) else None
+    hbm_src = "MEASURED_PEAKS.json (measured)" if hbm_peak else "fallback 6800 GB/s"
     hbm_peak = hbm_peak or 6800.0
-    l2_peak = l2_bps / 1e9
-    roofline = {"bound": "l2", "achieved": achieved_gbs, "peak": l2_peak, "unit": "GB/s",
-                "frac": achieved_gbs / l2_peak, "traffic": None,
-                "kernel": "walk_kernel (start cells given)",
-                "peak_source": f"measured in this run: random 32-byte sector gathers over a {table_bytes} B table "
-                               "(cct_measure_gather)",
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "ms_per_launch": walk_ms,
-                "hbm": {"peak": hbm_peak, "frac": achieved_gbs / hbm_peak, "source": hbm_src}}
+    roofline = {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
+                "traffic": None, "kernel": "walk_kernel (start cells given), all six scenes",
+                "peak_source": "measured live: random 32-byte sector gathers over tables of each scene's size "
+                               "(cct_measure_gather), weighted by each scene's bytes",
+                "algorithmic_bytes_per_step": alg_bytes_tot, "walk_ms_per_step": walk_ms_tot,
+                "bytes_model": "32 B per walk step (one triangle record) + 32 B per ray (16 B ray, 4 B start, "
+                               "12 B result)",
+                "hbm": {"peak": hbm_peak, "frac": achieved / hbm_peak, "source": hbm_src}}
 
-    # ---- end to end through the public API with host buffers
-    pin = {k: torch.from_numpy(getattr(rays, k)).pin_memory() for k in ("ox", "oy", "dx", "dy")}
+    # ---- end to end through the public API with host buffers (pinned), every scene
+    for sc in scenes:
+        sc["pin"] = {k: torch.from_numpy(getattr(sc["rays"], k)).pin_memory() for k in ("ox", "oy", "dx", "dy")}
     out_h = (torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.float32).pin_memory(),
              torch.empty(n, dtype=torch.int32).pin_memory())
+    dbuf = {k: torch.empty(n, dtype=torch.int32 if k in ("ox", "oy") else torch.float32, device=dev)
+            for k in ("ox", "oy", "dx", "dy")}
 
     def e2e_step():
-        dox = pin["ox"].to(dev, non_blocking=True)
-        doy = pin["oy"].to(dev, non_blocking=True)
-        ddx = pin["dx"].to(dev, non_blocking=True)
-        ddy = pin["dy"].to(dev, non_blocking=True)
-        cct.cct_trace(scene.handle, dox, doy, ddx, ddy, None, hit, t, steps, flags, stream)
-        out_h[0].copy_(hit, non_blocking=True)
-        out_h[1].copy_(t, non_blocking=True)
-        out_h[2].copy_(steps, non_blocking=True)
+        for sc in scenes:
+            for k in dbuf:
+                dbuf[k].copy_(sc["pin"][k], non_blocking=True)
+            cct.cct_trace(sc["scene"].handle, dbuf["ox"], dbuf["oy"], dbuf["dx"], dbuf["dy"], None, hit, t, steps,
+                          flags, stream)
+            out_h[0].copy_(hit, non_blocking=True)
+            out_h[1].copy_(t, non_blocking=True)
+            out_h[2].copy_(steps, non_blocking=True)
+        torch.cuda.synchronize(dev)
 
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize(dev)
-    k_e2e = max(3, args.steps // 4)
+    e2e_step()
+    k_e2e = max(2, args.steps // 4)
     t0 = time.perf_counter()
     for _ in range(k_e2e):
         e2e_step()
-    torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / k_e2e
-    e2e = {"value": n * world / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 12 * n}
+    e2e = {"value": rays_per_step * world / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": 16 * rays_per_step,
+           "d2h_bytes_per_step": 12 * rays_per_step}
 
     line = {"metric": "closest-hit rays/s", "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64+fp32-filter", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "segments": int(segs.shape[0]), "triangles": tri.n_tri,
-                       "rays_per_step": n, "path": path, "path_ms_tried": tried,
-                       "l2": "inputs larger than L2 (rays + results 512 MB); triangle table L2-resident",
+            "config": {"workload": WORKLOAD, "families": list(FAMILIES), "segments_per_scene": N_SEGMENTS,
+                       "rays_per_step": rays_per_step, "path": path, "path_ms_tried": tried,
+                       "l2": "inputs larger than L2 (6 x 2^24 rays + results, 2 GB); triangle tables L2-resident",
                        "parallelism": f"replicas x{world}"},
-            "steps_per_ray": steps_per_ray,
-            "fallback_rate": stats["exact_fallbacks"] / max(1, stats["side_tests"]),
-            "locate_steps_per_ray": stats["locate_steps"] / max(1, stats["located"]),
-            "roofline": roofline, "e2e": e2e, "gpu_launches": kernels_per_step * args.steps}
+            "steps_per_ray": tot["steps"] / max(1, tot["rays"]),
+            "fallback_rate": tot["exact_fallbacks"] / max(1, tot["side_tests"]),
+            "locate_steps_per_ray": tot["locate_steps"] / max(1, tot["located"]),
+            "per_scene": per, "roofline": roofline, "e2e": e2e,
+            "gpu_launches": kernels_per_trace * len(scenes) * args.steps}
     if rank == 0 and not args.no_cpu_baseline:
-        rate, cores, sample_n, dt = cpu_oracle_rate(tri, rays)
+        rate, cores, sample_n, dt = cpu_oracle_rate(work)
         line["cpu_baseline"] = {"value": rate, "unit": "rays/s", "cores": cores, "kind": "oracle",
-                                "sample": f"oracle walk from given start cells over the first {sample_n} rays "
-                                          f"({dt:.1f} s wall)"}
+                                "sample": f"oracle walk from given start cells over the first {sample_n} rays of "
+                                          f"each of the {len(work)} scenes ({dt:.1f} s wall)"}
     if rank == 0:
         line["clocks"] = clk.summary()
         print(json.dumps(line))
-    scene.free()
+    for sc in scenes:
+        sc["scene"].free()
     if dist:
         dist.destroy_process_group()
     return 0
