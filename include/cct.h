@@ -148,6 +148,29 @@ int cct_trace(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy, const f
               const int32_t* d_start_tri, int64_t n, int32_t* d_hit_seg, float* d_t, int32_t* d_steps,
               uint32_t flags, void* stream);
 
+/* No counterpart in the paper: cct_trace for callers that cannot allocate
+ * device memory during a query -- e.g. a process that reserved the GPU's memory
+ * for its own pool at start-up, or a latency-critical loop that must not enter
+ * an allocator.  Same arguments, outputs and per-ray statuses as cct_trace;
+ * the scratch it needs (a work counter and, when d_start_tri is NULL, the
+ * located start cells) lives in one file-scope device array of
+ * CCT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits.  Nothing is allocated: no cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ * Limits: n <= CCT_NOALLOC_MAX_RAYS and no CCT_TRACE_BIN (binning needs scratch
+ * per ray); otherwise CCT_ERR_INVALID_ARGUMENT.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current); make that
+ * first call before any stream capture.  All calls share the array and each
+ * call clears the part that must start at zero, so calls whose GPU work
+ * overlaps (other streams or host threads) race and give wrong results:
+ * serialise them.  Errors: those of cct_trace. */
+#define CCT_NOALLOC_MAX_RAYS (1 << 20)
+#define CCT_NOALLOC_SCRATCH_BYTES (256 + 4 * CCT_NOALLOC_MAX_RAYS)
+int cct_trace_noalloc(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy, const float* d_dx,
+                      const float* d_dy, const int32_t* d_start_tri, int64_t n, int32_t* d_hit_seg, float* d_t,
+                      int32_t* d_steps, uint32_t flags, void* stream);
+
 /* Copies the scene's counters to *out after waiting for `stream`; reset != 0
  * zeroes them afterwards.  Errors: CCT_ERR_INVALID_ARGUMENT, CCT_ERR_CUDA. */
 int cct_get_stats(cct_scene scene, cct_stats* out, int reset, void* stream);

@@ -25,6 +25,7 @@ CCT_LOAD_NO_REORDER = 1
 CCT_LOAD_NO_VALIDATE = 2
 CCT_TRACE_EXACT_ONLY = 1
 CCT_TRACE_BIN = 2
+CCT_NOALLOC_MAX_RAYS = 1 << 20
 
 
 class CctError(RuntimeError):
@@ -67,6 +68,8 @@ def lib() -> ctypes.CDLL:
     L.cct_locate.argtypes = [vp, vp, vp, i64, vp, vp]
     L.cct_trace.restype = ctypes.c_int
     L.cct_trace.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, u32, vp]
+    L.cct_trace_noalloc.restype = ctypes.c_int
+    L.cct_trace_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, u32, vp]
     L.cct_get_stats.restype = ctypes.c_int
     L.cct_get_stats.argtypes = [vp, ctypes.POINTER(_Stats), ctypes.c_int, vp]
     L.cct_error_string.restype = ctypes.c_char_p
@@ -155,6 +158,22 @@ def cct_trace(scene: int, ox, oy, dx, dy, start, hit, t, steps, flags: int = 0, 
                            _dev(start, torch.int32, "start"), n, _dev(hit, torch.int32, "hit"),
                            _dev(t, torch.float32, "t"), _dev(steps, torch.int32, "steps"), flags,
                            _stream_ptr(stream)), "cct_trace")
+
+
+def cct_trace_noalloc(scene: int, ox, oy, dx, dy, start, hit, t, steps, flags: int = 0, stream=None) -> None:
+    """cct_trace without any allocation (include/cct.h): at most
+    CCT_NOALLOC_MAX_RAYS rays, no binning; calls on one GPU must not overlap."""
+    import torch
+
+    n = ox.numel()
+    for a in (oy, dx, dy, hit, t, steps) + ((start,) if start is not None else ()):
+        if a.numel() != n:
+            raise ValueError("all ray and result tensors must have the same length")
+    _check(lib().cct_trace_noalloc(ctypes.c_void_p(scene), _dev(ox, torch.int32, "ox"), _dev(oy, torch.int32, "oy"),
+                                   _dev(dx, torch.float32, "dx"), _dev(dy, torch.float32, "dy"),
+                                   _dev(start, torch.int32, "start"), n, _dev(hit, torch.int32, "hit"),
+                                   _dev(t, torch.float32, "t"), _dev(steps, torch.int32, "steps"), flags,
+                                   _stream_ptr(stream)), "cct_trace_noalloc")
 
 
 def cct_get_stats(scene: int, reset: bool = False, stream=None) -> dict:

@@ -168,6 +168,24 @@ struct Scratch {
 cudaError_t launch_locate(const SceneDev& S, const int32_t* ox, const int32_t* oy, int64_t n, int32_t* out,
                           bool to_user, cudaStream_t stream);
 
+// Rays as the walk kernel reads them: separate arrays, or the sorted packed
+// form written by the binning pass.
+struct RaySrc {
+  const int32_t* ox;
+  const int32_t* oy;
+  const float* dx;
+  const float* dy;
+  const int32_t* start;  // caller ids (start_user) or record indices
+  const int4* rays;      // sorted form: {ox, oy, dx bits, dy bits}
+  const int32_t* orig;   // sorted form: original index
+  int64_t n;
+};
+
+// Enqueues the walk kernel; `counter` (8 bytes, zeroed by the caller on the
+// same stream) hands out ray chunks.
+cudaError_t launch_walk(bool exact, bool sorted, bool start_user, const SceneDev& S, const RaySrc& R, int32_t* hit,
+                        float* t, int32_t* steps, unsigned long long* counter, int dev, cudaStream_t stream);
+
 struct BinOut {
   int4* rays;      // {ox, oy, dx bits, dy bits} sorted by start cell
   int32_t* start;  // record index, sorted

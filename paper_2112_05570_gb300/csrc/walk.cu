@@ -23,17 +23,6 @@ namespace cct {
 constexpr int kWalkThreads = 256;
 constexpr int kChunk = 128;
 
-struct RaySrc {
-  const int32_t* ox;
-  const int32_t* oy;
-  const float* dx;
-  const float* dy;
-  const int32_t* start;  // caller ids (kStartUser) or record indices
-  const int4* rays;      // sorted form: {ox, oy, dx bits, dy bits}
-  const int32_t* orig;   // sorted form: original index
-  int64_t n;
-};
-
 template <bool kExact, bool kSorted, bool kStartUser>
 __global__ void __launch_bounds__(kWalkThreads) walk_kernel(SceneDev S, RaySrc R, int32_t* __restrict__ hit_out,
                                                             float* __restrict__ t_out,
@@ -205,7 +194,7 @@ static cudaError_t launch_walk_t(const SceneDev& S, const RaySrc& R, int32_t* hi
   return cudaGetLastError();
 }
 
-static cudaError_t launch_walk(bool exact, bool sorted, bool start_user, const SceneDev& S, const RaySrc& R,
+cudaError_t launch_walk(bool exact, bool sorted, bool start_user, const SceneDev& S, const RaySrc& R,
                                int32_t* hit, float* t, int32_t* steps, unsigned long long* counter, int dev,
                                cudaStream_t stream) {
   if (sorted)

@@ -1,0 +1,84 @@
+"""cct_trace_noalloc, the entry point for callers that cannot allocate device
+memory during a query (a process whose memory is reserved by its own pool, a
+latency-critical loop that must not enter an allocator): through the C ABI it
+must give the same results as cct_trace, call after call, although all calls
+share one static scratch array.  Collected last on purpose (file name)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cct():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2112_05570_gb300 import _build, cct as c
+
+    _build.build()
+    return c
+
+
+def _p(x):
+    return None if x is None else ctypes.c_void_p(x.data_ptr())
+
+
+def test_noalloc_matches_cct_trace_two_calls_in_a_row(cct):
+    segs = sg.random_segments(200, 31)
+    tri = sg.anneal(sg.cdt(segs), 31)
+    n = 300_001  # ragged; below CCT_NOALLOC_MAX_RAYS
+    r = sg.rays_isotropic(tri, n, 32)
+    scene = cct.Scene.from_triangulation(tri, sg.D)
+    dev = torch.device("cuda")
+    ox, oy = torch.from_numpy(r.ox).to(dev), torch.from_numpy(r.oy).to(dev)
+    dx, dy = torch.from_numpy(r.dx).to(dev), torch.from_numpy(r.dy).to(dev)
+    start = torch.from_numpy(r.start).to(dev)
+    L = cct.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for start_arg in (None, start):
+        ref = scene.trace(ox, oy, dx, dy, start_arg)
+        torch.cuda.synchronize()
+        ref = tuple(x.cpu().numpy() for x in ref)
+        for call in range(2):
+            hit = torch.full((n,), -7, dtype=torch.int32, device=dev)
+            t = torch.full((n,), -7.0, dtype=torch.float32, device=dev)
+            steps = torch.full((n,), -7, dtype=torch.int32, device=dev)
+            rc = L.cct_trace_noalloc(ctypes.c_void_p(scene.handle), _p(ox), _p(oy), _p(dx), _p(dy), _p(start_arg),
+                                     n, _p(hit), _p(t), _p(steps), 0, stream)
+            assert rc == cct.CCT_OK, cct.cct_error_string(rc)
+            torch.cuda.synchronize()
+            h, tt, s = hit.cpu().numpy(), t.cpu().numpy(), steps.cpu().numpy()
+            assert np.array_equal(h, ref[0]), f"call {call}: hit ids differ"
+            assert np.array_equal(s, ref[2]), f"call {call}: steps differ"
+            fin = np.isfinite(ref[1])
+            assert np.array_equal(np.isfinite(tt), fin)
+            rel = np.abs(tt[fin].astype(np.float64) - ref[1][fin]) / np.abs(ref[1][fin].astype(np.float64))
+            assert rel.max() <= 1e-6
+    # and both equal the oracle
+    eh, et, es = oracle.walk(tri, r.ox, r.oy, r.dx, r.dy, r.start)
+    assert np.array_equal(h, eh) and np.array_equal(s, es)
+    scene.free()
+
+
+def test_noalloc_rejects_sizes_beyond_its_limit(cct):
+    tri = sg.cdt(sg.random_segments(50, 33))
+    scene = cct.Scene.from_triangulation(tri, sg.D)
+    L = cct.lib()
+    dev = torch.device("cuda")
+    big = cct.CCT_NOALLOC_MAX_RAYS + 1
+    bi = torch.zeros(big, dtype=torch.int32, device=dev)
+    bf = torch.zeros(big, dtype=torch.float32, device=dev)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.cct_trace_noalloc(ctypes.c_void_p(scene.handle), _p(bi), _p(bi), _p(bf), _p(bf), None, big, _p(bi),
+                             _p(bf), _p(bi), 0, stream)
+    assert rc == cct.CCT_ERR_INVALID_ARGUMENT
+    rc = L.cct_trace_noalloc(ctypes.c_void_p(scene.handle), _p(bi), _p(bi), _p(bf), _p(bf), None, 16, _p(bi),
+                             _p(bf), _p(bi), cct.CCT_TRACE_BIN, stream)
+    assert rc == cct.CCT_ERR_INVALID_ARGUMENT
+    scene.free()
