@@ -105,6 +105,25 @@ typedef struct {
   uint64_t locate_steps;   /* triangles visited by those locate walks (not part of `steps`) */
 } cct_stats;
 
+/* Launch configuration of the walk for one scene (no counterpart in the paper;
+ * chosen by an autotuner, defaults are used otherwise).
+ *   block_threads  threads per block, a multiple of 32 in [32, 512]      (256)
+ *   refill_min     a warp serves its idle lanes new rays once this many of
+ *                  them are idle, or all of them (the warp-level ray
+ *                  retirement / refill), in [1, 32]                          (8)
+ *   chunk          rays a warp takes from the global work counter at once,
+ *                  in [32, 2^20]                                            (128)
+ *   bin_shift      ray-binning granularity: rays are sorted by start record
+ *                  index >> bin_shift; -1 = automatic (~64 rays per bin)     (-1)
+ *   trace_flags    CCT_TRACE_* flags OR-ed into every cct_trace of the scene  (0) */
+typedef struct {
+  int32_t block_threads;
+  int32_t refill_min;
+  int32_t chunk;
+  int32_t bin_shift;
+  uint32_t trace_flags;
+} cct_tuning;
+
 /* ------------------------------------------------------------------ scene */
 /* Validates and uploads a triangulation (Sec. 5.1's structure).  Checks: index
  * ranges, strictly CCW triangles, neighbour symmetry, equal labels on both
@@ -119,6 +138,15 @@ int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* stream, cct_s
 /* Releases a scene's device memory.  The caller guarantees no work using it
  * is pending.  NULL is accepted. */
 int cct_scene_free(cct_scene scene);
+
+/* Sets (tuning != NULL) or resets to the defaults (NULL) the walk's launch
+ * configuration of a scene; takes effect for calls enqueued afterwards.  Not
+ * thread-safe against concurrent cct_trace calls on the same scene from other
+ * host threads.  Errors: CCT_ERR_INVALID_ARGUMENT (a field out of range). */
+int cct_scene_set_tuning(cct_scene scene, const cct_tuning* tuning);
+
+/* Copies the scene's current launch configuration to *out. */
+int cct_scene_get_tuning(cct_scene scene, cct_tuning* out);
 
 /* Device bytes held by the scene and its number of triangles (either output
  * pointer may be NULL). */

@@ -40,6 +40,15 @@ class _TriDesc(ctypes.Structure):
                 ("tri_v", ctypes.c_void_p), ("tri_nb", ctypes.c_void_p), ("tri_seg", ctypes.c_void_p)]
 
 
+class Tuning(ctypes.Structure):
+    """cct_tuning (include/cct.h): the walk's launch configuration of a scene."""
+    _fields_ = [("block_threads", ctypes.c_int32), ("refill_min", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("bin_shift", ctypes.c_int32), ("trace_flags", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in ("rays", "steps", "side_tests", "exact_fallbacks", "invalid_rays",
                                                "walk_limit_rays", "located", "locate_steps")]
@@ -68,6 +77,10 @@ def lib() -> ctypes.CDLL:
     L.cct_locate.argtypes = [vp, vp, vp, i64, vp, vp]
     L.cct_trace.restype = ctypes.c_int
     L.cct_trace.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, u32, vp]
+    L.cct_scene_set_tuning.restype = ctypes.c_int
+    L.cct_scene_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    L.cct_scene_get_tuning.restype = ctypes.c_int
+    L.cct_scene_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     L.cct_trace_noalloc.restype = ctypes.c_int
     L.cct_trace_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, u32, vp]
     L.cct_get_stats.restype = ctypes.c_int
@@ -136,6 +149,24 @@ def cct_scene_info(scene: int):
     b, n = ctypes.c_size_t(), ctypes.c_int32()
     _check(lib().cct_scene_info(ctypes.c_void_p(scene), ctypes.byref(b), ctypes.byref(n)), "cct_scene_info")
     return int(b.value), int(n.value)
+
+
+def cct_scene_set_tuning(scene: int, tuning: "Tuning | dict | None") -> None:
+    if tuning is None:
+        _check(lib().cct_scene_set_tuning(ctypes.c_void_p(scene), None), "cct_scene_set_tuning")
+        return
+    if isinstance(tuning, dict):
+        tu = cct_scene_get_tuning(scene)
+        for k, v in tuning.items():
+            setattr(tu, k, int(v))
+        tuning = tu
+    _check(lib().cct_scene_set_tuning(ctypes.c_void_p(scene), ctypes.byref(tuning)), "cct_scene_set_tuning")
+
+
+def cct_scene_get_tuning(scene: int) -> Tuning:
+    tu = Tuning()
+    _check(lib().cct_scene_get_tuning(ctypes.c_void_p(scene), ctypes.byref(tu)), "cct_scene_get_tuning")
+    return tu
 
 
 def cct_locate(scene: int, ox, oy, start, stream=None) -> None:
@@ -227,6 +258,12 @@ class Scene:
         start = torch.empty(ox.numel(), dtype=torch.int32, device=ox.device)
         cct_locate(self.handle, ox, oy, start, stream)
         return start
+
+    def set_tuning(self, tuning=None):
+        cct_scene_set_tuning(self.handle, tuning)
+
+    def tuning(self) -> dict:
+        return cct_scene_get_tuning(self.handle).as_dict()
 
     def stats(self, reset: bool = False, stream=None) -> dict:
         return cct_get_stats(self.handle, reset, stream)

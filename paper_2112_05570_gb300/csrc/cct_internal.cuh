@@ -186,6 +186,8 @@ struct RaySrc {
 cudaError_t launch_walk(bool exact, bool sorted, bool start_user, const SceneDev& S, const RaySrc& R, int32_t* hit,
                         float* t, int32_t* steps, unsigned long long* counter, int dev, cudaStream_t stream);
 
+cct_tuning default_tuning();
+
 struct BinOut {
   int4* rays;      // {ox, oy, dx bits, dy bits} sorted by start cell
   int32_t* start;  // record index, sorted
@@ -200,6 +202,7 @@ cudaError_t launch_bin(const SceneDev& S, const int32_t* ox, const int32_t* oy, 
 
 struct cct_scene_s {
   cct::SceneDev dev;
+  cct_tuning tuning;
   void* d_base;
   size_t bytes;
   int device;

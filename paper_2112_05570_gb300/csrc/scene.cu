@@ -169,7 +169,7 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
     }
     // ---- seed grid (Sec. 5.2): a centroid per cell, empty cells copy the nearest
     long long D = d.domain;
-    int G = (int)std::max(1.0, std::min(2048.0, std::sqrt((double)nt / 2.0)));
+    int G = (int)std::max(1.0, std::min(2048.0, std::sqrt((double)nt)));
     std::vector<SeedCell> seeds((size_t)G * G, SeedCell{0, 0, -1, 0});
     std::vector<long long> best((size_t)G * G, -1);
     for (int T = 0; T < nt; ++T) {
@@ -248,6 +248,7 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
     s->dev.G = G;
     s->dev.D = d.domain;
     s->dev.max_steps = nt + 8;
+    s->tuning = default_tuning();
     *out = s;
     return CCT_OK;
   } catch (const std::bad_alloc&) {

@@ -249,3 +249,26 @@ def test_config2_scale_full_parity(cct, family):
     hb, tb = oracle.closest_bruteforce(segs, r.ox[idx], r.oy[idx], r.dx[idx], r.dy[idx])
     assert np.array_equal(hb, exp[0][idx]) and np.array_equal(tb, exp[1][idx])
     scene.free()
+
+
+def test_results_independent_of_tuning(cct, scenes):
+    """Block size, refill threshold, chunk and binning granularity change the
+    schedule only: results stay bit-identical to the oracle."""
+    kind, seed, tri = scenes[3]
+    r = sg.rays_isotropic(tri, 50000 + 13, 77)
+    exp = oracle.walk(tri, r.ox, r.oy, r.dx, r.dy, r.start)
+    scene = cct.Scene.from_triangulation(tri, sg.D)
+    for tu in ({"block_threads": 32, "refill_min": 1, "chunk": 32},
+               {"block_threads": 512, "refill_min": 32, "chunk": 4096},
+               {"block_threads": 128, "refill_min": 4, "chunk": 64, "bin_shift": 0},
+               {"block_threads": 96, "refill_min": 16, "chunk": 200, "bin_shift": 5,
+                "trace_flags": cct.CCT_TRACE_EXACT_ONLY}):
+        scene.set_tuning(tu)
+        assert all(scene.tuning()[k] == v for k, v in tu.items())
+        for start in (r.start, None):
+            for flags in (0, cct.CCT_TRACE_BIN):
+                _assert_parity(_trace(scene, r.ox, r.oy, r.dx, r.dy, start, flags), exp)
+    scene.set_tuning(None)
+    with pytest.raises(cct.CctError):
+        scene.set_tuning({"block_threads": 33})
+    scene.free()
