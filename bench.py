@@ -183,6 +183,49 @@ def _time_loop(torch, dev, stream, fn, k):
     return e0.elapsed_time(e1) / k
 
 
+TUNE_PARAMS = (0.25, 0.5, 1.0, 2.0, 4.0)
+
+
+def comparison_structures(torch, cct, sg, sc, dev, stream, n_timed):
+    """Sec. 5.3 baselines on the scene's own rays: a BVH and a roped kd-tree per
+    cost parameter, the parameter with the fewest measured operations kept
+    (the paper's per-scene tuning on the measured rays); then ops/ray and the
+    GPU rays/s of the kept structures."""
+    d = sc["d"]
+    n = d["ox"].numel()
+    out = {}
+    for kind in ("bvh", "kd"):
+        best = None
+        for prm in TUNE_PARAMS:
+            host = sg.bvh(sc["segs"], prm) if kind == "bvh" else sg.kdtree(sc["segs"], prm)
+            g = cct.Bvh(host) if kind == "bvh" else cct.KdTree(host, sg.D)
+            h, t, ops = g.trace(d["ox"], d["oy"], d["dx"], d["dy"], stream)
+            ops = ops.to(torch.int64)
+            if kind == "bvh":
+                cost = float(ops.sum()) / n
+                detail = {"aabb_per_ray": float(ops[:, 0].sum()) / n, "prim_per_ray": float(ops[:, 1].sum()) / n}
+            else:
+                cost = float((ops[:, 0] + ops[:, 3] + ops[:, 4]).sum()) / n
+                detail = {"leaves_per_ray": float(ops[:, 0].sum()) / n,
+                          "unique_prims_per_ray": float(ops[:, 3].sum()) / n,
+                          "rope_log2_per_ray": float(ops[:, 4].sum()) / n,
+                          "prim_tests_per_ray": float(ops[:, 2].sum()) / n,
+                          "descent_nodes_per_ray": float(ops[:, 1].sum()) / n,
+                          "mailbox_overflow_rays": int((ops[:, 5] > 0).sum())}
+            if best is None or cost < best[0]:
+                if best is not None:
+                    best[2].free()
+                best = (cost, prm, g, detail, host)
+            else:
+                g.free()
+        cost, prm, g, detail, host = best
+        ms = _time_loop(torch, dev, stream, lambda: g.trace(d["ox"], d["oy"], d["dx"], d["dy"], stream), n_timed)
+        out[kind] = {"ops_per_ray": cost, "param": prm, "rays_per_s": n / (ms * 1e-3),
+                     "nodes": int(host.n_nodes), **detail}
+        g.free()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -309,7 +352,9 @@ def main():
         cct.cct_trace(cdt_scene.handle, d["ox"], d["oy"], d["dx"], d["dy"], None, hit, t, steps, 0, stream)
         cst = cdt_scene.stats()
         cdt_scene.free()
+        cmp = comparison_structures(torch, cct, sg, sc, dev, stream, 2)
         per[sc["name"]] = {"segments": int(sc["segs"].shape[0]), "triangles": sc["tri"].n_tri,
+                           "kd": cmp["kd"], "bvh": cmp["bvh"],
                            "walk_rays_per_s": n / (wms * 1e-3), "steps_per_ray": wsteps / n,
                            "steps_per_ray_cdt": cst["steps"] / max(1, cst["rays"]),
                            "length_annealed_over_cdt": sc["tri"].length(True) / sc["cdt"].length(True),
@@ -365,6 +410,9 @@ def main():
                        "l2": "inputs larger than L2 (6 x 2^24 rays + results, 2 GB); triangle tables L2-resident",
                        "parallelism": f"replicas x{world}"},
             "steps_per_ray": tot["steps"] / max(1, tot["rays"]),
+            "kd_ops_per_ray": float(np.mean([p["kd"]["ops_per_ray"] for p in per.values()])),
+            "bvh_ops_per_ray": float(np.mean([p["bvh"]["ops_per_ray"] for p in per.values()])),
+            "walk_steps_per_ray_mean_over_scenes": float(np.mean([p["steps_per_ray"] for p in per.values()])),
             "fallback_rate": tot["exact_fallbacks"] / max(1, tot["side_tests"]),
             "locate_steps_per_ray": tot["locate_steps"] / max(1, tot["located"]),
             "per_scene": per, "roofline": roofline, "e2e": e2e,

@@ -203,6 +203,97 @@ int cct_trace_noalloc(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy,
  * zeroes them afterwards.  Errors: CCT_ERR_INVALID_ARGUMENT, CCT_ERR_CUDA. */
 int cct_get_stats(cct_scene scene, cct_stats* out, int reset, void* stream);
 
+/* ------------------------------------------------------------------ comparison structures (Sec. 5.3) */
+/* The two classical structures the paper compares against, traversed on the
+ * GPU with the same exact hit rule as the walk, so all three return the same
+ * closest hit (segment id and t).  They exist to measure operations per ray
+ * the way Sec. 5.3/5.4 counts them, on the same rays. */
+
+typedef struct cct_bvh_s* cct_bvh;
+
+/* SAH BVH over the scene segments (Sec. 5.3.1), host arrays:
+ *   box     [4*n_nodes]  closed integer box x0 y0 x1 y1 of every node
+ *   child0  [n_nodes]    >= 0: inner node, left child; < 0: leaf whose first
+ *                        primitive is prims[-child0 - 1]
+ *   child1  [n_nodes]    inner: right child; leaf: primitive count
+ *   prims   [n_prims]    segment ids
+ *   seg     [4*n_seg]    segments x0 y0 x1 y1
+ * Children must follow their parent in the arrays; depth <= 61. */
+typedef struct {
+  int32_t n_nodes;
+  int32_t n_prims;
+  int32_t n_seg;
+  const int32_t* box;
+  const int32_t* child0;
+  const int32_t* child1;
+  const int32_t* prims;
+  const int32_t* seg;
+} cct_bvh_desc;
+
+/* Validates (index ranges, child order, depth) and uploads; waits for the
+ * upload on `stream`.  Errors: CCT_ERR_INVALID_ARGUMENT, CCT_ERR_OUT_OF_MEMORY,
+ * CCT_ERR_CUDA, CCT_ERR_NO_DEVICE. */
+int cct_bvh_load(const cct_bvh_desc* desc, void* stream, cct_bvh* out);
+int cct_bvh_free(cct_bvh bvh);
+
+/* Closest hit of n rays (device arrays as cct_trace) by stack traversal from
+ * the root, nearer child first.  d_ops[2i] = AABB tests, d_ops[2i+1] = segment
+ * tests of ray i (Sec. 5.3.1's two operation kinds); -1 for an invalid ray
+ * (direction off the 2^-22 grid or zero; hit -1, t NaN). */
+int cct_trace_bvh(cct_bvh bvh, const int32_t* d_ox, const int32_t* d_oy, const float* d_dx, const float* d_dy,
+                  int64_t n, int32_t* d_hit_seg, float* d_t, int32_t* d_ops, void* stream);
+
+typedef struct cct_kdtree_s* cct_kdtree;
+
+/* Roped kd-tree over the scene segments in [0, D]^2 (Sec. 5.3.2), host arrays:
+ *   axis      [n_nodes]    0: split on x, 1: split on y, 2: leaf
+ *   split     [n_nodes]    split coordinate of an inner node
+ *   child     [n_nodes]    inner: left child (right child = left + 1, after
+ *                          the parent); leaf: first index into refs
+ *   count     [n_nodes]    leaf: number of refs
+ *   box       [4*n_nodes]  node region x0 y0 x1 y1 (closed)
+ *   rope      [4*n_nodes]  leaf ropes across faces x-min, x-max, y-min, y-max:
+ *                          the deepest node holding the whole region across
+ *                          the face, or -1 outside the domain
+ *   rope_log2 [4*n_nodes]  ceil(log2 of the leaves adjacent across each face),
+ *                          the cost of an ideal rope tree (0..255)
+ *   refs      [n_refs]     segment ids (a segment is in every leaf it touches)
+ *   seg       [4*n_seg]    segments */
+typedef struct {
+  int32_t n_nodes;
+  int32_t n_refs;
+  int32_t n_seg;
+  int32_t domain;
+  const int32_t* axis;
+  const int32_t* split;
+  const int32_t* child;
+  const int32_t* count;
+  const int32_t* box;
+  const int32_t* rope;
+  const int32_t* rope_log2;
+  const int32_t* refs;
+  const int32_t* seg;
+} cct_kdtree_desc;
+
+/* Validates (index ranges, child order) and uploads; waits on `stream`. */
+int cct_kdtree_load(const cct_kdtree_desc* desc, void* stream, cct_kdtree* out);
+int cct_kdtree_free(cct_kdtree kd);
+
+/* Closest hit of n rays by stackless rope traversal from the leaf holding the
+ * origin (known a priori, Sec. 5.4): segments of a leaf are accepted up to the
+ * leaf's exit; otherwise the rope of the exit face is followed and the leaf
+ * holding the exit point is found by descending (exit through a corner: the
+ * x face; a point on a split plane: the side the ray moves to).  Six counts
+ * per ray in d_ops[6i..6i+5]: leaves visited, inner nodes passed in rope
+ * descents, segment tests, unique segment tests (ideal mailbox), sum of the
+ * crossed faces' rope_log2 (ideal rope tree), mailbox overflow flag (1 when a
+ * ray tested more than 256 distinct segments: its unique count is then an
+ * upper bound).  The paper's ideal operation count is leaves + rope_log2 sum
+ * + unique tests.  -1 in all six for an invalid ray.  Scratch (the mailboxes)
+ * from the stream-ordered allocator on `stream`. */
+int cct_trace_kdtree(cct_kdtree kd, const int32_t* d_ox, const int32_t* d_oy, const float* d_dx, const float* d_dy,
+                     int64_t n, int32_t* d_hit_seg, float* d_t, int32_t* d_ops, void* stream);
+
 /* Static text for a status code. */
 const char* cct_error_string(int code);
 

@@ -65,6 +65,10 @@ def _load(mutant: int = 0) -> ctypes.CDLL:
     L.oracle_interior_length.argtypes = [i64, vp, vp, vp, vp]
     L.oracle_count_line_crossings.restype = ctypes.c_int
     L.oracle_count_line_crossings.argtypes = [i64, vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    L.oracle_bvh_trace.restype = ctypes.c_int
+    L.oracle_bvh_trace.argtypes = [i32, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, i32]
+    L.oracle_kd_trace.restype = ctypes.c_int
+    L.oracle_kd_trace.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, i32]
     L.oracle_mutant.restype = i32
     _libs[mutant] = L
     return L
@@ -189,3 +193,30 @@ def crofton_lines(n, seed, D):
     lo, hi = proj.min(0), proj.max(0)
     p = lo + (hi - lo) * rng.uniform(0.0, 1.0, n)
     return cx, cy, p
+
+
+def bvh_trace(b, ox, oy, dx, dy, n_threads=None):
+    """BVH traversal of Sec. 5.3.1: (hit, t, ops (n,2): AABB tests, segment tests)."""
+    L = _load()
+    box, c0, c1, pr = (_c(x, np.int32) for x in (b.box, b.child0, b.child1, b.prims))
+    segs = _c(b.segs, np.int32)
+    ox, oy, dx, dy = _c(ox, np.int32), _c(oy, np.int32), _c(dx, np.float32), _c(dy, np.float32)
+    n = ox.size
+    hit, t, ops = np.empty(n, np.int32), np.empty(n, np.float32), np.empty((n, 2), np.int32)
+    L.oracle_bvh_trace(c0.size, _p(box), _p(c0), _p(c1), _p(pr), _p(segs), n, _p(ox), _p(oy), _p(dx), _p(dy),
+                       _p(hit), _p(t), _p(ops), _nthreads(n_threads))
+    return hit, t, ops
+
+
+def kd_trace(k, ox, oy, dx, dy, n_threads=None):
+    """Roped kd-tree traversal of Sec. 5.3.2: (hit, t, ops (n,6)): leaves,
+    descent nodes, segment tests, distinct segments, log2 rope sum, 0."""
+    L = _load()
+    arrs = [_c(x, np.int32) for x in (k.axis, k.split, k.child, k.count, k.box, k.rope, k.rope_log2, k.refs,
+                                      k.segs)]
+    ox, oy, dx, dy = _c(ox, np.int32), _c(oy, np.int32), _c(dx, np.float32), _c(dy, np.float32)
+    n = ox.size
+    hit, t, ops = np.empty(n, np.int32), np.empty(n, np.float32), np.empty((n, 6), np.int32)
+    L.oracle_kd_trace(arrs[0].size, *[_p(a) for a in arrs], n, _p(ox), _p(oy), _p(dx), _p(dy), _p(hit), _p(t),
+                      _p(ops), _nthreads(n_threads))
+    return hit, t, ops

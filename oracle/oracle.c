@@ -629,4 +629,276 @@ int oracle_count_line_crossings(int64_t n_tri, const int32_t* vx, const int32_t*
   return 0;
 }
 
+/* ------------------------------------------------------------------ comparison structures (Sec. 5.3) */
+/* Parameters along the ray as exact rationals of t / 2^22: a slab parameter
+ * (X - o) / k and a segment parameter num / den, denominators positive; a
+ * zero denominator stands for +infinity. */
+typedef struct {
+  int64_t num, den;
+} q64;
+
+static int q_cmp(q64 a, q64 b) { /* sign of a - b */
+  if (a.den == 0 && b.den == 0) return 0;
+  if (a.den == 0) return 1;
+  if (b.den == 0) return -1;
+  i128 l = (i128)a.num * b.den, r = (i128)b.num * a.den;
+  return (l > r) - (l < r);
+}
+
+typedef struct {
+  int32_t seg;
+  ratio t;
+  int64_t wx, wy; /* right-hand endpoint of the best segment */
+} best_hit;
+
+/* The segment test of the brute force, keeping the closest hit; `limit`
+ * (den > 0) bounds the accepted parameter (inclusive). */
+static void consider(best_hit* b, const int32_t* q, int32_t sid, int64_t ox, int64_t oy, int64_t kx, int64_t ky,
+                     const q64* limit) {
+  int64_t ax = q[0], ay = q[1], bx = q[2], by = q[3];
+  int sa = side(kx, ky, ox, oy, ax, ay), sb = side(kx, ky, ox, oy, bx, by);
+  if (sa == sb) return;
+  ratio r = seg_param(kx, ky, ox, oy, ax, ay, bx, by);
+  if (r.num <= 0) return;
+  if (limit) {
+    q64 rq = {r.num, r.den};
+    if (q_cmp(rq, *limit) > 0) return;
+  }
+  int64_t wx = sa == ORC_SIDE_R ? ax : bx, wy = sa == ORC_SIDE_R ? ay : by;
+  int64_t vx = sa == ORC_SIDE_R ? bx : ax, vy = sa == ORC_SIDE_R ? by : ay;
+  int take = b->seg < 0;
+  if (!take) {
+    int c = ratio_cmp(r, b->t);
+    take = c < 0 || (c == 0 && tie_cmp(kx, ky, wx - vx, wy - vy, b->wx - vx, b->wy - vy) < 0);
+  }
+  if (take) {
+    b->seg = sid;
+    b->t = r;
+    b->wx = wx;
+    b->wy = wy;
+  }
+}
+
+/* Entry parameter of the ray into a closed box; 0 if it misses the box. */
+static int slab(const int32_t* B, int64_t ox, int64_t oy, int64_t kx, int64_t ky, q64* tn) {
+  q64 nr = {0, 1}, fr = {0, 0};
+  int64_t lo[2] = {B[0], B[1]}, hi[2] = {B[2], B[3]}, o[2] = {ox, oy}, k[2] = {kx, ky};
+  for (int a = 0; a < 2; ++a) {
+    if (k[a] == 0) {
+      if (o[a] < lo[a] || o[a] > hi[a]) return 0;
+      continue;
+    }
+    q64 near = k[a] > 0 ? (q64){lo[a] - o[a], k[a]} : (q64){o[a] - hi[a], -k[a]};
+    q64 far = k[a] > 0 ? (q64){hi[a] - o[a], k[a]} : (q64){o[a] - lo[a], -k[a]};
+    if (q_cmp(near, nr) > 0) nr = near;
+    if (q_cmp(far, fr) < 0) fr = far;
+  }
+  if (q_cmp(fr, nr) < 0) return 0;
+  *tn = nr;
+  return 1;
+}
+
+typedef struct {
+  int32_t n_nodes;
+  const int32_t *box, *c0, *c1, *prims, *seg;
+  const int32_t *ox, *oy;
+  const float *dx, *dy;
+  int32_t *hit, *ops;
+  float* t;
+} bvh_ctx;
+
+static void bvh_range(void* p, int64_t lo, int64_t hi) {
+  bvh_ctx* c = (bvh_ctx*)p;
+  for (int64_t i = lo; i < hi; ++i) {
+    int64_t kx, ky, ox = c->ox[i], oy = c->oy[i];
+    if (!dir_to_int(c->dx[i], &kx) || !dir_to_int(c->dy[i], &ky) || (kx == 0 && ky == 0)) {
+      c->hit[i] = -1;
+      c->t[i] = NAN;
+      c->ops[2 * i] = c->ops[2 * i + 1] = -1;
+      continue;
+    }
+    best_hit b = {-1, {0, 1}, 0, 0};
+    int32_t n_aabb = 1, n_prim = 0;
+    int32_t stack[128];
+    q64 st_t[128];
+    int sp = 0;
+    q64 tn;
+    if (slab(c->box, ox, oy, kx, ky, &tn)) {
+      stack[sp] = 0;
+      st_t[sp++] = tn;
+    }
+    while (sp > 0) {
+      --sp;
+      int32_t N = stack[sp];
+      q64 bt = {b.t.num, b.t.den};
+      if (b.seg >= 0 && q_cmp(st_t[sp], bt) > 0) continue; /* entered beyond the best hit */
+      int32_t c0 = c->c0[N], c1 = c->c1[N];
+      if (c0 < 0) { /* leaf: test every segment */
+        for (int32_t k = 0; k < c1; ++k) {
+          int32_t sid = c->prims[-1 - c0 + k];
+          ++n_prim;
+          consider(&b, c->seg + 4 * (int64_t)sid, sid, ox, oy, kx, ky, NULL);
+        }
+        continue;
+      }
+      q64 t0, t1;
+      n_aabb += 2;
+      int h0 = slab(c->box + 4 * (int64_t)c0, ox, oy, kx, ky, &t0);
+      int h1 = slab(c->box + 4 * (int64_t)c1, ox, oy, kx, ky, &t1);
+      bt = (q64){b.t.num, b.t.den};
+      if (h0 && b.seg >= 0 && q_cmp(t0, bt) > 0) h0 = 0;
+      if (h1 && b.seg >= 0 && q_cmp(t1, bt) > 0) h1 = 0;
+      if (h0 && h1) { /* the nearer child is visited first; the left one on equal entry */
+        int left_first = q_cmp(t0, t1) <= 0;
+        stack[sp] = left_first ? c1 : c0;
+        st_t[sp++] = left_first ? t1 : t0;
+        stack[sp] = left_first ? c0 : c1;
+        st_t[sp++] = left_first ? t0 : t1;
+      } else if (h0) {
+        stack[sp] = c0;
+        st_t[sp++] = t0;
+      } else if (h1) {
+        stack[sp] = c1;
+        st_t[sp++] = t1;
+      }
+    }
+    c->hit[i] = b.seg;
+    c->t[i] = b.seg >= 0 ? ratio_to_t(b.t) : INFINITY;
+    c->ops[2 * i] = n_aabb;
+    c->ops[2 * i + 1] = n_prim;
+  }
+}
+
+/* BVH traversal (Sec. 5.3.1): from the root, nearer child first, boxes
+ * entered beyond the best hit skipped.  ops: AABB tests, segment tests. */
+int oracle_bvh_trace(int32_t n_nodes, const int32_t* box, const int32_t* c0, const int32_t* c1, const int32_t* prims,
+                     const int32_t* seg, int64_t n, const int32_t* ox, const int32_t* oy, const float* dx,
+                     const float* dy, int32_t* hit, float* t, int32_t* ops, int32_t n_threads) {
+  bvh_ctx c = {n_nodes, box, c0, c1, prims, seg, ox, oy, dx, dy, hit, ops, t};
+  run_parallel(bvh_range, &c, n, n_threads);
+  return 0;
+}
+
+typedef struct {
+  int32_t n_nodes;
+  const int32_t *axis, *split, *child, *count, *box, *rope, *rope_log2, *refs, *seg;
+  const int32_t *ox, *oy;
+  const float *dx, *dy;
+  int32_t *hit, *ops;
+  float* t;
+} kd_ctx;
+
+static int i32_cmp(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+/* Which child of a split at s on axis a holds a point at coordinate s: the side
+ * the ray moves to, or (moving parallel to the plane) the side it is shifted
+ * to -- its right, normal (ky, -kx).  1 = the child with coordinates >= s. */
+static int plane_side(int a, int64_t kx, int64_t ky) {
+  int64_t ka = a == 0 ? kx : ky;
+  if (ka != 0) return ka > 0;
+  return (a == 0 ? ky : -kx) > 0;
+}
+
+static void kd_range(void* p, int64_t lo, int64_t hi) {
+  kd_ctx* c = (kd_ctx*)p;
+  int32_t cap = 1024, *tested = (int32_t*)malloc(sizeof(int32_t) * cap);
+  for (int64_t i = lo; i < hi; ++i) {
+    int32_t* o = c->ops + 6 * i;
+    int64_t kx, ky, ox = c->ox[i], oy = c->oy[i];
+    const int32_t* rb = c->box;
+    if (!dir_to_int(c->dx[i], &kx) || !dir_to_int(c->dy[i], &ky) || (kx == 0 && ky == 0) || ox < rb[0] ||
+        ox > rb[2] || oy < rb[1] || oy > rb[3]) {
+      c->hit[i] = -1;
+      c->t[i] = NAN;
+      for (int q = 0; q < 6; ++q) o[q] = -1;
+      continue;
+    }
+    /* start leaf: descend with the origin (known a priori, not counted) */
+    int32_t L = 0;
+    while (c->axis[L] != 2) {
+      int a = c->axis[L];
+      int64_t v = (a == 0 ? ox : oy) - c->split[L];
+      L = c->child[L] + ((v > 0 || (v == 0 && plane_side(a, kx, ky))) ? 1 : 0);
+    }
+    best_hit b = {-1, {0, 1}, 0, 0};
+    int32_t leaves = 0, desc = 0, tests = 0, ropes = 0, n_tested = 0;
+    for (;;) {
+      ++leaves;
+      if (leaves > c->n_nodes + 8) {
+        b.seg = -1;
+        break;
+      }
+      const int32_t* B = c->box + 4 * (int64_t)L;
+      /* exit face and parameter */
+      q64 tx = kx > 0 ? (q64){B[2] - ox, kx} : (kx < 0 ? (q64){ox - B[0], -kx} : (q64){0, 0});
+      q64 ty = ky > 0 ? (q64){B[3] - oy, ky} : (ky < 0 ? (q64){oy - B[1], -ky} : (q64){0, 0});
+      int xface = q_cmp(ty, tx) >= 0; /* a corner exit takes the x face */
+      q64 te = xface ? tx : ty;
+      int face = xface ? (kx > 0 ? 1 : 0) : (ky > 0 ? 3 : 2);
+      int32_t first = c->child[L], cnt = c->count[L];
+      for (int32_t q = 0; q < cnt; ++q) {
+        int32_t sid = c->refs[first + q];
+        ++tests;
+        if (n_tested == cap) {
+          cap *= 2;
+          tested = (int32_t*)realloc(tested, sizeof(int32_t) * cap);
+        }
+        tested[n_tested++] = sid;
+        consider(&b, c->seg + 4 * (int64_t)sid, sid, ox, oy, kx, ky, &te);
+      }
+      if (b.seg >= 0) break;
+      int32_t nxt = c->rope[4 * (int64_t)L + face];
+      if (nxt < 0) break;
+      ropes += c->rope_log2[4 * (int64_t)L + face];
+      int fa = face / 2;
+      int64_t plane = face == 0 ? B[0] : (face == 1 ? B[2] : (face == 2 ? B[1] : B[3]));
+      int32_t N = nxt;
+      while (c->axis[N] != 2) {
+        int a = c->axis[N];
+        int64_t s = c->split[N];
+        int right;
+        if (a == fa) {
+          right = plane > s || (plane == s && plane_side(a, kx, ky));
+        } else { /* exit point coordinate o_a + te * k_a compared with s */
+          int64_t v = ((a == 0 ? ox : oy) - s) * te.den + te.num * (a == 0 ? kx : ky);
+          right = v > 0 || (v == 0 && plane_side(a, kx, ky));
+        }
+        N = c->child[N] + right;
+        ++desc;
+      }
+      L = N;
+    }
+    /* ideal mailbox: distinct segments tested */
+    qsort(tested, (size_t)n_tested, sizeof(int32_t), i32_cmp);
+    int32_t uniq = 0;
+    for (int32_t q = 0; q < n_tested; ++q)
+      if (q == 0 || tested[q] != tested[q - 1]) ++uniq;
+    c->hit[i] = b.seg;
+    c->t[i] = b.seg >= 0 ? ratio_to_t(b.t) : INFINITY;
+    o[0] = leaves;
+    o[1] = desc;
+    o[2] = tests;
+    o[3] = uniq;
+    o[4] = ropes;
+    o[5] = 0;
+    n_tested = 0;
+  }
+  free(tested);
+}
+
+/* Roped kd-tree traversal (Sec. 5.3.2) from the leaf holding the origin.
+ * ops per ray: leaves visited, nodes passed in rope descents, segment tests,
+ * distinct segments tested, sum of log2 rope counts, 0. */
+int oracle_kd_trace(int32_t n_nodes, const int32_t* axis, const int32_t* split, const int32_t* child,
+                    const int32_t* count, const int32_t* box, const int32_t* rope, const int32_t* rope_log2,
+                    const int32_t* refs, const int32_t* seg, int64_t n, const int32_t* ox, const int32_t* oy,
+                    const float* dx, const float* dy, int32_t* hit, float* t, int32_t* ops, int32_t n_threads) {
+  kd_ctx c = {n_nodes, axis, split, child, count, box, rope, rope_log2, refs, seg, ox, oy, dx, dy, hit, ops, t};
+  run_parallel(kd_range, &c, n, n_threads);
+  return 0;
+}
+
 int32_t oracle_mutant(void) { return ORACLE_MUTANT; }

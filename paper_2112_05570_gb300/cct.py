@@ -49,6 +49,19 @@ class Tuning(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class _BvhDesc(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("n_prims", ctypes.c_int32), ("n_seg", ctypes.c_int32),
+                ("box", ctypes.c_void_p), ("child0", ctypes.c_void_p), ("child1", ctypes.c_void_p),
+                ("prims", ctypes.c_void_p), ("seg", ctypes.c_void_p)]
+
+
+class _KdDesc(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("n_refs", ctypes.c_int32), ("n_seg", ctypes.c_int32),
+                ("domain", ctypes.c_int32)] + [(k, ctypes.c_void_p) for k in
+                                                ("axis", "split", "child", "count", "box", "rope", "rope_log2",
+                                                 "refs", "seg")]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in ("rays", "steps", "side_tests", "exact_fallbacks", "invalid_rays",
                                                "walk_limit_rays", "located", "locate_steps")]
@@ -81,6 +94,18 @@ def lib() -> ctypes.CDLL:
     L.cct_scene_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     L.cct_scene_get_tuning.restype = ctypes.c_int
     L.cct_scene_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    L.cct_bvh_load.restype = ctypes.c_int
+    L.cct_bvh_load.argtypes = [ctypes.POINTER(_BvhDesc), vp, ctypes.POINTER(vp)]
+    L.cct_bvh_free.restype = ctypes.c_int
+    L.cct_bvh_free.argtypes = [vp]
+    L.cct_trace_bvh.restype = ctypes.c_int
+    L.cct_trace_bvh.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    L.cct_kdtree_load.restype = ctypes.c_int
+    L.cct_kdtree_load.argtypes = [ctypes.POINTER(_KdDesc), vp, ctypes.POINTER(vp)]
+    L.cct_kdtree_free.restype = ctypes.c_int
+    L.cct_kdtree_free.argtypes = [vp]
+    L.cct_trace_kdtree.restype = ctypes.c_int
+    L.cct_trace_kdtree.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp, vp]
     L.cct_trace_noalloc.restype = ctypes.c_int
     L.cct_trace_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, u32, vp]
     L.cct_get_stats.restype = ctypes.c_int
@@ -274,6 +299,111 @@ class Scene:
     def free(self):
         if self.handle:
             cct_scene_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- comparison structures (Sec. 5.3)
+def _i32(a):
+    return np.ascontiguousarray(a, np.int32).ravel()
+
+
+def cct_bvh_load(box, child0, child1, prims, segs, stream=None) -> int:
+    arrs = [_i32(a) for a in (box, child0, child1, prims, segs)]
+    d = _BvhDesc(arrs[1].size, arrs[3].size, arrs[4].size // 4, *[ctypes.c_void_p(a.ctypes.data) for a in arrs])
+    h = ctypes.c_void_p()
+    _check(lib().cct_bvh_load(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)), "cct_bvh_load")
+    return h.value
+
+
+def cct_bvh_free(h: int) -> None:
+    _check(lib().cct_bvh_free(ctypes.c_void_p(h)), "cct_bvh_free")
+
+
+def cct_trace_bvh(h: int, ox, oy, dx, dy, hit, t, ops, stream=None) -> None:
+    import torch
+
+    _check(lib().cct_trace_bvh(ctypes.c_void_p(h), _dev(ox, torch.int32, "ox"), _dev(oy, torch.int32, "oy"),
+                               _dev(dx, torch.float32, "dx"), _dev(dy, torch.float32, "dy"), ox.numel(),
+                               _dev(hit, torch.int32, "hit"), _dev(t, torch.float32, "t"),
+                               _dev(ops, torch.int32, "ops"), _stream_ptr(stream)), "cct_trace_bvh")
+
+
+def cct_kdtree_load(axis, split, child, count, box, rope, rope_log2, refs, segs, domain: int, stream=None) -> int:
+    arrs = [_i32(a) for a in (axis, split, child, count, box, rope, rope_log2, refs, segs)]
+    d = _KdDesc(arrs[0].size, arrs[7].size, arrs[8].size // 4, int(domain),
+                *[ctypes.c_void_p(a.ctypes.data) for a in arrs])
+    h = ctypes.c_void_p()
+    _check(lib().cct_kdtree_load(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)), "cct_kdtree_load")
+    return h.value
+
+
+def cct_kdtree_free(h: int) -> None:
+    _check(lib().cct_kdtree_free(ctypes.c_void_p(h)), "cct_kdtree_free")
+
+
+def cct_trace_kdtree(h: int, ox, oy, dx, dy, hit, t, ops, stream=None) -> None:
+    import torch
+
+    _check(lib().cct_trace_kdtree(ctypes.c_void_p(h), _dev(ox, torch.int32, "ox"), _dev(oy, torch.int32, "oy"),
+                                  _dev(dx, torch.float32, "dx"), _dev(dy, torch.float32, "dy"), ox.numel(),
+                                  _dev(hit, torch.int32, "hit"), _dev(t, torch.float32, "t"),
+                                  _dev(ops, torch.int32, "ops"), _stream_ptr(stream)), "cct_trace_kdtree")
+
+
+class Bvh:
+    """A device-resident BVH (owns its handle); built by scenegen.bvh."""
+
+    def __init__(self, b, stream=None):
+        self.handle = cct_bvh_load(b.box, b.child0, b.child1, b.prims, b.segs, stream)
+
+    def trace(self, ox, oy, dx, dy, stream=None):
+        import torch
+
+        n = ox.numel()
+        hit = torch.empty(n, dtype=torch.int32, device=ox.device)
+        t = torch.empty(n, dtype=torch.float32, device=ox.device)
+        ops = torch.empty((n, 2), dtype=torch.int32, device=ox.device)
+        cct_trace_bvh(self.handle, ox, oy, dx, dy, hit, t, ops, stream)
+        return hit, t, ops
+
+    def free(self):
+        if self.handle:
+            cct_bvh_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class KdTree:
+    """A device-resident roped kd-tree (owns its handle); built by scenegen.kdtree."""
+
+    def __init__(self, k, domain: int, stream=None):
+        self.handle = cct_kdtree_load(k.axis, k.split, k.child, k.count, k.box, k.rope, k.rope_log2, k.refs,
+                                      k.segs, domain, stream)
+
+    def trace(self, ox, oy, dx, dy, stream=None):
+        import torch
+
+        n = ox.numel()
+        hit = torch.empty(n, dtype=torch.int32, device=ox.device)
+        t = torch.empty(n, dtype=torch.float32, device=ox.device)
+        ops = torch.empty((n, 6), dtype=torch.int32, device=ox.device)
+        cct_trace_kdtree(self.handle, ox, oy, dx, dy, hit, t, ops, stream)
+        return hit, t, ops
+
+    def free(self):
+        if self.handle:
+            cct_kdtree_free(self.handle)
             self.handle = 0
 
     def __del__(self):

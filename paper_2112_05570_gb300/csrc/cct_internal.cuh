@@ -126,6 +126,55 @@ __device__ __forceinline__ float hit_param(int ax, int ay, int bx, int by, int o
   return __fmul_rn(__fdiv_rn(__ll2float_rn(num), __ll2float_rn(den)), kDirScale);
 }
 
+// One step of the Sec. 5.2 locate walk from the seed point p (kept as 3p)
+// towards the origin o, in record r = triangle T entered through its edge j
+// (j = 3: T is the seed's own triangle).  Returns 1 when T holds o strictly
+// inside, -1 when o lies on an edge or a vertex (or the walk leaves the
+// domain), 0 after moving to the next triangle (T, j updated).  The walk
+// crosses constrained edges (neighbours from cnb): it locates a point, it does
+// not trace a ray.
+__device__ __forceinline__ int locate_step(const SceneDev& S, const TriRec& r, int& T, int& j, int ox, int oy,
+                                           int px3, int py3) {
+  const int qx = 3 * ox - px3, qy = 3 * oy - py3;  // direction p -> o, in thirds
+  int e;
+  if (j == 3) {
+    const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
+    const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
+    const long long o0 = orient_ll(x1, y1, x2, y2, ox, oy);
+    const long long o1 = orient_ll(x2, y2, x0, y0, ox, oy);
+    const long long o2 = orient_ll(x0, y0, x1, y1, ox, oy);
+    if (o0 > 0 && o1 > 0 && o2 > 0) return 1;
+    if (o0 >= 0 && o1 >= 0 && o2 >= 0) return -1;
+    const bool s0 = (long long)qx * (3 * y0 - py3) - (long long)qy * (3 * x0 - px3) >= 0;
+    const bool s1 = (long long)qx * (3 * y1 - py3) - (long long)qy * (3 * x1 - px3) >= 0;
+    const bool s2 = (long long)qx * (3 * y2 - py3) - (long long)qy * (3 * x2 - px3) >= 0;
+    e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
+  } else {
+    // the entry edge's two sides are known: decide the apex, then test o
+    // against the exit edge only (o beyond the entry edge by induction)
+    const int cx = vx_of(r, j), cy = vy_of(r, j);
+    const bool sc = (long long)qx * (3 * cy - py3) - (long long)qy * (3 * cx - px3) >= 0;
+    e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
+    const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
+    const long long oe = orient_ll(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), ox, oy);
+    if (oe == 0) return -1;
+    if (oe > 0) {
+      // o lies before the exit edge: inside T unless on one of its other edges
+      const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
+      const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
+      const bool in = orient_ll(x1, y1, x2, y2, ox, oy) > 0 && orient_ll(x2, y2, x0, y0, ox, oy) > 0 &&
+                      orient_ll(x0, y0, x1, y1, ox, oy) > 0;
+      return in ? 1 : -1;
+    }
+  }
+  int32_t w = nb_of(r, e);
+  if (w <= -2) w = S.cnb[3 * T + e];
+  if (w < 0) return -1;
+  T = w >> 2;
+  j = w & 3;
+  return 0;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

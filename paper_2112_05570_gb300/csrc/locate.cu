@@ -2,10 +2,10 @@
 //
 // The paper's option without an extra data structure: from a point p whose
 // triangle is known, follow the traversal towards the origin o until the
-// current triangle holds o.  Seeds sit on a regular grid (one per cell, found
-// at load time): p is a triangle centroid, kept as 3p so all arithmetic stays
-// exact in int64.  The locate walk crosses constrained edges (it is a point
-// location, not a ray query), reading their neighbours from `cnb`.
+// current triangle holds o.  Seeds sit on a regular grid: one per cell, its
+// centre, located exactly at load time (kept as 3p, as the kernel's exact
+// int64 arithmetic expects).  The locate walk crosses constrained edges (it
+// is a point location, not a ray query), reading their neighbours from `cnb`.
 #include <algorithm>
 
 #include "cct_internal.cuh"
@@ -27,9 +27,7 @@ __global__ void __launch_bounds__(kLocateThreads) locate_kernel(SceneDev S, cons
       const int ix = (int)min((long long)G - 1, (long long)qx * G / S.D);
       const int iy = (int)min((long long)G - 1, (long long)qy * G / S.D);
       const SeedCell sd = S.seeds[(long long)iy * G + ix];
-      const long long px3 = sd.px3, py3 = sd.py3;
-      const long long kx = 3ll * qx - px3, ky = 3ll * qy - py3;  // direction p -> o, in thirds
-      int T = sd.tri;
+      int T = sd.tri, j = 3;
       int steps = 0;
       while (true) {
         if (++steps > S.max_steps) {
@@ -37,31 +35,11 @@ __global__ void __launch_bounds__(kLocateThreads) locate_kernel(SceneDev S, cons
           break;
         }
         const TriRec r = load_rec(S.rec + T);
-        const long long x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
-        const long long x2 = vx_of(r, 2), y2 = vy_of(r, 2);
-        const long long o0 = orient_ll(x1, y1, x2, y2, qx, qy);
-        const long long o1 = orient_ll(x2, y2, x0, y0, qx, qy);
-        const long long o2 = orient_ll(x0, y0, x1, y1, qx, qy);
-        if (o0 > 0 && o1 > 0 && o2 > 0) {
-          res = T;
+        const int st = locate_step(S, r, T, j, qx, qy, sd.px3, sd.py3);
+        if (st != 0) {
+          res = st > 0 ? T : -1;
           break;
         }
-        if (o0 >= 0 && o1 >= 0 && o2 >= 0) {  // on an edge or a vertex of T
-          res = -1;
-          break;
-        }
-        // leave along p -> o through the CCW edge (a -> b) with s(a) = R, s(b) = L
-        const bool s0 = kx * (3 * y0 - py3) - ky * (3 * x0 - px3) >= 0;
-        const bool s1 = kx * (3 * y1 - py3) - ky * (3 * x1 - px3) >= 0;
-        const bool s2 = kx * (3 * y2 - py3) - ky * (3 * x2 - px3) >= 0;
-        const int e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
-        int32_t w = nb_of(r, e);
-        if (w <= -2) w = S.cnb[3ll * T + e];
-        if (w < 0) {
-          res = -1;
-          break;
-        }
-        T = w >> 2;
       }
       ++c_loc;
       c_steps += (unsigned)steps;

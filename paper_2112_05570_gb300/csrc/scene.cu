@@ -13,7 +13,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <deque>
 #include <new>
 #include <vector>
 
@@ -95,6 +94,54 @@ static int validate(const cct_tri_desc& d) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Exact host point location over the packed records (used once, for seeds).
+struct HostLocator {
+  const std::vector<TriRec>& rec;
+  const std::vector<int32_t>& cnb;
+  HostLocator(const std::vector<TriRec>& r, const std::vector<int32_t>& c) : rec(r), cnb(c) {}
+  static long long vx(const TriRec& r, int i) { return (long long)((r.X >> (kCoordBits * i)) & kCoordMask); }
+  static long long vy(const TriRec& r, int i) { return (long long)((r.Y >> (kCoordBits * i)) & kCoordMask); }
+  // 1 strictly inside, 0 on the boundary, -1 outside
+  int contains(int T, long long x, long long y) const {
+    const TriRec& r = rec[T];
+    int zero = 0;
+    for (int i = 0; i < 3; ++i) {
+      const int a = (i + 1) % 3, b = (i + 2) % 3;
+      long long o = orient_h(vx(r, a), vy(r, a), vx(r, b), vy(r, b), x, y);
+      if (o < 0) return -1;
+      if (o == 0) zero = 1;
+    }
+    return zero ? 0 : 1;
+  }
+  int scan(long long x, long long y) const {
+    for (int T = 0; T < (int)rec.size(); ++T) {
+      int c = contains(T, x, y);
+      if (c == 1) return T;
+      if (c == 0) return -1;
+    }
+    return -1;
+  }
+  // From (px, py) strictly inside T along the segment to (qx, qy); the triangle
+  // holding q strictly, or -1 if q lies on an edge or a vertex.
+  int walk(int T, long long px, long long py, long long qx, long long qy) const {
+    const long long kx = qx - px, ky = qy - py;
+    for (size_t guard = 0; guard <= rec.size() + 8; ++guard) {
+      const int c = contains(T, qx, qy);
+      if (c == 1) return T;
+      if (c == 0) return -1;
+      const TriRec& r = rec[T];
+      bool s[3];
+      for (int i = 0; i < 3; ++i) s[i] = kx * (vy(r, i) - py) - ky * (vx(r, i) - px) >= 0;
+      const int e = (!s[1] && s[2]) ? 0 : ((!s[2] && s[0]) ? 1 : 2);
+      int32_t w = r.nb[e];
+      if (w <= -2) w = cnb[3 * (size_t)T + e];
+      if (w < 0) return -1;
+      T = w >> 2;
+    }
+    return -1;
+  }
+};
+
 }  // namespace cct
 
 using namespace cct;
@@ -167,44 +214,48 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
       }
       rec[T] = r;
     }
-    // ---- seed grid (Sec. 5.2): a centroid per cell, empty cells copy the nearest
+    // ---- seed grid (Sec. 5.2): per cell, the cell centre (nudged off edges)
+    // and the triangle whose interior holds it, found by exact walks
     long long D = d.domain;
-    int G = (int)std::max(1.0, std::min(2048.0, std::sqrt((double)nt)));
+    int G = (int)std::max(1.0, std::min(4096.0, std::sqrt((double)nt) * 1.5));
     std::vector<SeedCell> seeds((size_t)G * G, SeedCell{0, 0, -1, 0});
-    std::vector<long long> best((size_t)G * G, -1);
-    for (int T = 0; T < nt; ++T) {
-      const int u = dev2user[T];
-      const int32_t* tv = d.tri_v + 3 * u;
-      long long px3 = (long long)d.vx[tv[0]] + d.vx[tv[1]] + d.vx[tv[2]];
-      long long py3 = (long long)d.vy[tv[0]] + d.vy[tv[1]] + d.vy[tv[2]];
-      int ix = (int)std::min<long long>(G - 1, px3 * G / (3 * D));
-      int iy = (int)std::min<long long>(G - 1, py3 * G / (3 * D));
-      // distance (x9) of the centroid to the cell centre, in thirds
-      long long ccx = (3 * D * (2 * ix + 1)) / (2 * G), ccy = (3 * D * (2 * iy + 1)) / (2 * G);
-      long long dist = (px3 - ccx) * (px3 - ccx) + (py3 - ccy) * (py3 - ccy);
-      size_t c = (size_t)iy * G + ix;
-      if (best[c] < 0 || dist < best[c]) {
-        best[c] = dist;
-        seeds[c] = SeedCell{(int32_t)px3, (int32_t)py3, T, 0};
-      }
-    }
     {
-      std::deque<int> q;
-      for (int c = 0; c < G * G; ++c)
-        if (seeds[c].tri >= 0) q.push_back(c);
-      while (!q.empty()) {
-        int c = q.front();
-        q.pop_front();
-        int ix = c % G, iy = c / G;
-        const int nbx[4] = {ix - 1, ix + 1, ix, ix}, nby[4] = {iy, iy, iy - 1, iy + 1};
-        for (int k = 0; k < 4; ++k) {
-          if (nbx[k] < 0 || nby[k] < 0 || nbx[k] >= G || nby[k] >= G) continue;
-          int c2 = nby[k] * G + nbx[k];
-          if (seeds[c2].tri >= 0) continue;
-          seeds[c2] = seeds[c];
-          q.push_back(c2);
+      HostLocator loc(rec, cnb);
+      int prev_tri = -1;
+      long long prev_x = 0, prev_y = 0;
+      for (int iy = 0; iy < G; ++iy)
+        for (int jx = 0; jx < G; ++jx) {
+          const int ix = (iy & 1) ? G - 1 - jx : jx;  // boustrophedon: short walks
+          const long long cx0 = (D * (2ll * ix + 1)) / (2ll * G), cy0 = (D * (2ll * iy + 1)) / (2ll * G);
+          int tri = -1;
+          long long cx = cx0, cy = cy0;
+          for (int k = 0; k < 16 && tri < 0; ++k) {
+            cx = std::min(D - 1, std::max(1ll, cx0 + (k % 4))), cy = std::min(D - 1, std::max(1ll, cy0 + (k / 4)));
+            tri = prev_tri < 0 ? loc.scan(cx, cy) : loc.walk(prev_tri, prev_x, prev_y, cx, cy);
+          }
+          if (tri < 0) {
+            // only on a triangulation loaded without validation: fall back to
+            // the previous cell's seed, or to the centroid of record 0 (which
+            // lies inside its own triangle); locate walks then end at their
+            // step limit or report the origin invalid, never out of bounds
+            if (prev_tri >= 0) {
+              seeds[(size_t)iy * G + ix] = SeedCell{(int32_t)(3 * prev_x), (int32_t)(3 * prev_y), prev_tri, 0};
+            } else {
+              const TriRec& r0 = rec[0];
+              long long sx = 0, sy = 0;
+              for (int q = 0; q < 3; ++q) {
+                sx += (long long)((r0.X >> (kCoordBits * q)) & kCoordMask);
+                sy += (long long)((r0.Y >> (kCoordBits * q)) & kCoordMask);
+              }
+              seeds[(size_t)iy * G + ix] = SeedCell{(int32_t)sx, (int32_t)sy, 0, 0};
+            }
+            continue;
+          }
+          seeds[(size_t)iy * G + ix] = SeedCell{(int32_t)(3 * cx), (int32_t)(3 * cy), tri, 0};
+          prev_tri = tri;
+          prev_x = cx;
+          prev_y = cy;
         }
-      }
     }
     // ---- device allocation and upload
     size_t o_rec = 0;

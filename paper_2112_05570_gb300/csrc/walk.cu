@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
             px3 = sd.px3;
             py3 = sd.py3;
             s = sd.tri;
+            j = 3;
             mode = kModeLocate;
             lsteps = 0;
             ++c_loc;
@@ -144,33 +145,15 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
         // Sec. 5.2: walk from the seed point towards the origin until the
         // current triangle holds it (this triangle is then the start triangle)
         ++lsteps;
-        const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
-        const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
-        const long long o0 = orient_ll(x1, y1, x2, y2, ox, oy);
-        const long long o1 = orient_ll(x2, y2, x0, y0, ox, oy);
-        const long long o2 = orient_ll(x0, y0, x1, y1, ox, oy);
-        if (o0 > 0 && o1 > 0 && o2 > 0) {
+        const int res = locate_step(S, r, T, j, ox, oy, px3, py3);
+        if (res > 0) {
           mode = kModeFirst;
           c_lsteps += (unsigned)lsteps;
-        } else if ((o0 >= 0 && o1 >= 0 && o2 >= 0) || lsteps > S.max_steps) {
+        } else if (res < 0 || lsteps > S.max_steps) {
           done = true;  // origin on an edge or a vertex: not a valid ray origin
           ++c_inv;
           c_lsteps += (unsigned)lsteps;
         } else {
-          const int qx = 3 * ox - px3, qy = 3 * oy - py3;
-          const bool s0 = (long long)qx * (3 * y0 - py3) - (long long)qy * (3 * x0 - px3) >= 0;
-          const bool s1 = (long long)qx * (3 * y1 - py3) - (long long)qy * (3 * x1 - px3) >= 0;
-          const bool s2 = (long long)qx * (3 * y2 - py3) - (long long)qy * (3 * x2 - px3) >= 0;
-          const int e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
-          int32_t w = nb_of(r, e);
-          if (w <= -2) w = S.cnb[3 * T + e];
-          if (w < 0) {
-            done = true;
-            ++c_inv;
-            c_lsteps += (unsigned)lsteps;
-          } else {
-            T = w >> 2;
-          }
           advance = false;
         }
       }

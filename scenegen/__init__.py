@@ -78,6 +78,22 @@ def _load():
     L.sg_rays_isotropic.argtypes = [vp, i64, u64, vp, vp, vp, vp, vp, i32]
     L.sg_rays_pinhole.restype = i64
     L.sg_rays_pinhole.argtypes = [vp, i64, i64, dbl, u64, vp, vp, vp, vp, vp, i32]
+    L.sg_bvh_build.restype = vp
+    L.sg_bvh_build.argtypes = [i64, vp, ctypes.c_float]
+    L.sg_bvh_sizes.restype = None
+    L.sg_bvh_sizes.argtypes = [vp, P(i64), P(i64)]
+    L.sg_bvh_export.restype = None
+    L.sg_bvh_export.argtypes = [vp, vp, vp, vp, vp]
+    L.sg_bvh_free.restype = None
+    L.sg_bvh_free.argtypes = [vp]
+    L.sg_kd_build.restype = vp
+    L.sg_kd_build.argtypes = [i64, vp, i32, ctypes.c_float, i32]
+    L.sg_kd_sizes.restype = None
+    L.sg_kd_sizes.argtypes = [vp, P(i64), P(i64)]
+    L.sg_kd_export.restype = None
+    L.sg_kd_export.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.sg_kd_free.restype = None
+    L.sg_kd_free.argtypes = [vp]
     _lib = L
     return L
 
@@ -265,3 +281,82 @@ def rays_pinhole(tri: Triangulation, n_eyes: int, rays_per_eye: int, seed: int, 
     L.sg_rays_pinhole(tri._h, n_eyes, rays_per_eye, fov_deg, seed, _ptr(r.ox), _ptr(r.oy), _ptr(r.dx),
                       _ptr(r.dy), _ptr(r.start), threads or _threads())
     return r
+
+
+# ----------------------------------------------------------------------------- baselines (Sec. 5.3)
+@dataclass
+class Bvh:
+    """SAH BVH over segments: box (N,4) closed integer boxes; child0 >= 0 is an
+    inner node's left child, child0 < 0 a leaf whose first primitive is
+    -child0-1; child1 = right child or primitive count; prims = segment ids."""
+
+    box: np.ndarray
+    child0: np.ndarray
+    child1: np.ndarray
+    prims: np.ndarray
+    segs: np.ndarray
+    alpha: float
+
+    @property
+    def n_nodes(self):
+        return int(self.child0.size)
+
+
+def bvh(segs: np.ndarray, alpha: float = 1.0) -> Bvh:
+    """Greedy top-down 2D SAH BVH (Sec. 5.3.1); alpha = AABB-test cost relative
+    to a segment test (the per-scene tuned parameter)."""
+    L = _load()
+    segs = np.ascontiguousarray(segs, np.int32).reshape(-1, 4)
+    h = L.sg_bvh_build(segs.shape[0], _ptr(segs), float(alpha))
+    nn, npr = ctypes.c_int64(), ctypes.c_int64()
+    L.sg_bvh_sizes(h, ctypes.byref(nn), ctypes.byref(npr))
+    box = np.zeros((nn.value, 4), np.int32)
+    c0 = np.zeros(nn.value, np.int32)
+    c1 = np.zeros(nn.value, np.int32)
+    pr = np.zeros(max(1, npr.value), np.int32)
+    L.sg_bvh_export(h, _ptr(box), _ptr(c0), _ptr(c1), _ptr(pr))
+    L.sg_bvh_free(h)
+    return Bvh(box, c0, c1, pr[:npr.value].copy(), segs, float(alpha))
+
+
+@dataclass
+class KdTree:
+    """Roped SAH kd-tree over segments in [0,D]^2: axis 0/1 split on x/y, 2 leaf;
+    split coordinate; child = left child (right = left + 1) or first reference;
+    count = references in a leaf; box (N,4); rope (N,4) node across faces
+    x-min, x-max, y-min, y-max (-1 none); rope_log2 (N,4) = ceil(log2 of the
+    leaves adjacent across that face); refs = segment ids."""
+
+    axis: np.ndarray
+    split: np.ndarray
+    child: np.ndarray
+    count: np.ndarray
+    box: np.ndarray
+    rope: np.ndarray
+    rope_log2: np.ndarray
+    refs: np.ndarray
+    segs: np.ndarray
+    lam: float
+
+    @property
+    def n_nodes(self):
+        return int(self.axis.size)
+
+
+def kdtree(segs: np.ndarray, lam: float = 1.0, max_depth: int = 40) -> KdTree:
+    """Greedy top-down 2D SAH kd-tree with split candidates at every segment
+    endpoint coordinate and ropes on leaf faces (Sec. 5.3.2); lam = traversal
+    cost relative to a segment test (the per-scene tuned parameter)."""
+    L = _load()
+    segs = np.ascontiguousarray(segs, np.int32).reshape(-1, 4)
+    h = L.sg_kd_build(segs.shape[0], _ptr(segs), D, float(lam), int(max_depth))
+    nn, nr = ctypes.c_int64(), ctypes.c_int64()
+    L.sg_kd_sizes(h, ctypes.byref(nn), ctypes.byref(nr))
+    n = nn.value
+    axis, split, child, count = (np.zeros(n, np.int32) for _ in range(4))
+    box, rope, rl = np.zeros((n, 4), np.int32), np.zeros((n, 4), np.int32), np.zeros((n, 4), np.int32)
+    refs = np.zeros(max(1, nr.value), np.int32)
+    L.sg_kd_export(h, _ptr(axis), _ptr(split), _ptr(child), _ptr(count), _ptr(box), _ptr(rope), _ptr(rl),
+                   _ptr(refs))
+    L.sg_kd_free(h)
+    return KdTree(axis, split, child, count, box, rope, rl, refs[:nr.value].copy(), segs, float(lam))

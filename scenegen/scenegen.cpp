@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <climits>
 #include <cstring>
 #include <thread>
 #include <unordered_map>
@@ -844,6 +845,270 @@ static void parallel_for(int64_t n, int n_threads, F f) {
   for (auto& x : th) x.join();
 }
 
+// ---------------------------------------------------------------- BVH (Sec. 5.3.1)
+// Greedy top-down 2D SAH ("perimeter heuristic"): for both axes, sort the
+// segments by centroid and try every split k; cost(split) = 2 alpha +
+// (P_L N_L + P_R N_R) / P (alpha = cost of an AABB test relative to a segment
+// test, P = box perimeter); stop when that is not below the leaf cost N.
+struct BvhBuild {
+  const int32_t* seg;
+  float alpha;
+  int max_depth = 60;
+  std::vector<int32_t> box, c0, c1, prims;
+
+  void seg_box(int s, int32_t b[4]) const {
+    const int32_t* q = seg + 4 * s;
+    b[0] = std::min(q[0], q[2]);
+    b[1] = std::min(q[1], q[3]);
+    b[2] = std::max(q[0], q[2]);
+    b[3] = std::max(q[1], q[3]);
+  }
+  static float perim(const int32_t b[4]) { return 2.0f * ((float)(b[2] - b[0]) + (float)(b[3] - b[1])); }
+  static void grow(int32_t b[4], const int32_t o[4]) {
+    b[0] = std::min(b[0], o[0]);
+    b[1] = std::min(b[1], o[1]);
+    b[2] = std::max(b[2], o[2]);
+    b[3] = std::max(b[3], o[3]);
+  }
+  int build(std::vector<int32_t>& ids, int lo, int hi, int depth) {
+    const int node = (int)c0.size();
+    c0.push_back(0);
+    c1.push_back(0);
+    int32_t nb[4] = {INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN};
+    for (int k = lo; k < hi; ++k) {
+      int32_t b[4];
+      seg_box(ids[k], b);
+      grow(nb, b);
+    }
+    for (int q = 0; q < 4; ++q) box.push_back(nb[q]);
+    const int n = hi - lo;
+    const float P = perim(nb);
+    float best = (float)n;
+    int best_axis = -1, best_k = 0;
+    if (n > 1 && depth < max_depth && P > 0.f) {
+      std::vector<float> left(n);
+      for (int axis = 0; axis < 2; ++axis) {
+        std::sort(ids.begin() + lo, ids.begin() + hi, [&](int a, int b) {
+          const int64_t ca = (int64_t)seg[4 * a + axis] + seg[4 * a + 2 + axis];
+          const int64_t cb = (int64_t)seg[4 * b + axis] + seg[4 * b + 2 + axis];
+          return ca < cb || (ca == cb && a < b);
+        });
+        int32_t acc[4] = {INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN};
+        for (int k = 0; k < n; ++k) {
+          int32_t b[4];
+          seg_box(ids[lo + k], b);
+          grow(acc, b);
+          left[k] = perim(acc);
+        }
+        int32_t rb[4] = {INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN};
+        for (int k = n - 1; k >= 1; --k) {
+          int32_t b[4];
+          seg_box(ids[lo + k], b);
+          grow(rb, b);
+          const float cost = 2.0f * alpha + (left[k - 1] * (float)k + perim(rb) * (float)(n - k)) / P;
+          if (cost < best) {
+            best = cost;
+            best_axis = axis;
+            best_k = k;
+          }
+        }
+      }
+    }
+    if (best_axis < 0) {
+      c0[node] = -1 - (int32_t)prims.size();
+      c1[node] = n;
+      for (int k = lo; k < hi; ++k) prims.push_back(ids[k]);
+      return node;
+    }
+    const int axis = best_axis;
+    std::sort(ids.begin() + lo, ids.begin() + hi, [&](int a, int b) {
+      const int64_t ca = (int64_t)seg[4 * a + axis] + seg[4 * a + 2 + axis];
+      const int64_t cb = (int64_t)seg[4 * b + axis] + seg[4 * b + 2 + axis];
+      return ca < cb || (ca == cb && a < b);
+    });
+    const int l = build(ids, lo, lo + best_k, depth + 1);
+    const int r = build(ids, lo + best_k, hi, depth + 1);
+    c0[node] = l;
+    c1[node] = r;
+    return node;
+  }
+};
+
+// ---------------------------------------------------------------- roped kd-tree (Sec. 5.3.2)
+// Greedy top-down 2D SAH; candidate planes at every segment-endpoint
+// coordinate strictly inside the node (both axes); cost(split) = lambda +
+// (P_L N_L + P_R N_R) / P, leaf when not below N.  A segment belongs to every
+// node whose closed box it touches.  Leaves get ropes (one per face) to the
+// deepest node that contains the whole region across that face, and the count
+// of leaves adjacent across the face (for the paper's ideal log2 rope cost).
+static bool seg_hits_box(const int32_t* q, int64_t x0, int64_t y0, int64_t x1, int64_t y1) {
+  const int64_t ax = q[0], ay = q[1], bx = q[2], by = q[3];
+  if (std::max(ax, bx) < x0 || std::min(ax, bx) > x1 || std::max(ay, by) < y0 || std::min(ay, by) > y1) return false;
+  if ((ax >= x0 && ax <= x1 && ay >= y0 && ay <= y1) || (bx >= x0 && bx <= x1 && by >= y0 && by <= y1)) return true;
+  const int64_t cx[4] = {x0, x1, x1, x0}, cy[4] = {y0, y0, y1, y1};
+  int pos = 0, neg = 0;
+  for (int k = 0; k < 4; ++k) {
+    const int64_t o = (bx - ax) * (cy[k] - ay) - (by - ay) * (cx[k] - ax);
+    if (o > 0) ++pos;
+    if (o < 0) ++neg;
+  }
+  return !(pos == 4 || neg == 4);
+}
+
+struct KdBuild {
+  const int32_t* seg;
+  float lambda;
+  int max_depth = 40;
+  std::vector<int32_t> axis, split, child, count, box, rope, rope_log2, refs;
+
+  int new_node(const int64_t b[4]) {
+    const int id = (int)axis.size();
+    axis.push_back(2);
+    split.push_back(0);
+    child.push_back(-1);
+    count.push_back(0);
+    for (int k = 0; k < 4; ++k) box.push_back((int32_t)b[k]);
+    for (int k = 0; k < 4; ++k) rope.push_back(-1);
+    for (int k = 0; k < 4; ++k) rope_log2.push_back(0);
+    return id;
+  }
+
+  void build(int node, std::vector<int32_t>& ids, int depth) {
+    const int64_t b[4] = {box[4 * node], box[4 * node + 1], box[4 * node + 2], box[4 * node + 3]};
+    const int n = (int)ids.size();
+    const float P = 2.0f * ((float)(b[2] - b[0]) + (float)(b[3] - b[1]));
+    float best = (float)n;
+    int best_axis = -1;
+    int64_t best_s = 0;
+    if (n > 0 && depth < max_depth && P > 0.f) {
+      std::vector<int64_t> lo(n), hi(n), cand;
+      for (int a = 0; a < 2; ++a) {
+        cand.clear();
+        for (int k = 0; k < n; ++k) {
+          const int32_t* q = seg + 4 * ids[k];
+          const int64_t e0 = q[a], e1 = q[2 + a];
+          lo[k] = std::max(std::min(e0, e1), b[a]);
+          hi[k] = std::min(std::max(e0, e1), b[2 + a]);
+          if (e0 > b[a] && e0 < b[2 + a]) cand.push_back(e0);
+          if (e1 > b[a] && e1 < b[2 + a]) cand.push_back(e1);
+        }
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        std::vector<int64_t> ls = lo, hs = hi;
+        std::sort(ls.begin(), ls.end());
+        std::sort(hs.begin(), hs.end());
+        const float ext_other = (float)(b[3 - a] - b[1 - a]);
+        for (int64_t sp : cand) {
+          const int nl = (int)(std::lower_bound(ls.begin(), ls.end(), sp) - ls.begin());       // lo < sp
+          const int nr = n - (int)(std::upper_bound(hs.begin(), hs.end(), sp) - hs.begin());  // hi > sp
+          const float pl = 2.0f * ((float)(sp - b[a]) + ext_other);
+          const float pr = 2.0f * ((float)(b[2 + a] - sp) + ext_other);
+          const float cost = lambda + (pl * (float)nl + pr * (float)nr) / P;
+          if (cost < best) {
+            best = cost;
+            best_axis = a;
+            best_s = sp;
+          }
+        }
+      }
+    }
+    if (best_axis < 0) {
+      axis[node] = 2;
+      child[node] = (int32_t)refs.size();
+      count[node] = n;
+      for (int32_t s : ids) refs.push_back(s);
+      return;
+    }
+    int64_t lb[4] = {b[0], b[1], b[2], b[3]}, rb[4] = {b[0], b[1], b[2], b[3]};
+    lb[2 + best_axis] = best_s;
+    rb[best_axis] = best_s;
+    std::vector<int32_t> lids, rids;
+    for (int32_t s : ids) {
+      if (seg_hits_box(seg + 4 * s, lb[0], lb[1], lb[2], lb[3])) lids.push_back(s);
+      if (seg_hits_box(seg + 4 * s, rb[0], rb[1], rb[2], rb[3])) rids.push_back(s);
+    }
+    ids.clear();
+    ids.shrink_to_fit();
+    const int l = new_node(lb);
+    const int r = new_node(rb);
+    axis[node] = best_axis;
+    split[node] = (int32_t)best_s;
+    child[node] = l;
+    (void)r;  // right child = left + 1
+    build(l, lids, depth + 1);
+    build(r, rids, depth + 1);
+  }
+
+  // faces: 0 x-min, 1 x-max, 2 y-min, 3 y-max
+  void ropes(int node, const int32_t in[4]) {
+    if (axis[node] == 2) {
+      for (int f = 0; f < 4; ++f) {
+        int32_t r = optimise(node, f, in[f]);
+        rope[4 * node + f] = r;
+        int cnt = r < 0 ? 0 : adjacent_leaves(node, f, r);
+        int lg = 0;
+        while ((1 << lg) < cnt) ++lg;
+        rope_log2[4 * node + f] = lg;
+      }
+      return;
+    }
+    const int a = axis[node], l = child[node], r = l + 1;
+    int32_t rl[4] = {in[0], in[1], in[2], in[3]}, rr[4] = {in[0], in[1], in[2], in[3]};
+    rl[2 * a + 1] = r;  // left child's max face on the split axis
+    rr[2 * a] = l;      // right child's min face
+    ropes(l, rl);
+    ropes(r, rr);
+  }
+  int32_t optimise(int leaf, int f, int32_t N) const {
+    if (N < 0) return N;
+    const int fa = f / 2;  // axis normal to the face
+    const bool fmax = (f & 1) != 0;
+    const int32_t* lb = &box[4 * leaf];
+    const int32_t plane = fmax ? lb[2 + fa] : lb[fa];
+    const int32_t f0 = lb[1 - fa], f1 = lb[3 - fa];  // face extent on the other axis
+    while (axis[N] != 2) {
+      const int a = axis[N];
+      const int32_t sp = split[N];
+      const int l = child[N];
+      if (a == fa) {
+        if (fmax)
+          N = (sp > plane) ? l : l + 1;
+        else
+          N = (sp >= plane) ? l : l + 1;
+      } else {
+        if (sp <= f0)
+          N = l + 1;
+        else if (sp >= f1)
+          N = l;
+        else
+          break;
+      }
+    }
+    return N;
+  }
+  int adjacent_leaves(int leaf, int f, int32_t N) const {
+    const int fa = f / 2;
+    const int32_t* lb = &box[4 * leaf];
+    const int32_t f0 = lb[1 - fa], f1 = lb[3 - fa];
+    int cnt = 0;
+    std::vector<int32_t> st{N};
+    while (!st.empty()) {
+      const int32_t x = st.back();
+      st.pop_back();
+      const int32_t* xb = &box[4 * x];
+      const int32_t o0 = std::max(f0, xb[1 - fa]), o1 = std::min(f1, xb[3 - fa]);
+      if (o1 <= o0) continue;  // touches the face in a point at most
+      if (axis[x] == 2) {
+        ++cnt;
+      } else {
+        st.push_back(child[x]);
+        st.push_back(child[x] + 1);
+      }
+    }
+    return std::max(1, cnt);
+  }
+};
+
 }  // namespace
 
 // =============================================================== C ABI
@@ -1092,5 +1357,79 @@ int64_t sg_rays_pinhole(void* h, int64_t n_eyes, int64_t rays_per_eye, double fo
   });
   return n_eyes * rays_per_eye;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- baselines
+extern "C" {
+
+// SAH BVH over the segments (4 int32 each).  alpha = AABB-test cost relative to a
+// segment test.  Returns a handle; sizes via sg_bvh_sizes, arrays via sg_bvh_export.
+void* sg_bvh_build(int64_t n_seg, const int32_t* seg, float alpha) {
+  auto* b = new BvhBuild();
+  b->seg = seg;
+  b->alpha = alpha;
+  std::vector<int32_t> ids(n_seg);
+  for (int64_t k = 0; k < n_seg; ++k) ids[k] = (int32_t)k;
+  if (n_seg > 0)
+    b->build(ids, 0, (int)n_seg, 0);
+  else {
+    b->c0.push_back(-1);
+    b->c1.push_back(0);
+    for (int q = 0; q < 4; ++q) b->box.push_back(0);
+  }
+  b->seg = nullptr;
+  return b;
+}
+void sg_bvh_sizes(void* h, int64_t* n_nodes, int64_t* n_prims) {
+  auto* b = (BvhBuild*)h;
+  *n_nodes = (int64_t)b->c0.size();
+  *n_prims = (int64_t)b->prims.size();
+}
+void sg_bvh_export(void* h, int32_t* box, int32_t* c0, int32_t* c1, int32_t* prims) {
+  auto* b = (BvhBuild*)h;
+  std::copy(b->box.begin(), b->box.end(), box);
+  std::copy(b->c0.begin(), b->c0.end(), c0);
+  std::copy(b->c1.begin(), b->c1.end(), c1);
+  std::copy(b->prims.begin(), b->prims.end(), prims);
+}
+void sg_bvh_free(void* h) { delete (BvhBuild*)h; }
+
+// Roped SAH kd-tree over the segments inside [0, D]^2.  lambda = traversal cost
+// relative to a segment test.
+void* sg_kd_build(int64_t n_seg, const int32_t* seg, int32_t D, float lambda, int32_t max_depth) {
+  auto* k = new KdBuild();
+  k->seg = seg;
+  k->lambda = lambda;
+  k->max_depth = max_depth;
+  const int64_t root_box[4] = {0, 0, D, D};
+  const int root = k->new_node(root_box);
+  std::vector<int32_t> ids;
+  for (int64_t s = 0; s < n_seg; ++s)
+    if (seg_hits_box(seg + 4 * s, 0, 0, D, D)) ids.push_back((int32_t)s);
+  k->build(root, ids, 0);
+  const int32_t none[4] = {-1, -1, -1, -1};
+  k->ropes(root, none);
+  k->seg = nullptr;
+  return k;
+}
+void sg_kd_sizes(void* h, int64_t* n_nodes, int64_t* n_refs) {
+  auto* k = (KdBuild*)h;
+  *n_nodes = (int64_t)k->axis.size();
+  *n_refs = (int64_t)k->refs.size();
+}
+void sg_kd_export(void* h, int32_t* axis, int32_t* split, int32_t* child, int32_t* count, int32_t* box,
+                  int32_t* rope, int32_t* rope_log2, int32_t* refs) {
+  auto* k = (KdBuild*)h;
+  std::copy(k->axis.begin(), k->axis.end(), axis);
+  std::copy(k->split.begin(), k->split.end(), split);
+  std::copy(k->child.begin(), k->child.end(), child);
+  std::copy(k->count.begin(), k->count.end(), count);
+  std::copy(k->box.begin(), k->box.end(), box);
+  std::copy(k->rope.begin(), k->rope.end(), rope);
+  std::copy(k->rope_log2.begin(), k->rope_log2.end(), rope_log2);
+  std::copy(k->refs.begin(), k->refs.end(), refs);
+}
+void sg_kd_free(void* h) { delete (KdBuild*)h; }
 
 }  // extern "C"
