@@ -46,17 +46,18 @@ def family_segments(name):
     return sg.dash_grid(N_SEGMENTS, float(name[4:]))
 
 
-def build_workload(n_rays=N_RAYS, families=FAMILIES):
-    """[(name, segs, cdt, annealed, rays)] for the scene families."""
+def build_workload(n_rays=N_RAYS, families=FAMILIES, with_refined=False):
+    """[(name, segs, cdt, annealed, rays)] for the scene families (annealed =
+    optimally refined CDT polished with edge flips); with_refined appends the
+    refined CDT to each tuple."""
     import scenegen as sg
 
     out = []
     for k, name in enumerate(families):
         segs = family_segments(name)
-        cdt = sg.cdt(segs)
-        tri = sg.anneal(cdt, SCENE_SEED + k, sweeps=4)
+        cdt, ref, tri = sg.pipeline(segs, SCENE_SEED + k, sweeps=4)
         rays = sg.rays_isotropic(tri, n_rays, 100 + k)
-        out.append((name, segs, cdt, tri, rays))
+        out.append((name, segs, cdt, tri, rays) + ((ref,) if with_refined else ()))
     return out
 
 
@@ -125,12 +126,14 @@ def cpu_oracle_rate(work, seconds_target=4.0):
     threads = os.cpu_count() or 1
     n = 1 << 14
     t0 = time.perf_counter()
-    for name, segs, cdt, tri, r in work:
+    for w in work:
+        tri, r = w[3], w[4]
         oracle.walk(tri, r.ox[:n], r.oy[:n], r.dx[:n], r.dy[:n], r.start[:n], n_threads=threads)
     dt = time.perf_counter() - t0
     n2 = int(min(N_RAYS, max(n, n * seconds_target / max(dt, 1e-6))))
     t0 = time.perf_counter()
-    for name, segs, cdt, tri, r in work:
+    for w in work:
+        tri, r = w[3], w[4]
         oracle.walk(tri, r.ox[:n2], r.oy[:n2], r.dx[:n2], r.dy[:n2], r.start[:n2], n_threads=threads)
     dt = time.perf_counter() - t0
     return n2 * len(work) / dt, threads, n2, dt
@@ -260,16 +263,16 @@ def main():
     _build.build()
     import scenegen as sg
 
-    work = build_workload()
+    work = build_workload(with_refined=True)
     stream = torch.cuda.current_stream(dev)
     n = N_RAYS
     hit = torch.empty(n, dtype=torch.int32, device=dev)
     t = torch.empty(n, dtype=torch.float32, device=dev)
     steps = torch.empty(n, dtype=torch.int32, device=dev)
     scenes = []
-    for name, segs, cdt, tri, r in work:
+    for name, segs, cdt, tri, r, ref in work:
         d = {k: torch.from_numpy(getattr(r, k)).to(dev) for k in ("ox", "oy", "dx", "dy", "start")}
-        scenes.append(dict(name=name, segs=segs, cdt=cdt, tri=tri, rays=r, d=d,
+        scenes.append(dict(name=name, segs=segs, cdt=cdt, ref=ref, tri=tri, rays=r, d=d,
                            scene=cct.Scene.from_triangulation(tri, sg.D)))
 
     def trace(sc, start, flags, s=None):
@@ -347,17 +350,23 @@ def main():
         walk_ms_tot += wms
         alg_bytes_tot += alg
         alg_over_peak += alg / bps
-        cdt_scene = cct.Scene.from_triangulation(sc["cdt"], sg.D)
         d = sc["d"]
-        cct.cct_trace(cdt_scene.handle, d["ox"], d["oy"], d["dx"], d["dy"], None, hit, t, steps, 0, stream)
-        cst = cdt_scene.stats()
-        cdt_scene.free()
+        other = {}
+        for kind in ("cdt", "ref"):
+            o_scene = cct.Scene.from_triangulation(sc[kind], sg.D)
+            cct.cct_trace(o_scene.handle, d["ox"], d["oy"], d["dx"], d["dy"], None, hit, t, steps, 0, stream)
+            other[kind] = o_scene.stats()
+            o_scene.free()
+        cst = other["cdt"]
         cmp = comparison_structures(torch, cct, sg, sc, dev, stream, 2)
         per[sc["name"]] = {"segments": int(sc["segs"].shape[0]), "triangles": sc["tri"].n_tri,
                            "kd": cmp["kd"], "bvh": cmp["bvh"],
                            "walk_rays_per_s": n / (wms * 1e-3), "steps_per_ray": wsteps / n,
                            "steps_per_ray_cdt": cst["steps"] / max(1, cst["rays"]),
+                           "steps_per_ray_refined_cdt": other["ref"]["steps"] / max(1, other["ref"]["rays"]),
+                           "refine_params": list(getattr(sc["ref"], "refine_params", (0.0, 0.0))),
                            "length_annealed_over_cdt": sc["tri"].length(True) / sc["cdt"].length(True),
+                           "length_refined_over_cdt": sc["ref"].length(True) / sc["cdt"].length(True),
                            "walk_l2_frac": (alg / (wms * 1e-3)) / bps, "gather_peak_gbs": bps / 1e9}
     achieved = alg_bytes_tot / (walk_ms_tot * 1e-3) / 1e9
     l2_peak = alg_bytes_tot / alg_over_peak / 1e9  # time-weighted gather peak over the scenes' table sizes

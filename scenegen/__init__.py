@@ -78,6 +78,10 @@ def _load():
     L.sg_rays_isotropic.argtypes = [vp, i64, u64, vp, vp, vp, vp, vp, i32]
     L.sg_rays_pinhole.restype = i64
     L.sg_rays_pinhole.argtypes = [vp, i64, i64, dbl, u64, vp, vp, vp, vp, vp, i32]
+    L.sg_refine.restype = i64
+    L.sg_refine.argtypes = [vp, dbl, dbl, i64]
+    L.sg_refine_optimal.restype = vp
+    L.sg_refine_optimal.argtypes = [vp, vp, i32, vp, i32, i64, i32, P(dbl), P(dbl)]
     L.sg_bvh_build.restype = vp
     L.sg_bvh_build.argtypes = [i64, vp, ctypes.c_float]
     L.sg_bvh_sizes.restype = None
@@ -226,6 +230,51 @@ def anneal(tri: Triangulation, seed: int, sweeps=20.0, T0=0.02, T1=1e-4) -> Tria
     h = L.sg_tri_copy(tri._h)
     L.sg_anneal(h, seed, float(sweeps), float(T0) * D, float(T1) * D)
     return _export(h, tri.segs, "annealed")
+
+
+def refine(tri: Triangulation, min_angle_deg: float = 20.0, max_area: float = 0.0,
+           max_insert: int | None = None) -> Triangulation:
+    """A quality-refined copy of ``tri`` (Delaunay refinement on the integer
+    grid: circumcentres of triangles with a smaller angle or a larger area,
+    lattice midpoints of encroached constrained edges); max_area in grid units."""
+    L = _load()
+    h = L.sg_tri_copy(tri._h)
+    cap = 4 * tri.n_vert + 1024 if max_insert is None else int(max_insert)
+    if L.sg_refine(h, float(min_angle_deg), float(max_area), cap) < 0:
+        L.sg_tri_free(h)
+        raise RuntimeError("refinement failed")
+    return _export(h, tri.segs, "refined")
+
+
+OPT_ANGLES = (5.0, 10.0, 15.0, 20.0, 25.0)
+OPT_AREA_FRACTIONS = (0.0, 4.0, 1.0, 0.25)  # max area = f * D^2 / n_segments (0 = no bound)
+
+
+def refine_optimal(tri: Triangulation, angles=OPT_ANGLES, area_fractions=OPT_AREA_FRACTIONS,
+                   max_insert: int | None = None, threads: int | None = None) -> Triangulation:
+    """The optimally refined CDT (Sec. 3.5.1): of all (min angle, max area)
+    refinements of the grid (and the unrefined CDT), the one with the shortest
+    total edge length.  Sets .refine_params = (angle, max_area)."""
+    L = _load()
+    n_seg = max(1, int(np.asarray(tri.segs).reshape(-1, 4).shape[0]))
+    ang = np.ascontiguousarray(angles, np.float64)
+    areas = np.ascontiguousarray([0.0 if f == 0 else f * float(D) * D / n_seg for f in area_fractions], np.float64)
+    cap = 4 * tri.n_vert + 1024 if max_insert is None else int(max_insert)
+    ba, bA = ctypes.c_double(), ctypes.c_double()
+    h = L.sg_refine_optimal(tri._h, _ptr(ang), ang.size, _ptr(areas), areas.size, cap, threads or _threads(),
+                            ctypes.byref(ba), ctypes.byref(bA))
+    out = _export(h, tri.segs, "refined")
+    out.refine_params = (float(ba.value), float(bA.value))
+    return out
+
+
+def pipeline(segs: np.ndarray, seed: int, sweeps: float = 4.0):
+    """The offline build of the paper's triangulations: (unrefined CDT, optimally
+    refined CDT (Sec. 3.5.1), annealed = the refined CDT polished with greedy and
+    simulated-annealing edge flips (Sec. 3.2.7, 3.3))."""
+    c = cdt(segs)
+    r = refine_optimal(c)
+    return c, r, anneal(r, seed, sweeps=sweeps)
 
 
 def from_arrays(vx, vy, tri_v, tri_nb, tri_seg, segs, kind="given") -> Triangulation:

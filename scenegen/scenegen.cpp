@@ -18,6 +18,7 @@
 // int128 in-circle), so the CDT is built without tolerances.
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <climits>
@@ -845,6 +846,112 @@ static void parallel_for(int64_t n, int n_threads, F f) {
   for (auto& x : th) x.join();
 }
 
+// ---------------------------------------------------------------- quality refinement (Sec. 3.5.1)
+// The paper starts from a quality CDT (Shewchuk's Triangle) whose minimum-angle
+// and maximum-area bounds are chosen, by brute force, to give the shortest
+// total edge length.  This is a Delaunay refinement of our own on the integer
+// grid: a triangle is bad if its smallest angle is below min_angle or its area
+// above max_area; its circumcentre, rounded to the grid, is inserted; a
+// constrained edge whose diametral circle holds that point is split at its
+// midpoint instead, when the midpoint is a lattice point (otherwise the
+// triangle is left as it is).  Insertions are capped.  Circumcentres are
+// constructed in fp64 and rounded; every predicate stays exact.
+static double smallest_angle_cos(const Pt& a, const Pt& b, const Pt& c) {
+  const double la = (double)len2(b, c), lb = (double)len2(c, a), lc = (double)len2(a, b);
+  // the smallest angle is opposite the shortest side
+  double s, u, v;
+  if (la <= lb && la <= lc) {
+    s = la; u = lb; v = lc;
+  } else if (lb <= la && lb <= lc) {
+    s = lb; u = la; v = lc;
+  } else {
+    s = lc; u = la; v = lb;
+  }
+  return (u + v - s) / (2.0 * std::sqrt(u * v));
+}
+
+static bool circumcentre(const Pt& a, const Pt& b, const Pt& c, Pt& out) {
+  const double bx = (double)b.x - a.x, by = (double)b.y - a.y, cx = (double)c.x - a.x, cy = (double)c.y - a.y;
+  const double d = 2.0 * (bx * cy - by * cx);
+  if (d == 0.0) return false;
+  const double b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+  const double ux = (cy * b2 - by * c2) / d, uy = (bx * c2 - cx * b2) / d;
+  const double X = a.x + ux, Y = a.y + uy;
+  if (!(X > -1e12 && X < 1e12 && Y > -1e12 && Y < 1e12)) return false;
+  out = Pt{(int32_t)std::llround(X), (int32_t)std::llround(Y)};
+  return true;
+}
+
+static int64_t refine(Triangulation& tr, double min_angle_deg, double max_area, int64_t max_insert) {
+  const double cos_min = min_angle_deg > 0 ? std::cos(min_angle_deg * 3.141592653589793 / 180.0) : 2.0;
+  const int32_t D = tr.D;
+  auto bad = [&](int t) {
+    const Tri& x = tr.T[t];
+    const Pt &a = tr.P[x.v[0]], &b = tr.P[x.v[1]], &c = tr.P[x.v[2]];
+    if (max_area > 0 && 0.5 * (double)orient(a, b, c) > max_area) return true;
+    if (cos_min < 1.5 && smallest_angle_cos(a, b, c) > cos_min) return true;
+    return false;
+  };
+  auto key = [&](int t) {
+    int v[3] = {tr.T[t].v[0], tr.T[t].v[1], tr.T[t].v[2]};
+    std::sort(v, v + 3);
+    return ((uint64_t)(uint32_t)v[0] * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)(uint32_t)v[1] << 21) ^ (uint64_t)v[2];
+  };
+  std::unordered_map<uint64_t, char> tried;
+  std::vector<int> work;
+  for (int t = 0; t < (int)tr.T.size(); ++t) work.push_back(t);
+  int64_t inserted = 0;
+  auto push_fan = [&](int v) {
+    tr.for_fan(v, [&](int t, int) {
+      work.push_back(t);
+      return false;
+    });
+  };
+  while (!work.empty() && inserted < max_insert && tr.status == 0) {
+    const int t = work.back();
+    work.pop_back();
+    if (t >= (int)tr.T.size() || !bad(t)) continue;
+    const uint64_t k = key(t);
+    if (tried.count(k)) continue;
+    tried[k] = 1;
+    const Tri x = tr.T[t];
+    Pt c;
+    if (!circumcentre(tr.P[x.v[0]], tr.P[x.v[1]], tr.P[x.v[2]], c)) continue;
+    if (c.x <= 0 || c.y <= 0 || c.x >= D || c.y >= D) continue;  // the hull is not split
+    const int loc = tr.locate(c, t, tr.rng);
+    if (loc < 0) continue;
+    // a constrained edge of the containing triangle that c encroaches is split
+    // at its midpoint (a lattice point) instead
+    bool handled = false;
+    for (int e = 0; e < 3 && !handled; ++e) {
+      if (tr.T[loc].c[e] < 0) continue;
+      const Pt& p = tr.P[tr.T[loc].v[(e + 1) % 3]];
+      const Pt& q = tr.P[tr.T[loc].v[(e + 2) % 3]];
+      const int64_t dot = (int64_t)(p.x - c.x) * (q.x - c.x) + (int64_t)(p.y - c.y) * (q.y - c.y);
+      if (dot > 0) continue;
+      handled = true;
+      if (((p.x + q.x) & 1) || ((p.y + q.y) & 1)) break;  // no lattice midpoint: leave it
+      const Pt m{(p.x + q.x) / 2, (p.y + q.y) / 2};
+      tr.last = loc;
+      const size_t nv = tr.P.size();
+      const int v = tr.insert_point(m);
+      if (v >= 0 && (size_t)v >= nv) {
+        ++inserted;
+        push_fan(v);
+      }
+    }
+    if (handled) continue;
+    tr.last = loc;
+    const size_t nv = tr.P.size();
+    const int v = tr.insert_point(c);
+    if (v >= 0 && (size_t)v >= nv) {
+      ++inserted;
+      push_fan(v);
+    }
+  }
+  return inserted;
+}
+
 // ---------------------------------------------------------------- BVH (Sec. 5.3.1)
 // Greedy top-down 2D SAH ("perimeter heuristic"): for both axes, sort the
 // segments by centroid and try every split k; cost(split) = 2 alpha +
@@ -1431,5 +1538,60 @@ void sg_kd_export(void* h, int32_t* axis, int32_t* split, int32_t* child, int32_
   std::copy(k->refs.begin(), k->refs.end(), refs);
 }
 void sg_kd_free(void* h) { delete (KdBuild*)h; }
+
+}  // extern "C"
+
+extern "C" {
+
+// Quality refinement of a CDT in place (see refine above): min_angle_deg (0 =
+// none), max_area (0 = none, grid units^2), at most max_insert new vertices.
+// Returns the number of vertices inserted, or -1 on a construction failure.
+int64_t sg_refine(void* h, double min_angle_deg, double max_area, int64_t max_insert) {
+  auto* tr = (Triangulation*)h;
+  int64_t n = refine(*tr, min_angle_deg, max_area, max_insert);
+  return tr->status < 0 ? -1 : n;
+}
+
+// The optimally refined CDT (Sec. 3.5.1): refine copies of the CDT with every
+// (angle, area) pair of the given grids, in parallel, and keep the one with
+// the shortest total edge length (the unrefined CDT competes too).  Writes the
+// chosen pair to *best_angle / *best_area; returns a new handle.
+void* sg_refine_optimal(void* h, const double* angles, int32_t n_angles, const double* areas, int32_t n_areas,
+                        int64_t max_insert, int32_t n_threads, double* best_angle, double* best_area) {
+  auto* base = (Triangulation*)h;
+  struct Cand {
+    double a, A;
+    Triangulation* tr = nullptr;
+    float len = 0.f;
+  };
+  std::vector<Cand> cands;
+  cands.push_back(Cand{0.0, 0.0});
+  for (int i = 0; i < n_angles; ++i)
+    for (int j = 0; j < n_areas; ++j)
+      if (angles[i] > 0 || areas[j] > 0) cands.push_back(Cand{angles[i], areas[j]});
+  std::vector<std::thread> th;
+  std::atomic<size_t> next{0};
+  const int nt = std::max(1, std::min<int>(n_threads, (int)cands.size()));
+  for (int w = 0; w < nt; ++w)
+    th.emplace_back([&]() {
+      while (true) {
+        const size_t k = next.fetch_add(1);
+        if (k >= cands.size()) break;
+        auto* tr = new Triangulation(*base);
+        if (cands[k].a > 0 || cands[k].A > 0) refine(*tr, cands[k].a, cands[k].A, max_insert);
+        cands[k].tr = tr;
+        cands[k].len = tr->status < 0 ? 3.4e38f : (float)tr->total_length(false);
+      }
+    });
+  for (auto& x : th) x.join();
+  size_t best = 0;
+  for (size_t k = 1; k < cands.size(); ++k)
+    if (cands[k].len < cands[best].len) best = k;
+  for (size_t k = 0; k < cands.size(); ++k)
+    if (k != best) delete cands[k].tr;
+  *best_angle = cands[best].a;
+  *best_area = cands[best].A;
+  return cands[best].tr;
+}
 
 }  // extern "C"

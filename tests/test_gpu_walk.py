@@ -233,12 +233,17 @@ def test_empty_scene_and_tiny_domain(cct):
     scene.free()
 
 
-@pytest.mark.parametrize("family", ["circles", "dash22", "clustered"])
+@pytest.mark.parametrize("family", ["circles", "circles_refined", "dash22", "clustered"])
 def test_config2_scale_full_parity(cct, family):
-    """Config-2-sized scenes (3e4 segments), 2^20 rays: every output checked."""
-    segs = {"circles": lambda: sg.circles(30000, 3), "dash22": lambda: sg.dash_grid(30000, 22.5),
-            "clustered": lambda: sg.clustered(30000, 3)}[family]()
-    tri = sg.anneal(sg.cdt(segs), 3, sweeps=2)
+    """Config-2-sized scenes (3e4 segments), 2^20 rays: every output checked.
+    circles_refined: the optimally refined + annealed pipeline, whose
+    constrained edges are split at Steiner points."""
+    segs = {"circles": lambda: sg.circles(30000, 3), "circles_refined": lambda: sg.circles(30000, 3),
+            "dash22": lambda: sg.dash_grid(30000, 22.5), "clustered": lambda: sg.clustered(30000, 3)}[family]()
+    if family == "circles_refined":
+        tri = sg.pipeline(segs, 3, sweeps=2)[2]
+    else:
+        tri = sg.anneal(sg.cdt(segs), 3, sweeps=2)
     r = sg.rays_isotropic(tri, 1 << 20, 4)
     exp = oracle.walk(tri, r.ox, r.oy, r.dx, r.dy, r.start)
     scene = cct.Scene.from_triangulation(tri, sg.D)

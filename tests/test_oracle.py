@@ -371,3 +371,27 @@ def test_scene_families_triangulate(gen):
     hb, tb = oracle.closest_bruteforce(segs, r.ox, r.oy, r.dx, r.dy)
     hw, tw, sw = oracle.walk(ann, r.ox, r.oy, r.dx, r.dy, r.start)
     assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
+
+
+@pytest.mark.parametrize("gen", ["config1", "circles"])
+def test_refined_cdt_is_valid_and_optimal(gen):
+    """The optimally refined CDT (Sec. 3.5.1): still a valid constrained
+    Delaunay triangulation covering every segment (constrained edges may be
+    split at lattice midpoints), never longer than the unrefined CDT (which
+    competes in the search), and the walk on it equals the brute force."""
+    segs = sg.random_segments(200, 13) if gen == "config1" else sg.circles(3000, 13)
+    cdt = sg.cdt(segs)
+    ref = sg.refine_optimal(cdt)
+    assert oracle.check_triangulation(ref, sg.D, check_delaunay=True) == 0
+    assert oracle.interior_length(ref) <= oracle.interior_length(cdt) * (1 + 1e-6)
+    for tri in (ref, sg.refine(cdt, 25.0), sg.anneal(ref, 13, sweeps=2)):
+        assert oracle.check_triangulation(tri, sg.D) == 0
+        r = sg.rays_isotropic(tri, 5000, 14)
+        hb, tb = oracle.closest_bruteforce(segs, r.ox, r.oy, r.dx, r.dy)
+        hw, tw, sw = oracle.walk(tri, r.ox, r.oy, r.dx, r.dy, r.start)
+        assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
+        assert np.array_equal(sw[:500], oracle.steps_bruteforce(tri, r.ox[:500], r.oy[:500], r.dx[:500],
+                                                                 r.dy[:500], hb[:500]))
+    if gen == "circles":
+        # polygon interiors: refinement shortens the triangulation markedly
+        assert oracle.interior_length(ref) < 0.5 * oracle.interior_length(cdt)
