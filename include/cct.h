@@ -203,6 +203,59 @@ int cct_trace_noalloc(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy,
  * zeroes them afterwards.  Errors: CCT_ERR_INVALID_ARGUMENT, CCT_ERR_CUDA. */
 int cct_get_stats(cct_scene scene, cct_stats* out, int reset, void* stream);
 
+/* ------------------------------------------------------------------ many scenes in one launch */
+/* No counterpart in the paper (a GPU batching layer over Sec. 5.1/5.2): one
+ * persistent launch walks the rays of many items, each item a ray batch
+ * against one of a set of device-resident scenes.  Items are cut into chunks
+ * of `chunk` rays (cct_tuning) that the launch's warps take from one work
+ * counter, so scenes and batches of very different sizes share the GPU. */
+typedef struct {
+  int32_t scene;              /* index into the scene array of the batch */
+  int32_t ray_stride;         /* 0 or 1: separate ray arrays; 4: ray i's ox, oy, dx, dy are 4
+                                 consecutive 32-bit words (d_ox = record base, d_oy = d_ox + 1, ...) */
+  int64_t n;                  /* rays, < 2^31 */
+  const int32_t* d_ox;        /* device arrays as in cct_trace */
+  const int32_t* d_oy;
+  const float* d_dx;
+  const float* d_dy;
+  const int32_t* d_start_tri; /* caller numbering of that scene, or NULL: locate */
+  int32_t* d_hit_seg;
+  float* d_t;
+  int32_t* d_steps;
+} cct_batch_item;
+
+typedef struct cct_batch_s* cct_batch;
+
+/* A reusable batch over n_scenes loaded scenes (all on one device) for up to
+ * max_items items; flags: 0 or CCT_TRACE_EXACT_ONLY.  Holds a device work table
+ * and a pinned host staging copy of it.  The scenes must outlive the batch. */
+int cct_batch_create(const cct_scene* scenes, int32_t n_scenes, int32_t max_items, uint32_t flags, cct_batch* out);
+int cct_batch_free(cct_batch batch);
+
+/* Block size, refill threshold and chunk of later stages and enqueues (bin_shift
+ * and trace_flags are ignored); NULL = defaults. */
+int cct_batch_set_tuning(cct_batch batch, const cct_tuning* tuning);
+
+/* Writes the work list into the host staging copy (host only, no GPU work).
+ * Must not be called while an enqueued copy of the staging buffer may still be
+ * pending on the GPU.  Errors: CCT_ERR_INVALID_ARGUMENT (scene index, counts,
+ * null arrays, more than max_items). */
+int cct_batch_stage(cct_batch batch, const cct_batch_item* items, int32_t n_items);
+
+/* Enqueues on `stream`: the copy of the staged table to the device (its full
+ * fixed size), the work-counter reset and the persistent kernel.  Its three
+ * operations have fixed arguments, so one stream capture of this call can be
+ * replayed after every cct_batch_stage. */
+int cct_batch_enqueue(cct_batch batch, void* stream);
+
+/* Counters accumulated by this batch's launches (per-scene counters of
+ * cct_get_stats do not include batched work); waits for `stream`. */
+int cct_batch_get_stats(cct_batch batch, cct_stats* out, int reset, void* stream);
+
+/* One-shot convenience: create, stage, enqueue, wait for `stream`, free. */
+int cct_trace_batched(const cct_scene* scenes, int32_t n_scenes, const cct_batch_item* items, int32_t n_items,
+                      uint32_t flags, void* stream);
+
 /* ------------------------------------------------------------------ comparison structures (Sec. 5.3) */
 /* The two classical structures the paper compares against, traversed on the
  * GPU with the same exact hit rule as the walk, so all three return the same

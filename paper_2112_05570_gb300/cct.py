@@ -62,6 +62,11 @@ class _KdDesc(ctypes.Structure):
                                                  "refs", "seg")]
 
 
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_int32), ("ray_stride", ctypes.c_int32), ("n", ctypes.c_int64)] + [
+        (k, ctypes.c_void_p) for k in ("d_ox", "d_oy", "d_dx", "d_dy", "d_start_tri", "d_hit_seg", "d_t", "d_steps")]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in ("rays", "steps", "side_tests", "exact_fallbacks", "invalid_rays",
                                                "walk_limit_rays", "located", "locate_steps")]
@@ -94,6 +99,20 @@ def lib() -> ctypes.CDLL:
     L.cct_scene_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     L.cct_scene_get_tuning.restype = ctypes.c_int
     L.cct_scene_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    L.cct_batch_create.restype = ctypes.c_int
+    L.cct_batch_create.argtypes = [ctypes.POINTER(vp), i32, i32, u32, ctypes.POINTER(vp)]
+    L.cct_batch_free.restype = ctypes.c_int
+    L.cct_batch_free.argtypes = [vp]
+    L.cct_batch_set_tuning.restype = ctypes.c_int
+    L.cct_batch_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    L.cct_batch_stage.restype = ctypes.c_int
+    L.cct_batch_stage.argtypes = [vp, ctypes.POINTER(_BatchItem), i32]
+    L.cct_batch_enqueue.restype = ctypes.c_int
+    L.cct_batch_enqueue.argtypes = [vp, vp]
+    L.cct_batch_get_stats.restype = ctypes.c_int
+    L.cct_batch_get_stats.argtypes = [vp, ctypes.POINTER(_Stats), ctypes.c_int, vp]
+    L.cct_trace_batched.restype = ctypes.c_int
+    L.cct_trace_batched.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(_BatchItem), i32, u32, vp]
     L.cct_bvh_load.restype = ctypes.c_int
     L.cct_bvh_load.argtypes = [ctypes.POINTER(_BvhDesc), vp, ctypes.POINTER(vp)]
     L.cct_bvh_free.restype = ctypes.c_int
@@ -411,3 +430,109 @@ class KdTree:
             self.free()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------- many scenes per launch
+def _items(items):
+    """items: sequence of (scene_index, ox, oy, dx, dy, start | None, hit, t, steps) with CUDA tensors."""
+    import torch
+
+    arr = (_BatchItem * max(1, len(items)))()
+    for k, (sc, ox, oy, dx, dy, st, hit, t, steps) in enumerate(items):
+        arr[k] = _BatchItem(int(sc), 0, int(ox.numel()), _dev(ox, torch.int32, "ox"), _dev(oy, torch.int32, "oy"),
+                            _dev(dx, torch.float32, "dx"), _dev(dy, torch.float32, "dy"),
+                            _dev(st, torch.int32, "start"), _dev(hit, torch.int32, "hit"),
+                            _dev(t, torch.float32, "t"), _dev(steps, torch.int32, "steps"))
+    return arr
+
+
+def cct_trace_batched(scenes, items, flags: int = 0, stream=None) -> None:
+    """One-shot batched trace (synchronises the stream): scenes = handles or Scene
+    objects; items as in Batch.stage."""
+    hs = [s.handle if isinstance(s, Scene) else s for s in scenes]
+    harr = (ctypes.c_void_p * len(hs))(*hs)
+    arr = _items(items)
+    _check(lib().cct_trace_batched(harr, len(hs), arr, len(items), flags, _stream_ptr(stream)), "cct_trace_batched")
+
+
+class Batch:
+    """A reusable multi-scene launch (include/cct.h, cct_batch_*): stage a work
+    list on the host, enqueue (or replay a captured CUDA graph of the enqueue)."""
+
+    def __init__(self, scenes, max_items: int, flags: int = 0):
+        hs = [s.handle if isinstance(s, Scene) else s for s in scenes]
+        self._harr = (ctypes.c_void_p * len(hs))(*hs)
+        h = ctypes.c_void_p()
+        _check(lib().cct_batch_create(self._harr, len(hs), int(max_items), flags, ctypes.byref(h)), "cct_batch_create")
+        self.handle = h.value
+        self._keep = None
+        self.graph = None
+
+    def set_tuning(self, tuning=None):
+        if tuning is None:
+            _check(lib().cct_batch_set_tuning(ctypes.c_void_p(self.handle), None), "cct_batch_set_tuning")
+            return
+        tu = Tuning(256, 8, 128, -1, 0)
+        for k, v in dict(tuning).items():
+            setattr(tu, k, int(v))
+        _check(lib().cct_batch_set_tuning(ctypes.c_void_p(self.handle), ctypes.byref(tu)), "cct_batch_set_tuning")
+
+    def stage(self, items):
+        arr = _items(items)
+        _check(lib().cct_batch_stage(ctypes.c_void_p(self.handle), arr, len(items)), "cct_batch_stage")
+        self._keep = items  # the tensors must outlive the launch
+
+    def stage_raw(self, items, ray_stride: int = 1):
+        """items: (scene, n, ox, oy, dx, dy, start, hit, t, steps) with raw device
+        addresses (ints, start may be 0 for none); ray_stride 4 for interleaved
+        ray records.  The caller keeps the memory alive."""
+        arr = (_BatchItem * max(1, len(items)))()
+        for k, it in enumerate(items):
+            arr[k] = _BatchItem(int(it[0]), int(ray_stride), int(it[1]),
+                                *[ctypes.c_void_p(x) if x else None for x in it[2:]])
+        _check(lib().cct_batch_stage(ctypes.c_void_p(self.handle), arr, len(items)), "cct_batch_stage")
+
+    def enqueue(self, stream=None):
+        _check(lib().cct_batch_enqueue(ctypes.c_void_p(self.handle), _stream_ptr(stream)), "cct_batch_enqueue")
+
+    def capture(self):
+        """Captures one enqueue in a CUDA graph (stage something first); replay()
+        then re-runs it with whatever is staged at that time."""
+        import torch
+
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.enqueue(s)  # warm-up launch outside the capture
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            self.enqueue()
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def stats(self, reset: bool = False, stream=None) -> dict:
+        st = _Stats()
+        _check(lib().cct_batch_get_stats(ctypes.c_void_p(self.handle), ctypes.byref(st), 1 if reset else 0,
+                                         _stream_ptr(stream)), "cct_batch_get_stats")
+        return {k: int(getattr(st, k)) for k, _ in _Stats._fields_}
+
+    def free(self):
+        if self.handle:
+            self.graph = None
+            cct_batch_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def cct_batch_free(h: int) -> None:
+    _check(lib().cct_batch_free(ctypes.c_void_p(h)), "cct_batch_free")

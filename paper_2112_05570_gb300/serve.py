@@ -1,0 +1,315 @@
+"""Continuous-batching request server over device-resident scenes.
+
+Host orchestration of the batched walk (cct_batch_*, include/cct.h): no
+counterpart in the paper, whose Sec. 5 traces rays one query at a time.
+
+Requests (scene, n rays) arrive on an open-loop schedule.  Each tick:
+  1. arrivals join the pending queue;
+  2. admission: pending requests are admitted in arrival order while the
+     device-memory budget (28 bytes per ray: rays in, results out) has room;
+     an admitted request's rays are copied to the device on the copy stream;
+  3. every admitted request whose upload has finished and that is not yet on
+     the GPU joins this tick's work list; the list is staged into one of two
+     alternating cct_batch objects and launched by replaying that batch's
+     captured CUDA graph on the compute stream -- requests that arrive while
+     others are on the GPU are admitted into the next tick, so work from
+     different ticks overlaps on the device;
+  4. finished ticks copy their results back on the copy stream; a request is
+     done when its results are on the host, and its memory returns to the
+     budget.
+Latency of a request = its results on the host - its arrival.  The same loop
+with one plain cct_trace launch per request gives the unbatched comparison.
+"""
+from __future__ import annotations
+
+import collections
+import ctypes
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import cct
+
+BYTES_PER_RAY = 28  # ox, oy, dx, dy (16 B) + hit, t, steps (12 B)
+
+
+@dataclass
+class Request:
+    rid: int
+    scene: int
+    n: int
+    arrival: float          # seconds, relative to the start of the run
+    src: list               # pinned host slices of the scene's pool (wrapping around): ((k, 4) records, (4, k) arrays)
+    out: object = None      # pinned host (3, n) view: hit, t bits, steps, filled on completion
+    admitted: float = -1.0
+    done: float = -1.0
+    dev: object = None      # device int32 buffer of 7 n words while in flight: rays (n, 4), then results (3, n)
+    upload: object = None   # CUDA event: rays on the device
+    tick: int = -1
+
+
+@dataclass
+class ServeResult:
+    completed: int
+    offered: int
+    rays_completed: int
+    wall_s: float
+    latency_s: np.ndarray = field(repr=False)
+    queue_depth_end: int = 0
+    ticks: int = 0
+
+    @property
+    def p50_ms(self):
+        return float(np.percentile(self.latency_s, 50) * 1e3) if self.latency_s.size else float("nan")
+
+    @property
+    def p99_ms(self):
+        return float(np.percentile(self.latency_s, 99) * 1e3) if self.latency_s.size else float("nan")
+
+    @property
+    def rays_per_s(self):
+        return self.rays_completed / self.wall_s if self.wall_s > 0 else 0.0
+
+    def as_dict(self):
+        return {"completed": self.completed, "offered": self.offered, "rays_completed": self.rays_completed,
+                "wall_s": self.wall_s, "p50_ms": self.p50_ms, "p99_ms": self.p99_ms, "rays_per_s": self.rays_per_s,
+                "queue_depth_end": self.queue_depth_end, "ticks": self.ticks}
+
+
+def poisson_schedule(rate_hz: float, duration_s: float, n_scenes: int, min_rays: int, max_rays: int, seed: int):
+    """Open-loop arrivals: exponential gaps of mean 1/rate, a uniform scene and a
+    log-uniform ray count per request."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t >= duration_s:
+            break
+        n = int(np.exp(rng.uniform(np.log(min_rays), np.log(max_rays))))
+        out.append((t, int(rng.integers(0, n_scenes)), n))
+    return out
+
+
+class RayPool:
+    """Per scene, one pinned host pool of rays as interleaved 16-byte records
+    (ox, oy, dx bits, dy bits: an (m, 4) int32 array); a request takes
+    contiguous slices of it (wrapping around), and its results land in a
+    contiguous region of a pinned 1-D result ring (3 n int32: hit, t bits,
+    steps)."""
+
+    def __init__(self, rays_per_scene, capacity_out: int):
+        import torch
+
+        self.src, self.soa = [], []
+        for r in rays_per_scene:
+            a = np.stack([r.ox.astype(np.int32), r.oy.astype(np.int32), r.dx.view(np.int32), r.dy.view(np.int32)], 1)
+            self.src.append(torch.from_numpy(np.ascontiguousarray(a)).pin_memory())
+            # the same rays as four separate arrays (the layout cct_trace takes)
+            self.soa.append(torch.from_numpy(np.ascontiguousarray(a.T)).pin_memory())
+        self.n = [int(r.ox.shape[0]) for r in rays_per_scene]
+        self.out = torch.empty(3 * capacity_out, dtype=torch.int32).pin_memory()
+        self.out_cap = capacity_out
+        self.out_pos = 0
+
+    def take(self, scene: int, n: int, rng):
+        """n rays of `scene`: a list of (k, 4) pool slices (wrapping around the
+        pool when n exceeds it), and a (3, n') view of the result ring (n' = n,
+        or the ring's capacity if smaller)."""
+        m = self.n[scene]
+        lo = int(rng.integers(0, m))
+        parts, left, pos = [], n, lo
+        while left > 0:
+            k = min(left, m - pos)
+            parts.append((self.src[scene][pos:pos + k], self.soa[scene][:, pos:pos + k]))
+            left -= k
+            pos = 0
+        n_out = min(n, self.out_cap)
+        if self.out_pos + n_out > self.out_cap:
+            self.out_pos = 0
+        out = self.out[3 * self.out_pos:3 * (self.out_pos + n_out)].view(3, n_out)
+        self.out_pos += n_out
+        return parts, out, lo
+
+
+class Server:
+    """The continuous-batching loop over loaded cct.Scene objects."""
+
+    def __init__(self, scenes, budget_bytes: int, max_items: int = 4096, flags: int = 0, use_graph: bool = True,
+                 tuning: dict | None = None):
+        import torch
+
+        self.torch = torch
+        self.scenes = scenes
+        self.budget = int(budget_bytes)
+        self.flags = flags
+        self.max_items = max_items
+        self.batches = [cct.Batch(scenes, max_items, flags) for _ in range(2)]
+        if tuning:
+            for b in self.batches:
+                b.set_tuning(tuning)
+        self.compute = torch.cuda.Stream()
+        self.copy = torch.cuda.Stream()
+        self.use_graph = use_graph
+        self._graphs_ready = False
+
+    def _capture(self, probe):
+        torch = self.torch
+        for b in self.batches:
+            b.stage_raw([probe], ray_stride=4)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(self.compute):
+                b.enqueue(self.compute)  # warm-up outside capture
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=self.compute):
+                b.enqueue()
+            b.graph = g
+        torch.cuda.synchronize()
+        self._graphs_ready = True
+
+    def _alloc(self, n: int):
+        return self.torch.empty(7 * n, dtype=self.torch.int32, device="cuda")
+
+    @staticmethod
+    def _item(r, interleaved: bool = True):
+        """(scene, n, ox, oy, dx, dy, start, hit, t, steps) raw addresses of a
+        request: the rays (interleaved records, or four arrays), then the three
+        result rows."""
+        base, res, n = r.dev.data_ptr(), r.dev.data_ptr() + 16 * r.n, r.n
+        if interleaved:
+            return (r.scene, n, base, base + 4, base + 8, base + 12, 0, res, res + 4 * n, res + 8 * n)
+        return (r.scene, n, base, base + 4 * n, base + 8 * n, base + 12 * n, 0, res, res + 4 * n, res + 8 * n)
+
+    def run(self, schedule, pool: RayPool, batched: bool = True, seed: int = 0, drain: bool = True,
+            max_wall_s: float | None = None, keep_requests: bool = False):
+        """Serves the (arrival, scene, n) schedule; returns a ServeResult (and the
+        requests when keep_requests)."""
+        torch = self.torch
+        rng = np.random.default_rng(seed)
+        reqs = []
+        for k, (t, sc, n) in enumerate(schedule):
+            parts, out, _ = pool.take(sc, n, rng)
+            reqs.append(Request(k, sc, int(n), t, parts, out))
+        if batched and self.use_graph and not self._graphs_ready and reqs:
+            probe = Request(-1, reqs[0].scene, 1, 0.0, [(reqs[0].src[0][0][:1], None)])
+            probe.dev = self._alloc(1)
+            probe.dev[:4].copy_(probe.src[0][0].reshape(-1))
+            self._capture_item = self._item(probe)
+            self._capture(self._capture_item)
+            self._probe = probe
+        pending = collections.deque()
+        admitted = collections.deque()   # uploading
+        ticks_in_flight = collections.deque()  # (event, batch index, requests)
+        downloads = collections.deque()  # (event, requests)
+        used = 0
+        nxt = 0
+        done_lat, done_rays = [], 0
+        free_batch = [True, True]
+        tick = 0
+        start = time.perf_counter()
+        deadline = None if max_wall_s is None else start + max_wall_s
+        horizon = schedule[-1][0] if schedule else 0.0
+        while True:
+            now = time.perf_counter() - start
+            while nxt < len(reqs) and reqs[nxt].arrival <= now:
+                pending.append(reqs[nxt])
+                nxt += 1
+            # admission by memory budget, in arrival order
+            while pending and used + BYTES_PER_RAY * pending[0].n <= self.budget:
+                r = pending.popleft()
+                used += BYTES_PER_RAY * r.n
+                r.admitted = now
+                r.dev = self._alloc(r.n)
+                with torch.cuda.stream(self.copy):
+                    off = 0
+                    for aos, soa in r.src:
+                        k = int(aos.shape[0])
+                        if batched:  # interleaved records: one contiguous copy
+                            r.dev[4 * off:4 * (off + k)].copy_(aos.reshape(-1), non_blocking=True)
+                        else:  # four arrays
+                            for q in range(4):
+                                r.dev[q * r.n + off:q * r.n + off + k].copy_(soa[q], non_blocking=True)
+                        off += k
+                    r.upload = torch.cuda.Event()
+                    r.upload.record(self.copy)
+                admitted.append(r)
+            # completed downloads
+            while downloads and downloads[0][0].query():
+                _, rs = downloads.popleft()
+                t_done = time.perf_counter() - start
+                for r in rs:
+                    r.done = t_done
+                    done_lat.append(t_done - r.arrival)
+                    done_rays += r.n
+                    used -= BYTES_PER_RAY * r.n
+                    r.dev = None
+            # finished ticks -> download their results
+            while ticks_in_flight and ticks_in_flight[0][0].query():
+                ev, bi, rs = ticks_in_flight.popleft()
+                free_batch[bi] = True
+                with torch.cuda.stream(self.copy):
+                    self.copy.wait_event(ev)
+                    for r in rs:
+                        m = r.out.shape[1]
+                        res = r.dev[4 * r.n:].view(3, r.n)
+                        if m == r.n:
+                            r.out.view(-1).copy_(r.dev[4 * r.n:], non_blocking=True)
+                        else:
+                            r.out.copy_(res[:, :m], non_blocking=True)
+                    dev = torch.cuda.Event()
+                    dev.record(self.copy)
+                downloads.append((dev, rs))
+            # a tick: every uploaded request
+            ready = []
+            while admitted and admitted[0].upload.query() and len(ready) < self.max_items:
+                ready.append(admitted.popleft())
+            if ready:
+                if batched:
+                    bi = 0 if free_batch[0] else (1 if free_batch[1] else -1)
+                    if bi < 0:
+                        for r in reversed(ready):
+                            admitted.appendleft(r)
+                        ready = []
+                    else:
+                        b = self.batches[bi]
+                        b.stage_raw([self._item(r) for r in ready], ray_stride=4)
+                        with torch.cuda.stream(self.compute):
+                            if self.use_graph:
+                                b.graph.replay()
+                            else:
+                                b.enqueue(self.compute)
+                            ev = torch.cuda.Event()
+                            ev.record(self.compute)
+                        free_batch[bi] = False
+                        ticks_in_flight.append((ev, bi, ready))
+                        tick += 1
+                else:
+                    L = cct.lib()
+                    sp = cct._stream_ptr(self.compute)
+                    with torch.cuda.stream(self.compute):
+                        for r in ready:
+                            it = [ctypes.c_void_p(x) if x else None for x in self._item(r, interleaved=False)[2:]]
+                            rc = L.cct_trace(ctypes.c_void_p(self.scenes[r.scene].handle), *it[:5], r.n, *it[5:],
+                                             self.flags, sp)
+                            if rc != cct.CCT_OK:
+                                raise cct.CctError(rc, "cct_trace")
+                        ev = torch.cuda.Event()
+                        ev.record(self.compute)
+                    ticks_in_flight.append((ev, 0, ready))
+                    free_batch[0] = True
+                    tick += 1
+            finished = nxt >= len(reqs) and not pending and not admitted and not ticks_in_flight and not downloads
+            if finished:
+                break
+            t_now = time.perf_counter()
+            if not drain and (t_now - start) > horizon:
+                break
+            if deadline is not None and t_now > deadline:
+                break
+            if not ready and not (downloads and downloads[0][0].query()):
+                time.sleep(0.0002)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - start
+        res = ServeResult(len(done_lat), len(reqs), done_rays, wall, np.asarray(done_lat),
+                          len(pending) + len(admitted), tick)
+        return (res, reqs) if keep_requests else res
