@@ -229,6 +229,163 @@ def comparison_structures(torch, cct, sg, sc, dev, stream, n_timed):
     return out
 
 
+# ---------------------------------------------------------------------------------------------- configs 3-5
+def _parallel(fn, items, workers=None):
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(max_workers=workers or (os.cpu_count() or 1)) as ex:
+        return list(ex.map(fn, items))
+
+
+def config4_scenes(n_scenes=512, seed=4, pool_rays=0):
+    """512 config-1-generator scenes, segment counts log-uniform over 100-200,000
+    (lengths scaled by sqrt(200/N)), annealed (one sweep); rays per scene
+    log-uniform over 1k-1M; optional extra ray pools for the server."""
+    import scenegen as sg
+
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(100), np.log(200_000), n_scenes)).astype(int)
+    nr = np.exp(rng.uniform(np.log(1_000), np.log(1_000_000), n_scenes)).astype(int)
+
+    def build(k):
+        segs = sg.random_segments(int(ns[k]), 1000 + k)
+        tri = sg.anneal(sg.cdt(segs), k, sweeps=1)
+        r = sg.rays_isotropic(tri, int(nr[k]), 2000 + k, threads=1)
+        pool = sg.rays_isotropic(tri, pool_rays, 3000 + k, threads=1) if pool_rays else None
+        return segs, tri, r, pool
+
+    return _parallel(build, range(n_scenes))
+
+
+def run_config4(args, torch, cct, sg, dev):
+    from paper_2112_05570_gb300 import autotune
+
+    t0 = time.perf_counter()
+    work = config4_scenes()
+    build_s = time.perf_counter() - t0
+    scenes = [cct.Scene.from_triangulation(tri, sg.D) for segs, tri, r, _ in work]
+    stream = torch.cuda.current_stream(dev)
+    items = []
+    for k, (segs, tri, r, _) in enumerate(work):
+        n = len(r)
+        items.append((k, torch.from_numpy(r.ox).to(dev), torch.from_numpy(r.oy).to(dev),
+                      torch.from_numpy(r.dx).to(dev), torch.from_numpy(r.dy).to(dev), None,
+                      torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.float32, device=dev),
+                      torch.empty(n, dtype=torch.int32, device=dev)))
+    total = sum(len(w[2]) for w in work)
+    out = {}
+    for name, flags in (("filtered", 0), ("exact", cct.CCT_TRACE_EXACT_ONLY)):
+        b = cct.Batch(scenes, len(items), flags)
+        tune = autotune.tune_batch(b, items)
+        b.capture()
+        for _ in range(args.warmup):
+            b.replay()
+        b.stats(reset=True)
+        ms = _time_loop(torch, dev, stream, b.replay, args.steps)
+        st = b.stats(reset=True)
+        out[name] = {"rays_per_s": total / (ms * 1e-3), "ms_per_launch": ms, "tuning": tune["tuning"],
+                     "steps_per_ray": st["steps"] / max(1, st["rays"]),
+                     "fallback_rate": st["exact_fallbacks"] / max(1, st["side_tests"])}
+        b.free()
+
+    def plain():
+        for it in items:
+            cct.cct_trace(scenes[it[0]].handle, *it[1:5], None, *it[6:9], 0, stream)
+
+    plain()
+    ms_plain = _time_loop(torch, dev, stream, plain, max(2, args.steps // 2))
+    line = {"metric": "closest-hit rays/s (batched multi-scene)", "value": out["filtered"]["rays_per_s"],
+            "unit": "rays/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["filtered"]["ms_per_launch"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64+fp32-filter", "data": "synthetic",
+            "config": {"workload": "config4-512-scenes-100..200k-segments-1k..1M-rays", "scenes": len(scenes),
+                       "segments_total": int(sum(w[0].shape[0] for w in work)),
+                       "triangles_total": int(sum(w[1].n_tri for w in work)), "rays_per_step": total,
+                       "table_bytes_total": int(sum(w[1].n_tri for w in work)) * 32,
+                       "build_s": build_s, "launch": "one persistent batched kernel, CUDA-graph replay"},
+            "batched": out, "plain_512_launches": {"rays_per_s": total / (ms_plain * 1e-3), "ms": ms_plain},
+            "gpu_launches": args.steps}
+    print(json.dumps(line))
+    return work, scenes, out
+
+
+def run_config5(args, torch, cct, sg, dev):
+    from paper_2112_05570_gb300 import serve
+
+    t0 = time.perf_counter()
+    work = config4_scenes(pool_rays=1 << 18)
+    build_s = time.perf_counter() - t0
+    scenes = [cct.Scene.from_triangulation(tri, sg.D) for segs, tri, r, pool in work]
+    pool = serve.RayPool([w[3] for w in work], capacity_out=1 << 26)
+    mean_rays = (4_000_000 - 1_000) / np.log(4_000_000 / 1_000)
+    srv = serve.Server(scenes, budget_bytes=60 << 30, max_items=4096)
+    # capacity: a saturated, fully staged burst through the same server
+    burst = [(0.0, int(k % len(scenes)), 1 << 20) for k in range(64)]
+    srv.run(burst, pool, batched=True, seed=1)
+    res_cap = srv.run(burst, pool, batched=True, seed=2)
+    capacity = res_cap.rays_per_s
+    runs = {}
+    nominal = serve.poisson_schedule(20_000.0, 2.0, len(scenes), 1_000, 4_000_000, seed=5)
+    runs["nominal_20k_req_s"] = srv.run(nominal, pool, batched=True, seed=6, drain=False,
+                                        max_wall_s=6.0).as_dict()
+    rate = 0.6 * capacity / mean_rays
+    sust = serve.poisson_schedule(rate, 3.0, len(scenes), 1_000, 4_000_000, seed=7)
+    runs["sustainable_batched"] = srv.run(sust, pool, batched=True, seed=8).as_dict()
+    runs["sustainable_plain_per_request"] = srv.run(sust, pool, batched=False, seed=8).as_dict()
+    r = runs["sustainable_batched"]
+    line = {"metric": "p50/p99 request latency (continuous batching)", "value": r["p99_ms"], "unit": "ms",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": r["wall_s"] * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64+fp32-filter", "data": "synthetic",
+            "config": {"workload": "config5-poisson-512-scenes-1k..4M-rays-60GB", "build_s": build_s,
+                       "offered_nominal_rays_per_s": 20_000 * mean_rays, "capacity_rays_per_s": capacity,
+                       "sustainable_rate_req_s": rate},
+            "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "rays_per_s": r["rays_per_s"], "runs": runs}
+    print(json.dumps(line))
+
+
+def run_config3(args, torch, cct, sg, dev):
+    """Ring of circles, N = 1e3 .. 1e6 in a fixed domain; 2^26 isotropic rays and
+    4096 pinhole fans of 4096 rays; start cells from the GPU locate."""
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    for N in (1_000, 10_000, 100_000, 1_000_000):
+        t0 = time.perf_counter()
+        segs = sg.ring_of_circles(N)
+        cdt, ref, tri = sg.pipeline(segs, 3, sweeps=1)
+        iso = sg.rays_isotropic(tri, 1 << 26, 11)
+        fan = sg.rays_pinhole(tri, 4096, 4096, 12)
+        build_s = time.perf_counter() - t0
+        scene = cct.Scene.from_triangulation(tri, sg.D)
+        res = {"segments": int(segs.shape[0]), "triangles": tri.n_tri, "build_s": build_s,
+               "refine_params": list(ref.refine_params), "length_annealed_over_cdt": tri.length(True) / cdt.length(True)}
+        for name, r in (("incoherent", iso), ("coherent", fan)):
+            n = len(r)
+            d = [torch.from_numpy(getattr(r, k)).to(dev) for k in ("ox", "oy", "dx", "dy")]
+            h = torch.empty(n, dtype=torch.int32, device=dev)
+            t = torch.empty(n, dtype=torch.float32, device=dev)
+            s = torch.empty(n, dtype=torch.int32, device=dev)
+            for label, flags in (("plain", 0), ("binned", cct.CCT_TRACE_BIN)):
+                cct.cct_trace(scene.handle, *d, None, h, t, s, flags, stream)
+                scene.stats(reset=True)
+                ms = _time_loop(torch, dev, stream, lambda: cct.cct_trace(scene.handle, *d, None, h, t, s, flags,
+                                                                           stream), 3)
+                st = scene.stats(reset=True)
+                res[f"{name}_{label}"] = {"rays": n, "rays_per_s": n / (ms * 1e-3), "ms": ms,
+                                          "steps_per_ray": st["steps"] / max(1, st["rays"]),
+                                          "locate_steps_per_ray": st["locate_steps"] / max(1, st["located"]),
+                                          "invalid": st["invalid_rays"] / 3}
+            del d, h, t, s
+        scene.free()
+        out[str(N)] = res
+        torch.cuda.empty_cache()
+    line = {"metric": "closest-hit rays/s and steps/ray vs N", "value": out["1000000"]["incoherent_plain"]["rays_per_s"],
+            "unit": "rays/s", "n_gpus": 1, "steps": 3, "warmup": 1, "ms_per_step": out["1000000"]["incoherent_plain"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+fp32-filter",
+            "data": "synthetic", "config": {"workload": "config3-ring-of-circles-1e3..1e6-2^26-iso-2^24-fans"},
+            "by_n": out}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -237,9 +394,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--flags", default="auto", help="auto | plain | bin")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="2", choices=["2", "3", "4", "5"],
+                    help="2 (default): the six config-2 scene families; 3: scaling in N; 4: 512 scenes in one "
+                         "batched launch; 5: the continuous-batching server")
     ap.add_argument("--profile", action="store_true",
-                    help="profiling mode: per scene, 2 warm-up walk launches then 1 walk launch (start cells "
-                         "given); no timing, no JSON")
+                    help="profiling mode: per scene, 2 warm-up traces, then one trace with start cells given and "
+                         "one with the fused locate; no timing, no JSON")
+    ap.add_argument("--families", default=",".join(FAMILIES),
+                    help="comma-separated scene families (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -263,7 +425,12 @@ def main():
     _build.build()
     import scenegen as sg
 
-    work = build_workload(with_refined=True)
+    if args.config != "2":
+        fn = {"3": run_config3, "4": run_config4, "5": run_config5}[args.config]
+        fn(args, torch, cct, sg, dev)
+        return 0
+    fams = tuple(f for f in args.families.split(",") if f) if args.profile else FAMILIES
+    work = build_workload(families=fams, with_refined=True)
     stream = torch.cuda.current_stream(dev)
     n = N_RAYS
     hit = torch.empty(n, dtype=torch.int32, device=dev)
@@ -282,8 +449,10 @@ def main():
 
     if args.profile:
         for sc in scenes:
-            for _ in range(3):
+            for _ in range(2):
                 trace(sc, sc["d"]["start"], 0)
+            trace(sc, sc["d"]["start"], 0)
+            trace(sc, None, 0)
         torch.cuda.synchronize(dev)
         return 0
 
