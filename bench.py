@@ -448,12 +448,22 @@ def main():
                       stream if s is None else s)
 
     if args.profile:
+        # per scene: 2 warm-up traces, then start cells given / fused locate, each
+        # with the fp32 filter and exact-only; CUDA-event times of 3 more of each
+        ex = cct.CCT_TRACE_EXACT_ONLY
+        variants = (("given", "start", 0), ("given_exact", "start", ex), ("locate", None, 0), ("locate_exact", None, ex))
+        times = {}
         for sc in scenes:
             for _ in range(2):
                 trace(sc, sc["d"]["start"], 0)
-            trace(sc, sc["d"]["start"], 0)
-            trace(sc, None, 0)
+            for name, st, fl in variants:
+                trace(sc, sc["d"][st] if st else None, fl)
         torch.cuda.synchronize(dev)
+        for sc in scenes:
+            for name, st, fl in variants:
+                times[f"{sc['name']}/{name}"] = _time_loop(
+                    torch, dev, stream, lambda st=st, fl=fl: trace(sc, sc["d"][st] if st else None, fl), 3)
+        print(json.dumps({"profile_ms": times}))
         return 0
 
     def step(flags):

@@ -58,6 +58,26 @@ __device__ __forceinline__ int find_item(const BatchItemDev* items, int n_items,
   return lo;
 }
 
+__device__ __forceinline__ void batch_complete(const BatchItemDev& it, const TriRec* __restrict__ rec, int T, int e,
+                                               int st, int ox, int oy, int kx, int ky, int idx) {
+  int32_t h = -1;
+  float t = __int_as_float(0x7fc00000);
+  if (st > 0) {
+    const TriRec r = load_rec(rec + T);
+    const int32_t w = nb_of(r, e);
+    if (w <= -2) {
+      h = -2 - w;
+      const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
+      t = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), ox, oy, kx, ky);
+    } else {
+      t = __int_as_float(0x7f800000);
+    }
+  }
+  it.hit[idx] = h;
+  it.t[idx] = t;
+  it.steps[idx] = st;
+}
+
 template <bool kExact>
 __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev* __restrict__ scenes,
                                                                  const BatchHeader* __restrict__ hdr,
@@ -71,8 +91,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
   // warp-uniform pool: a range of rays of one item
   int p_item = -1, p_next = 0, p_end = 0;
   bool exhausted = n_items <= 0;
-  // lane state
-  bool active = false;
+  // lane state: walking (active), finished with a parked result (done), or idle
+  bool active = false, done = false;
   int mode = 1, item = 0, idx = 0, ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0, lsteps = 0;
   int px3 = 0, py3 = 0, max_steps = 0, scene = 0;
   float fdx = 0.f, fdy = 0.f;
@@ -84,6 +104,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
       const unsigned need = __ballot_sync(FULL, !active);
       if (need == 0u) break;
       if (__popc(need) < refill_min && need != FULL) break;
+      if (done) {
+        batch_complete(items[item], rec, T, j, nsteps, ox, oy, kx, ky, idx);
+        done = false;
+      }
       if (p_next >= p_end) {
         int c = 0;
         if (lane == 0) c = (int)atomicAdd(counter, 1ull);
@@ -116,10 +140,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
         int s = -1;
         if (it.start == nullptr) {
           if (ok && ox >= 0 && oy >= 0 && ox <= S.D && oy <= S.D) {
-            const int G = S.G;
-            const int ix = min(G - 1, (int)((long long)ox * G / S.D));
-            const int iy = min(G - 1, (int)((long long)oy * G / S.D));
-            const SeedCell sd = S.seeds[iy * G + ix];
+            const SeedCell sd = S.seeds[seed_cell(S, ox, oy)];
             px3 = sd.px3;
             py3 = sd.py3;
             s = sd.tri;
@@ -136,6 +157,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
           ok = ok && s >= 0;
           mode = 1;
         }
+        ++c_rays;
         if (ok) {
           T = s;
           nsteps = 0;
@@ -145,7 +167,6 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
           it.t[idx] = __int_as_float(0x7fc00000);
           it.steps[idx] = CCT_RAY_INVALID;
           ++c_inv;
-          ++c_rays;
         }
       }
       p_next += min(__popc(need), avail);
@@ -156,9 +177,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
     }
     if (active) {
       const TriRec r = load_rec(rec + T);
-      bool done = false;
-      int32_t res_hit = -1, res_steps = CCT_RAY_INVALID;
-      float res_t = __int_as_float(0x7fc00000);
+      int status = 0;
       bool advance = true;
       if (mode == 0) {
         ++lsteps;
@@ -166,15 +185,16 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
         if (res > 0) {
           mode = 1;
           c_lsteps += (unsigned)lsteps;
-        } else if (res < 0 || lsteps > max_steps) {
-          done = true;
-          ++c_inv;
-          c_lsteps += (unsigned)lsteps;
         } else {
           advance = false;
+          if (res < 0 || lsteps > max_steps) {
+            status = CCT_RAY_INVALID;
+            ++c_inv;
+            c_lsteps += (unsigned)lsteps;
+          }
         }
       }
-      if (!done && advance) {
+      if (advance) {
         int e;
         if (mode == 1) {
           const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
@@ -188,7 +208,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
           e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
           mode = 2;
           if (!inside) {
-            done = true;
+            status = CCT_RAY_INVALID;
             ++c_inv;
           }
         } else {
@@ -196,42 +216,32 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
           ++c_side;
           e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
         }
-        if (!done) {
+        if (status == 0) {
           ++nsteps;
           const int32_t w = nb_of(r, e);
           if (w >= 0) {
             if (nsteps >= max_steps) {
-              done = true;
-              res_steps = CCT_RAY_WALK_LIMIT;
+              status = CCT_RAY_WALK_LIMIT;
               ++c_lim;
             } else {
               T = w >> 2;
               j = w & 3;
             }
           } else {
-            done = true;
-            res_steps = nsteps;
+            status = nsteps;
+            j = e;
             c_steps += (unsigned)nsteps;
-            if (w <= -2) {
-              res_hit = -2 - w;
-              const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
-              res_t = hit_param(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), ox, oy, kx, ky);
-            } else {
-              res_t = __int_as_float(0x7f800000);
-            }
           }
         }
       }
-      if (done) {
-        const BatchItemDev& it = items[item];
-        it.hit[idx] = res_hit;
-        it.t[idx] = res_t;
-        it.steps[idx] = res_steps;
-        ++c_rays;
+      if (status != 0) {
+        nsteps = status;
         active = false;
+        done = true;
       }
     }
   }
+  if (done) batch_complete(items[item], rec, T, j, nsteps, ox, oy, kx, ky, idx);
   const unsigned long long w_steps = warp_sum((unsigned long long)c_steps);
   const unsigned long long w_side = warp_sum((unsigned long long)c_side);
   const unsigned long long w_rays = warp_sum((unsigned long long)c_rays);

@@ -75,8 +75,16 @@ __device__ __forceinline__ TriRec load_rec(const TriRec* p) {
   return r;
 }
 
-__device__ __forceinline__ int vx_of(const TriRec& r, int i) { return (int)((r.X >> (kCoordBits * i)) & kCoordMask); }
-__device__ __forceinline__ int vy_of(const TriRec& r, int i) { return (int)((r.Y >> (kCoordBits * i)) & kCoordMask); }
+// Coordinate i (0..2) of a 3 x 21-bit packed word, with 32-bit funnel shifts
+// only (bits [0,21), [21,42) and [42,63) of the 64-bit word).
+__device__ __forceinline__ int coord_of(uint64_t w, int i) {
+  const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
+  const uint32_t a = i == 2 ? hi : lo;
+  const uint32_t sh = i == 0 ? 0u : (i == 1 ? 21u : 10u);
+  return (int)(__funnelshift_r(a, hi, sh) & (uint32_t)kCoordMask);
+}
+__device__ __forceinline__ int vx_of(const TriRec& r, int i) { return coord_of(r.X, i); }
+__device__ __forceinline__ int vy_of(const TriRec& r, int i) { return coord_of(r.Y, i); }
 
 __device__ __forceinline__ int32_t nb_of(const TriRec& r, int e) { return e == 0 ? r.nb[0] : (e == 1 ? r.nb[1] : r.nb[2]); }
 
@@ -113,6 +121,12 @@ __device__ __forceinline__ long long orient_ll(long long ax, long long ay, long 
   return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
 }
 
+// The same orientation for points of [0, 2^20]^2 (all differences fit in
+// int32): two widening 32 x 32 -> 64-bit multiplies.
+__device__ __forceinline__ long long orient_i(int ax, int ay, int bx, int by, int cx, int cy) {
+  return (long long)(bx - ax) * (cy - ay) - (long long)(by - ay) * (cx - ax);
+}
+
 // t of the crossing of the ray (o, k / 2^22) with the line of edge (a, b):
 // t = 2^22 num / den, num = cross(b - a, a - o), den = cross(b - a, k); fp32.
 __device__ __forceinline__ float hit_param(int ax, int ay, int bx, int by, int ox, int oy, int kx, int ky) {
@@ -124,6 +138,29 @@ __device__ __forceinline__ float hit_param(int ax, int ay, int bx, int by, int o
     den = -den;
   }
   return __fmul_rn(__fdiv_rn(__ll2float_rn(num), __ll2float_rn(den)), kDirScale);
+}
+
+// The same parameter with the fast reciprocal-based division (<= 2 ulp for
+// divisors in [2^-126, 2^126]; den <= 2^44 here): with the two conversions,
+// within 4 ulp of the exact rational.
+__device__ __forceinline__ float hit_param_fast(int ax, int ay, int bx, int by, int ox, int oy, int kx, int ky) {
+  const long long ex = bx - ax, ey = by - ay;
+  long long num = ex * (long long)(ay - oy) - ey * (long long)(ax - ox);
+  long long den = ex * (long long)ky - ey * (long long)kx;
+  if (den < 0) {
+    num = -num;
+    den = -den;
+  }
+  return __fdividef(__ll2float_rn(num), __ll2float_rn(den)) * kDirScale;
+}
+
+// Seed cell of an origin: any cell is correct (the locate walk finds the
+// triangle from any seed), so an fp32 scale suffices.
+__device__ __forceinline__ int seed_cell(const SceneDev& S, int ox, int oy) {
+  const float sc = (float)S.G / (float)S.D;
+  const int ix = min(S.G - 1, max(0, __float2int_rz((float)ox * sc)));
+  const int iy = min(S.G - 1, max(0, __float2int_rz((float)oy * sc)));
+  return iy * S.G + ix;
 }
 
 // One step of the Sec. 5.2 locate walk from the seed point p (kept as 3p)
@@ -140,9 +177,9 @@ __device__ __forceinline__ int locate_step(const SceneDev& S, const TriRec& r, i
   if (j == 3) {
     const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
     const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
-    const long long o0 = orient_ll(x1, y1, x2, y2, ox, oy);
-    const long long o1 = orient_ll(x2, y2, x0, y0, ox, oy);
-    const long long o2 = orient_ll(x0, y0, x1, y1, ox, oy);
+    const long long o0 = orient_i(x1, y1, x2, y2, ox, oy);
+    const long long o1 = orient_i(x2, y2, x0, y0, ox, oy);
+    const long long o2 = orient_i(x0, y0, x1, y1, ox, oy);
     if (o0 > 0 && o1 > 0 && o2 > 0) return 1;
     if (o0 >= 0 && o1 >= 0 && o2 >= 0) return -1;
     const bool s0 = (long long)qx * (3 * y0 - py3) - (long long)qy * (3 * x0 - px3) >= 0;
@@ -156,14 +193,14 @@ __device__ __forceinline__ int locate_step(const SceneDev& S, const TriRec& r, i
     const bool sc = (long long)qx * (3 * cy - py3) - (long long)qy * (3 * cx - px3) >= 0;
     e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
     const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
-    const long long oe = orient_ll(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), ox, oy);
+    const long long oe = orient_i(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), ox, oy);
     if (oe == 0) return -1;
     if (oe > 0) {
       // o lies before the exit edge: inside T unless on one of its other edges
       const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
       const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
-      const bool in = orient_ll(x1, y1, x2, y2, ox, oy) > 0 && orient_ll(x2, y2, x0, y0, ox, oy) > 0 &&
-                      orient_ll(x0, y0, x1, y1, ox, oy) > 0;
+      const bool in = orient_i(x1, y1, x2, y2, ox, oy) > 0 && orient_i(x2, y2, x0, y0, ox, oy) > 0 &&
+                      orient_i(x0, y0, x1, y1, ox, oy) > 0;
       return in ? 1 : -1;
     }
   }

@@ -24,6 +24,8 @@ namespace cct {
 
 enum : int { kModeLocate = 0, kModeFirst = 1, kModeWalk = 2 };
 enum : int { kSrcPlainUser = 0, kSrcPlainDev = 1, kSrcSorted = 2, kSrcLocate = 3 };
+// rare per-warp counters (shared memory)
+enum : int { kCntRays = 0, kCntFallback, kCntInvalid, kCntLimit, kCntLocated, kCntLocSteps, kRareCounters };
 
 constexpr int kWalkMaxThreads = 512;
 
@@ -31,6 +33,30 @@ struct WalkParams {
   int refill_min;  // serve idle lanes once this many are idle (or the whole warp is)
   int chunk;       // ray indices a warp takes from the global counter at once
 };
+
+// Writes the parked result of a finished lane: hit id and t come from its
+// final record (reloaded: it was read one iteration ago, so from L1/L2),
+// `st` is the step count or a negative per-ray status.
+__device__ __forceinline__ void complete_ray(const TriRec* __restrict__ rec, int T, int e, int st, int ox, int oy,
+                                             int kx, int ky, int idx, int32_t* __restrict__ hit_out,
+                                             float* __restrict__ t_out, int32_t* __restrict__ steps_out) {
+  int32_t h = -1;
+  float t = __int_as_float(0x7fc00000);  // NaN: invalid ray
+  if (st > 0) {
+    const TriRec r = load_rec(rec + T);
+    const int32_t w = nb_of(r, e);
+    if (w <= -2) {
+      h = -2 - w;
+      const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
+      t = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), ox, oy, kx, ky);
+    } else {
+      t = __int_as_float(0x7f800000);  // +inf: left through the hull
+    }
+  }
+  hit_out[idx] = h;
+  t_out[idx] = t;
+  steps_out[idx] = st;
+}
 
 template <bool kExact, int kSrc>
 __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySrc R, WalkParams P,
@@ -46,20 +72,32 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
   int pool_next = 0, pool_end = 0;
   bool exhausted = false;
 
-  bool active = false;
+  // lane state: walking (active), finished with a parked result (done), or idle;
+  // in locate mode nsteps counts locate steps
+  bool active = false, done = false;
   int mode = kModeFirst;
-  int idx = 0, ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0, lsteps = 0;
-  int px3 = 0, py3 = 0;  // locate seed point x 3 (kLocate)
+  int idx = 0, ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0;
   float fdx = 0.f, fdy = 0.f;
 
-  unsigned c_steps = 0, c_side = 0, c_fb = 0, c_rays = 0, c_inv = 0, c_lim = 0, c_loc = 0, c_lsteps = 0;
+  // hot counters in registers, rare ones per warp in shared memory
+  unsigned c_steps = 0, c_side = 0;
+  __shared__ unsigned s_cnt[kWalkMaxThreads / 32][kRareCounters];
+  unsigned* cnt = s_cnt[threadIdx.x >> 5];
+  if (lane < kRareCounters) cnt[lane] = 0;
+  __syncwarp();
 
   while (true) {
     // ---------------------------------------------------------------- serve idle lanes
+    // (also where finished lanes write their parked results: a batch of
+    // completions costs the warp one pass, not one per iteration)
     while (!exhausted) {
       const unsigned need = __ballot_sync(FULL, !active);
       if (need == 0u) break;
       if (__popc(need) < P.refill_min && need != FULL) break;
+      if (done) {
+        complete_ray(S.rec, T, j, nsteps, ox, oy, kx, ky, idx, hit_out, t_out, steps_out);
+        done = false;
+      }
       if (pool_next >= pool_end) {
         int base = 0;
         if (lane == 0) base = (int)atomicAdd(counter, (unsigned long long)P.chunk);
@@ -93,28 +131,23 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
             if (kSrc == kSrcPlainUser) s = (s >= 0 && s < S.n_tri) ? S.user2dev[s] : -1;
           }
         }
-        bool ok = dir_to_k(fdx, kx) && dir_to_k(fdy, ky) && (kx | ky) != 0;
+        // origins outside the domain lie in no triangle; rejecting them here
+        // keeps every coordinate difference of the walk within int32
+        bool ok = dir_to_k(fdx, kx) && dir_to_k(fdy, ky) && (kx | ky) != 0 && ox >= 0 && oy >= 0 && ox <= S.D &&
+                  oy <= S.D;
         if (kLocate) {
-          if (ok && ox >= 0 && oy >= 0 && ox <= S.D && oy <= S.D) {
-            const int G = S.G;
-            const int ix = min(G - 1, (int)((long long)ox * G / S.D));
-            const int iy = min(G - 1, (int)((long long)oy * G / S.D));
-            const SeedCell sd = S.seeds[iy * G + ix];
-            px3 = sd.px3;
-            py3 = sd.py3;
-            s = sd.tri;
+          if (ok) {
+            s = S.seeds[seed_cell(S, ox, oy)].tri;
             j = 3;
             mode = kModeLocate;
-            lsteps = 0;
-            ++c_loc;
-          } else {
-            ok = false;
+            atomicAdd(&cnt[kCntLocated], 1u);
           }
         } else {
           mode = kModeFirst;
           ok = ok && s >= 0 && s < S.n_tri;
         }
         if (kSrc == kSrcSorted) idx = R.orig[idx];
+        atomicAdd(&cnt[kCntRays], 1u);
         if (ok) {
           T = s;
           nsteps = 0;
@@ -123,8 +156,7 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
           hit_out[idx] = -1;
           t_out[idx] = __int_as_float(0x7fc00000);
           steps_out[idx] = CCT_RAY_INVALID;
-          ++c_inv;
-          ++c_rays;
+          atomicAdd(&cnt[kCntInvalid], 1u);
         }
       }
       pool_next += min(__popc(need), avail);
@@ -137,94 +169,89 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     // ---------------------------------------------------------------- one record per active lane
     if (active) {
       const TriRec r = load_rec(S.rec + T);
-      bool done = false;
-      int32_t res_hit = -1, res_steps = CCT_RAY_INVALID;
-      float res_t = __int_as_float(0x7fc00000);
+      int status = 0;  // 0 walking on, > 0 finished (steps), < 0 per-ray status
       bool advance = true;
       if (kLocate && mode == kModeLocate) {
         // Sec. 5.2: walk from the seed point towards the origin until the
-        // current triangle holds it (this triangle is then the start triangle)
-        ++lsteps;
-        const int res = locate_step(S, r, T, j, ox, oy, px3, py3);
-        if (res > 0) {
-          mode = kModeFirst;
-          c_lsteps += (unsigned)lsteps;
-        } else if (res < 0 || lsteps > S.max_steps) {
-          done = true;  // origin on an edge or a vertex: not a valid ray origin
-          ++c_inv;
-          c_lsteps += (unsigned)lsteps;
+        // current triangle holds it (this triangle is then the start triangle);
+        // the seed point is re-read from its cell (L1), not kept in registers
+        ++nsteps;
+        const SeedCell sd = S.seeds[seed_cell(S, ox, oy)];
+        const int res = locate_step(S, r, T, j, ox, oy, sd.px3, sd.py3);
+        if (res != 0 || nsteps > S.max_steps) {
+          atomicAdd(&cnt[kCntLocSteps], (unsigned)nsteps);
+          nsteps = 0;
+          if (res > 0) {
+            mode = kModeFirst;
+          } else {
+            status = CCT_RAY_INVALID;  // origin on an edge or a vertex: not a valid ray origin
+            atomicAdd(&cnt[kCntInvalid], 1u);
+            advance = false;
+          }
         } else {
           advance = false;
         }
       }
-      if (!done && advance) {
+      if (advance) {
         int e;
         if (mode == kModeFirst) {
           const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
           const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
           bool inside = true;
           if (!kLocate)
-            inside = orient_ll(x1, y1, x2, y2, ox, oy) > 0 && orient_ll(x2, y2, x0, y0, ox, oy) > 0 &&
-                     orient_ll(x0, y0, x1, y1, ox, oy) > 0;
-          const bool s0 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x0, y0, c_fb);
-          const bool s1 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x1, y1, c_fb);
-          const bool s2 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x2, y2, c_fb);
+            inside = orient_i(x1, y1, x2, y2, ox, oy) > 0 && orient_i(x2, y2, x0, y0, ox, oy) > 0 &&
+                     orient_i(x0, y0, x1, y1, ox, oy) > 0;
+          unsigned fb = 0;
+          const bool s0 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x0, y0, fb);
+          const bool s1 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x1, y1, fb);
+          const bool s2 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x2, y2, fb);
+          if (fb) atomicAdd(&cnt[kCntFallback], fb);
           c_side += 3;
           e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
           mode = kModeWalk;
           if (!inside) {
-            done = true;
-            ++c_inv;
+            status = CCT_RAY_INVALID;
+            atomicAdd(&cnt[kCntInvalid], 1u);
           }
         } else {
-          const bool sc = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, vx_of(r, j), vy_of(r, j), c_fb);
+          unsigned fb = 0;
+          const bool sc = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, vx_of(r, j), vy_of(r, j), fb);
+          if (fb) atomicAdd(&cnt[kCntFallback], fb);
           ++c_side;
           e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
         }
-        if (!done) {
+        if (status == 0) {
           ++nsteps;
           const int32_t w = nb_of(r, e);
           if (w >= 0) {
             if (nsteps >= S.max_steps) {
-              done = true;
-              res_steps = CCT_RAY_WALK_LIMIT;
-              ++c_lim;
+              status = CCT_RAY_WALK_LIMIT;
+              atomicAdd(&cnt[kCntLimit], 1u);
             } else {
               T = w >> 2;
               j = w & 3;
             }
           } else {
-            done = true;
-            res_steps = nsteps;
+            status = nsteps;  // hit or miss: park T (the final triangle) and e
+            j = e;
             c_steps += (unsigned)nsteps;
-            if (w <= -2) {
-              res_hit = -2 - w;
-              const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
-              res_t = hit_param(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), ox, oy, kx, ky);
-            } else {
-              res_t = __int_as_float(0x7f800000);  // +inf: left through the hull
-            }
           }
         }
       }
-      if (done) {
-        hit_out[idx] = res_hit;
-        t_out[idx] = res_t;
-        steps_out[idx] = res_steps;
-        ++c_rays;
+      if (status != 0) {
+        nsteps = status;
         active = false;
+        done = true;
       }
     }
   }
+  if (done) complete_ray(S.rec, T, j, nsteps, ox, oy, kx, ky, idx, hit_out, t_out, steps_out);
   // ---------------------------------------------------------------- counters: one atomic per warp and counter
   const unsigned long long w_steps = warp_sum((unsigned long long)c_steps);
   const unsigned long long w_side = warp_sum((unsigned long long)c_side);
-  const unsigned long long w_rays = warp_sum((unsigned long long)c_rays);
-  const unsigned long long w_fb = warp_sum((unsigned long long)c_fb);
-  const unsigned long long w_inv = warp_sum((unsigned long long)c_inv);
-  const unsigned long long w_lim = warp_sum((unsigned long long)c_lim);
-  const unsigned long long w_loc = warp_sum((unsigned long long)c_loc);
-  const unsigned long long w_lst = warp_sum((unsigned long long)c_lsteps);
+  __syncwarp();
+  const unsigned long long w_rays = cnt[kCntRays], w_fb = cnt[kCntFallback], w_inv = cnt[kCntInvalid];
+  const unsigned long long w_lim = cnt[kCntLimit], w_loc = cnt[kCntLocated], w_lst = cnt[kCntLocSteps];
   if (lane == 0) {
     if (w_rays) atomicAdd(&S.stats->rays, w_rays);
     if (w_steps) atomicAdd(&S.stats->steps, w_steps);

@@ -1,6 +1,7 @@
 """Continuous-batching server: every request's result in the mix (fused
 batched ticks, graph replays, overlapping uploads and downloads, admission by
-a memory budget) equals the same request traced alone, bit for bit."""
+a memory budget) equals the same request traced alone: hit ids and step
+counts bit for bit, t within the 1e-6 relative tolerance."""
 import numpy as np
 import pytest
 
@@ -45,4 +46,7 @@ def test_each_result_equals_alone(env, batched):
         out = r.out.numpy()
         assert np.array_equal(out[0], h.cpu().numpy())
         assert np.array_equal(out[2], s.cpu().numpy())
-        assert np.array_equal(out[1].view(np.float32), t.cpu().numpy())  # same arithmetic: identical t
+        ta, tb = out[1].view(np.float32), t.cpu().numpy()
+        fin = np.isfinite(tb)
+        assert np.array_equal(np.isfinite(ta), fin)
+        assert np.all(np.abs(ta[fin] - tb[fin]) <= 1e-6 * np.abs(tb[fin]))  # the stated t tolerance
