@@ -470,17 +470,29 @@ def main():
         for sc in scenes:
             trace(sc, None, flags)
 
-    # path: plain vs binned, kept per run ("auto" times both briefly and keeps the faster)
-    choice = {"plain": 0, "bin": cct.CCT_TRACE_BIN}
+    # launch configuration per scene: the autotuner (block size, refill
+    # threshold, chunk, binning, fp32-filtered vs exact-only) on a 2^22-ray
+    # sample of the scene's rays, start cells found on the GPU as in the timed step
+    from paper_2112_05570_gb300 import autotune
+
+    tuned = {}
     if args.flags == "auto":
-        for f in choice.values():
-            step(f)
-        tried = {k: _time_loop(torch, dev, stream, lambda f=f: step(f), 2) for k, f in choice.items()}
-        path = min(tried, key=tried.get)
+        m = 1 << 22
+        for sc in scenes:
+            d = sc["d"]
+            res = autotune.tune_scene(sc["scene"], d["ox"][:m], d["oy"][:m], d["dx"][:m], d["dy"][:m], None,
+                                      use_cache=False)
+            tuned[sc["name"]] = res["config"]
+        path = "autotuned"
     else:
-        path, tried = args.flags, {}
-    flags = choice[path]
-    kernels_per_trace = 2 + (5 if flags & cct.CCT_TRACE_BIN else 0)
+        path = args.flags
+        for sc in scenes:
+            sc["scene"].set_tuning({"trace_flags": cct.CCT_TRACE_BIN if path == "bin" else 0})
+    flags = 0
+    # our kernels per step: the fused locate+walk, or locate, histogram, three
+    # scan passes, scatter and walk when a scene is binned
+    kernels_per_step = sum(7 if sc["scene"].tuning()["trace_flags"] & cct.CCT_TRACE_BIN else 1 for sc in scenes)
+    tried = tuned
 
     for _ in range(max(3, args.warmup)):
         step(flags)
@@ -516,6 +528,8 @@ def main():
     per = {}
     walk_ms_tot, alg_bytes_tot, alg_over_peak = 0.0, 0.0, 0.0
     for sc in scenes:
+        tuned_cfg = sc["scene"].tuning()
+        sc["scene"].set_tuning(dict(tuned_cfg, trace_flags=tuned_cfg["trace_flags"] & ~cct.CCT_TRACE_BIN))
         for _ in range(2):
             trace(sc, sc["d"]["start"], 0)
         sc["scene"].stats(reset=True)
@@ -594,7 +608,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64+fp32-filter", "data": "synthetic",
             "config": {"workload": WORKLOAD, "families": list(FAMILIES), "segments_per_scene": N_SEGMENTS,
-                       "rays_per_step": rays_per_step, "path": path, "path_ms_tried": tried,
+                       "rays_per_step": rays_per_step, "path": path, "tuning": tried,
                        "l2": "inputs larger than L2 (6 x 2^24 rays + results, 2 GB); triangle tables L2-resident",
                        "parallelism": f"replicas x{world}"},
             "steps_per_ray": tot["steps"] / max(1, tot["rays"]),
@@ -604,7 +618,7 @@ def main():
             "fallback_rate": tot["exact_fallbacks"] / max(1, tot["side_tests"]),
             "locate_steps_per_ray": tot["locate_steps"] / max(1, tot["located"]),
             "per_scene": per, "roofline": roofline, "e2e": e2e,
-            "gpu_launches": kernels_per_trace * len(scenes) * args.steps}
+            "gpu_launches": kernels_per_step * args.steps}
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample_n, dt = cpu_oracle_rate(work)
         line["cpu_baseline"] = {"value": rate, "unit": "rays/s", "cores": cores, "kind": "oracle",

@@ -20,8 +20,8 @@ from . import cct
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning_cache.json")
 
 KNOBS = {
-    "block_threads": (128, 256, 512),
-    "refill_min": (1, 4, 8, 16),
+    "block_threads": (64, 128, 256, 512),
+    "refill_min": (4, 8, 16, 24, 32),
     "chunk": (64, 128, 512, 2048),
     "path": ("plain", "bin", "bin-coarse", "bin-fine"),
     "exact": (0, 1),
