@@ -400,6 +400,9 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="profiling mode: per scene, 2 warm-up traces, then one trace with start cells given and "
                          "one with the fused locate; no timing, no JSON")
+    ap.add_argument("--seed-densities", default="",
+                    help="with --profile: also time the fused locate with these seed-grid densities (k: 2^k cells "
+                         "per triangle), e.g. 1,2,3,4")
     ap.add_argument("--families", default=",".join(FAMILIES),
                     help="comma-separated scene families (profiling runs)")
     args = ap.parse_args()
@@ -451,7 +454,9 @@ def main():
         # per scene: 2 warm-up traces, then start cells given / fused locate, each
         # with the fp32 filter and exact-only; CUDA-event times of 3 more of each
         ex = cct.CCT_TRACE_EXACT_ONLY
-        variants = (("given", "start", 0), ("given_exact", "start", ex), ("locate", None, 0), ("locate_exact", None, ex))
+        sp = cct.CCT_TRACE_SPLIT_LOCATE
+        variants = (("given", "start", 0), ("given_exact", "start", ex), ("locate", None, 0), ("locate_exact", None, ex),
+                    ("split", None, sp), ("split_exact", None, sp | ex))
         times = {}
         for sc in scenes:
             for _ in range(2):
@@ -463,7 +468,34 @@ def main():
             for name, st, fl in variants:
                 times[f"{sc['name']}/{name}"] = _time_loop(
                     torch, dev, stream, lambda st=st, fl=fl: trace(sc, sc["d"][st] if st else None, fl), 3)
-        print(json.dumps({"profile_ms": times}))
+        # the locate kernel alone (start cells into a preallocated buffer)
+        loc_out = torch.empty(n, dtype=torch.int32, device=dev)
+        for sc in scenes:
+            d = sc["d"]
+            run = lambda d=d, sc=sc: cct.cct_locate(sc["scene"].handle, d["ox"], d["oy"], loc_out, stream)
+            run()
+            times[f"{sc['name']}/locate_kernel"] = _time_loop(torch, dev, stream, run, 3)
+        out = {"profile_ms": times}
+        if args.seed_densities:
+            # the fused locate under other seed-grid densities (2^k cells per
+            # triangle): time and locate steps per origin
+            sweep = {}
+            for sc in scenes:
+                for k in (int(x) for x in args.seed_densities.split(",")):
+                    other = cct.Scene.from_triangulation(sc["tri"], sg.D, flags=cct.CCT_LOAD_SEED_DENSITY(k))
+                    d = sc["d"]
+                    run = lambda other=other, d=d: cct.cct_trace(other.handle, d["ox"], d["oy"], d["dx"], d["dy"],
+                                                                None, hit, t, steps, 0, stream)
+                    run()
+                    other.stats(reset=True)
+                    run()
+                    torch.cuda.synchronize(dev)
+                    st = other.stats()
+                    sweep[f"{sc['name']}/k{k}"] = {"ms": _time_loop(torch, dev, stream, run, 3),
+                                                   "locate_steps": st["locate_steps"] / max(1, st["located"])}
+                    other.free()
+            out["seed_density"] = sweep
+        print(json.dumps(out))
         return 0
 
     def step(flags):
@@ -489,9 +521,11 @@ def main():
         for sc in scenes:
             sc["scene"].set_tuning({"trace_flags": cct.CCT_TRACE_BIN if path == "bin" else 0})
     flags = 0
-    # our kernels per step: the fused locate+walk, or locate, histogram, three
-    # scan passes, scatter and walk when a scene is binned
-    kernels_per_step = sum(7 if sc["scene"].tuning()["trace_flags"] & cct.CCT_TRACE_BIN else 1 for sc in scenes)
+    # our kernels per step: the fused locate+walk; locate and walk (split);
+    # or locate, histogram, three scan passes, scatter and walk (binned)
+    kernels_per_step = sum(7 if sc["scene"].tuning()["trace_flags"] & cct.CCT_TRACE_BIN else
+                           2 if sc["scene"].tuning()["trace_flags"] & cct.CCT_TRACE_SPLIT_LOCATE else 1
+                           for sc in scenes)
     tried = tuned
 
     for _ in range(max(3, args.warmup)):

@@ -65,9 +65,17 @@ extern "C" {
 #define CCT_LOAD_NO_REORDER 1u  /* keep the caller's triangle order (default: Hilbert order) */
 #define CCT_LOAD_NO_VALIDATE 2u /* skip the geometric checks of cct_scene_load (fault-injection tests);
                                    index ranges are always checked */
+
+/* Density of the locate seed grid (Sec. 5.2): square cells of side 2^s with
+ * about 2^k cells per triangle, k in [0, 8] (at most 8192 cells per side; 4
+ * bytes per cell), encoded in bits 8..11 of the load flags.  Without it k = 2. */
+#define CCT_LOAD_SEED_DENSITY(k) ((uint32_t)((k) + 1) << 8)
+
 /* cct_trace */
 #define CCT_TRACE_EXACT_ONLY 1u /* decide every side in int64 (no fp32 filter) */
 #define CCT_TRACE_BIN 2u        /* sort rays by start cell before walking (ray binning) */
+#define CCT_TRACE_SPLIT_LOCATE 4u /* without start cells: locate all origins in a separate kernel
+                                     first (default: inside the walk kernel) */
 
 /* ------------------------------------------------------------------ types */
 typedef struct cct_scene_s* cct_scene; /* opaque; the library owns all device memory of a scene */

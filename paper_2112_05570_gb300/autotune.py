@@ -3,7 +3,9 @@
 No counterpart in the paper.  Knobs: threads per block, the refill threshold
 (idle lanes a warp collects before serving new rays), the chunk of rays a warp
 takes from the work counter ("rays per warp"), ray binning and its
-granularity, and the side test (fp32-filtered vs exact int64).  Coordinate
+granularity, where start cells are found when none are given (inside the walk
+kernel, or by a separate locate kernel first), and the side test
+(fp32-filtered vs exact int64).  Coordinate
 descent from the defaults: each knob in turn takes the value with the lowest
 median CUDA-event time on a ray sample, others fixed; two passes.  Results are
 cached per (GPU, triangle-count class, ray-count class, start cells given)
@@ -23,7 +25,7 @@ KNOBS = {
     "block_threads": (64, 128, 256, 512),
     "refill_min": (4, 8, 16, 24, 32),
     "chunk": (64, 128, 512, 2048),
-    "path": ("plain", "bin", "bin-coarse", "bin-fine"),
+    "path": ("plain", "split", "bin", "bin-coarse", "bin-fine"),
     "exact": (0, 1),
 }
 
@@ -53,7 +55,9 @@ def _save_cache(c: dict) -> None:
 def _to_tuning(cfg: dict, n_tri: int, n_rays: int) -> dict:
     flags = cct.CCT_TRACE_EXACT_ONLY if cfg["exact"] else 0
     shift = -1
-    if cfg["path"] != "plain":
+    if cfg["path"] == "split":
+        flags |= cct.CCT_TRACE_SPLIT_LOCATE
+    elif cfg["path"] != "plain":
         flags |= cct.CCT_TRACE_BIN
         target = max(1024, n_rays // 64)
         auto = 0

@@ -23,8 +23,16 @@ CCT_RAY_INVALID = -1
 CCT_RAY_WALK_LIMIT = -2
 CCT_LOAD_NO_REORDER = 1
 CCT_LOAD_NO_VALIDATE = 2
+
+
+def CCT_LOAD_SEED_DENSITY(k: int) -> int:
+    """Load flag: about 2^k locate seed cells per triangle (k in [0, 8])."""
+    return (int(k) + 1) << 8
+
+
 CCT_TRACE_EXACT_ONLY = 1
 CCT_TRACE_BIN = 2
+CCT_TRACE_SPLIT_LOCATE = 4
 CCT_NOALLOC_MAX_RAYS = 1 << 20
 
 

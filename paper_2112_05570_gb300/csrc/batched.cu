@@ -93,8 +93,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
   bool exhausted = n_items <= 0;
   // lane state: walking (active), finished with a parked result (done), or idle
   bool active = false, done = false;
+  // modes: 0 locate past the seed triangle, 1 first triangle, 2 walk, 3 seed triangle
   int mode = 1, item = 0, idx = 0, ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0, lsteps = 0;
-  int px3 = 0, py3 = 0, max_steps = 0, scene = 0;
+  int max_steps = 0, scene = 0;
   float fdx = 0.f, fdy = 0.f;
   const TriRec* rec = nullptr;
   unsigned c_steps = 0, c_side = 0, c_fb = 0, c_rays = 0, c_inv = 0, c_lim = 0, c_loc = 0, c_lsteps = 0;
@@ -140,12 +141,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
         int s = -1;
         if (it.start == nullptr) {
           if (ok && ox >= 0 && oy >= 0 && ox <= S.D && oy <= S.D) {
-            const SeedCell sd = S.seeds[seed_cell(S, ox, oy)];
-            px3 = sd.px3;
-            py3 = sd.py3;
-            s = sd.tri;
-            j = 3;
-            mode = 0;
+            s = S.seeds[seed_cell(S, ox, oy)];
+            mode = 3;
             lsteps = 0;
             ++c_loc;
           } else {
@@ -178,45 +175,70 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
     if (active) {
       const TriRec r = load_rec(rec + T);
       int status = 0;
-      bool advance = true;
+      bool step = true;
       if (mode == 0) {
         ++lsteps;
-        const int res = locate_step(scenes[scene], r, T, j, ox, oy, px3, py3);
+        int cx, cy;
+        seed_point(scenes[scene], ox, oy, cx, cy);
+        const int res = locate_step_entered(scenes[scene], r, T, j, ox, oy, cx, cy);
+        step = false;
         if (res > 0) {
           mode = 1;
+          step = true;
           c_lsteps += (unsigned)lsteps;
-        } else {
-          advance = false;
-          if (res < 0 || lsteps > max_steps) {
-            status = CCT_RAY_INVALID;
-            ++c_inv;
-            c_lsteps += (unsigned)lsteps;
-          }
+        } else if (res < 0 || lsteps > max_steps) {
+          status = CCT_RAY_INVALID;
+          ++c_inv;
+          c_lsteps += (unsigned)lsteps;
         }
       }
-      if (advance) {
-        int e;
-        if (mode == 1) {
+      if (step) {
+        int e = 0;
+        if (mode != 2) {
           const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
           const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
-          const bool inside = orient_ll(x1, y1, x2, y2, ox, oy) > 0 && orient_ll(x2, y2, x0, y0, ox, oy) > 0 &&
-                              orient_ll(x0, y0, x1, y1, ox, oy) > 0;
-          const bool s0 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x0, y0, c_fb);
-          const bool s1 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x1, y1, c_fb);
-          const bool s2 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x2, y2, c_fb);
-          c_side += 3;
-          e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
-          mode = 2;
-          if (!inside) {
-            status = CCT_RAY_INVALID;
-            ++c_inv;
+          bool inside = true;
+          if (mode == 3 || mode == 1) {
+            const long long o0 = orient_i(x1, y1, x2, y2, ox, oy), o1 = orient_i(x2, y2, x0, y0, ox, oy);
+            const long long o2 = orient_i(x0, y0, x1, y1, ox, oy);
+            inside = o0 > 0 && o1 > 0 && o2 > 0;
+            if (mode == 3) {
+              lsteps = 1;
+              if (!inside && (o0 < 0 || o1 < 0 || o2 < 0)) {
+                // outside the seed triangle: the Sec. 5.2 locate walk leaves it
+                int cx, cy;
+                seed_point(scenes[scene], ox, oy, cx, cy);
+                step = false;
+                if (locate_hop(scenes[scene], r, T, j, seed_exit(r, cx, cy, ox, oy))) {
+                  mode = 0;
+                } else {
+                  status = CCT_RAY_INVALID;
+                  ++c_inv;
+                  c_lsteps += 1u;
+                }
+              } else {
+                c_lsteps += 1u;
+              }
+            }
+          }
+          if (step) {
+            const bool s0 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x0, y0, c_fb);
+            const bool s1 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x1, y1, c_fb);
+            const bool s2 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x2, y2, c_fb);
+            c_side += 3;
+            e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
+            mode = 2;
+            if (!inside) {
+              status = CCT_RAY_INVALID;
+              ++c_inv;
+            }
           }
         } else {
           const bool sc = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, vx_of(r, j), vy_of(r, j), c_fb);
           ++c_side;
           e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
         }
-        if (status == 0) {
+        if (step && status == 0) {
           ++nsteps;
           const int32_t w = nb_of(r, e);
           if (w >= 0) {

@@ -7,8 +7,10 @@
 //                               only by the locate walk, which crosses them)
 //   user2dev  int32[n_tri]      caller triangle id -> record index
 //   dev2user  int32[n_tri]      record index -> caller triangle id
-//   seeds     SeedCell[G*G]     locate seed grid (Sec. 5.2): per cell a point
-//                               with a known triangle (a triangle centroid)
+//   seeds     int32[G*G]        locate seed grid (Sec. 5.2): square cells of
+//                               side 2^seed_shift; per cell the record index of
+//                               the triangle that holds its seed point (the
+//                               cell centre, symbolically perturbed)
 //   stats     DevStats          counters (cct_stats)
 #pragma once
 
@@ -37,12 +39,6 @@ struct __align__(32) TriRec {
 };
 static_assert(sizeof(TriRec) == 32, "TriRec must be one 32-byte sector");
 
-struct __align__(16) SeedCell {
-  int32_t px3, py3;  // 3 x seed point (the centroid of `tri`, exact in thirds)
-  int32_t tri;       // record index of the triangle that holds the seed point
-  int32_t pad;
-};
-
 struct DevStats {
   unsigned long long rays, steps, side_tests, exact_fallbacks, invalid_rays, walk_limit_rays, located,
       locate_steps;
@@ -53,10 +49,11 @@ struct SceneDev {
   const int32_t* cnb;
   const int32_t* user2dev;
   const int32_t* dev2user;
-  const SeedCell* seeds;
+  const int32_t* seeds;
   DevStats* stats;
   int32_t n_tri;
-  int32_t G;
+  int32_t G;           // seed cells per side: ceil(D / 2^seed_shift)
+  int32_t seed_shift;  // log2 of the seed cell side
   int32_t D;
   int32_t max_steps;
 };
@@ -154,26 +151,84 @@ __device__ __forceinline__ float hit_param_fast(int ax, int ay, int bx, int by, 
   return __fdividef(__ll2float_rn(num), __ll2float_rn(den)) * kDirScale;
 }
 
-// Seed cell of an origin: any cell is correct (the locate walk finds the
-// triangle from any seed), so an fp32 scale suffices.
+// Seed cell of an origin in [0, D]^2: square cells of side h = 2^seed_shift,
+// cell (ix, iy) = (min(ox >> s, G - 1), min(oy >> s, G - 1)); its seed point is
+// c = (min(ix h + h/2, D - 1), min(iy h + h/2, D - 1)) moved by eps (1, delta),
+// 0 < eps << delta << 1 (simulation of simplicity): the perturbed point lies on
+// no line through two grid points, so it is strictly inside exactly one
+// triangle and the line from it to an origin passes through no vertex other
+// than the origin.  Host and device use the same integer formulas.
 __device__ __forceinline__ int seed_cell(const SceneDev& S, int ox, int oy) {
-  const float sc = (float)S.G / (float)S.D;
-  const int ix = min(S.G - 1, max(0, __float2int_rz((float)ox * sc)));
-  const int iy = min(S.G - 1, max(0, __float2int_rz((float)oy * sc)));
+  const int ix = min(ox >> S.seed_shift, S.G - 1), iy = min(oy >> S.seed_shift, S.G - 1);
   return iy * S.G + ix;
 }
+__device__ __forceinline__ void seed_point(const SceneDev& S, int ox, int oy, int& cx, int& cy) {
+  const int s = S.seed_shift, half = (1 << s) >> 1;
+  cx = min((min(ox >> s, S.G - 1) << s) + half, S.D - 1);
+  cy = min((min(oy >> s, S.G - 1) << s) + half, S.D - 1);
+}
 
-// One step of the Sec. 5.2 locate walk from the seed point p (kept as 3p)
-// towards the origin o, in record r = triangle T entered through its edge j
-// (j = 3: T is the seed's own triangle).  Returns 1 when T holds o strictly
-// inside, -1 when o lies on an edge or a vertex (or the walk leaves the
-// domain), 0 after moving to the next triangle (T, j updated).  The walk
-// crosses constrained edges (neighbours from cnb): it locates a point, it does
-// not trace a ray.
+// Side of vertex v relative to the directed line from the perturbed seed point
+// p = c + eps (1, delta) to the origin o; true = L.  (o - p) x (v - p) =
+// (o - c) x (v - c) + eps ((v - o) x (1, delta)): when the first term is zero
+// the sign is that of (vx - ox) delta - (vy - oy), i.e. of oy - vy, else of
+// vx - ox.  Exact (|coordinate differences| <= 2^20).
+__device__ __forceinline__ bool seed_side_L(int cx, int cy, int ox, int oy, int vx, int vy) {
+  const long long e = (long long)(ox - cx) * (vy - cy) - (long long)(oy - cy) * (vx - cx);
+  if (e != 0) return e > 0;
+  return vy != oy ? vy < oy : vx > ox;
+}
+
+// Exit edge of the seed triangle (whose interior holds the perturbed seed
+// point) on the way from the seed point to o: the CCW edge (a -> b) with
+// s(a) = R, s(b) = L relative to that line.
+__device__ __forceinline__ int seed_exit(const TriRec& r, int cx, int cy, int ox, int oy) {
+  const bool s0 = seed_side_L(cx, cy, ox, oy, vx_of(r, 0), vy_of(r, 0));
+  const bool s1 = seed_side_L(cx, cy, ox, oy, vx_of(r, 1), vy_of(r, 1));
+  const bool s2 = seed_side_L(cx, cy, ox, oy, vx_of(r, 2), vy_of(r, 2));
+  return (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
+}
+
+// Moves the locate walk across edge e of record T (the walk crosses
+// constrained edges: their neighbours come from cnb).  False at the hull.
+__device__ __forceinline__ bool locate_hop(const SceneDev& S, const TriRec& r, int& T, int& j, int e) {
+  int32_t w = nb_of(r, e);
+  if (w <= -2) w = S.cnb[3 * T + e];
+  if (w < 0) return false;
+  T = w >> 2;
+  j = w & 3;
+  return true;
+}
+
+// A locate step in a triangle T entered through its edge j < 3 (see
+// locate_step): the entry edge's two sides are known, so decide the apex,
+// then test o against the exit edge only (o lies beyond the entry edge by
+// induction).
+__device__ __forceinline__ int locate_step_entered(const SceneDev& S, const TriRec& r, int& T, int& j, int ox,
+                                                   int oy, int cx, int cy) {
+  const bool sc = seed_side_L(cx, cy, ox, oy, vx_of(r, j), vy_of(r, j));
+  const int e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
+  const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
+  const long long oe = orient_i(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), ox, oy);
+  if (oe == 0) return -1;
+  if (oe > 0) {
+    // o lies before the exit edge: inside T unless on one of its other edges
+    const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
+    const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
+    const bool in = orient_i(x1, y1, x2, y2, ox, oy) > 0 && orient_i(x2, y2, x0, y0, ox, oy) > 0 &&
+                    orient_i(x0, y0, x1, y1, ox, oy) > 0;
+    return in ? 1 : -1;
+  }
+  return locate_hop(S, r, T, j, e) ? 0 : -1;
+}
+
+// One step of the Sec. 5.2 locate walk from the seed point of o's cell (c,
+// perturbed) towards the origin o, in record r = triangle T entered through
+// its edge j (j = 3: T is the seed's own triangle).  Returns 1 when T holds o
+// strictly inside, -1 when o lies on an edge or a vertex (or the walk leaves
+// the domain), 0 after moving to the next triangle (T, j updated).
 __device__ __forceinline__ int locate_step(const SceneDev& S, const TriRec& r, int& T, int& j, int ox, int oy,
-                                           int px3, int py3) {
-  const int qx = 3 * ox - px3, qy = 3 * oy - py3;  // direction p -> o, in thirds
-  int e;
+                                           int cx, int cy) {
   if (j == 3) {
     const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
     const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
@@ -182,34 +237,9 @@ __device__ __forceinline__ int locate_step(const SceneDev& S, const TriRec& r, i
     const long long o2 = orient_i(x0, y0, x1, y1, ox, oy);
     if (o0 > 0 && o1 > 0 && o2 > 0) return 1;
     if (o0 >= 0 && o1 >= 0 && o2 >= 0) return -1;
-    const bool s0 = (long long)qx * (3 * y0 - py3) - (long long)qy * (3 * x0 - px3) >= 0;
-    const bool s1 = (long long)qx * (3 * y1 - py3) - (long long)qy * (3 * x1 - px3) >= 0;
-    const bool s2 = (long long)qx * (3 * y2 - py3) - (long long)qy * (3 * x2 - px3) >= 0;
-    e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
-  } else {
-    // the entry edge's two sides are known: decide the apex, then test o
-    // against the exit edge only (o beyond the entry edge by induction)
-    const int cx = vx_of(r, j), cy = vy_of(r, j);
-    const bool sc = (long long)qx * (3 * cy - py3) - (long long)qy * (3 * cx - px3) >= 0;
-    e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
-    const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
-    const long long oe = orient_i(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), ox, oy);
-    if (oe == 0) return -1;
-    if (oe > 0) {
-      // o lies before the exit edge: inside T unless on one of its other edges
-      const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
-      const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
-      const bool in = orient_i(x1, y1, x2, y2, ox, oy) > 0 && orient_i(x2, y2, x0, y0, ox, oy) > 0 &&
-                      orient_i(x0, y0, x1, y1, ox, oy) > 0;
-      return in ? 1 : -1;
-    }
+    return locate_hop(S, r, T, j, seed_exit(r, cx, cy, ox, oy)) ? 0 : -1;
   }
-  int32_t w = nb_of(r, e);
-  if (w <= -2) w = S.cnb[3 * T + e];
-  if (w < 0) return -1;
-  T = w >> 2;
-  j = w & 3;
-  return 0;
+  return locate_step_entered(S, r, T, j, ox, oy, cx, cy);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -2,10 +2,12 @@
 //
 // The paper's option without an extra data structure: from a point p whose
 // triangle is known, follow the traversal towards the origin o until the
-// current triangle holds o.  Seeds sit on a regular grid: one per cell, its
-// centre, located exactly at load time (kept as 3p, as the kernel's exact
-// int64 arithmetic expects).  The locate walk crosses constrained edges (it
-// is a point location, not a ray query), reading their neighbours from `cnb`.
+// current triangle holds o.  Seeds sit on a regular grid of power-of-two
+// cells: the seed point of a cell is its centre under a symbolic perturbation
+// (computed from o with shifts, never stored), located exactly at load time,
+// so a cell costs one 4-byte triangle index.  The locate walk crosses
+// constrained edges (it is a point location, not a ray query), reading their
+// neighbours from `cnb`.
 #include <algorithm>
 
 #include "cct_internal.cuh"
@@ -23,11 +25,8 @@ __global__ void __launch_bounds__(kLocateThreads) locate_kernel(SceneDev S, cons
     const int qx = ox[i], qy = oy[i];
     int32_t res = -1;
     if (qx >= 0 && qy >= 0 && qx <= S.D && qy <= S.D) {
-      const int G = S.G;
-      const int ix = (int)min((long long)G - 1, (long long)qx * G / S.D);
-      const int iy = (int)min((long long)G - 1, (long long)qy * G / S.D);
-      const SeedCell sd = S.seeds[(long long)iy * G + ix];
-      int T = sd.tri, j = 3;
+      int T = S.seeds[seed_cell(S, qx, qy)], j = 3, cx, cy;
+      seed_point(S, qx, qy, cx, cy);
       int steps = 0;
       while (true) {
         if (++steps > S.max_steps) {
@@ -35,7 +34,7 @@ __global__ void __launch_bounds__(kLocateThreads) locate_kernel(SceneDev S, cons
           break;
         }
         const TriRec r = load_rec(S.rec + T);
-        const int st = locate_step(S, r, T, j, qx, qy, sd.px3, sd.py3);
+        const int st = locate_step(S, r, T, j, qx, qy, cx, cy);
         if (st != 0) {
           res = st > 0 ? T : -1;
           break;

@@ -7,9 +7,9 @@
 //   2. Hilbert order of the triangle centroids, so that triangles adjacent in
 //      space are adjacent in memory (walk and locate locality);
 //   3. one 32-byte record per triangle (coordinates + neighbour words);
-//   4. the locate seed grid of Sec. 5.2: G x G cells, each with a seed point
-//      whose triangle is known -- a triangle centroid inside the cell, or the
-//      nearest filled cell's seed for cells that hold no centroid.
+//   4. the locate seed grid of Sec. 5.2: G x G square cells of side 2^s, each
+//      holding the triangle of its seed point (the cell centre, symbolically
+//      perturbed: see seed_point in cct_internal.cuh), found by exact walks.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -94,44 +94,48 @@ static int validate(const cct_tri_desc& d) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Exact host point location over the packed records (used once, for seeds).
+// Exact host point location of perturbed seed points c + eps (1, delta)
+// (0 < eps << delta << 1) over the packed records (used once, at load).
 struct HostLocator {
   const std::vector<TriRec>& rec;
   const std::vector<int32_t>& cnb;
   HostLocator(const std::vector<TriRec>& r, const std::vector<int32_t>& c) : rec(r), cnb(c) {}
   static long long vx(const TriRec& r, int i) { return (long long)((r.X >> (kCoordBits * i)) & kCoordMask); }
   static long long vy(const TriRec& r, int i) { return (long long)((r.Y >> (kCoordBits * i)) & kCoordMask); }
-  // 1 strictly inside, 0 on the boundary, -1 outside
-  int contains(int T, long long x, long long y) const {
+  // orientation of (a, b, c + eps (1, delta)): orient(a, b, c) + eps ((bx - ax) delta - (by - ay)); never 0
+  static bool left_sos(long long ax, long long ay, long long bx, long long by, long long cx, long long cy) {
+    const long long o = orient_h(ax, ay, bx, by, cx, cy);
+    if (o != 0) return o > 0;
+    return ay != by ? ay > by : bx > ax;
+  }
+  bool contains(int T, long long x, long long y) const {
     const TriRec& r = rec[T];
-    int zero = 0;
     for (int i = 0; i < 3; ++i) {
       const int a = (i + 1) % 3, b = (i + 2) % 3;
-      long long o = orient_h(vx(r, a), vy(r, a), vx(r, b), vy(r, b), x, y);
-      if (o < 0) return -1;
-      if (o == 0) zero = 1;
+      if (!left_sos(vx(r, a), vy(r, a), vx(r, b), vy(r, b), x, y)) return false;
     }
-    return zero ? 0 : 1;
+    return true;
   }
   int scan(long long x, long long y) const {
-    for (int T = 0; T < (int)rec.size(); ++T) {
-      int c = contains(T, x, y);
-      if (c == 1) return T;
-      if (c == 0) return -1;
-    }
+    for (int T = 0; T < (int)rec.size(); ++T)
+      if (contains(T, x, y)) return T;
     return -1;
   }
-  // From (px, py) strictly inside T along the segment to (qx, qy); the triangle
-  // holding q strictly, or -1 if q lies on an edge or a vertex.
+  // From the perturbed p (inside T) along the segment to the perturbed q (both
+  // moved by the same eps (1, delta)); the triangle holding q, or -1 if the
+  // walk leaves the domain (a triangulation loaded without validation).
   int walk(int T, long long px, long long py, long long qx, long long qy) const {
     const long long kx = qx - px, ky = qy - py;
+    // side of v: k x (v - p) - eps (kx delta - ky); tie: sign of ky, else of -kx
+    const bool tie_left = ky != 0 ? ky > 0 : kx < 0;
     for (size_t guard = 0; guard <= rec.size() + 8; ++guard) {
-      const int c = contains(T, qx, qy);
-      if (c == 1) return T;
-      if (c == 0) return -1;
+      if (contains(T, qx, qy)) return T;
       const TriRec& r = rec[T];
       bool s[3];
-      for (int i = 0; i < 3; ++i) s[i] = kx * (vy(r, i) - py) - ky * (vx(r, i) - px) >= 0;
+      for (int i = 0; i < 3; ++i) {
+        const long long e = kx * (vy(r, i) - py) - ky * (vx(r, i) - px);
+        s[i] = e != 0 ? e > 0 : tie_left;
+      }
       const int e = (!s[1] && s[2]) ? 0 : ((!s[2] && s[0]) ? 1 : 2);
       int32_t w = r.nb[e];
       if (w <= -2) w = cnb[3 * (size_t)T + e];
@@ -214,44 +218,39 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
       }
       rec[T] = r;
     }
-    // ---- seed grid (Sec. 5.2): per cell, the cell centre (nudged off edges)
-    // and the triangle whose interior holds it, found by exact walks
-    long long D = d.domain;
-    int G = (int)std::max(1.0, std::min(4096.0, std::sqrt((double)nt) * 1.5));
-    std::vector<SeedCell> seeds((size_t)G * G, SeedCell{0, 0, -1, 0});
+    // ---- seed grid (Sec. 5.2): per cell, the triangle whose interior holds
+    // the perturbed cell centre; about 2^k cells per triangle, k from the flags
+    const long long D = d.domain;
+    int shift = 0, G = 1;
+    {
+      const unsigned kd = (flags >> 8) & 15u;
+      const int k = kd == 0 ? 2 : std::min(8, (int)kd - 1);
+      const double h = (double)D / std::sqrt(std::ldexp(1.0, k) * (double)nt);
+      shift = std::max(0, (int)std::lround(std::log2(std::max(1.0, h))));
+      while (((D + (1ll << shift) - 1) >> shift) > 8192) ++shift;
+      G = (int)((D + (1ll << shift) - 1) >> shift);
+    }
+    std::vector<int32_t> seeds((size_t)G * G, 0);
     {
       HostLocator loc(rec, cnb);
+      const long long half = (1ll << shift) >> 1;
       int prev_tri = -1;
       long long prev_x = 0, prev_y = 0;
       for (int iy = 0; iy < G; ++iy)
         for (int jx = 0; jx < G; ++jx) {
           const int ix = (iy & 1) ? G - 1 - jx : jx;  // boustrophedon: short walks
-          const long long cx0 = (D * (2ll * ix + 1)) / (2ll * G), cy0 = (D * (2ll * iy + 1)) / (2ll * G);
-          int tri = -1;
-          long long cx = cx0, cy = cy0;
-          for (int k = 0; k < 16 && tri < 0; ++k) {
-            cx = std::min(D - 1, std::max(1ll, cx0 + (k % 4))), cy = std::min(D - 1, std::max(1ll, cy0 + (k / 4)));
-            tri = prev_tri < 0 ? loc.scan(cx, cy) : loc.walk(prev_tri, prev_x, prev_y, cx, cy);
-          }
+          const long long cx = std::min(((long long)ix << shift) + half, D - 1);
+          const long long cy = std::min(((long long)iy << shift) + half, D - 1);
+          const int tri = prev_tri < 0 ? loc.scan(cx, cy) : loc.walk(prev_tri, prev_x, prev_y, cx, cy);
           if (tri < 0) {
-            // only on a triangulation loaded without validation: fall back to
-            // the previous cell's seed, or to the centroid of record 0 (which
-            // lies inside its own triangle); locate walks then end at their
-            // step limit or report the origin invalid, never out of bounds
-            if (prev_tri >= 0) {
-              seeds[(size_t)iy * G + ix] = SeedCell{(int32_t)(3 * prev_x), (int32_t)(3 * prev_y), prev_tri, 0};
-            } else {
-              const TriRec& r0 = rec[0];
-              long long sx = 0, sy = 0;
-              for (int q = 0; q < 3; ++q) {
-                sx += (long long)((r0.X >> (kCoordBits * q)) & kCoordMask);
-                sy += (long long)((r0.Y >> (kCoordBits * q)) & kCoordMask);
-              }
-              seeds[(size_t)iy * G + ix] = SeedCell{(int32_t)sx, (int32_t)sy, 0, 0};
-            }
+            // only on a triangulation loaded without validation: keep the
+            // previous cell's triangle (or record 0); locate walks from there
+            // end at their step limit or report the origin invalid, and every
+            // index they follow was range-checked
+            seeds[(size_t)iy * G + ix] = std::max(prev_tri, 0);
             continue;
           }
-          seeds[(size_t)iy * G + ix] = SeedCell{(int32_t)(3 * cx), (int32_t)(3 * cy), tri, 0};
+          seeds[(size_t)iy * G + ix] = tri;
           prev_tri = tri;
           prev_x = cx;
           prev_y = cy;
@@ -263,7 +262,7 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
     size_t o_u2d = o_cnb + align256(sizeof(int32_t) * 3 * (size_t)nt);
     size_t o_d2u = o_u2d + align256(sizeof(int32_t) * (size_t)nt);
     size_t o_seed = o_d2u + align256(sizeof(int32_t) * (size_t)nt);
-    size_t o_stats = o_seed + align256(sizeof(SeedCell) * (size_t)G * G);
+    size_t o_stats = o_seed + align256(sizeof(int32_t) * (size_t)G * G);
     size_t total = o_stats + align256(sizeof(DevStats));
     char* base = nullptr;
     if (cudaMalloc(&base, total) != cudaSuccess) {
@@ -278,7 +277,7 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
     up(o_cnb, cnb.data(), sizeof(int32_t) * 3 * (size_t)nt);
     up(o_u2d, user2dev.data(), sizeof(int32_t) * (size_t)nt);
     up(o_d2u, dev2user.data(), sizeof(int32_t) * (size_t)nt);
-    up(o_seed, seeds.data(), sizeof(SeedCell) * (size_t)G * G);
+    up(o_seed, seeds.data(), sizeof(int32_t) * (size_t)G * G);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_stats, 0, sizeof(DevStats), stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
@@ -293,10 +292,11 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
     s->dev.cnb = (const int32_t*)(base + o_cnb);
     s->dev.user2dev = (const int32_t*)(base + o_u2d);
     s->dev.dev2user = (const int32_t*)(base + o_d2u);
-    s->dev.seeds = (const SeedCell*)(base + o_seed);
+    s->dev.seeds = (const int32_t*)(base + o_seed);
     s->dev.stats = (DevStats*)(base + o_stats);
     s->dev.n_tri = nt;
     s->dev.G = G;
+    s->dev.seed_shift = shift;
     s->dev.D = d.domain;
     s->dev.max_steps = nt + 8;
     s->tuning = default_tuning();

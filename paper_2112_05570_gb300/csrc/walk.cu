@@ -11,10 +11,13 @@
 // GPU mapping.  One ray per lane.  A warp draws ray indices from a global
 // counter in chunks and serves idle lanes (ballot + prefix popcount) once at
 // least `refill_min` of them are idle, so divergent ray lengths do not idle
-// the warp; a served lane starts in locate mode (no start cells given: the
-// Sec. 5.2 seed walk runs inside this kernel) or in first-triangle mode.
-// Every loop iteration issues exactly one dependent 32-byte record load per
-// active lane, whatever its mode.
+// the warp.  A served lane starts in first-triangle mode, in the given start
+// triangle or -- no start cells given: the Sec. 5.2 seed walk runs inside this
+// kernel -- in the seed triangle of its origin's grid cell.  The seed
+// triangle's inside test is the first-triangle step's own (the given start
+// triangle is checked the same way), so only origins outside it take further
+// locate iterations.  Every loop iteration issues exactly one dependent
+// 32-byte record load per active lane, whatever its mode.
 #include <algorithm>
 #include <cmath>
 
@@ -22,7 +25,7 @@
 
 namespace cct {
 
-enum : int { kModeLocate = 0, kModeFirst = 1, kModeWalk = 2 };
+enum : int { kModeLocate = 0, kModeFirst = 1, kModeWalk = 2, kModeSeed = 3 };
 enum : int { kSrcPlainUser = 0, kSrcPlainDev = 1, kSrcSorted = 2, kSrcLocate = 3 };
 // rare per-warp counters (shared memory)
 enum : int { kCntRays = 0, kCntFallback, kCntInvalid, kCntLimit, kCntLocated, kCntLocSteps, kRareCounters };
@@ -137,9 +140,8 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
                   oy <= S.D;
         if (kLocate) {
           if (ok) {
-            s = S.seeds[seed_cell(S, ox, oy)].tri;
-            j = 3;
-            mode = kModeLocate;
+            s = S.seeds[seed_cell(S, ox, oy)];
+            mode = kModeSeed;
             atomicAdd(&cnt[kCntLocated], 1u);
           }
         } else {
@@ -170,48 +172,72 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     if (active) {
       const TriRec r = load_rec(S.rec + T);
       int status = 0;  // 0 walking on, > 0 finished (steps), < 0 per-ray status
-      bool advance = true;
+      bool step = true;  // take a walk step in T this iteration
       if (kLocate && mode == kModeLocate) {
-        // Sec. 5.2: walk from the seed point towards the origin until the
-        // current triangle holds it (this triangle is then the start triangle);
-        // the seed point is re-read from its cell (L1), not kept in registers
+        // Sec. 5.2 past the seed triangle: T was entered through edge j on the
+        // way from the seed point to the origin; nsteps counts locate steps
         ++nsteps;
-        const SeedCell sd = S.seeds[seed_cell(S, ox, oy)];
-        const int res = locate_step(S, r, T, j, ox, oy, sd.px3, sd.py3);
+        int cx, cy;
+        seed_point(S, ox, oy, cx, cy);
+        const int res = locate_step_entered(S, r, T, j, ox, oy, cx, cy);
+        step = false;
         if (res != 0 || nsteps > S.max_steps) {
           atomicAdd(&cnt[kCntLocSteps], (unsigned)nsteps);
           nsteps = 0;
           if (res > 0) {
-            mode = kModeFirst;
+            mode = kModeFirst;  // T holds the origin: its first walk step follows
+            step = true;
           } else {
             status = CCT_RAY_INVALID;  // origin on an edge or a vertex: not a valid ray origin
             atomicAdd(&cnt[kCntInvalid], 1u);
-            advance = false;
           }
-        } else {
-          advance = false;
         }
       }
-      if (advance) {
-        int e;
-        if (mode == kModeFirst) {
+      if (step) {
+        int e = 0;
+        if (mode != kModeWalk) {
+          // first triangle: the given start triangle, the seed triangle
+          // (kModeSeed) or the triangle where the locate walk found the origin
           const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
           const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
           bool inside = true;
-          if (!kLocate)
-            inside = orient_i(x1, y1, x2, y2, ox, oy) > 0 && orient_i(x2, y2, x0, y0, ox, oy) > 0 &&
-                     orient_i(x0, y0, x1, y1, ox, oy) > 0;
-          unsigned fb = 0;
-          const bool s0 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x0, y0, fb);
-          const bool s1 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x1, y1, fb);
-          const bool s2 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x2, y2, fb);
-          if (fb) atomicAdd(&cnt[kCntFallback], fb);
-          c_side += 3;
-          e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
-          mode = kModeWalk;
-          if (!inside) {
-            status = CCT_RAY_INVALID;
-            atomicAdd(&cnt[kCntInvalid], 1u);
+          if (!kLocate || mode == kModeSeed) {
+            const long long o0 = orient_i(x1, y1, x2, y2, ox, oy), o1 = orient_i(x2, y2, x0, y0, ox, oy);
+            const long long o2 = orient_i(x0, y0, x1, y1, ox, oy);
+            inside = o0 > 0 && o1 > 0 && o2 > 0;
+            if (kLocate) {
+              if (!inside && (o0 < 0 || o1 < 0 || o2 < 0)) {
+                // the origin lies outside the seed triangle: the locate walk
+                // leaves it towards the origin
+                int cx, cy;
+                seed_point(S, ox, oy, cx, cy);
+                nsteps = 1;
+                step = false;
+                if (locate_hop(S, r, T, j, seed_exit(r, cx, cy, ox, oy))) {
+                  mode = kModeLocate;
+                } else {
+                  status = CCT_RAY_INVALID;
+                  atomicAdd(&cnt[kCntInvalid], 1u);
+                  atomicAdd(&cnt[kCntLocSteps], 1u);
+                }
+              } else {
+                atomicAdd(&cnt[kCntLocSteps], 1u);  // located in one step (or on the seed triangle's boundary)
+              }
+            }
+          }
+          if (step) {
+            unsigned fb = 0;
+            const bool s0 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x0, y0, fb);
+            const bool s1 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x1, y1, fb);
+            const bool s2 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x2, y2, fb);
+            if (fb) atomicAdd(&cnt[kCntFallback], fb);
+            c_side += 3;
+            e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
+            mode = kModeWalk;
+            if (!inside) {
+              status = CCT_RAY_INVALID;
+              atomicAdd(&cnt[kCntInvalid], 1u);
+            }
           }
         } else {
           unsigned fb = 0;
@@ -220,7 +246,7 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
           ++c_side;
           e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
         }
-        if (status == 0) {
+        if (step && status == 0) {
           ++nsteps;
           const int32_t w = nb_of(r, e);
           if (w >= 0) {
@@ -331,12 +357,13 @@ static int trace_impl(cct_scene scene, const int32_t* ox, const int32_t* oy, con
   flags |= tu.trace_flags;
   const bool exact = (flags & CCT_TRACE_EXACT_ONLY) != 0;
   const bool bin = (flags & CCT_TRACE_BIN) != 0;
+  const bool split = !start && !bin && (flags & CCT_TRACE_SPLIT_LOCATE) != 0;
   // launches of at most 2^30 rays keep every in-kernel index in 32 bits
   constexpr int64_t kMaxLaunch = 1ll << 30;
   const int64_t n_max = std::min<int64_t>(n, kMaxLaunch);
   const int shift = bin ? (tu.bin_shift >= 0 ? tu.bin_shift : default_bin_shift(n_max, S.n_tri)) : 0;
   const size_t o_start = 256;
-  const size_t o_bin = o_start + ((bin && !start) ? al256(sizeof(int32_t) * (size_t)n_max) : 0);
+  const size_t o_bin = o_start + (((bin || split) && !start) ? al256(sizeof(int32_t) * (size_t)n_max) : 0);
   const size_t total = o_bin + (bin ? bin_scratch_bytes(n_max, S.n_tri, shift) : 0);
   Scratch sc;
   sc.stream = stream;
@@ -357,6 +384,15 @@ static int trace_impl(cct_scene scene, const int32_t* ox, const int32_t* oy, con
     int32_t* h = hit + off;
     int32_t* s = steps + off;
     float* tt = t + off;
+    if (split) {
+      // start cells from the locate kernel (record numbering), then the walk
+      int32_t* sbuf = (int32_t*)(sc.base + o_start);
+      if (launch_locate(S, sx, sy, m, sbuf, false, stream) != cudaSuccess) return CCT_ERR_CUDA;
+      RaySrc R{sx, sy, sdx, sdy, sbuf, nullptr, nullptr, m};
+      if (launch_walk_src(exact, kSrcPlainDev, S, R, tu, h, tt, s, counter, scene->device, stream) != cudaSuccess)
+        return CCT_ERR_CUDA;
+      continue;
+    }
     if (!bin) {
       RaySrc R{sx, sy, sdx, sdy, sst, nullptr, nullptr, m};
       const int src = sst ? kSrcPlainUser : kSrcLocate;
@@ -406,7 +442,7 @@ extern "C" int cct_scene_set_tuning(cct_scene scene, const cct_tuning* tu) {
   }
   if (tu->block_threads < 32 || tu->block_threads > kWalkMaxThreads || tu->block_threads % 32 != 0 ||
       tu->refill_min < 1 || tu->refill_min > 32 || tu->chunk < 32 || tu->chunk > (1 << 20) || tu->bin_shift > 30 ||
-      (tu->trace_flags & ~(CCT_TRACE_EXACT_ONLY | CCT_TRACE_BIN)) != 0)
+      (tu->trace_flags & ~(CCT_TRACE_EXACT_ONLY | CCT_TRACE_BIN | CCT_TRACE_SPLIT_LOCATE)) != 0)
     return CCT_ERR_INVALID_ARGUMENT;
   scene->tuning = *tu;
   return CCT_OK;

@@ -82,13 +82,13 @@ def test_config1_locate_then_walk(cct, scenes):
         r = sg.rays_isotropic(tri, 65536 + 37, 20 + seed)  # ragged tail
         exp = oracle.walk(tri, r.ox, r.oy, r.dx, r.dy, r.start)
         scene = cct.Scene.from_triangulation(tri, sg.D)
-        for flags in (0, cct.CCT_TRACE_BIN):
+        for flags in (0, cct.CCT_TRACE_BIN, cct.CCT_TRACE_SPLIT_LOCATE):
             _assert_parity(_trace(scene, r.ox, r.oy, r.dx, r.dy, None, flags), exp)
         st = scene.locate(_dev(r.ox), _dev(r.oy))
         torch.cuda.synchronize()
         assert np.array_equal(st.cpu().numpy(), r.start)
         stats = scene.stats()
-        assert stats["located"] == 2 * len(r) + len(r)
+        assert stats["located"] == 3 * len(r) + len(r)
         scene.free()
 
 
@@ -111,6 +111,32 @@ def test_locate_edges_vertices_and_outside(cct, scenes):
     got = scene.locate(_dev(px), _dev(py))
     torch.cuda.synchronize()
     assert np.array_equal(got.cpu().numpy(), exp)
+    scene.free()
+
+
+@pytest.mark.parametrize("density", [0, 2, 5, 8])
+def test_locate_seed_ties_on_lattice(cct, lattice, density):
+    """Seed points (cell centres) that fall on vertices and edges, and origins
+    collinear with seed points and vertices: every integer point of a small
+    lattice triangulation, located and traced from no start cell, equals the
+    brute-force location and the oracle walk.  Density 8 gives cells of side 1,
+    so every seed point is a lattice point."""
+    tri = lattice()
+    g = np.arange(-1, tri.D + 2, dtype=np.int32)
+    px, py = [np.ascontiguousarray(a.ravel()) for a in np.meshgrid(g, g)]
+    exp = oracle.locate_bruteforce(tri, px, py)
+    exp = np.where(exp < 0, -1, exp)
+    scene = cct.Scene.from_triangulation(tri, tri.D, flags=cct.CCT_LOAD_SEED_DENSITY(density))
+    got = scene.locate(_dev(px), _dev(py))
+    torch.cuda.synchronize()
+    assert np.array_equal(got.cpu().numpy(), exp)
+    rng = np.random.default_rng(density)
+    ang = rng.uniform(0, 2 * np.pi, px.size)
+    dx = (np.round(np.cos(ang) * K) / K).astype(np.float32)
+    dy = (np.round(np.sin(ang) * K) / K).astype(np.float32)
+    ref = oracle.walk(tri, px, py, dx, dy, exp)
+    for flags in (0, cct.CCT_TRACE_EXACT_ONLY, cct.CCT_TRACE_BIN, cct.CCT_TRACE_SPLIT_LOCATE):
+        _assert_parity(_trace(scene, px, py, dx, dy, None, flags), ref)
     scene.free()
 
 
@@ -267,7 +293,8 @@ def test_results_independent_of_tuning(cct, scenes):
                {"block_threads": 512, "refill_min": 32, "chunk": 4096},
                {"block_threads": 128, "refill_min": 4, "chunk": 64, "bin_shift": 0},
                {"block_threads": 96, "refill_min": 16, "chunk": 200, "bin_shift": 5,
-                "trace_flags": cct.CCT_TRACE_EXACT_ONLY}):
+                "trace_flags": cct.CCT_TRACE_EXACT_ONLY},
+               {"block_threads": 64, "refill_min": 24, "chunk": 64, "trace_flags": cct.CCT_TRACE_SPLIT_LOCATE}):
         scene.set_tuning(tu)
         assert all(scene.tuning()[k] == v for k, v in tu.items())
         for start in (r.start, None):

@@ -395,3 +395,25 @@ def test_refined_cdt_is_valid_and_optimal(gen):
     if gen == "circles":
         # polygon interiors: refinement shortens the triangulation markedly
         assert oracle.interior_length(ref) < 0.5 * oracle.interior_length(cdt)
+
+
+def test_lattice_fixture_valid_and_walk_matches_bruteforce(lattice):
+    """The hand-made lattice triangulation (many collinear lattice points)
+    passes every invariant, and on it the oracle walk from brute-force-located
+    start triangles equals the all-segment closest-hit scan."""
+    tri = lattice()
+    assert oracle.check_triangulation(tri, tri.D) == 0
+    g = np.arange(-1, tri.D + 2, dtype=np.int32)
+    px, py = [a.ravel() for a in np.meshgrid(g, g)]
+    start = oracle.locate_bruteforce(tri, px, py)
+    ok = start >= 0
+    # per square of side 4: 3 x 3 interior lattice points, 3 of them on the diagonal
+    assert ok.sum() == 12 * 12 * 6
+    rng = np.random.default_rng(3)
+    ang = rng.uniform(0, 2 * np.pi, px.size)
+    dx = (np.round(np.cos(ang) * K) / K).astype(np.float32)
+    dy = (np.round(np.sin(ang) * K) / K).astype(np.float32)
+    h, t, s = oracle.walk(tri, px, py, dx, dy, start)
+    hb, tb = oracle.closest_bruteforce(tri.segs, px[ok], py[ok], dx[ok], dy[ok])
+    assert np.array_equal(h[ok], hb)
+    assert (s[~ok] == -1).all() and (s[ok] >= 1).all()
