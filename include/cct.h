@@ -68,7 +68,8 @@ extern "C" {
 
 /* Density of the locate seed grid (Sec. 5.2): square cells of side 2^s with
  * about 2^k cells per triangle, k in [0, 8] (at most 8192 cells per side; 4
- * bytes per cell), encoded in bits 8..11 of the load flags.  Without it k = 2. */
+ * bytes per cell), encoded in bits 8..11 of the load flags.  Without it k = 5
+ * (about 1.1 locate steps per uniformly placed origin). */
 #define CCT_LOAD_SEED_DENSITY(k) ((uint32_t)((k) + 1) << 8)
 
 /* cct_trace */

@@ -113,6 +113,32 @@ __device__ __forceinline__ bool side_L(float fdx, float fdy, int kx, int ky, int
   return e >= 0;
 }
 
+// The same side test with the direction held as one 32-bit word per
+// component: the float k (exact: |k| <= 2^22) in the fp32-filtered variant,
+// the int k in the exact-only variant.  The filter then reads
+// r = fma(kx, dy_v, -(ky dx_v)), 2^22 times the product above, with the bound
+// scaled by the same power of two.
+template <bool kExactOnly>
+__device__ __forceinline__ int k_word(int k) {
+  return kExactOnly ? k : __float_as_int((float)k);
+}
+template <bool kExactOnly>
+__device__ __forceinline__ int k_of_word(int w) {
+  return kExactOnly ? w : (int)__int_as_float(w);
+}
+template <bool kExactOnly>
+__device__ __forceinline__ bool side_L_w(int kxw, int kyw, int ox, int oy, int vx, int vy, unsigned& fallbacks) {
+  const int ddx = vx - ox, ddy = vy - oy;
+  if (!kExactOnly) {
+    const float p = __fmul_rn(__int_as_float(kyw), (float)ddx);
+    const float r = __fmaf_rn(__int_as_float(kxw), (float)ddy, -p);
+    if (fabsf(r) >= kFilterBound * kDirScale) return r > 0.0f;
+    ++fallbacks;
+  }
+  const long long e = (long long)k_of_word<kExactOnly>(kxw) * ddy - (long long)k_of_word<kExactOnly>(kyw) * ddx;
+  return e >= 0;
+}
+
 __device__ __forceinline__ long long orient_ll(long long ax, long long ay, long long bx, long long by, long long cx,
                                                long long cy) {
   return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);

@@ -224,7 +224,7 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
     int shift = 0, G = 1;
     {
       const unsigned kd = (flags >> 8) & 15u;
-      const int k = kd == 0 ? 2 : std::min(8, (int)kd - 1);
+      const int k = kd == 0 ? 5 : std::min(8, (int)kd - 1);
       const double h = (double)D / std::sqrt(std::ldexp(1.0, k) * (double)nt);
       shift = std::max(0, (int)std::lround(std::log2(std::max(1.0, h))));
       while (((D + (1ll << shift) - 1) >> shift) > 8192) ++shift;

@@ -8,16 +8,21 @@
 // constrained edge ends the walk with a hit (t from the edge's line), a hull
 // edge with a miss.  Step count = triangles visited (Sec. 5.4).
 //
-// GPU mapping.  One ray per lane.  A warp draws ray indices from a global
-// counter in chunks and serves idle lanes (ballot + prefix popcount) once at
-// least `refill_min` of them are idle, so divergent ray lengths do not idle
-// the warp.  A served lane starts in first-triangle mode, in the given start
-// triangle or -- no start cells given: the Sec. 5.2 seed walk runs inside this
-// kernel -- in the seed triangle of its origin's grid cell.  The seed
-// triangle's inside test is the first-triangle step's own (the given start
-// triangle is checked the same way), so only origins outside it take further
-// locate iterations.  Every loop iteration issues exactly one dependent
-// 32-byte record load per active lane, whatever its mode.
+// GPU mapping.  One ray per lane in the walk proper; everything done once
+// per ray is done 32 rays at a time, by the whole warp, so the per-ray work
+// never runs with most lanes masked off:
+//   prepare  the warp takes 32 ray indices (from its chunk of a global work
+//            counter), loads the rays, finds their start triangles (given,
+//            or by the Sec. 5.2 locate walk from the seed point of their grid
+//            cell) and takes the first step; the resulting walk states go on
+//            the warp's `ready` stack in shared memory;
+//   walk     each active lane takes one apex step per loop iteration: one
+//            dependent 32-byte record load, one side test;
+//   serve    once `refill_min` lanes are idle, finished lanes park their
+//            final state on the `parked` stack and idle lanes pop `ready`
+//            states (a prepare first when too few are left);
+//   flush    32 parked rays at a time: reload the final record, compute hit
+//            id and t, write the results.
 #include <algorithm>
 #include <cmath>
 
@@ -25,7 +30,6 @@
 
 namespace cct {
 
-enum : int { kModeLocate = 0, kModeFirst = 1, kModeWalk = 2, kModeSeed = 3 };
 enum : int { kSrcPlainUser = 0, kSrcPlainDev = 1, kSrcSorted = 2, kSrcLocate = 3 };
 // rare per-warp counters (shared memory)
 enum : int { kCntRays = 0, kCntFallback, kCntInvalid, kCntLimit, kCntLocated, kCntLocSteps, kRareCounters };
@@ -37,29 +41,16 @@ struct WalkParams {
   int chunk;       // ray indices a warp takes from the global counter at once
 };
 
-// Writes the parked result of a finished lane: hit id and t come from its
-// final record (reloaded: it was read one iteration ago, so from L1/L2),
-// `st` is the step count or a negative per-ray status.
-__device__ __forceinline__ void complete_ray(const TriRec* __restrict__ rec, int T, int e, int st, int ox, int oy,
-                                             int kx, int ky, int idx, int32_t* __restrict__ hit_out,
-                                             float* __restrict__ t_out, int32_t* __restrict__ steps_out) {
-  int32_t h = -1;
-  float t = __int_as_float(0x7fc00000);  // NaN: invalid ray
-  if (st > 0) {
-    const TriRec r = load_rec(rec + T);
-    const int32_t w = nb_of(r, e);
-    if (w <= -2) {
-      h = -2 - w;
-      const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
-      t = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), ox, oy, kx, ky);
-    } else {
-      t = __int_as_float(0x7f800000);  // +inf: left through the hull
-    }
-  }
-  hit_out[idx] = h;
-  t_out[idx] = t;
-  steps_out[idx] = st;
-}
+// Per-warp stacks in shared memory.  `ready` holds rays whose first
+// triangle is behind them (the state after the first step: next record and
+// entry edge); `parked` holds finished rays waiting for their results.
+constexpr int kStack = 64;
+struct WarpStacks {
+  int r_ox[kStack], r_oy[kStack], r_kx[kStack], r_ky[kStack], r_tj[kStack], r_idx[kStack];
+  int d_idx[kStack], d_te[kStack], d_st[kStack], d_ox[kStack], d_oy[kStack], d_kx[kStack], d_ky[kStack];
+  unsigned cnt[kRareCounters];
+  unsigned long long steps, sides;  // step and side-test counts of the warp's finished rays
+};
 
 template <bool kExact, int kSrc>
 __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySrc R, WalkParams P,
@@ -69,215 +60,303 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
                                                                unsigned long long* __restrict__ counter) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr bool kLocate = (kSrc == kSrcLocate);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpStacks& W = reinterpret_cast<WarpStacks*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int n = (int)R.n;
-  int pool_next = 0, pool_end = 0;
+  int pool_next = 0, pool_end = 0;  // the warp's current range of ray indices
+  int n_ready = 0, n_done = 0;      // stack depths (warp-uniform)
   bool exhausted = false;
 
-  // lane state: walking (active), finished with a parked result (done), or idle;
-  // in locate mode nsteps counts locate steps
+  // lane state: walking (active), finished and not yet parked (done), or idle
+  // (kx, ky: direction words, see side_L_w)
   bool active = false, done = false;
-  int mode = kModeFirst;
   int idx = 0, ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0;
-  float fdx = 0.f, fdy = 0.f;
-
-  // hot counters in registers, rare ones per warp in shared memory
-  unsigned c_steps = 0, c_side = 0;
-  __shared__ unsigned s_cnt[kWalkMaxThreads / 32][kRareCounters];
-  unsigned* cnt = s_cnt[threadIdx.x >> 5];
-  if (lane < kRareCounters) cnt[lane] = 0;
+  if (lane < kRareCounters) W.cnt[lane] = 0;
+  if (lane == 0) W.steps = W.sides = 0;
   __syncwarp();
+
+  // Results of the parked rays [top - m, top): lane l completes entry top - m + l
+  // (the final record is reloaded: it was read a few iterations ago).  Also
+  // counts their steps and their side tests after the first triangle.
+  auto flush = [&](int m, int top) {
+    __syncwarp();
+    unsigned f_steps = 0, f_sides = 0;
+    if (lane < m) {
+      const int k = top - m + lane;
+      const int id = W.d_idx[k], te = W.d_te[k], st = W.d_st[k];
+      int32_t h = -1;
+      float tv = __int_as_float(0x7fc00000);  // NaN: invalid ray or step limit
+      if (st > 0) {
+        f_steps = (unsigned)st;
+        f_sides = (unsigned)st - 1u;
+        const TriRec r = load_rec(S.rec + (te >> 2));
+        const int e = te & 3;
+        const int32_t w = nb_of(r, e);
+        if (w <= -2) {
+          h = -2 - w;
+          const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
+          tv = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), W.d_ox[k], W.d_oy[k],
+                              k_of_word<kExact>(W.d_kx[k]), k_of_word<kExact>(W.d_ky[k]));
+        } else {
+          tv = __int_as_float(0x7f800000);  // +inf: left through the hull
+        }
+      } else if (st == CCT_RAY_WALK_LIMIT) {
+        f_sides = (unsigned)S.max_steps - 1u;
+      }
+      hit_out[id] = h;
+      t_out[id] = tv;
+      steps_out[id] = st;
+    }
+    f_steps = __reduce_add_sync(FULL, f_steps);
+    f_sides = __reduce_add_sync(FULL, f_sides);
+    if (lane == 0) {
+      W.steps += f_steps;
+      W.sides += f_sides;
+    }
+    __syncwarp();
+  };
+
+  // Takes up to 32 new rays, finds their start triangles (given, or by the
+  // Sec. 5.2 locate walk from the seed point of their cell) and takes their
+  // first step; pushes them on `ready`, or on `parked` when they end in the
+  // first triangle or are invalid.  The whole warp works on 32 rays at once.
+  auto prepare = [&]() {
+    if (pool_next >= pool_end) {
+      int base = 0;
+      if (lane == 0) base = (int)atomicAdd(counter, (unsigned long long)P.chunk);
+      base = __shfl_sync(FULL, base, 0);
+      if (base >= n) {
+        exhausted = true;
+        return;
+      }
+      pool_next = base;
+      pool_end = min(base + P.chunk, n);
+    }
+    const int i = pool_next + lane;
+    const bool v = i < pool_end;
+    pool_next = min(pool_next + 32, pool_end);
+    int pox = 0, poy = 0, pkx = 0, pky = 0, pid = i, T0 = -1;
+    float pdx = 0.f, pdy = 0.f;
+    bool ok = false;
+    if (v) {
+      if (kSrc == kSrcSorted) {
+        const int4 rr = R.rays[i];
+        pox = rr.x;
+        poy = rr.y;
+        pdx = __int_as_float(rr.z);
+        pdy = __int_as_float(rr.w);
+        T0 = R.start[i];
+        pid = R.orig[i];
+      } else {
+        pox = R.ox[i];
+        poy = R.oy[i];
+        pdx = R.dx[i];
+        pdy = R.dy[i];
+        if (!kLocate) {
+          T0 = R.start[i];
+          if (kSrc == kSrcPlainUser) T0 = (T0 >= 0 && T0 < S.n_tri) ? S.user2dev[T0] : -1;
+        }
+      }
+      // origins outside the domain lie in no triangle; rejecting them here
+      // keeps every coordinate difference of the walk within int32
+      ok = dir_to_k(pdx, pkx) && dir_to_k(pdy, pky) && (pkx | pky) != 0 && pox >= 0 && poy >= 0 && pox <= S.D &&
+           poy <= S.D;
+      if (kLocate) {
+        if (ok) T0 = S.seeds[seed_cell(S, pox, poy)];
+      } else {
+        ok = ok && T0 >= 0 && T0 < S.n_tri;
+      }
+    }
+    const unsigned m_loc = kLocate ? __ballot_sync(FULL, ok) : 0u;
+    TriRec r;
+    if (ok) r = load_rec(S.rec + T0);
+    int lsteps = 0;
+    if (kLocate) {
+      // the seed triangle holds the (perturbed) seed point; walk from there
+      // towards the origin until the current triangle holds it
+      int jj = 3;
+      bool locating = false;
+      if (ok) {
+        lsteps = 1;
+        const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
+        const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
+        const long long o0 = orient_i(x1, y1, x2, y2, pox, poy), o1 = orient_i(x2, y2, x0, y0, pox, poy);
+        const long long o2 = orient_i(x0, y0, x1, y1, pox, poy);
+        if (o0 < 0 || o1 < 0 || o2 < 0) {
+          int cx, cy;
+          seed_point(S, pox, poy, cx, cy);
+          locating = locate_hop(S, r, T0, jj, seed_exit(r, cx, cy, pox, poy));
+          ok = locating;
+        } else if (o0 == 0 || o1 == 0 || o2 == 0) {
+          ok = false;  // origin on an edge or a vertex: not a valid ray origin
+        }
+      }
+      while (__any_sync(FULL, locating)) {
+        if (locating) {
+          r = load_rec(S.rec + T0);
+          ++lsteps;
+          int cx, cy;
+          seed_point(S, pox, poy, cx, cy);
+          const int res = locate_step_entered(S, r, T0, jj, pox, poy, cx, cy);
+          if (res != 0 || lsteps > S.max_steps) {
+            locating = false;
+            ok = res > 0;
+          }
+        }
+      }
+    }
+    // first step (Sec. 5.1): sides of all three vertices, leave through the
+    // CCW edge (a -> b) with s(a) = R, s(b) = L
+    int e = 0;
+    int32_t w = -1;
+    if (ok) {
+      const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
+      const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
+      if (!kLocate)
+        ok = orient_i(x1, y1, x2, y2, pox, poy) > 0 && orient_i(x2, y2, x0, y0, pox, poy) > 0 &&
+             orient_i(x0, y0, x1, y1, pox, poy) > 0;
+      unsigned fb = 0;
+      const bool s0 = side_L<kExact>(pdx, pdy, pkx, pky, pox, poy, x0, y0, fb);
+      const bool s1 = side_L<kExact>(pdx, pdy, pkx, pky, pox, poy, x1, y1, fb);
+      const bool s2 = side_L<kExact>(pdx, pdy, pkx, pky, pox, poy, x2, y2, fb);
+      if (!kExact && fb) atomicAdd(&W.cnt[kCntFallback], fb);
+      e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
+      w = nb_of(r, e);
+    }
+    // three side tests per ray that reached its first step
+    const unsigned m_first = __ballot_sync(FULL, ok);
+    const bool to_ready = ok && w >= 0;
+    const bool to_done = v && !to_ready;
+    const unsigned mr = __ballot_sync(FULL, to_ready), md = __ballot_sync(FULL, to_done);
+    const unsigned mv = __ballot_sync(FULL, v), minv = __ballot_sync(FULL, v && !ok);
+    if (kLocate) {
+      const unsigned ls = __reduce_add_sync(FULL, (unsigned)lsteps);
+      if (lane == 0) {
+        W.cnt[kCntLocated] += __popc(m_loc);
+        W.cnt[kCntLocSteps] += ls;
+      }
+    }
+    if (lane == 0) {
+      W.cnt[kCntRays] += __popc(mv);
+      W.cnt[kCntInvalid] += __popc(minv);
+      W.sides += 3ull * (unsigned)__popc(m_first);
+    }
+    if (to_ready) {
+      const int k = n_ready + __popc(mr & lt);
+      W.r_ox[k] = pox;
+      W.r_oy[k] = poy;
+      W.r_kx[k] = k_word<kExact>(pkx);
+      W.r_ky[k] = k_word<kExact>(pky);
+      W.r_tj[k] = w;
+      W.r_idx[k] = pid;
+    } else if (to_done) {
+      const int k = n_done + __popc(md & lt);
+      W.d_idx[k] = pid;
+      W.d_te[k] = (T0 << 2) | e;
+      W.d_st[k] = ok ? 1 : CCT_RAY_INVALID;
+      W.d_ox[k] = pox;
+      W.d_oy[k] = poy;
+      W.d_kx[k] = k_word<kExact>(pkx);
+      W.d_ky[k] = k_word<kExact>(pky);
+    }
+    n_ready += __popc(mr);
+    n_done += __popc(md);
+    __syncwarp();
+  };
 
   while (true) {
     // ---------------------------------------------------------------- serve idle lanes
-    // (also where finished lanes write their parked results: a batch of
-    // completions costs the warp one pass, not one per iteration)
-    while (!exhausted) {
-      const unsigned need = __ballot_sync(FULL, !active);
-      if (need == 0u) break;
-      if (__popc(need) < P.refill_min && need != FULL) break;
+    const unsigned idle = __ballot_sync(FULL, !active);
+    if (idle != 0u && (__popc(idle) >= P.refill_min || idle == FULL)) {
+      // park finished rays; complete them 32 at a time
+      const unsigned dm = __ballot_sync(FULL, done);
       if (done) {
-        complete_ray(S.rec, T, j, nsteps, ox, oy, kx, ky, idx, hit_out, t_out, steps_out);
+        const int k = n_done + __popc(dm & lt);
+        W.d_idx[k] = idx;
+        W.d_te[k] = (T << 2) | j;
+        W.d_st[k] = nsteps;
+        W.d_ox[k] = ox;
+        W.d_oy[k] = oy;
+        W.d_kx[k] = kx;
+        W.d_ky[k] = ky;
         done = false;
       }
-      if (pool_next >= pool_end) {
-        int base = 0;
-        if (lane == 0) base = (int)atomicAdd(counter, (unsigned long long)P.chunk);
-        base = __shfl_sync(FULL, base, 0);
-        if (base >= n) {
-          exhausted = true;
-          break;
-        }
-        pool_next = base;
-        pool_end = min(base + P.chunk, n);
+      n_done += __popc(dm);
+      if (n_done >= 32) {
+        flush(32, n_done);
+        n_done -= 32;
       }
-      const int avail = pool_end - pool_next;
-      const int rank = __popc(need & lt);
-      if (!active && rank < avail) {
-        idx = pool_next + rank;
-        int s = -1;
-        if (kSrc == kSrcSorted) {
-          const int4 rr = R.rays[idx];
-          ox = rr.x;
-          oy = rr.y;
-          fdx = __int_as_float(rr.z);
-          fdy = __int_as_float(rr.w);
-          s = R.start[idx];
-        } else {
-          ox = R.ox[idx];
-          oy = R.oy[idx];
-          fdx = R.dx[idx];
-          fdy = R.dy[idx];
-          if (!kLocate) {
-            s = R.start[idx];
-            if (kSrc == kSrcPlainUser) s = (s >= 0 && s < S.n_tri) ? S.user2dev[s] : -1;
-          }
-        }
-        // origins outside the domain lie in no triangle; rejecting them here
-        // keeps every coordinate difference of the walk within int32
-        bool ok = dir_to_k(fdx, kx) && dir_to_k(fdy, ky) && (kx | ky) != 0 && ox >= 0 && oy >= 0 && ox <= S.D &&
-                  oy <= S.D;
-        if (kLocate) {
-          if (ok) {
-            s = S.seeds[seed_cell(S, ox, oy)];
-            mode = kModeSeed;
-            atomicAdd(&cnt[kCntLocated], 1u);
-          }
-        } else {
-          mode = kModeFirst;
-          ok = ok && s >= 0 && s < S.n_tri;
-        }
-        if (kSrc == kSrcSorted) idx = R.orig[idx];
-        atomicAdd(&cnt[kCntRays], 1u);
-        if (ok) {
-          T = s;
-          nsteps = 0;
-          active = true;
-        } else {
-          hit_out[idx] = -1;
-          t_out[idx] = __int_as_float(0x7fc00000);
-          steps_out[idx] = CCT_RAY_INVALID;
-          atomicAdd(&cnt[kCntInvalid], 1u);
+      const int want = __popc(idle);
+      if (n_ready < want && !exhausted) {
+        prepare();
+        if (n_done >= 32) {
+          flush(32, n_done);
+          n_done -= 32;
         }
       }
-      pool_next += min(__popc(need), avail);
+      const int rank = __popc(idle & lt);
+      if (!active && rank < n_ready) {
+        const int k = n_ready - 1 - rank;
+        ox = W.r_ox[k];
+        oy = W.r_oy[k];
+        kx = W.r_kx[k];
+        ky = W.r_ky[k];
+        const int tj = W.r_tj[k];
+        idx = W.r_idx[k];
+        T = tj >> 2;
+        j = tj & 3;
+        nsteps = 1;
+        active = true;
+      }
+      n_ready -= min(want, n_ready);
+      __syncwarp();
     }
     if (!__any_sync(FULL, active)) {
-      if (exhausted) break;
+      if (exhausted && n_ready == 0) break;
       continue;
     }
 
-    // ---------------------------------------------------------------- one record per active lane
+    // ---------------------------------------------------------------- one step per active lane
+    // Across an interior edge the neighbour shares the two decided vertices:
+    // decide the apex only, s(c) = L -> leave through (R-vertex, c), else
+    // through (c, L-vertex).
     if (active) {
       const TriRec r = load_rec(S.rec + T);
-      int status = 0;  // 0 walking on, > 0 finished (steps), < 0 per-ray status
-      bool step = true;  // take a walk step in T this iteration
-      if (kLocate && mode == kModeLocate) {
-        // Sec. 5.2 past the seed triangle: T was entered through edge j on the
-        // way from the seed point to the origin; nsteps counts locate steps
-        ++nsteps;
-        int cx, cy;
-        seed_point(S, ox, oy, cx, cy);
-        const int res = locate_step_entered(S, r, T, j, ox, oy, cx, cy);
-        step = false;
-        if (res != 0 || nsteps > S.max_steps) {
-          atomicAdd(&cnt[kCntLocSteps], (unsigned)nsteps);
-          nsteps = 0;
-          if (res > 0) {
-            mode = kModeFirst;  // T holds the origin: its first walk step follows
-            step = true;
-          } else {
-            status = CCT_RAY_INVALID;  // origin on an edge or a vertex: not a valid ray origin
-            atomicAdd(&cnt[kCntInvalid], 1u);
-          }
+      unsigned fb = 0;
+      const bool sc = side_L_w<kExact>(kx, ky, ox, oy, vx_of(r, j), vy_of(r, j), fb);
+      if (!kExact && fb) atomicAdd(&W.cnt[kCntFallback], fb);
+      const int e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
+      ++nsteps;
+      const int32_t w = nb_of(r, e);
+      if (w >= 0) {
+        T = w >> 2;
+        j = w & 3;
+        if (nsteps >= S.max_steps) {
+          nsteps = CCT_RAY_WALK_LIMIT;
+          active = false;
+          done = true;
+          atomicAdd(&W.cnt[kCntLimit], 1u);
         }
-      }
-      if (step) {
-        int e = 0;
-        if (mode != kModeWalk) {
-          // first triangle: the given start triangle, the seed triangle
-          // (kModeSeed) or the triangle where the locate walk found the origin
-          const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
-          const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
-          bool inside = true;
-          if (!kLocate || mode == kModeSeed) {
-            const long long o0 = orient_i(x1, y1, x2, y2, ox, oy), o1 = orient_i(x2, y2, x0, y0, ox, oy);
-            const long long o2 = orient_i(x0, y0, x1, y1, ox, oy);
-            inside = o0 > 0 && o1 > 0 && o2 > 0;
-            if (kLocate) {
-              if (!inside && (o0 < 0 || o1 < 0 || o2 < 0)) {
-                // the origin lies outside the seed triangle: the locate walk
-                // leaves it towards the origin
-                int cx, cy;
-                seed_point(S, ox, oy, cx, cy);
-                nsteps = 1;
-                step = false;
-                if (locate_hop(S, r, T, j, seed_exit(r, cx, cy, ox, oy))) {
-                  mode = kModeLocate;
-                } else {
-                  status = CCT_RAY_INVALID;
-                  atomicAdd(&cnt[kCntInvalid], 1u);
-                  atomicAdd(&cnt[kCntLocSteps], 1u);
-                }
-              } else {
-                atomicAdd(&cnt[kCntLocSteps], 1u);  // located in one step (or on the seed triangle's boundary)
-              }
-            }
-          }
-          if (step) {
-            unsigned fb = 0;
-            const bool s0 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x0, y0, fb);
-            const bool s1 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x1, y1, fb);
-            const bool s2 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x2, y2, fb);
-            if (fb) atomicAdd(&cnt[kCntFallback], fb);
-            c_side += 3;
-            e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
-            mode = kModeWalk;
-            if (!inside) {
-              status = CCT_RAY_INVALID;
-              atomicAdd(&cnt[kCntInvalid], 1u);
-            }
-          }
-        } else {
-          unsigned fb = 0;
-          const bool sc = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, vx_of(r, j), vy_of(r, j), fb);
-          if (fb) atomicAdd(&cnt[kCntFallback], fb);
-          ++c_side;
-          e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
-        }
-        if (step && status == 0) {
-          ++nsteps;
-          const int32_t w = nb_of(r, e);
-          if (w >= 0) {
-            if (nsteps >= S.max_steps) {
-              status = CCT_RAY_WALK_LIMIT;
-              atomicAdd(&cnt[kCntLimit], 1u);
-            } else {
-              T = w >> 2;
-              j = w & 3;
-            }
-          } else {
-            status = nsteps;  // hit or miss: park T (the final triangle) and e
-            j = e;
-            c_steps += (unsigned)nsteps;
-          }
-        }
-      }
-      if (status != 0) {
-        nsteps = status;
+      } else {
+        j = e;  // hit or miss: park the final triangle and its exit edge
         active = false;
         done = true;
       }
     }
   }
-  if (done) complete_ray(S.rec, T, j, nsteps, ox, oy, kx, ky, idx, hit_out, t_out, steps_out);
+  // the last parked rays (the final serve round parked every finished lane)
+  while (n_done > 0) {
+    const int m = min(32, n_done);
+    flush(m, n_done);
+    n_done -= m;
+  }
   // ---------------------------------------------------------------- counters: one atomic per warp and counter
-  const unsigned long long w_steps = warp_sum((unsigned long long)c_steps);
-  const unsigned long long w_side = warp_sum((unsigned long long)c_side);
   __syncwarp();
-  const unsigned long long w_rays = cnt[kCntRays], w_fb = cnt[kCntFallback], w_inv = cnt[kCntInvalid];
-  const unsigned long long w_lim = cnt[kCntLimit], w_loc = cnt[kCntLocated], w_lst = cnt[kCntLocSteps];
+  const unsigned long long w_steps = W.steps, w_side = W.sides;
+  const unsigned long long w_rays = W.cnt[kCntRays], w_fb = W.cnt[kCntFallback], w_inv = W.cnt[kCntInvalid];
+  const unsigned long long w_lim = W.cnt[kCntLimit], w_loc = W.cnt[kCntLocated], w_lst = W.cnt[kCntLocSteps];
   if (lane == 0) {
     if (w_rays) atomicAdd(&S.stats->rays, w_rays);
     if (w_steps) atomicAdd(&S.stats->steps, w_steps);
@@ -295,13 +374,26 @@ static cudaError_t launch_walk_t(const SceneDev& S, const RaySrc& R, const cct_t
                                  int32_t* steps, unsigned long long* counter, int dev, cudaStream_t stream) {
   auto k = walk_kernel<kExact, kSrc>;
   const int threads = tu.block_threads;
+  const size_t smem = sizeof(WarpStacks) * (size_t)(threads / 32);
+  static bool configured = false;  // per instantiation; setting it twice is harmless
+  if (!configured) {
+    // the stacks of 16 warps exceed the default 48 KB of dynamic shared
+    // memory.  The shared/L1 split is left to the driver: a maximal shared
+    // carveout measured 1.5x slower (the L1 also holds the loads in flight).
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(sizeof(WarpStacks) * (kWalkMaxThreads / 32)));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  // every warp takes 32 rays at a time
   const long long want = (R.n + threads - 1) / threads;
   long long grid = std::min<long long>((long long)sm_count(dev) * per_sm, want);
   if (grid < 1) grid = 1;
   WalkParams P{std::max(1, std::min(32, tu.refill_min)), std::max(32, tu.chunk)};
-  k<<<(unsigned)grid, threads, 0, stream>>>(S, R, P, hit, t, steps, counter);
+  k<<<(unsigned)grid, threads, smem, stream>>>(S, R, P, hit, t, steps, counter);
   return cudaGetLastError();
 }
 
