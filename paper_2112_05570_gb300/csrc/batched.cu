@@ -58,25 +58,20 @@ __device__ __forceinline__ int find_item(const BatchItemDev* items, int n_items,
   return lo;
 }
 
-__device__ __forceinline__ void batch_complete(const BatchItemDev& it, const TriRec* __restrict__ rec, int T, int e,
-                                               int st, int ox, int oy, int kx, int ky, int idx) {
-  int32_t h = -1;
-  float t = __int_as_float(0x7fc00000);
-  if (st > 0) {
-    const TriRec r = load_rec(rec + T);
-    const int32_t w = nb_of(r, e);
-    if (w <= -2) {
-      h = -2 - w;
-      const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
-      t = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), ox, oy, kx, ky);
-    } else {
-      t = __int_as_float(0x7f800000);
-    }
-  }
-  it.hit[idx] = h;
-  it.t[idx] = t;
-  it.steps[idx] = st;
-}
+// Per-warp stacks in shared memory, as in the single-scene walk: `ready`
+// holds rays past their first triangle, `parked` finished rays awaiting
+// their results; each entry carries its item and scene.
+constexpr int kBStack = 64;
+enum : int { kBRays = 0, kBFallback, kBInvalid, kBLimit, kBLocated, kBLocSteps, kBCounters };
+struct BatchStacks {
+  int r_ox[kBStack], r_oy[kBStack], r_kx[kBStack], r_ky[kBStack], r_tj[kBStack], r_idx[kBStack], r_item[kBStack],
+      r_scene[kBStack];
+  int d_idx[kBStack], d_te[kBStack], d_st[kBStack], d_ox[kBStack], d_oy[kBStack], d_kx[kBStack], d_ky[kBStack],
+      d_item[kBStack], d_scene[kBStack];
+  int l_idx[32], l_item[32], l_scene[32];  // the walking lanes' cold state (read when they park)
+  unsigned cnt[kBCounters];
+  unsigned long long steps, sides;
+};
 
 template <bool kExact>
 __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev* __restrict__ scenes,
@@ -85,193 +80,290 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
                                                                  int refill_min, unsigned long long* counter,
                                                                  DevStats* bstats) {
   constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BatchStacks& W = reinterpret_cast<BatchStacks*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int n_items = hdr->n_items, total = hdr->total_chunks, chunk = hdr->chunk;
   // warp-uniform pool: a range of rays of one item
-  int p_item = -1, p_next = 0, p_end = 0;
+  int p_item = 0, p_next = 0, p_end = 0;
+  int n_ready = 0, n_done = 0;
   bool exhausted = n_items <= 0;
-  // lane state: walking (active), finished with a parked result (done), or idle
+  // lane state: walking (active), finished and not yet parked (done), or idle
   bool active = false, done = false;
-  // modes: 0 locate past the seed triangle, 1 first triangle, 2 walk, 3 seed triangle
-  int mode = 1, item = 0, idx = 0, ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0, lsteps = 0;
-  int max_steps = 0, scene = 0;
-  float fdx = 0.f, fdy = 0.f;
+  int ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0, max_steps = 0;
   const TriRec* rec = nullptr;
-  unsigned c_steps = 0, c_side = 0, c_fb = 0, c_rays = 0, c_inv = 0, c_lim = 0, c_loc = 0, c_lsteps = 0;
+  if (lane < kBCounters) W.cnt[lane] = 0;
+  if (lane == 0) W.steps = W.sides = 0;
+  W.l_scene[lane] = 0;
+  __syncwarp();
+
+  auto flush = [&](int m, int top) {
+    __syncwarp();
+    unsigned f_steps = 0, f_sides = 0;
+    if (lane < m) {
+      const int k = top - m + lane;
+      const int id = W.d_idx[k], te = W.d_te[k], st = W.d_st[k];
+      const BatchItemDev& it = items[W.d_item[k]];
+      int32_t h = -1;
+      float tv = __int_as_float(0x7fc00000);
+      if (st > 0) {
+        f_steps = (unsigned)st;
+        f_sides = (unsigned)st - 1u;
+        const TriRec r = load_rec(scenes[W.d_scene[k]].rec + (te >> 2));
+        const int e = te & 3;
+        const int32_t w = nb_of(r, e);
+        if (w <= -2) {
+          h = -2 - w;
+          const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
+          tv = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), W.d_ox[k], W.d_oy[k],
+                              k_of_word<kExact>(W.d_kx[k]), k_of_word<kExact>(W.d_ky[k]));
+        } else {
+          tv = __int_as_float(0x7f800000);
+        }
+      } else if (st == CCT_RAY_WALK_LIMIT) {
+        f_sides = (unsigned)scenes[W.d_scene[k]].max_steps - 1u;
+      }
+      it.hit[id] = h;
+      it.t[id] = tv;
+      it.steps[id] = st;
+    }
+    f_steps = __reduce_add_sync(FULL, f_steps);
+    f_sides = __reduce_add_sync(FULL, f_sides);
+    if (lane == 0) {
+      W.steps += f_steps;
+      W.sides += f_sides;
+    }
+    __syncwarp();
+  };
+
+  // 32 rays of the pool's item at once: load, start triangle (given, or the
+  // Sec. 5.2 locate walk), first step; onto `ready` or `parked`
+  auto prepare = [&]() {
+    if (p_next >= p_end) {
+      int c = 0;
+      if (lane == 0) c = (int)atomicAdd(counter, 1ull);
+      c = __shfl_sync(FULL, c, 0);
+      if (c >= total) {
+        exhausted = true;
+        return;
+      }
+      p_item = find_item(items, n_items, c);
+      const BatchItemDev& it = items[p_item];
+      p_next = (c - it.chunk_begin) * chunk;
+      p_end = min(p_next + chunk, it.n);
+    }
+    const BatchItemDev& it = items[p_item];
+    const int sc = it.scene;
+    const SceneDev& S = scenes[sc];
+    const int i = p_next + lane;
+    const bool v = i < p_end;
+    p_next = min(p_next + 32, p_end);
+    int pox = 0, poy = 0, pkx = 0, pky = 0, T0 = -1;  // pkx, pky: direction words
+    bool ok = false;
+    const bool locate = it.start == nullptr;
+    if (v) {
+      const long long ri = (long long)i * it.stride;
+      pox = it.ox[ri];
+      poy = it.oy[ri];
+      const float pdx = it.dx[ri], pdy = it.dy[ri];
+      ok = dir_to_k(pdx, pkx) && dir_to_k(pdy, pky) && (pkx | pky) != 0 && pox >= 0 && poy >= 0 && pox <= S.D &&
+           poy <= S.D;
+      pkx = k_word<kExact>(pkx);
+      pky = k_word<kExact>(pky);
+      if (locate) {
+        if (ok) T0 = S.seeds[seed_cell(S, pox, poy)];
+      } else {
+        T0 = it.start[i];
+        T0 = (T0 >= 0 && T0 < S.n_tri) ? S.user2dev[T0] : -1;
+        ok = ok && T0 >= 0;
+      }
+    }
+    const unsigned m_loc = locate ? __ballot_sync(FULL, ok) : 0u;
+    TriRec r;
+    if (ok) r = load_rec(S.rec + T0);
+    int lsteps = 0;
+    if (locate) {
+      int jj = 3;
+      bool locating = false;
+      if (ok) {
+        lsteps = 1;
+        const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
+        const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
+        const long long o0 = orient_i(x1, y1, x2, y2, pox, poy), o1 = orient_i(x2, y2, x0, y0, pox, poy);
+        const long long o2 = orient_i(x0, y0, x1, y1, pox, poy);
+        if (o0 < 0 || o1 < 0 || o2 < 0) {
+          int cx, cy;
+          seed_point(S, pox, poy, cx, cy);
+          locating = locate_hop(S, r, T0, jj, seed_exit(r, cx, cy, pox, poy));
+          ok = locating;
+        } else if (o0 == 0 || o1 == 0 || o2 == 0) {
+          ok = false;
+        }
+      }
+      while (__any_sync(FULL, locating)) {
+        if (locating) {
+          r = load_rec(S.rec + T0);
+          ++lsteps;
+          int cx, cy;
+          seed_point(S, pox, poy, cx, cy);
+          const int res = locate_step_entered(S, r, T0, jj, pox, poy, cx, cy);
+          if (res != 0 || lsteps > S.max_steps) {
+            locating = false;
+            ok = res > 0;
+          }
+        }
+      }
+    }
+    int e = 0;
+    int32_t w = -1;
+    if (ok) {
+      const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
+      const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
+      if (!locate)
+        ok = orient_i(x1, y1, x2, y2, pox, poy) > 0 && orient_i(x2, y2, x0, y0, pox, poy) > 0 &&
+             orient_i(x0, y0, x1, y1, pox, poy) > 0;
+      unsigned fb = 0;
+      const bool s0 = side_L_w<kExact>(pkx, pky, pox, poy, x0, y0, fb);
+      const bool s1 = side_L_w<kExact>(pkx, pky, pox, poy, x1, y1, fb);
+      const bool s2 = side_L_w<kExact>(pkx, pky, pox, poy, x2, y2, fb);
+      if (!kExact && fb) atomicAdd(&W.cnt[kBFallback], fb);
+      e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
+      w = nb_of(r, e);
+    }
+    const unsigned m_first = __ballot_sync(FULL, ok);
+    const bool to_ready = ok && w >= 0;
+    const bool to_done = v && !to_ready;
+    const unsigned mr = __ballot_sync(FULL, to_ready), md = __ballot_sync(FULL, to_done);
+    const unsigned mv = __ballot_sync(FULL, v), minv = __ballot_sync(FULL, v && !ok);
+    if (locate) {
+      const unsigned ls = __reduce_add_sync(FULL, (unsigned)lsteps);
+      if (lane == 0) {
+        W.cnt[kBLocated] += __popc(m_loc);
+        W.cnt[kBLocSteps] += ls;
+      }
+    }
+    if (lane == 0) {
+      W.cnt[kBRays] += __popc(mv);
+      W.cnt[kBInvalid] += __popc(minv);
+      W.sides += 3ull * (unsigned)__popc(m_first);
+    }
+    if (to_ready) {
+      const int k = n_ready + __popc(mr & lt);
+      W.r_ox[k] = pox;
+      W.r_oy[k] = poy;
+      W.r_kx[k] = pkx;
+      W.r_ky[k] = pky;
+      W.r_tj[k] = w;
+      W.r_idx[k] = i;
+      W.r_item[k] = p_item;
+      W.r_scene[k] = sc;
+    } else if (to_done) {
+      const int k = n_done + __popc(md & lt);
+      W.d_idx[k] = i;
+      W.d_te[k] = (T0 << 2) | e;
+      W.d_st[k] = ok ? 1 : CCT_RAY_INVALID;
+      W.d_ox[k] = pox;
+      W.d_oy[k] = poy;
+      W.d_kx[k] = pkx;
+      W.d_ky[k] = pky;
+      W.d_item[k] = p_item;
+      W.d_scene[k] = sc;
+    }
+    n_ready += __popc(mr);
+    n_done += __popc(md);
+    __syncwarp();
+  };
 
   while (true) {
-    while (!exhausted) {
-      const unsigned need = __ballot_sync(FULL, !active);
-      if (need == 0u) break;
-      if (__popc(need) < refill_min && need != FULL) break;
+    const unsigned idle = __ballot_sync(FULL, !active);
+    if (idle != 0u && (__popc(idle) >= refill_min || idle == FULL)) {
+      const unsigned dm = __ballot_sync(FULL, done);
       if (done) {
-        batch_complete(items[item], rec, T, j, nsteps, ox, oy, kx, ky, idx);
+        const int k = n_done + __popc(dm & lt);
+        W.d_idx[k] = W.l_idx[lane];
+        W.d_te[k] = (T << 2) | j;
+        W.d_st[k] = nsteps;
+        W.d_ox[k] = ox;
+        W.d_oy[k] = oy;
+        W.d_kx[k] = kx;
+        W.d_ky[k] = ky;
+        W.d_item[k] = W.l_item[lane];
+        W.d_scene[k] = W.l_scene[lane];
         done = false;
       }
-      if (p_next >= p_end) {
-        int c = 0;
-        if (lane == 0) c = (int)atomicAdd(counter, 1ull);
-        c = __shfl_sync(FULL, c, 0);
-        if (c >= total) {
-          exhausted = true;
-          break;
-        }
-        p_item = find_item(items, n_items, c);
-        const BatchItemDev& it = items[p_item];
-        p_next = (c - it.chunk_begin) * chunk;
-        p_end = min(p_next + chunk, it.n);
+      n_done += __popc(dm);
+      if (n_done >= 32) {
+        flush(32, n_done);
+        n_done -= 32;
       }
-      const int avail = p_end - p_next;
-      const int rank = __popc(need & lt);
-      if (!active && rank < avail) {
-        const BatchItemDev& it = items[p_item];
-        const SceneDev& S = scenes[it.scene];
-        item = p_item;
-        scene = it.scene;
-        idx = p_next + rank;
-        const long long ri = (long long)idx * it.stride;
-        ox = it.ox[ri];
-        oy = it.oy[ri];
-        fdx = it.dx[ri];
-        fdy = it.dy[ri];
-        rec = S.rec;
-        max_steps = S.max_steps;
-        bool ok = dir_to_k(fdx, kx) && dir_to_k(fdy, ky) && (kx | ky) != 0;
-        int s = -1;
-        if (it.start == nullptr) {
-          if (ok && ox >= 0 && oy >= 0 && ox <= S.D && oy <= S.D) {
-            s = S.seeds[seed_cell(S, ox, oy)];
-            mode = 3;
-            lsteps = 0;
-            ++c_loc;
-          } else {
-            ok = false;
-          }
-        } else {
-          s = it.start[idx];
-          s = (s >= 0 && s < S.n_tri) ? S.user2dev[s] : -1;
-          ok = ok && s >= 0;
-          mode = 1;
-        }
-        ++c_rays;
-        if (ok) {
-          T = s;
-          nsteps = 0;
-          active = true;
-        } else {
-          it.hit[idx] = -1;
-          it.t[idx] = __int_as_float(0x7fc00000);
-          it.steps[idx] = CCT_RAY_INVALID;
-          ++c_inv;
+      const int want = __popc(idle);
+      if (n_ready < want && !exhausted) {
+        prepare();
+        if (n_done >= 32) {
+          flush(32, n_done);
+          n_done -= 32;
         }
       }
-      p_next += min(__popc(need), avail);
+      const int rank = __popc(idle & lt);
+      if (!active && rank < n_ready) {
+        const int k = n_ready - 1 - rank;
+        ox = W.r_ox[k];
+        oy = W.r_oy[k];
+        kx = W.r_kx[k];
+        ky = W.r_ky[k];
+        const int tj = W.r_tj[k];
+        const int scene = W.r_scene[k];
+        W.l_idx[lane] = W.r_idx[k];
+        W.l_item[lane] = W.r_item[k];
+        W.l_scene[lane] = scene;
+        T = tj >> 2;
+        j = tj & 3;
+        rec = scenes[scene].rec;
+        max_steps = scenes[scene].max_steps;
+        nsteps = 1;
+        active = true;
+      }
+      n_ready -= min(want, n_ready);
+      __syncwarp();
     }
     if (!__any_sync(FULL, active)) {
-      if (exhausted) break;
+      if (exhausted && n_ready == 0) break;
       continue;
     }
     if (active) {
       const TriRec r = load_rec(rec + T);
-      int status = 0;
-      bool step = true;
-      if (mode == 0) {
-        ++lsteps;
-        int cx, cy;
-        seed_point(scenes[scene], ox, oy, cx, cy);
-        const int res = locate_step_entered(scenes[scene], r, T, j, ox, oy, cx, cy);
-        step = false;
-        if (res > 0) {
-          mode = 1;
-          step = true;
-          c_lsteps += (unsigned)lsteps;
-        } else if (res < 0 || lsteps > max_steps) {
-          status = CCT_RAY_INVALID;
-          ++c_inv;
-          c_lsteps += (unsigned)lsteps;
+      unsigned fb = 0;
+      const bool sc = side_L_w<kExact>(kx, ky, ox, oy, vx_of(r, j), vy_of(r, j), fb);
+      if (!kExact && fb) atomicAdd(&W.cnt[kBFallback], fb);
+      const int e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
+      ++nsteps;
+      const int32_t w = nb_of(r, e);
+      if (w >= 0) {
+        T = w >> 2;
+        j = w & 3;
+        if (nsteps >= max_steps) {
+          nsteps = CCT_RAY_WALK_LIMIT;
+          active = false;
+          done = true;
+          atomicAdd(&W.cnt[kBLimit], 1u);
         }
-      }
-      if (step) {
-        int e = 0;
-        if (mode != 2) {
-          const int x0 = vx_of(r, 0), y0 = vy_of(r, 0), x1 = vx_of(r, 1), y1 = vy_of(r, 1);
-          const int x2 = vx_of(r, 2), y2 = vy_of(r, 2);
-          bool inside = true;
-          if (mode == 3 || mode == 1) {
-            const long long o0 = orient_i(x1, y1, x2, y2, ox, oy), o1 = orient_i(x2, y2, x0, y0, ox, oy);
-            const long long o2 = orient_i(x0, y0, x1, y1, ox, oy);
-            inside = o0 > 0 && o1 > 0 && o2 > 0;
-            if (mode == 3) {
-              lsteps = 1;
-              if (!inside && (o0 < 0 || o1 < 0 || o2 < 0)) {
-                // outside the seed triangle: the Sec. 5.2 locate walk leaves it
-                int cx, cy;
-                seed_point(scenes[scene], ox, oy, cx, cy);
-                step = false;
-                if (locate_hop(scenes[scene], r, T, j, seed_exit(r, cx, cy, ox, oy))) {
-                  mode = 0;
-                } else {
-                  status = CCT_RAY_INVALID;
-                  ++c_inv;
-                  c_lsteps += 1u;
-                }
-              } else {
-                c_lsteps += 1u;
-              }
-            }
-          }
-          if (step) {
-            const bool s0 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x0, y0, c_fb);
-            const bool s1 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x1, y1, c_fb);
-            const bool s2 = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, x2, y2, c_fb);
-            c_side += 3;
-            e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
-            mode = 2;
-            if (!inside) {
-              status = CCT_RAY_INVALID;
-              ++c_inv;
-            }
-          }
-        } else {
-          const bool sc = side_L<kExact>(fdx, fdy, kx, ky, ox, oy, vx_of(r, j), vy_of(r, j), c_fb);
-          ++c_side;
-          e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
-        }
-        if (step && status == 0) {
-          ++nsteps;
-          const int32_t w = nb_of(r, e);
-          if (w >= 0) {
-            if (nsteps >= max_steps) {
-              status = CCT_RAY_WALK_LIMIT;
-              ++c_lim;
-            } else {
-              T = w >> 2;
-              j = w & 3;
-            }
-          } else {
-            status = nsteps;
-            j = e;
-            c_steps += (unsigned)nsteps;
-          }
-        }
-      }
-      if (status != 0) {
-        nsteps = status;
+      } else {
+        j = e;
         active = false;
         done = true;
       }
     }
   }
-  if (done) batch_complete(items[item], rec, T, j, nsteps, ox, oy, kx, ky, idx);
-  const unsigned long long w_steps = warp_sum((unsigned long long)c_steps);
-  const unsigned long long w_side = warp_sum((unsigned long long)c_side);
-  const unsigned long long w_rays = warp_sum((unsigned long long)c_rays);
-  const unsigned long long w_fb = warp_sum((unsigned long long)c_fb);
-  const unsigned long long w_inv = warp_sum((unsigned long long)c_inv);
-  const unsigned long long w_lim = warp_sum((unsigned long long)c_lim);
-  const unsigned long long w_loc = warp_sum((unsigned long long)c_loc);
-  const unsigned long long w_lst = warp_sum((unsigned long long)c_lsteps);
+  while (n_done > 0) {
+    const int m = min(32, n_done);
+    flush(m, n_done);
+    n_done -= m;
+  }
+  __syncwarp();
+  const unsigned long long w_steps = W.steps, w_side = W.sides;
+  const unsigned long long w_rays = W.cnt[kBRays], w_fb = W.cnt[kBFallback], w_inv = W.cnt[kBInvalid];
+  const unsigned long long w_lim = W.cnt[kBLimit], w_loc = W.cnt[kBLocated], w_lst = W.cnt[kBLocSteps];
   if (lane == 0) {
     if (w_rays) atomicAdd(&bstats->rays, w_rays);
     if (w_steps) atomicAdd(&bstats->steps, w_steps);
@@ -307,11 +399,19 @@ struct cct_batch_s {
   int staged;
 };
 
+static size_t batch_smem(int threads) { return sizeof(BatchStacks) * (size_t)(threads / 32); }
+
 static int batch_grid(cct_batch b) {
   int per_sm = 0;
   const int threads = b->tuning.block_threads;
   auto k = (b->flags & CCT_TRACE_EXACT_ONLY) ? batch_kernel<true> : batch_kernel<false>;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  // the stacks of 16 warps exceed the default 48 KB of dynamic shared memory
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem(kBatchMaxThreads)) !=
+      cudaSuccess)
+    cudaGetLastError();
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, batch_smem(threads)) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
   return sm_count(b->device) * per_sm;
 }
 
@@ -429,14 +529,15 @@ extern "C" int cct_batch_enqueue(cct_batch b, void* stream_v) {
     return CCT_ERR_CUDA;
   if (cudaMemsetAsync(b->d_counter, 0, 8, stream) != cudaSuccess) return CCT_ERR_CUDA;
   const auto* items = (const BatchItemDev*)((const char*)b->d_hdr + sizeof(BatchHeader));
+  const size_t smem = batch_smem(b->tuning.block_threads);
   if (b->flags & CCT_TRACE_EXACT_ONLY)
-    batch_kernel<true><<<b->grid, b->tuning.block_threads, 0, stream>>>(b->d_scenes, b->d_hdr, items,
-                                                                        b->tuning.refill_min, b->d_counter,
-                                                                        b->d_stats);
+    batch_kernel<true><<<b->grid, b->tuning.block_threads, smem, stream>>>(b->d_scenes, b->d_hdr, items,
+                                                                           b->tuning.refill_min, b->d_counter,
+                                                                           b->d_stats);
   else
-    batch_kernel<false><<<b->grid, b->tuning.block_threads, 0, stream>>>(b->d_scenes, b->d_hdr, items,
-                                                                         b->tuning.refill_min, b->d_counter,
-                                                                         b->d_stats);
+    batch_kernel<false><<<b->grid, b->tuning.block_threads, smem, stream>>>(b->d_scenes, b->d_hdr, items,
+                                                                            b->tuning.refill_min, b->d_counter,
+                                                                            b->d_stats);
   return cudaGetLastError() == cudaSuccess ? CCT_OK : CCT_ERR_CUDA;
 }
 

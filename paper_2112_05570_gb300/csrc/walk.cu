@@ -48,6 +48,7 @@ constexpr int kStack = 64;
 struct WarpStacks {
   int r_ox[kStack], r_oy[kStack], r_kx[kStack], r_ky[kStack], r_tj[kStack], r_idx[kStack];
   int d_idx[kStack], d_te[kStack], d_st[kStack], d_ox[kStack], d_oy[kStack], d_kx[kStack], d_ky[kStack];
+  int l_idx[32];  // the walking lanes' ray indices (read when they park)
   unsigned cnt[kRareCounters];
   unsigned long long steps, sides;  // step and side-test counts of the warp's finished rays
 };
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
   // lane state: walking (active), finished and not yet parked (done), or idle
   // (kx, ky: direction words, see side_L_w)
   bool active = false, done = false;
-  int idx = 0, ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0;
+  int ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0;
   if (lane < kRareCounters) W.cnt[lane] = 0;
   if (lane == 0) W.steps = W.sides = 0;
   __syncwarp();
@@ -137,10 +138,10 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     const int i = pool_next + lane;
     const bool v = i < pool_end;
     pool_next = min(pool_next + 32, pool_end);
-    int pox = 0, poy = 0, pkx = 0, pky = 0, pid = i, T0 = -1;
-    float pdx = 0.f, pdy = 0.f;
+    int pox = 0, poy = 0, pkx = 0, pky = 0, pid = i, T0 = -1;  // pkx, pky: direction words
     bool ok = false;
     if (v) {
+      float pdx, pdy;
       if (kSrc == kSrcSorted) {
         const int4 rr = R.rays[i];
         pox = rr.x;
@@ -163,6 +164,8 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
       // keeps every coordinate difference of the walk within int32
       ok = dir_to_k(pdx, pkx) && dir_to_k(pdy, pky) && (pkx | pky) != 0 && pox >= 0 && poy >= 0 && pox <= S.D &&
            poy <= S.D;
+      pkx = k_word<kExact>(pkx);
+      pky = k_word<kExact>(pky);
       if (kLocate) {
         if (ok) T0 = S.seeds[seed_cell(S, pox, poy)];
       } else {
@@ -218,9 +221,9 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
         ok = orient_i(x1, y1, x2, y2, pox, poy) > 0 && orient_i(x2, y2, x0, y0, pox, poy) > 0 &&
              orient_i(x0, y0, x1, y1, pox, poy) > 0;
       unsigned fb = 0;
-      const bool s0 = side_L<kExact>(pdx, pdy, pkx, pky, pox, poy, x0, y0, fb);
-      const bool s1 = side_L<kExact>(pdx, pdy, pkx, pky, pox, poy, x1, y1, fb);
-      const bool s2 = side_L<kExact>(pdx, pdy, pkx, pky, pox, poy, x2, y2, fb);
+      const bool s0 = side_L_w<kExact>(pkx, pky, pox, poy, x0, y0, fb);
+      const bool s1 = side_L_w<kExact>(pkx, pky, pox, poy, x1, y1, fb);
+      const bool s2 = side_L_w<kExact>(pkx, pky, pox, poy, x2, y2, fb);
       if (!kExact && fb) atomicAdd(&W.cnt[kCntFallback], fb);
       e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
       w = nb_of(r, e);
@@ -247,8 +250,8 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
       const int k = n_ready + __popc(mr & lt);
       W.r_ox[k] = pox;
       W.r_oy[k] = poy;
-      W.r_kx[k] = k_word<kExact>(pkx);
-      W.r_ky[k] = k_word<kExact>(pky);
+      W.r_kx[k] = pkx;
+      W.r_ky[k] = pky;
       W.r_tj[k] = w;
       W.r_idx[k] = pid;
     } else if (to_done) {
@@ -258,8 +261,8 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
       W.d_st[k] = ok ? 1 : CCT_RAY_INVALID;
       W.d_ox[k] = pox;
       W.d_oy[k] = poy;
-      W.d_kx[k] = k_word<kExact>(pkx);
-      W.d_ky[k] = k_word<kExact>(pky);
+      W.d_kx[k] = pkx;
+      W.d_ky[k] = pky;
     }
     n_ready += __popc(mr);
     n_done += __popc(md);
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
       const unsigned dm = __ballot_sync(FULL, done);
       if (done) {
         const int k = n_done + __popc(dm & lt);
-        W.d_idx[k] = idx;
+        W.d_idx[k] = W.l_idx[lane];
         W.d_te[k] = (T << 2) | j;
         W.d_st[k] = nsteps;
         W.d_ox[k] = ox;
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
         kx = W.r_kx[k];
         ky = W.r_ky[k];
         const int tj = W.r_tj[k];
-        idx = W.r_idx[k];
+        W.l_idx[lane] = W.r_idx[k];
         T = tj >> 2;
         j = tj & 3;
         nsteps = 1;
