@@ -186,6 +186,41 @@ def _time_loop(torch, dev, stream, fn, k):
     return e0.elapsed_time(e1) / k
 
 
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "walk_kernel_fused_locate_dram_six_scenes.md")
+TRAFFIC_SOURCES = ("paper_2112_05570_gb300/csrc/walk.cu", "paper_2112_05570_gb300/csrc/cct_internal.cuh",
+                   "paper_2112_05570_gb300/csrc/scene.cu")
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic():
+    """DRAM bytes per launch of the fused walk kernel from the committed ncu
+    summary, or None when the kernel sources changed since that capture."""
+    try:
+        text = open(TRAFFIC_SUMMARY).read()
+    except OSError:
+        return None, "no ncu summary"
+    import re
+
+    vals = dict(re.findall(r"^- `(\w+)`: `([^`]+)`", text, flags=re.M))
+    try:
+        b = float(vals["traffic_bytes_per_launch_mean"])
+        sha = vals["sources_sha256"]
+    except (KeyError, ValueError):
+        return None, "ncu summary unreadable"
+    if sha != kernel_sources_sha256():
+        return None, "kernel changed since the ncu capture"
+    return b, "DRAM read+write bytes per launch, mean over the six scenes, from " + os.path.basename(TRAFFIC_SUMMARY)
+
+
 TUNE_PARAMS = (0.25, 0.5, 1.0, 2.0, 4.0)
 
 
@@ -536,15 +571,24 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    # per-launch events on the launching stream bracket each scene's trace
+    # (one fused locate+walk kernel per scene on the plain path)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in scenes]
+          for _ in range(args.steps)]
     with ClockSampler(dev.index) as clk:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
-            step(flags)
+        for k in range(args.steps):
+            for sc, (a, b) in zip(scenes, ev[k]):
+                a.record(stream)
+                trace(sc, None, flags)
+                b.record(stream)
         e1.record(stream)
         e1.synchronize()
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.steps
+    scene_ms = [sum(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)) / args.steps
+                for i in range(len(scenes))]
     if dist:
         dist.barrier()
         m = torch.tensor([ms], device=dev)
@@ -553,14 +597,33 @@ def main():
     rays_per_step = n * len(scenes)
     value = rays_per_step * world / (ms * 1e-3)
     tot = {"rays": 0, "steps": 0, "side_tests": 0, "exact_fallbacks": 0, "located": 0, "locate_steps": 0}
+    timed_stats = []
     for sc in scenes:
         st = sc["scene"].stats(reset=True)
+        timed_stats.append(st)
         for k in tot:
             tot[k] += st[k]
 
-    # ---- per scene: the walk kernel alone (start cells given) -> roofline; CDT vs annealed steps
+    # ---- roofline of the timed kernel (fused locate + walk): algorithmic bytes
+    # per launch over its event-timed duration, against the random-sector
+    # gather peak measured over a table of the scene's size
+    alg_bytes_tot, alg_over_peak, timed_ms_tot = 0.0, 0.0, 0.0
+    gather_bps = {}
+    for i, sc in enumerate(scenes):
+        st = timed_stats[i]
+        reps = args.steps
+        # distinct record reads: locate triangles + walk triangles - 1 (the
+        # start triangle serves both); 4 B seed cell; 16 B ray in, 12 B out
+        alg = (32.0 * (st["steps"] + st["locate_steps"] - st["located"]) + 4.0 * st["located"]
+               + 28.0 * st["rays"]) / reps
+        _, bps = cct.cct_measure_gather(sc["tri"].n_tri * 32, 1 << 27, 5, stream)
+        gather_bps[sc["name"]] = bps
+        alg_bytes_tot += alg
+        alg_over_peak += alg / bps
+        timed_ms_tot += scene_ms[i]
+
+    # ---- per scene: the walk kernel alone (start cells given); CDT vs annealed steps
     per = {}
-    walk_ms_tot, alg_bytes_tot, alg_over_peak = 0.0, 0.0, 0.0
     for sc in scenes:
         tuned_cfg = sc["scene"].tuning()
         sc["scene"].set_tuning(dict(tuned_cfg, trace_flags=tuned_cfg["trace_flags"] & ~cct.CCT_TRACE_BIN))
@@ -572,11 +635,7 @@ def main():
         st = sc["scene"].stats(reset=True)
         wsteps = st["steps"] / k_rep
         alg = wsteps * 32.0 + n * 32.0
-        table_bytes = sc["tri"].n_tri * 32
-        _, bps = cct.cct_measure_gather(table_bytes, 1 << 27, 5, stream)
-        walk_ms_tot += wms
-        alg_bytes_tot += alg
-        alg_over_peak += alg / bps
+        bps = gather_bps[sc["name"]]
         d = sc["d"]
         other = {}
         for kind in ("cdt", "ref"):
@@ -595,19 +654,23 @@ def main():
                            "length_annealed_over_cdt": sc["tri"].length(True) / sc["cdt"].length(True),
                            "length_refined_over_cdt": sc["ref"].length(True) / sc["cdt"].length(True),
                            "walk_l2_frac": (alg / (wms * 1e-3)) / bps, "gather_peak_gbs": bps / 1e9}
-    achieved = alg_bytes_tot / (walk_ms_tot * 1e-3) / 1e9
-    l2_peak = alg_bytes_tot / alg_over_peak / 1e9  # time-weighted gather peak over the scenes' table sizes
+    n_launch = len(scenes)
+    achieved = alg_bytes_tot / (timed_ms_tot * 1e-3) / 1e9
+    l2_peak = alg_bytes_tot / alg_over_peak / 1e9  # byte-weighted gather peak over the scenes' table sizes
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = json.load(open(peaks_path)).get("hbm_gbs") if os.path.exists(peaks_path) else None
     hbm_src = "MEASURED_PEAKS.json (measured)" if hbm_peak else "fallback 6800 GB/s"
     hbm_peak = hbm_peak or 6800.0
+    traffic, traffic_note = captured_traffic()
     roofline = {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
-                "traffic": None, "kernel": "walk_kernel (start cells given), all six scenes",
+                "traffic": traffic, "traffic_note": traffic_note,
+                "kernel": "walk_kernel with the fused locate (the timed step's only kernel), one launch per scene",
+                "launch_ms_mean": timed_ms_tot / n_launch,
+                "algorithmic_bytes_per_launch_mean": alg_bytes_tot / n_launch,
                 "peak_source": "measured live: random 32-byte sector gathers over tables of each scene's size "
                                "(cct_measure_gather), weighted by each scene's bytes",
-                "algorithmic_bytes_per_step": alg_bytes_tot, "walk_ms_per_step": walk_ms_tot,
-                "bytes_model": "32 B per walk step (one triangle record) + 32 B per ray (16 B ray, 4 B start, "
-                               "12 B result)",
+                "bytes_model": "32 B per distinct triangle record read (walk steps + locate steps - 1 per ray) + "
+                               "4 B seed cell + 28 B per ray (16 B ray in, 12 B result out)",
                 "hbm": {"peak": hbm_peak, "frac": achieved / hbm_peak, "source": hbm_src}}
 
     # ---- end to end through the public API with host buffers (pinned), every scene
