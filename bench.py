@@ -77,7 +77,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -118,13 +118,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(work, seconds_target=4.0):
+def cpu_oracle_rate(work, seconds_target=12.0):
     """Oracle walk (given start cells) on all host cores over a bounded sample:
     the first rays of every scene, sized to take about seconds_target."""
     import oracle
 
     threads = os.cpu_count() or 1
-    n = 1 << 14
+    n = 1 << 17  # pilot, large enough that thread start-up does not dominate
     t0 = time.perf_counter()
     for w in work:
         tri, r = w[3], w[4]
@@ -424,7 +424,7 @@ def run_config3(args, torch, cct, sg, dev):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--flags", default="auto", help="auto | plain | bin")
