@@ -44,14 +44,26 @@ struct WalkParams {
 // Per-warp stacks in shared memory.  `ready` holds rays whose first
 // triangle is behind them (the state after the first step: next record and
 // entry edge); `parked` holds finished rays waiting for their results.
+// Entries are 16- and 8-byte words, so a push or a pop is two accesses.
+// The whole structure stays near 4 KB per warp: more shared memory per SM
+// shrinks the L1 that holds the record loads in flight (measured slower).
 constexpr int kStack = 64;
+template <int kPfRows>
 struct WarpStacks {
-  int r_ox[kStack], r_oy[kStack], r_kx[kStack], r_ky[kStack], r_tj[kStack], r_idx[kStack];
-  int d_idx[kStack], d_te[kStack], d_st[kStack], d_ox[kStack], d_oy[kStack], d_kx[kStack], d_ky[kStack];
-  int l_idx[32];  // the walking lanes' ray indices (read when they park)
+  int4 r_a[kStack];    // ready: ox, oy, kx word, ky word
+  int2 r_b[kStack];    // ready: next record << 2 | entry edge, ray index
+  int4 d_a[kStack];    // parked: ox, oy, kx word, ky word
+  int2 d_b[kStack];    // parked: ray index, final record << 2 | exit edge
+  int d_st[kStack];    // parked: steps or status
+  int pf[kPfRows][32];  // the next batch's ray inputs, copied in while the warp walks (see prefetch)
   unsigned cnt[kRareCounters];
   unsigned long long steps, sides;  // step and side-test counts of the warp's finished rays
 };
+// rows of the prefetch buffer: ox, oy, dx, dy (+ start) (+ original index)
+template <int kSrc>
+__host__ __device__ constexpr int pf_rows() {
+  return kSrc == kSrcSorted ? 6 : (kSrc == kSrcLocate ? 4 : 5);
+}
 
 template <bool kExact, int kSrc>
 __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySrc R, WalkParams P,
@@ -62,18 +74,20 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
   constexpr unsigned FULL = 0xffffffffu;
   constexpr bool kLocate = (kSrc == kSrcLocate);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpStacks& W = reinterpret_cast<WarpStacks*>(smem_raw)[threadIdx.x >> 5];
+  using Stacks = WarpStacks<pf_rows<kSrc>()>;
+  Stacks& W = reinterpret_cast<Stacks*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int n = (int)R.n;
   int pool_next = 0, pool_end = 0;  // the warp's current range of ray indices
+  int pf_base = 0, pf_end = 0;      // the batch in `pf` ([pf_base, pf_end)); pf_base < 0: none left
   int n_ready = 0, n_done = 0;      // stack depths (warp-uniform)
   bool exhausted = false;
 
   // lane state: walking (active), finished and not yet parked (done), or idle
   // (kx, ky: direction words, see side_L_w)
   bool active = false, done = false;
-  int ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0;
+  int idx = 0, ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0;
   if (lane < kRareCounters) W.cnt[lane] = 0;
   if (lane == 0) W.steps = W.sides = 0;
   __syncwarp();
@@ -86,7 +100,8 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     unsigned f_steps = 0, f_sides = 0;
     if (lane < m) {
       const int k = top - m + lane;
-      const int id = W.d_idx[k], te = W.d_te[k], st = W.d_st[k];
+      const int2 b = W.d_b[k];
+      const int id = b.x, te = b.y, st = W.d_st[k];
       int32_t h = -1;
       float tv = __int_as_float(0x7fc00000);  // NaN: invalid ray or step limit
       if (st > 0) {
@@ -98,8 +113,9 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
         if (w <= -2) {
           h = -2 - w;
           const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
-          tv = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), W.d_ox[k], W.d_oy[k],
-                              k_of_word<kExact>(W.d_kx[k]), k_of_word<kExact>(W.d_ky[k]));
+          const int4 o = W.d_a[k];
+          tv = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), o.x, o.y, k_of_word<kExact>(o.z),
+                              k_of_word<kExact>(o.w));
         } else {
           tv = __int_as_float(0x7f800000);  // +inf: left through the hull
         }
@@ -119,47 +135,77 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     __syncwarp();
   };
 
-  // Takes up to 32 new rays, finds their start triangles (given, or by the
-  // Sec. 5.2 locate walk from the seed point of their cell) and takes their
-  // first step; pushes them on `ready`, or on `parked` when they end in the
-  // first triangle or are invalid.  The whole warp works on 32 rays at once.
-  auto prepare = [&]() {
+  // Starts the copies of the next (up to) 32 rays of the warp's pool into
+  // `pf` (a new chunk from the global counter when the pool is empty).
+  auto prefetch = [&]() {
     if (pool_next >= pool_end) {
       int base = 0;
       if (lane == 0) base = (int)atomicAdd(counter, (unsigned long long)P.chunk);
       base = __shfl_sync(FULL, base, 0);
       if (base >= n) {
-        exhausted = true;
+        pf_base = -1;
         return;
       }
       pool_next = base;
       pool_end = min(base + P.chunk, n);
     }
-    const int i = pool_next + lane;
-    const bool v = i < pool_end;
-    pool_next = min(pool_next + 32, pool_end);
-    int pox = 0, poy = 0, pkx = 0, pky = 0, pid = i, T0 = -1;  // pkx, pky: direction words
-    bool ok = false;
-    if (v) {
-      float pdx, pdy;
+    pf_base = pool_next;
+    pf_end = min(pool_next + 32, pool_end);
+    pool_next = pf_end;
+    const int i = pf_base + lane;
+    if (i < pf_end) {
       if (kSrc == kSrcSorted) {
-        const int4 rr = R.rays[i];
+        cp_async16(&W.pf[0][4 * lane], R.rays + i);  // rows 0..3 hold 32 int4
+        cp_async4(&W.pf[4][lane], R.start + i);
+        cp_async4(&W.pf[5][lane], R.orig + i);
+      } else {
+        cp_async4(&W.pf[0][lane], R.ox + i);
+        cp_async4(&W.pf[1][lane], R.oy + i);
+        cp_async4(&W.pf[2][lane], R.dx + i);
+        cp_async4(&W.pf[3][lane], R.dy + i);
+        if (!kLocate) cp_async4(&W.pf[4][lane], R.start + i);
+      }
+    }
+    cp_async_commit();
+  };
+
+  // Takes the prefetched rays (up to 32), starts the copies of the next
+  // batch, finds their start triangles (given, or by the Sec. 5.2 locate walk
+  // from the seed point of their cell) and takes their first step; pushes
+  // them on `ready`, or on `parked` when they end in the first triangle or
+  // are invalid.  The whole warp works on 32 rays at once.
+  auto prepare = [&]() {
+    if (pf_base < 0) {
+      exhausted = true;
+      return;
+    }
+    cp_async_wait_all();
+    const int i = pf_base + lane;
+    const bool v = i < pf_end;
+    int pox = 0, poy = 0, pkx = 0, pky = 0, pid = i, T0 = -1;  // pkx, pky: direction words
+    float pdx = 0.f, pdy = 0.f;
+    if (v) {
+      if (kSrc == kSrcSorted) {
+        const int4 rr = *reinterpret_cast<const int4*>(&W.pf[0][4 * lane]);
         pox = rr.x;
         poy = rr.y;
         pdx = __int_as_float(rr.z);
         pdy = __int_as_float(rr.w);
-        T0 = R.start[i];
-        pid = R.orig[i];
+        T0 = W.pf[4][lane];
+        pid = W.pf[5][lane];
       } else {
-        pox = R.ox[i];
-        poy = R.oy[i];
-        pdx = R.dx[i];
-        pdy = R.dy[i];
-        if (!kLocate) {
-          T0 = R.start[i];
-          if (kSrc == kSrcPlainUser) T0 = (T0 >= 0 && T0 < S.n_tri) ? S.user2dev[T0] : -1;
-        }
+        pox = W.pf[0][lane];
+        poy = W.pf[1][lane];
+        pdx = __int_as_float(W.pf[2][lane]);
+        pdy = __int_as_float(W.pf[3][lane]);
+        if (!kLocate) T0 = W.pf[4][lane];
       }
+    }
+    __syncwarp();
+    prefetch();  // the next batch arrives while this one is prepared and walked
+    bool ok = false;
+    if (v) {
+      if (kSrc == kSrcPlainUser) T0 = (T0 >= 0 && T0 < S.n_tri) ? S.user2dev[T0] : -1;
       // origins outside the domain lie in no triangle; rejecting them here
       // keeps every coordinate difference of the walk within int32
       ok = dir_to_k(pdx, pkx) && dir_to_k(pdy, pky) && (pkx | pky) != 0 && pox >= 0 && poy >= 0 && pox <= S.D &&
@@ -248,27 +294,20 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     }
     if (to_ready) {
       const int k = n_ready + __popc(mr & lt);
-      W.r_ox[k] = pox;
-      W.r_oy[k] = poy;
-      W.r_kx[k] = pkx;
-      W.r_ky[k] = pky;
-      W.r_tj[k] = w;
-      W.r_idx[k] = pid;
+      W.r_a[k] = make_int4(pox, poy, pkx, pky);
+      W.r_b[k] = make_int2(w, pid);
     } else if (to_done) {
       const int k = n_done + __popc(md & lt);
-      W.d_idx[k] = pid;
-      W.d_te[k] = (T0 << 2) | e;
+      W.d_a[k] = make_int4(pox, poy, pkx, pky);
+      W.d_b[k] = make_int2(pid, (T0 << 2) | e);
       W.d_st[k] = ok ? 1 : CCT_RAY_INVALID;
-      W.d_ox[k] = pox;
-      W.d_oy[k] = poy;
-      W.d_kx[k] = pkx;
-      W.d_ky[k] = pky;
     }
     n_ready += __popc(mr);
     n_done += __popc(md);
     __syncwarp();
   };
 
+  prefetch();
   while (true) {
     // ---------------------------------------------------------------- serve idle lanes
     const unsigned idle = __ballot_sync(FULL, !active);
@@ -277,13 +316,9 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
       const unsigned dm = __ballot_sync(FULL, done);
       if (done) {
         const int k = n_done + __popc(dm & lt);
-        W.d_idx[k] = W.l_idx[lane];
-        W.d_te[k] = (T << 2) | j;
+        W.d_a[k] = make_int4(ox, oy, kx, ky);
+        W.d_b[k] = make_int2(idx, (T << 2) | j);
         W.d_st[k] = nsteps;
-        W.d_ox[k] = ox;
-        W.d_oy[k] = oy;
-        W.d_kx[k] = kx;
-        W.d_ky[k] = ky;
         done = false;
       }
       n_done += __popc(dm);
@@ -302,14 +337,15 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
       const int rank = __popc(idle & lt);
       if (!active && rank < n_ready) {
         const int k = n_ready - 1 - rank;
-        ox = W.r_ox[k];
-        oy = W.r_oy[k];
-        kx = W.r_kx[k];
-        ky = W.r_ky[k];
-        const int tj = W.r_tj[k];
-        W.l_idx[lane] = W.r_idx[k];
-        T = tj >> 2;
-        j = tj & 3;
+        const int4 a = W.r_a[k];
+        const int2 b = W.r_b[k];
+        ox = a.x;
+        oy = a.y;
+        kx = a.z;
+        ky = a.w;
+        idx = b.y;
+        T = b.x >> 2;
+        j = b.x & 3;
         nsteps = 1;
         active = true;
       }
@@ -377,14 +413,14 @@ static cudaError_t launch_walk_t(const SceneDev& S, const RaySrc& R, const cct_t
                                  int32_t* steps, unsigned long long* counter, int dev, cudaStream_t stream) {
   auto k = walk_kernel<kExact, kSrc>;
   const int threads = tu.block_threads;
-  const size_t smem = sizeof(WarpStacks) * (size_t)(threads / 32);
+  const size_t smem = sizeof(WarpStacks<pf_rows<kSrc>()>) * (size_t)(threads / 32);
   static bool configured = false;  // per instantiation; setting it twice is harmless
   if (!configured) {
     // the stacks of 16 warps exceed the default 48 KB of dynamic shared
     // memory.  The shared/L1 split is left to the driver: a maximal shared
     // carveout measured 1.5x slower (the L1 also holds the loads in flight).
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(sizeof(WarpStacks) * (kWalkMaxThreads / 32)));
+                                               (int)(sizeof(WarpStacks<pf_rows<kSrc>()>) * (kWalkMaxThreads / 32)));
     if (e != cudaSuccess) return e;
     configured = true;
   }
