@@ -64,11 +64,12 @@ __device__ __forceinline__ int find_item(const BatchItemDev* items, int n_items,
 constexpr int kBStack = 64;
 enum : int { kBRays = 0, kBFallback, kBInvalid, kBLimit, kBLocated, kBLocSteps, kBCounters };
 struct BatchStacks {
-  int r_ox[kBStack], r_oy[kBStack], r_kx[kBStack], r_ky[kBStack], r_tj[kBStack], r_idx[kBStack], r_item[kBStack],
-      r_scene[kBStack];
-  int d_idx[kBStack], d_te[kBStack], d_st[kBStack], d_ox[kBStack], d_oy[kBStack], d_kx[kBStack], d_ky[kBStack],
-      d_item[kBStack], d_scene[kBStack];
-  int l_idx[32], l_item[32], l_scene[32];  // the walking lanes' cold state (read when they park)
+  int4 r_a[kBStack];  // ready: ox, oy, kx word, ky word
+  int4 r_b[kBStack];  // ready: next record << 2 | entry edge, ray index, item, scene
+  int4 d_a[kBStack];  // parked: ox, oy, kx word, ky word
+  int4 d_b[kBStack];  // parked: ray index, final record << 2 | exit edge, steps or status, item
+  int pf[5][32];      // the next batch's ray inputs (ox, oy, dx, dy, start), copied in while the warp walks
+  int l_idx[32], l_item[32];  // the walking lanes' cold state (read when they park)
   unsigned cnt[kBCounters];
   unsigned long long steps, sides;
 };
@@ -85,8 +86,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int n_items = hdr->n_items, total = hdr->total_chunks, chunk = hdr->chunk;
-  // warp-uniform pool: a range of rays of one item
+  // warp-uniform pool: a range of rays of one item; the batch in `pf`:
+  // [pf_base, pf_end) of item pf_item (pf_base < 0: none left)
   int p_item = 0, p_next = 0, p_end = 0;
+  int pf_item = 0, pf_base = 0, pf_end = 0;
   int n_ready = 0, n_done = 0;
   bool exhausted = n_items <= 0;
   // lane state: walking (active), finished and not yet parked (done), or idle
@@ -95,7 +98,6 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
   const TriRec* rec = nullptr;
   if (lane < kBCounters) W.cnt[lane] = 0;
   if (lane == 0) W.steps = W.sides = 0;
-  W.l_scene[lane] = 0;
   __syncwarp();
 
   auto flush = [&](int m, int top) {
@@ -103,26 +105,29 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
     unsigned f_steps = 0, f_sides = 0;
     if (lane < m) {
       const int k = top - m + lane;
-      const int id = W.d_idx[k], te = W.d_te[k], st = W.d_st[k];
-      const BatchItemDev& it = items[W.d_item[k]];
+      const int4 pb = W.d_b[k];
+      const int id = pb.x, te = pb.y, st = pb.z;
+      const BatchItemDev& it = items[pb.w];
+      const SceneDev& S = scenes[it.scene];
       int32_t h = -1;
       float tv = __int_as_float(0x7fc00000);
       if (st > 0) {
         f_steps = (unsigned)st;
         f_sides = (unsigned)st - 1u;
-        const TriRec r = load_rec(scenes[W.d_scene[k]].rec + (te >> 2));
+        const TriRec r = load_rec(S.rec + (te >> 2));
         const int e = te & 3;
         const int32_t w = nb_of(r, e);
         if (w <= -2) {
           h = -2 - w;
           const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
-          tv = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), W.d_ox[k], W.d_oy[k],
-                              k_of_word<kExact>(W.d_kx[k]), k_of_word<kExact>(W.d_ky[k]));
+          const int4 o = W.d_a[k];
+          tv = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), o.x, o.y, k_of_word<kExact>(o.z),
+                              k_of_word<kExact>(o.w));
         } else {
           tv = __int_as_float(0x7f800000);
         }
       } else if (st == CCT_RAY_WALK_LIMIT) {
-        f_sides = (unsigned)scenes[W.d_scene[k]].max_steps - 1u;
+        f_sides = (unsigned)S.max_steps - 1u;
       }
       it.hit[id] = h;
       it.t[id] = tv;
@@ -137,15 +142,15 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
     __syncwarp();
   };
 
-  // 32 rays of the pool's item at once: load, start triangle (given, or the
-  // Sec. 5.2 locate walk), first step; onto `ready` or `parked`
-  auto prepare = [&]() {
+  // Starts the copies of the next (up to) 32 rays of the warp's pool into
+  // `pf` (a new chunk from the global counter when the pool is empty).
+  auto prefetch = [&]() {
     if (p_next >= p_end) {
       int c = 0;
       if (lane == 0) c = (int)atomicAdd(counter, 1ull);
       c = __shfl_sync(FULL, c, 0);
       if (c >= total) {
-        exhausted = true;
+        pf_base = -1;
         return;
       }
       p_item = find_item(items, n_items, c);
@@ -153,20 +158,51 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
       p_next = (c - it.chunk_begin) * chunk;
       p_end = min(p_next + chunk, it.n);
     }
-    const BatchItemDev& it = items[p_item];
+    pf_item = p_item;
+    pf_base = p_next;
+    pf_end = min(p_next + 32, p_end);
+    p_next = pf_end;
+    const int i = pf_base + lane;
+    if (i < pf_end) {
+      const BatchItemDev& it = items[pf_item];
+      const long long ri = (long long)i * it.stride;
+      cp_async4(&W.pf[0][lane], it.ox + ri);
+      cp_async4(&W.pf[1][lane], it.oy + ri);
+      cp_async4(&W.pf[2][lane], it.dx + ri);
+      cp_async4(&W.pf[3][lane], it.dy + ri);
+      if (it.start) cp_async4(&W.pf[4][lane], it.start + i);
+    }
+    cp_async_commit();
+  };
+
+  // 32 rays of one item at once (the prefetched batch): start triangle
+  // (given, or the Sec. 5.2 locate walk), first step; onto `ready` or `parked`
+  auto prepare = [&]() {
+    if (pf_base < 0) {
+      exhausted = true;
+      return;
+    }
+    cp_async_wait_all();
+    const int it_idx = pf_item;
+    const BatchItemDev& it = items[it_idx];
     const int sc = it.scene;
     const SceneDev& S = scenes[sc];
-    const int i = p_next + lane;
-    const bool v = i < p_end;
-    p_next = min(p_next + 32, p_end);
-    int pox = 0, poy = 0, pkx = 0, pky = 0, T0 = -1;  // pkx, pky: direction words
-    bool ok = false;
+    const int i = pf_base + lane;
+    const bool v = i < pf_end;
     const bool locate = it.start == nullptr;
+    int pox = 0, poy = 0, pkx = 0, pky = 0, T0 = -1;  // pkx, pky: direction words
+    float pdx = 0.f, pdy = 0.f;
     if (v) {
-      const long long ri = (long long)i * it.stride;
-      pox = it.ox[ri];
-      poy = it.oy[ri];
-      const float pdx = it.dx[ri], pdy = it.dy[ri];
+      pox = W.pf[0][lane];
+      poy = W.pf[1][lane];
+      pdx = __int_as_float(W.pf[2][lane]);
+      pdy = __int_as_float(W.pf[3][lane]);
+      if (!locate) T0 = W.pf[4][lane];
+    }
+    __syncwarp();
+    prefetch();  // the next batch arrives while this one is prepared and walked
+    bool ok = false;
+    if (v) {
       ok = dir_to_k(pdx, pkx) && dir_to_k(pdy, pky) && (pkx | pky) != 0 && pox >= 0 && poy >= 0 && pox <= S.D &&
            poy <= S.D;
       pkx = k_word<kExact>(pkx);
@@ -174,7 +210,6 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
       if (locate) {
         if (ok) T0 = S.seeds[seed_cell(S, pox, poy)];
       } else {
-        T0 = it.start[i];
         T0 = (T0 >= 0 && T0 < S.n_tri) ? S.user2dev[T0] : -1;
         ok = ok && T0 >= 0;
       }
@@ -250,46 +285,27 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
     }
     if (to_ready) {
       const int k = n_ready + __popc(mr & lt);
-      W.r_ox[k] = pox;
-      W.r_oy[k] = poy;
-      W.r_kx[k] = pkx;
-      W.r_ky[k] = pky;
-      W.r_tj[k] = w;
-      W.r_idx[k] = i;
-      W.r_item[k] = p_item;
-      W.r_scene[k] = sc;
+      W.r_a[k] = make_int4(pox, poy, pkx, pky);
+      W.r_b[k] = make_int4(w, i, it_idx, sc);
     } else if (to_done) {
       const int k = n_done + __popc(md & lt);
-      W.d_idx[k] = i;
-      W.d_te[k] = (T0 << 2) | e;
-      W.d_st[k] = ok ? 1 : CCT_RAY_INVALID;
-      W.d_ox[k] = pox;
-      W.d_oy[k] = poy;
-      W.d_kx[k] = pkx;
-      W.d_ky[k] = pky;
-      W.d_item[k] = p_item;
-      W.d_scene[k] = sc;
+      W.d_a[k] = make_int4(pox, poy, pkx, pky);
+      W.d_b[k] = make_int4(i, (T0 << 2) | e, ok ? 1 : CCT_RAY_INVALID, it_idx);
     }
     n_ready += __popc(mr);
     n_done += __popc(md);
     __syncwarp();
   };
 
+  if (!exhausted) prefetch();
   while (true) {
     const unsigned idle = __ballot_sync(FULL, !active);
     if (idle != 0u && (__popc(idle) >= refill_min || idle == FULL)) {
       const unsigned dm = __ballot_sync(FULL, done);
       if (done) {
         const int k = n_done + __popc(dm & lt);
-        W.d_idx[k] = W.l_idx[lane];
-        W.d_te[k] = (T << 2) | j;
-        W.d_st[k] = nsteps;
-        W.d_ox[k] = ox;
-        W.d_oy[k] = oy;
-        W.d_kx[k] = kx;
-        W.d_ky[k] = ky;
-        W.d_item[k] = W.l_item[lane];
-        W.d_scene[k] = W.l_scene[lane];
+        W.d_a[k] = make_int4(ox, oy, kx, ky);
+        W.d_b[k] = make_int4(W.l_idx[lane], (T << 2) | j, nsteps, W.l_item[lane]);
         done = false;
       }
       n_done += __popc(dm);
@@ -308,17 +324,17 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
       const int rank = __popc(idle & lt);
       if (!active && rank < n_ready) {
         const int k = n_ready - 1 - rank;
-        ox = W.r_ox[k];
-        oy = W.r_oy[k];
-        kx = W.r_kx[k];
-        ky = W.r_ky[k];
-        const int tj = W.r_tj[k];
-        const int scene = W.r_scene[k];
-        W.l_idx[lane] = W.r_idx[k];
-        W.l_item[lane] = W.r_item[k];
-        W.l_scene[lane] = scene;
-        T = tj >> 2;
-        j = tj & 3;
+        const int4 a = W.r_a[k];
+        const int4 b = W.r_b[k];
+        ox = a.x;
+        oy = a.y;
+        kx = a.z;
+        ky = a.w;
+        const int scene = b.w;
+        W.l_idx[lane] = b.y;
+        W.l_item[lane] = b.z;
+        T = b.x >> 2;
+        j = b.x & 3;
         rec = scenes[scene].rec;
         max_steps = scenes[scene].max_steps;
         nsteps = 1;
