@@ -62,24 +62,35 @@ __device__ __forceinline__ int find_item(const BatchItemDev* items, int n_items,
 // holds rays past their first triangle, `parked` finished rays awaiting
 // their results; each entry carries its item and scene.
 constexpr int kBStack = 64;
-enum : int { kBRays = 0, kBFallback, kBInvalid, kBLimit, kBLocated, kBLocSteps, kBCounters };
+enum : int { kBRays = 0, kBInvalid, kBLocated, kBLocSteps, kBCounters };
 struct BatchStacks {
-  int4 r_a[kBStack];  // ready: ox, oy, kx word, ky word
-  int4 r_b[kBStack];  // ready: next record << 2 | entry edge, ray index, item, scene
-  int4 d_a[kBStack];  // parked: ox, oy, kx word, ky word
+  int4 r_a[kBStack];  // ready: ox word, oy word, kx word, ky word
+  int4 r_b[kBStack];  // ready: half-edge index, ray index, item, scene
+  int4 d_a[kBStack];  // parked: ox word, oy word, kx word, ky word
   int4 d_b[kBStack];  // parked: ray index, final record << 2 | exit edge, steps or status, item
   int pf[5][32];      // the next batch's ray inputs (ox, oy, dx, dy, start), copied in while the warp walks
-  int l_idx[32], l_item[32];  // the walking lanes' cold state (read when they park)
   unsigned cnt[kBCounters];
   unsigned long long steps, sides;
 };
 
+// One walk slot (see walk.cu), plus the item of its ray and its scene's
+// half-edge table.
+struct BSlot {
+  const int4* he;
+  int ox, oy, kx, ky, h, ns, id, item;
+  bool act, dn;
+};
+
+// max_steps: the largest step limit of the batch's scenes.  A slot walks
+// until that limit; a ray that needed more than its own scene's limit
+// becomes a walk-limit ray when its result is written, exactly as if it had
+// stopped at its own limit.
 template <bool kExact>
 __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev* __restrict__ scenes,
                                                                  const BatchHeader* __restrict__ hdr,
                                                                  const BatchItemDev* __restrict__ items,
-                                                                 int refill_min, unsigned long long* counter,
-                                                                 DevStats* bstats) {
+                                                                 int refill_min, int max_steps,
+                                                                 unsigned long long* counter, DevStats* bstats) {
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BatchStacks& W = reinterpret_cast<BatchStacks*>(smem_raw)[threadIdx.x >> 5];
@@ -92,23 +103,26 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
   int pf_item = 0, pf_base = 0, pf_end = 0;
   int n_ready = 0, n_done = 0;
   bool exhausted = n_items <= 0;
-  // lane state: walking (active), finished and not yet parked (done), or idle
-  bool active = false, done = false;
-  int ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0, max_steps = 0;
-  const TriRec* rec = nullptr;
+  unsigned n_fb = 0;  // this lane's int64 fallbacks
+  BSlot sl[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) sl[q] = BSlot{nullptr, 0, 0, 0, 0, 0, 0, 0, 0, false, false};
   if (lane < kBCounters) W.cnt[lane] = 0;
   if (lane == 0) W.steps = W.sides = 0;
   __syncwarp();
 
+  unsigned n_lim = 0;  // walk-limit rays completed by this lane
   auto flush = [&](int m, int top) {
     __syncwarp();
     unsigned f_steps = 0, f_sides = 0;
     if (lane < m) {
       const int k = top - m + lane;
       const int4 pb = W.d_b[k];
-      const int id = pb.x, te = pb.y, st = pb.z;
+      const int id = pb.x, te = pb.y;
+      int st = pb.z;
       const BatchItemDev& it = items[pb.w];
       const SceneDev& S = scenes[it.scene];
+      if (st > S.max_steps) st = CCT_RAY_WALK_LIMIT;  // walked past its own scene's limit
       int32_t h = -1;
       float tv = __int_as_float(0x7fc00000);
       if (st > 0) {
@@ -121,13 +135,14 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
           h = -2 - w;
           const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
           const int4 o = W.d_a[k];
-          tv = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), o.x, o.y, k_of_word<kExact>(o.z),
-                              k_of_word<kExact>(o.w));
+          tv = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), o_of_word<kExact>(o.x),
+                              o_of_word<kExact>(o.y), k_of_word<kExact>(o.z), k_of_word<kExact>(o.w));
         } else {
           tv = __int_as_float(0x7f800000);
         }
       } else if (st == CCT_RAY_WALK_LIMIT) {
         f_sides = (unsigned)S.max_steps - 1u;
+        ++n_lim;
       }
       it.hit[id] = h;
       it.t[id] = tv;
@@ -250,6 +265,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
         }
       }
     }
+    const int oxw = o_word<kExact>(pox), oyw = o_word<kExact>(poy);
     int e = 0;
     int32_t w = -1;
     if (ok) {
@@ -258,11 +274,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
       if (!locate)
         ok = orient_i(x1, y1, x2, y2, pox, poy) > 0 && orient_i(x2, y2, x0, y0, pox, poy) > 0 &&
              orient_i(x0, y0, x1, y1, pox, poy) > 0;
-      unsigned fb = 0;
-      const bool s0 = side_L_w<kExact>(pkx, pky, pox, poy, x0, y0, fb);
-      const bool s1 = side_L_w<kExact>(pkx, pky, pox, poy, x1, y1, fb);
-      const bool s2 = side_L_w<kExact>(pkx, pky, pox, poy, x2, y2, fb);
-      if (!kExact && fb) atomicAdd(&W.cnt[kBFallback], fb);
+      const bool s0 = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(x0), coord_word(y0), n_fb);
+      const bool s1 = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(x1), coord_word(y1), n_fb);
+      const bool s2 = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(x2), coord_word(y2), n_fb);
       e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
       w = nb_of(r, e);
     }
@@ -285,11 +299,11 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
     }
     if (to_ready) {
       const int k = n_ready + __popc(mr & lt);
-      W.r_a[k] = make_int4(pox, poy, pkx, pky);
+      W.r_a[k] = make_int4(oxw, oyw, pkx, pky);
       W.r_b[k] = make_int4(w, i, it_idx, sc);
     } else if (to_done) {
       const int k = n_done + __popc(md & lt);
-      W.d_a[k] = make_int4(pox, poy, pkx, pky);
+      W.d_a[k] = make_int4(oxw, oyw, pkx, pky);
       W.d_b[k] = make_int4(i, (T0 << 2) | e, ok ? 1 : CCT_RAY_INVALID, it_idx);
     }
     n_ready += __popc(mr);
@@ -297,23 +311,49 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
     __syncwarp();
   };
 
+  // One apex step of a walking slot on its half-edge record q (Sec. 5.1).
+  auto step = [&](BSlot& s, const int4& q) {
+    const bool sc = side_L_cw<kExact>(s.kx, s.ky, s.ox, s.oy, q.x, q.y, n_fb);
+    ++s.ns;
+    const int32_t w = sc ? q.z : q.w;
+    if (w >= 0 && s.ns < max_steps) {
+      s.h = w;
+      return;
+    }
+    if (w >= 0) {
+      s.ns = CCT_RAY_WALK_LIMIT;
+    } else {
+      const int T = he_tri(s.h), j = s.h - 3 * T;
+      const int e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
+      s.h = (T << 2) | e;
+    }
+    s.act = false;
+    s.dn = true;
+  };
+
   if (!exhausted) prefetch();
   while (true) {
-    const unsigned idle = __ballot_sync(FULL, !active);
-    if (idle != 0u && (__popc(idle) >= refill_min || idle == FULL)) {
-      const unsigned dm = __ballot_sync(FULL, done);
-      if (done) {
-        const int k = n_done + __popc(dm & lt);
-        W.d_a[k] = make_int4(ox, oy, kx, ky);
-        W.d_b[k] = make_int4(W.l_idx[lane], (T << 2) | j, nsteps, W.l_item[lane]);
-        done = false;
+    const unsigned idle0 = __ballot_sync(FULL, !sl[0].act), idle1 = __ballot_sync(FULL, !sl[1].act);
+    const int n_idle = __popc(idle0) + __popc(idle1);
+    if (n_idle != 0 && (n_idle >= refill_min || (idle0 & idle1) == FULL)) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const unsigned dm = __ballot_sync(FULL, sl[q].dn);
+        if (dm != 0u) {
+          if (sl[q].dn) {
+            const int k = n_done + __popc(dm & lt);
+            W.d_a[k] = make_int4(sl[q].ox, sl[q].oy, sl[q].kx, sl[q].ky);
+            W.d_b[k] = make_int4(sl[q].id, sl[q].h, sl[q].ns, sl[q].item);
+            sl[q].dn = false;
+          }
+          n_done += __popc(dm);
+          if (n_done >= 32) {
+            flush(32, n_done);
+            n_done -= 32;
+          }
+        }
       }
-      n_done += __popc(dm);
-      if (n_done >= 32) {
-        flush(32, n_done);
-        n_done -= 32;
-      }
-      const int want = __popc(idle);
+      const int want = min(n_idle, 32);
       if (n_ready < want && !exhausted) {
         prepare();
         if (n_done >= 32) {
@@ -321,55 +361,39 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
           n_done -= 32;
         }
       }
-      const int rank = __popc(idle & lt);
-      if (!active && rank < n_ready) {
-        const int k = n_ready - 1 - rank;
-        const int4 a = W.r_a[k];
-        const int4 b = W.r_b[k];
-        ox = a.x;
-        oy = a.y;
-        kx = a.z;
-        ky = a.w;
-        const int scene = b.w;
-        W.l_idx[lane] = b.y;
-        W.l_item[lane] = b.z;
-        T = b.x >> 2;
-        j = b.x & 3;
-        rec = scenes[scene].rec;
-        max_steps = scenes[scene].max_steps;
-        nsteps = 1;
-        active = true;
+      const int take = min(want, n_ready);
+      const int rank0 = __popc(idle0 & lt), rank1 = __popc(idle0) + __popc(idle1 & lt);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int rank = q == 0 ? rank0 : rank1;
+        if (!sl[q].act && rank < take) {
+          const int k = n_ready - 1 - rank;
+          const int4 a = W.r_a[k];
+          const int4 b = W.r_b[k];
+          sl[q].ox = a.x;
+          sl[q].oy = a.y;
+          sl[q].kx = a.z;
+          sl[q].ky = a.w;
+          sl[q].h = b.x;
+          sl[q].id = b.y;
+          sl[q].item = b.z;
+          sl[q].he = scenes[b.w].he;
+          sl[q].ns = 1;
+          sl[q].act = true;
+        }
       }
-      n_ready -= min(want, n_ready);
+      n_ready -= take;
       __syncwarp();
     }
-    if (!__any_sync(FULL, active)) {
+    if (!__any_sync(FULL, sl[0].act || sl[1].act)) {
       if (exhausted && n_ready == 0) break;
       continue;
     }
-    if (active) {
-      const TriRec r = load_rec(rec + T);
-      unsigned fb = 0;
-      const bool sc = side_L_w<kExact>(kx, ky, ox, oy, vx_of(r, j), vy_of(r, j), fb);
-      if (!kExact && fb) atomicAdd(&W.cnt[kBFallback], fb);
-      const int e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
-      ++nsteps;
-      const int32_t w = nb_of(r, e);
-      if (w >= 0) {
-        T = w >> 2;
-        j = w & 3;
-        if (nsteps >= max_steps) {
-          nsteps = CCT_RAY_WALK_LIMIT;
-          active = false;
-          done = true;
-          atomicAdd(&W.cnt[kBLimit], 1u);
-        }
-      } else {
-        j = e;
-        active = false;
-        done = true;
-      }
-    }
+    int4 q0 = make_int4(0, 0, 0, 0), q1 = make_int4(0, 0, 0, 0);
+    if (sl[0].act) q0 = load_he(sl[0].he + sl[0].h);
+    if (sl[1].act) q1 = load_he(sl[1].he + sl[1].h);
+    if (sl[0].act) step(sl[0], q0);
+    if (sl[1].act) step(sl[1], q1);
   }
   while (n_done > 0) {
     const int m = min(32, n_done);
@@ -377,16 +401,17 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
     n_done -= m;
   }
   __syncwarp();
+  const unsigned w_fb = __reduce_add_sync(FULL, n_fb), w_limit = __reduce_add_sync(FULL, n_lim);
   const unsigned long long w_steps = W.steps, w_side = W.sides;
-  const unsigned long long w_rays = W.cnt[kBRays], w_fb = W.cnt[kBFallback], w_inv = W.cnt[kBInvalid];
-  const unsigned long long w_lim = W.cnt[kBLimit], w_loc = W.cnt[kBLocated], w_lst = W.cnt[kBLocSteps];
+  const unsigned long long w_rays = W.cnt[kBRays], w_inv = W.cnt[kBInvalid];
+  const unsigned long long w_loc = W.cnt[kBLocated], w_lst = W.cnt[kBLocSteps];
   if (lane == 0) {
     if (w_rays) atomicAdd(&bstats->rays, w_rays);
     if (w_steps) atomicAdd(&bstats->steps, w_steps);
     if (w_side) atomicAdd(&bstats->side_tests, w_side);
-    if (w_fb) atomicAdd(&bstats->exact_fallbacks, w_fb);
+    if (w_fb) atomicAdd(&bstats->exact_fallbacks, (unsigned long long)w_fb);
     if (w_inv) atomicAdd(&bstats->invalid_rays, w_inv);
-    if (w_lim) atomicAdd(&bstats->walk_limit_rays, w_lim);
+    if (w_limit) atomicAdd(&bstats->walk_limit_rays, (unsigned long long)w_limit);
     if (w_loc) atomicAdd(&bstats->located, w_loc);
     if (w_lst) atomicAdd(&bstats->locate_steps, w_lst);
   }
@@ -413,6 +438,7 @@ struct cct_batch_s {
   size_t table_bytes;
   int grid;
   int staged;
+  int max_steps;  // the largest step limit of the batch's scenes
 };
 
 static size_t batch_smem(int threads) { return sizeof(BatchStacks) * (size_t)(threads / 32); }
@@ -468,7 +494,11 @@ extern "C" int cct_batch_create(const cct_scene* scenes, int32_t n_scenes, int32
   b->d_counter = (unsigned long long*)(b->d_base + o_counter);
   b->d_stats = (DevStats*)(b->d_base + o_stats);
   std::vector<SceneDev> sd(n_scenes);
-  for (int k = 0; k < n_scenes; ++k) sd[k] = scenes[k]->dev;
+  b->max_steps = 1;
+  for (int k = 0; k < n_scenes; ++k) {
+    sd[k] = scenes[k]->dev;
+    b->max_steps = std::max(b->max_steps, sd[k].max_steps);
+  }
   cudaError_t e = cudaMemcpy(b->d_scenes, sd.data(), sizeof(SceneDev) * n_scenes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->d_hdr, 0, b->table_bytes);
   if (e == cudaSuccess) e = cudaMemset(b->d_stats, 0, sizeof(DevStats));
@@ -548,12 +578,12 @@ extern "C" int cct_batch_enqueue(cct_batch b, void* stream_v) {
   const size_t smem = batch_smem(b->tuning.block_threads);
   if (b->flags & CCT_TRACE_EXACT_ONLY)
     batch_kernel<true><<<b->grid, b->tuning.block_threads, smem, stream>>>(b->d_scenes, b->d_hdr, items,
-                                                                           b->tuning.refill_min, b->d_counter,
-                                                                           b->d_stats);
+                                                                           b->tuning.refill_min, b->max_steps,
+                                                                           b->d_counter, b->d_stats);
   else
     batch_kernel<false><<<b->grid, b->tuning.block_threads, smem, stream>>>(b->d_scenes, b->d_hdr, items,
-                                                                            b->tuning.refill_min, b->d_counter,
-                                                                            b->d_stats);
+                                                                            b->tuning.refill_min, b->max_steps,
+                                                                            b->d_counter, b->d_stats);
   return cudaGetLastError() == cudaSuccess ? CCT_OK : CCT_ERR_CUDA;
 }
 

@@ -2,7 +2,14 @@
 //
 // Device scene layout (one allocation per scene, 256-byte aligned pieces):
 //   rec       TriRec[n_tri]     32-byte triangle records in Hilbert order of the
-//                               triangle centroids: one L2 sector per walk step
+//                               triangle centroids (coordinates + neighbour
+//                               words): the start triangle, the locate walk and
+//                               the result of a ray read these
+//   he        int4[3*n_tri]     16-byte half-edge records, one per (triangle T,
+//                               entry edge j) at index 3 T + j: what a walk
+//                               step after the first needs and nothing else
+//                               (the apex of the entry edge and the two
+//                               candidate exit words), one L2 sector per step
 //   cnb       int32[3*n_tri]    neighbour word across constrained edges (read
 //                               only by the locate walk, which crosses them)
 //   user2dev  int32[n_tri]      caller triangle id -> record index
@@ -27,8 +34,8 @@ constexpr float kDirScale = 4194304.0f;  // 2^22
 
 // One triangle.  X / Y hold the coordinates of vertex i at bits [21 i, 21 i + 21).
 // nb[i] describes the edge opposite vertex i (vertices CCW):
-//   nb >= 0 : interior edge; (neighbour record index << 2) | (index of the same
-//             edge in the neighbour)
+//   nb >= 0 : interior edge; the half-edge index 3 T' + j' of the neighbour
+//             T' entered through this edge (its edge j')
 //   nb == -1: hull edge (the ray leaves the domain: a miss)
 //   nb <= -2: constrained edge carrying scene segment -2 - nb (a hit)
 struct __align__(32) TriRec {
@@ -39,6 +46,21 @@ struct __align__(32) TriRec {
 };
 static_assert(sizeof(TriRec) == 32, "TriRec must be one 32-byte sector");
 
+// Half-edge record 3 T + j (triangle T entered through its edge j, so its
+// apex is vertex j and the two other vertices' sides are already known):
+//   x, y : apex coordinates as the fp32 bit patterns of 2^23 + coordinate
+//          (exact; the integer is the low 23 bits, see coord_of_word)
+//   z    : neighbour word of edge nxt(j), the exit when the apex is left (L)
+//   w    : neighbour word of edge prv(j), the exit when the apex is right (R)
+// with nxt(j) = (j + 1) mod 3, prv(j) = (j + 2) mod 3.
+constexpr int kCoordBias = 0x4B000000;  // fp32 bits of 2^23
+constexpr int kCoordLow = 0x7FFFFF;
+__host__ __device__ __forceinline__ int coord_word(int c) { return kCoordBias | c; }
+__host__ __device__ __forceinline__ int coord_of_word(int w) { return w & kCoordLow; }
+
+// Triangle and edge of a half-edge index (3 T + j; T < 2^29).
+__device__ __forceinline__ int he_tri(int h) { return (int)((unsigned)h / 3u); }
+
 struct DevStats {
   unsigned long long rays, steps, side_tests, exact_fallbacks, invalid_rays, walk_limit_rays, located,
       locate_steps;
@@ -46,6 +68,7 @@ struct DevStats {
 
 struct SceneDev {
   const TriRec* rec;
+  const int4* he;
   const int32_t* cnb;
   const int32_t* user2dev;
   const int32_t* dev2user;
@@ -69,6 +92,12 @@ __device__ __forceinline__ TriRec load_rec(const TriRec* p) {
   r.nb[1] = (int32_t)(uint32_t)(c >> 32);
   r.nb[2] = (int32_t)(uint32_t)d;
   r.pad = (int32_t)(uint32_t)(d >> 32);
+  return r;
+}
+
+__device__ __forceinline__ int4 load_he(const int4* p) {
+  int4 r;
+  asm volatile("ld.global.nc.v4.s32 {%0,%1,%2,%3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
   return r;
 }
 
@@ -137,6 +166,37 @@ __device__ __forceinline__ bool side_L_w(int kxw, int kyw, int ox, int oy, int v
   }
   const long long e = (long long)k_of_word<kExactOnly>(kxw) * ddy - (long long)k_of_word<kExactOnly>(kyw) * ddx;
   return e >= 0;
+}
+
+// Origin word of a ray in the walk state: the fp32 bits of 2^23 + o in the
+// filtered variant (so that apex - origin is one exact fp32 subtraction of two
+// numbers in [2^23, 2^24)), the integer o in the exact-only variant.
+template <bool kExactOnly>
+__device__ __forceinline__ int o_word(int o) {
+  return kExactOnly ? o : coord_word(o);
+}
+template <bool kExactOnly>
+__device__ __forceinline__ int o_of_word(int w) {
+  return kExactOnly ? w : coord_of_word(w);
+}
+
+// Side (true = L) of a vertex given by its coordinate words (coord_word)
+// relative to the ray with origin words (o_word) and direction words (k_word).
+// Filtered: dx_v = (2^23 + v_x) - (2^23 + o_x) is exact, so r is the same fp32
+// value as in side_L_w and the same bound decides; the int64 test otherwise.
+template <bool kExactOnly>
+__device__ __forceinline__ bool side_L_cw(int kxw, int kyw, int oxw, int oyw, int vxw, int vyw, unsigned& fallbacks) {
+  if (!kExactOnly) {
+    const float ddx = __fsub_rn(__int_as_float(vxw), __int_as_float(oxw));
+    const float ddy = __fsub_rn(__int_as_float(vyw), __int_as_float(oyw));
+    const float p = __fmul_rn(__int_as_float(kyw), ddx);
+    const float r = __fmaf_rn(__int_as_float(kxw), ddy, -p);
+    if (fabsf(r) >= kFilterBound * kDirScale) return r > 0.0f;
+    ++fallbacks;
+  }
+  const int ddx = coord_of_word(vxw) - o_of_word<kExactOnly>(oxw);
+  const int ddy = coord_of_word(vyw) - o_of_word<kExactOnly>(oyw);
+  return (long long)k_of_word<kExactOnly>(kxw) * ddy - (long long)k_of_word<kExactOnly>(kyw) * ddx >= 0;
 }
 
 __device__ __forceinline__ long long orient_ll(long long ax, long long ay, long long bx, long long by, long long cx,
@@ -221,8 +281,8 @@ __device__ __forceinline__ bool locate_hop(const SceneDev& S, const TriRec& r, i
   int32_t w = nb_of(r, e);
   if (w <= -2) w = S.cnb[3 * T + e];
   if (w < 0) return false;
-  T = w >> 2;
-  j = w & 3;
+  T = he_tri(w);
+  j = w - 3 * T;
   return true;
 }
 

@@ -6,7 +6,9 @@
 //   1. validation (exact integer checks, host);
 //   2. Hilbert order of the triangle centroids, so that triangles adjacent in
 //      space are adjacent in memory (walk and locate locality);
-//   3. one 32-byte record per triangle (coordinates + neighbour words);
+//   3. one 32-byte record per triangle (coordinates + neighbour words) and
+//      one 16-byte half-edge record per (triangle, entry edge) for the walk
+//      steps after the first;
 //   4. the locate seed grid of Sec. 5.2: G x G square cells of side 2^s, each
 //      holding the triangle of its seed point (the cell centre, symbolically
 //      perturbed: see seed_point in cct_internal.cuh), found by exact walks.
@@ -140,7 +142,7 @@ struct HostLocator {
       int32_t w = r.nb[e];
       if (w <= -2) w = cnb[3 * (size_t)T + e];
       if (w < 0) return -1;
-      T = w >> 2;
+      T = w / 3;
     }
     return -1;
   }
@@ -207,7 +209,7 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
           int j = 0;
           for (int k = 0; k < 3; ++k)
             if (d.tri_v[3 * nbu + (k + 1) % 3] == b && d.tri_v[3 * nbu + (k + 2) % 3] == a) j = k;
-          word = (user2dev[nbu] << 2) | j;
+          word = 3 * user2dev[nbu] + j;
         }
         if (seg >= 0) {
           cnb[3 * (size_t)T + i] = word;
@@ -217,6 +219,15 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
         }
       }
       rec[T] = r;
+    }
+    // half-edge records 3 T + j: apex j and the exit words of edges nxt(j), prv(j)
+    std::vector<int4> he(3 * (size_t)nt);
+    for (int T = 0; T < nt; ++T) {
+      const TriRec& r = rec[T];
+      for (int j = 0; j < 3; ++j) {
+        const int ax = (int)((r.X >> (kCoordBits * j)) & kCoordMask), ay = (int)((r.Y >> (kCoordBits * j)) & kCoordMask);
+        he[3 * (size_t)T + j] = make_int4(coord_word(ax), coord_word(ay), r.nb[(j + 1) % 3], r.nb[(j + 2) % 3]);
+      }
     }
     // ---- seed grid (Sec. 5.2): per cell, the triangle whose interior holds
     // the perturbed cell centre; about 2^k cells per triangle, k from the flags
@@ -258,7 +269,8 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
     }
     // ---- device allocation and upload
     size_t o_rec = 0;
-    size_t o_cnb = o_rec + align256(sizeof(TriRec) * (size_t)nt);
+    size_t o_he = o_rec + align256(sizeof(TriRec) * (size_t)nt);
+    size_t o_cnb = o_he + align256(sizeof(int4) * 3 * (size_t)nt);
     size_t o_u2d = o_cnb + align256(sizeof(int32_t) * 3 * (size_t)nt);
     size_t o_d2u = o_u2d + align256(sizeof(int32_t) * (size_t)nt);
     size_t o_seed = o_d2u + align256(sizeof(int32_t) * (size_t)nt);
@@ -274,6 +286,7 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
       if (e == cudaSuccess) e = cudaMemcpyAsync(base + off, src, n, cudaMemcpyHostToDevice, stream);
     };
     up(o_rec, rec.data(), sizeof(TriRec) * (size_t)nt);
+    up(o_he, he.data(), sizeof(int4) * 3 * (size_t)nt);
     up(o_cnb, cnb.data(), sizeof(int32_t) * 3 * (size_t)nt);
     up(o_u2d, user2dev.data(), sizeof(int32_t) * (size_t)nt);
     up(o_d2u, dev2user.data(), sizeof(int32_t) * (size_t)nt);
@@ -289,6 +302,7 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
     s->bytes = total;
     s->device = dev;
     s->dev.rec = (const TriRec*)(base + o_rec);
+    s->dev.he = (const int4*)(base + o_he);
     s->dev.cnb = (const int32_t*)(base + o_cnb);
     s->dev.user2dev = (const int32_t*)(base + o_u2d);
     s->dev.dev2user = (const int32_t*)(base + o_d2u);

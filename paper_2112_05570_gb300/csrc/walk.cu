@@ -8,21 +8,24 @@
 // constrained edge ends the walk with a hit (t from the edge's line), a hull
 // edge with a miss.  Step count = triangles visited (Sec. 5.4).
 //
-// GPU mapping.  One ray per lane in the walk proper; everything done once
-// per ray is done 32 rays at a time, by the whole warp, so the per-ray work
-// never runs with most lanes masked off:
+// GPU mapping.  Everything done once per ray is done 32 rays at a time, by
+// the whole warp, so the per-ray work never runs with most lanes masked off;
+// the steps after the first run on two walk slots per lane:
 //   prepare  the warp takes 32 ray indices (from its chunk of a global work
-//            counter), loads the rays, finds their start triangles (given,
-//            or by the Sec. 5.2 locate walk from the seed point of their grid
-//            cell) and takes the first step; the resulting walk states go on
-//            the warp's `ready` stack in shared memory;
-//   walk     each active lane takes one apex step per loop iteration: one
-//            dependent 32-byte record load, one side test;
-//   serve    once `refill_min` lanes are idle, finished lanes park their
-//            final state on the `parked` stack and idle lanes pop `ready`
-//            states (a prepare first when too few are left);
-//   flush    32 parked rays at a time: reload the final record, compute hit
-//            id and t, write the results.
+//            counter; the rays themselves were copied into shared memory
+//            while the warp walked), finds their start triangles (given, or
+//            by the Sec. 5.2 locate walk from the seed point of their grid
+//            cell) and takes the first step on the 32-byte triangle records;
+//            the resulting walk states go on the warp's `ready` stack;
+//   walk     each active slot takes one apex step per loop iteration: one
+//            dependent 16-byte half-edge load (apex + the two candidate exit
+//            words), one side test, one select.  A lane's two slots hold two
+//            independent rays, so their loads are in flight together;
+//   serve    once `refill_min` of the warp's 64 slots are idle, finished
+//            slots park their final state on the `parked` stack and idle
+//            slots pop `ready` states (a prepare first when too few are left);
+//   flush    32 parked rays at a time: reload the final triangle record,
+//            compute hit id and t, write the results.
 #include <algorithm>
 #include <cmath>
 
@@ -32,27 +35,28 @@ namespace cct {
 
 enum : int { kSrcPlainUser = 0, kSrcPlainDev = 1, kSrcSorted = 2, kSrcLocate = 3 };
 // rare per-warp counters (shared memory)
-enum : int { kCntRays = 0, kCntFallback, kCntInvalid, kCntLimit, kCntLocated, kCntLocSteps, kRareCounters };
+enum : int { kCntRays = 0, kCntInvalid, kCntLocated, kCntLocSteps, kRareCounters };
 
 constexpr int kWalkMaxThreads = 512;
 
 struct WalkParams {
-  int refill_min;  // serve idle lanes once this many are idle (or the whole warp is)
+  int refill_min;  // serve idle slots once this many (of the warp's 64) are idle, or the whole warp is
   int chunk;       // ray indices a warp takes from the global counter at once
 };
 
 // Per-warp stacks in shared memory.  `ready` holds rays whose first
-// triangle is behind them (the state after the first step: next record and
-// entry edge); `parked` holds finished rays waiting for their results.
-// Entries are 16- and 8-byte words, so a push or a pop is two accesses.
-// The whole structure stays near 4 KB per warp: more shared memory per SM
-// shrinks the L1 that holds the record loads in flight (measured slower).
+// triangle is behind them (the state after the first step: the half-edge of
+// the second triangle); `parked` holds finished rays waiting for their
+// results.  Entries are 16- and 8-byte words, so a push or a pop is two
+// accesses.  The whole structure stays near 4 KB per warp: more shared memory
+// per SM shrinks the L1 that holds the record loads in flight (measured
+// slower).
 constexpr int kStack = 64;
 template <int kPfRows>
 struct WarpStacks {
-  int4 r_a[kStack];    // ready: ox, oy, kx word, ky word
-  int2 r_b[kStack];    // ready: next record << 2 | entry edge, ray index
-  int4 d_a[kStack];    // parked: ox, oy, kx word, ky word
+  int4 r_a[kStack];    // ready: ox word, oy word, kx word, ky word
+  int2 r_b[kStack];    // ready: half-edge index, ray index
+  int4 d_a[kStack];    // parked: ox word, oy word, kx word, ky word
   int2 d_b[kStack];    // parked: ray index, final record << 2 | exit edge
   int d_st[kStack];    // parked: steps or status
   int pf[kPfRows][32];  // the next batch's ray inputs, copied in while the warp walks (see prefetch)
@@ -64,6 +68,16 @@ template <int kSrc>
 __host__ __device__ constexpr int pf_rows() {
   return kSrc == kSrcSorted ? 6 : (kSrc == kSrcLocate ? 4 : 5);
 }
+
+// One walk slot: a ray past its first triangle.  ox, oy: origin words
+// (o_word); kx, ky: direction words (k_word); h: the half-edge to enter next
+// while walking, final record << 2 | exit edge once finished; ns: triangles
+// visited (or a CCT_RAY_* status); id: ray index.
+struct Slot {
+  int ox, oy, kx, ky, h, ns, id;
+  bool act;  // walking
+  bool dn;   // finished, not yet parked
+};
 
 template <bool kExact, int kSrc>
 __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySrc R, WalkParams P,
@@ -79,22 +93,24 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int n = (int)R.n;
+  const int4* __restrict__ he_tab = S.he;
+  const int max_steps = S.max_steps;
   int pool_next = 0, pool_end = 0;  // the warp's current range of ray indices
   int pf_base = 0, pf_end = 0;      // the batch in `pf` ([pf_base, pf_end)); pf_base < 0: none left
   int n_ready = 0, n_done = 0;      // stack depths (warp-uniform)
   bool exhausted = false;
+  unsigned n_fb = 0, n_lim = 0;  // this lane's int64 fallbacks and walk-limit rays
 
-  // lane state: walking (active), finished and not yet parked (done), or idle
-  // (kx, ky: direction words, see side_L_w)
-  bool active = false, done = false;
-  int idx = 0, ox = 0, oy = 0, kx = 0, ky = 0, T = 0, j = 0, nsteps = 0;
+  Slot sl[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) sl[s] = Slot{0, 0, 0, 0, 0, 0, 0, false, false};
   if (lane < kRareCounters) W.cnt[lane] = 0;
   if (lane == 0) W.steps = W.sides = 0;
   __syncwarp();
 
   // Results of the parked rays [top - m, top): lane l completes entry top - m + l
-  // (the final record is reloaded: it was read a few iterations ago).  Also
-  // counts their steps and their side tests after the first triangle.
+  // (the final triangle record is reloaded).  Also counts their steps and
+  // their side tests after the first triangle.
   auto flush = [&](int m, int top) {
     __syncwarp();
     unsigned f_steps = 0, f_sides = 0;
@@ -114,8 +130,8 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
           h = -2 - w;
           const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
           const int4 o = W.d_a[k];
-          tv = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), o.x, o.y, k_of_word<kExact>(o.z),
-                              k_of_word<kExact>(o.w));
+          tv = hit_param_fast(vx_of(r, a), vy_of(r, a), vx_of(r, b), vy_of(r, b), o_of_word<kExact>(o.x),
+                              o_of_word<kExact>(o.y), k_of_word<kExact>(o.z), k_of_word<kExact>(o.w));
         } else {
           tv = __int_as_float(0x7f800000);  // +inf: left through the hull
         }
@@ -258,6 +274,7 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     }
     // first step (Sec. 5.1): sides of all three vertices, leave through the
     // CCW edge (a -> b) with s(a) = R, s(b) = L
+    const int oxw = o_word<kExact>(pox), oyw = o_word<kExact>(poy);
     int e = 0;
     int32_t w = -1;
     if (ok) {
@@ -266,11 +283,9 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
       if (!kLocate)
         ok = orient_i(x1, y1, x2, y2, pox, poy) > 0 && orient_i(x2, y2, x0, y0, pox, poy) > 0 &&
              orient_i(x0, y0, x1, y1, pox, poy) > 0;
-      unsigned fb = 0;
-      const bool s0 = side_L_w<kExact>(pkx, pky, pox, poy, x0, y0, fb);
-      const bool s1 = side_L_w<kExact>(pkx, pky, pox, poy, x1, y1, fb);
-      const bool s2 = side_L_w<kExact>(pkx, pky, pox, poy, x2, y2, fb);
-      if (!kExact && fb) atomicAdd(&W.cnt[kCntFallback], fb);
+      const bool s0 = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(x0), coord_word(y0), n_fb);
+      const bool s1 = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(x1), coord_word(y1), n_fb);
+      const bool s2 = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(x2), coord_word(y2), n_fb);
       e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
       w = nb_of(r, e);
     }
@@ -294,11 +309,11 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     }
     if (to_ready) {
       const int k = n_ready + __popc(mr & lt);
-      W.r_a[k] = make_int4(pox, poy, pkx, pky);
+      W.r_a[k] = make_int4(oxw, oyw, pkx, pky);
       W.r_b[k] = make_int2(w, pid);
     } else if (to_done) {
       const int k = n_done + __popc(md & lt);
-      W.d_a[k] = make_int4(pox, poy, pkx, pky);
+      W.d_a[k] = make_int4(oxw, oyw, pkx, pky);
       W.d_b[k] = make_int2(pid, (T0 << 2) | e);
       W.d_st[k] = ok ? 1 : CCT_RAY_INVALID;
     }
@@ -307,26 +322,55 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     __syncwarp();
   };
 
+  // One apex step of a walking slot on its half-edge record q (Sec. 5.1):
+  // s(c) = L -> leave through edge nxt(j) (word q.z), else through prv(j) (q.w).
+  auto step = [&](Slot& s, const int4& q) {
+    const bool sc = side_L_cw<kExact>(s.kx, s.ky, s.ox, s.oy, q.x, q.y, n_fb);
+    ++s.ns;
+    const int32_t w = sc ? q.z : q.w;
+    if (w >= 0 && s.ns < max_steps) {
+      s.h = w;
+      return;
+    }
+    if (w >= 0) {
+      s.ns = CCT_RAY_WALK_LIMIT;
+      ++n_lim;
+    } else {
+      // hit or miss: park the final triangle and its exit edge
+      const int T = he_tri(s.h), j = s.h - 3 * T;
+      const int e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
+      s.h = (T << 2) | e;
+    }
+    s.act = false;
+    s.dn = true;
+  };
+
   prefetch();
   while (true) {
-    // ---------------------------------------------------------------- serve idle lanes
-    const unsigned idle = __ballot_sync(FULL, !active);
-    if (idle != 0u && (__popc(idle) >= P.refill_min || idle == FULL)) {
+    // ---------------------------------------------------------------- serve idle slots
+    const unsigned idle0 = __ballot_sync(FULL, !sl[0].act), idle1 = __ballot_sync(FULL, !sl[1].act);
+    const int n_idle = __popc(idle0) + __popc(idle1);
+    if (n_idle != 0 && (n_idle >= P.refill_min || (idle0 & idle1) == FULL)) {
       // park finished rays; complete them 32 at a time
-      const unsigned dm = __ballot_sync(FULL, done);
-      if (done) {
-        const int k = n_done + __popc(dm & lt);
-        W.d_a[k] = make_int4(ox, oy, kx, ky);
-        W.d_b[k] = make_int2(idx, (T << 2) | j);
-        W.d_st[k] = nsteps;
-        done = false;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const unsigned dm = __ballot_sync(FULL, sl[q].dn);
+        if (dm != 0u) {
+          if (sl[q].dn) {
+            const int k = n_done + __popc(dm & lt);
+            W.d_a[k] = make_int4(sl[q].ox, sl[q].oy, sl[q].kx, sl[q].ky);
+            W.d_b[k] = make_int2(sl[q].id, sl[q].h);
+            W.d_st[k] = sl[q].ns;
+            sl[q].dn = false;
+          }
+          n_done += __popc(dm);
+          if (n_done >= 32) {
+            flush(32, n_done);
+            n_done -= 32;
+          }
+        }
       }
-      n_done += __popc(dm);
-      if (n_done >= 32) {
-        flush(32, n_done);
-        n_done -= 32;
-      }
-      const int want = __popc(idle);
+      const int want = min(n_idle, 32);
       if (n_ready < want && !exhausted) {
         prepare();
         if (n_done >= 32) {
@@ -334,58 +378,43 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
           n_done -= 32;
         }
       }
-      const int rank = __popc(idle & lt);
-      if (!active && rank < n_ready) {
-        const int k = n_ready - 1 - rank;
-        const int4 a = W.r_a[k];
-        const int2 b = W.r_b[k];
-        ox = a.x;
-        oy = a.y;
-        kx = a.z;
-        ky = a.w;
-        idx = b.y;
-        T = b.x >> 2;
-        j = b.x & 3;
-        nsteps = 1;
-        active = true;
+      // slot 0's idle lanes first, then slot 1's
+      const int take = min(want, n_ready);
+      const int rank0 = __popc(idle0 & lt), rank1 = __popc(idle0) + __popc(idle1 & lt);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int rank = q == 0 ? rank0 : rank1;
+        if (!sl[q].act && rank < take) {
+          const int k = n_ready - 1 - rank;
+          const int4 a = W.r_a[k];
+          const int2 b = W.r_b[k];
+          sl[q].ox = a.x;
+          sl[q].oy = a.y;
+          sl[q].kx = a.z;
+          sl[q].ky = a.w;
+          sl[q].h = b.x;
+          sl[q].id = b.y;
+          sl[q].ns = 1;
+          sl[q].act = true;
+        }
       }
-      n_ready -= min(want, n_ready);
+      n_ready -= take;
       __syncwarp();
     }
-    if (!__any_sync(FULL, active)) {
+    if (!__any_sync(FULL, sl[0].act || sl[1].act)) {
       if (exhausted && n_ready == 0) break;
       continue;
     }
 
-    // ---------------------------------------------------------------- one step per active lane
-    // Across an interior edge the neighbour shares the two decided vertices:
-    // decide the apex only, s(c) = L -> leave through (R-vertex, c), else
-    // through (c, L-vertex).
-    if (active) {
-      const TriRec r = load_rec(S.rec + T);
-      unsigned fb = 0;
-      const bool sc = side_L_w<kExact>(kx, ky, ox, oy, vx_of(r, j), vy_of(r, j), fb);
-      if (!kExact && fb) atomicAdd(&W.cnt[kCntFallback], fb);
-      const int e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
-      ++nsteps;
-      const int32_t w = nb_of(r, e);
-      if (w >= 0) {
-        T = w >> 2;
-        j = w & 3;
-        if (nsteps >= S.max_steps) {
-          nsteps = CCT_RAY_WALK_LIMIT;
-          active = false;
-          done = true;
-          atomicAdd(&W.cnt[kCntLimit], 1u);
-        }
-      } else {
-        j = e;  // hit or miss: park the final triangle and its exit edge
-        active = false;
-        done = true;
-      }
-    }
+    // ---------------------------------------------------------------- one step per walking slot
+    // both slots' loads first: two independent rays, two loads in flight
+    int4 q0 = make_int4(0, 0, 0, 0), q1 = make_int4(0, 0, 0, 0);
+    if (sl[0].act) q0 = load_he(he_tab + sl[0].h);
+    if (sl[1].act) q1 = load_he(he_tab + sl[1].h);
+    if (sl[0].act) step(sl[0], q0);
+    if (sl[1].act) step(sl[1], q1);
   }
-  // the last parked rays (the final serve round parked every finished lane)
+  // the last parked rays (the final serve round parked every finished slot)
   while (n_done > 0) {
     const int m = min(32, n_done);
     flush(m, n_done);
@@ -393,16 +422,17 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
   }
   // ---------------------------------------------------------------- counters: one atomic per warp and counter
   __syncwarp();
+  const unsigned w_fb = __reduce_add_sync(FULL, n_fb), w_limit = __reduce_add_sync(FULL, n_lim);
   const unsigned long long w_steps = W.steps, w_side = W.sides;
-  const unsigned long long w_rays = W.cnt[kCntRays], w_fb = W.cnt[kCntFallback], w_inv = W.cnt[kCntInvalid];
-  const unsigned long long w_lim = W.cnt[kCntLimit], w_loc = W.cnt[kCntLocated], w_lst = W.cnt[kCntLocSteps];
+  const unsigned long long w_rays = W.cnt[kCntRays], w_inv = W.cnt[kCntInvalid];
+  const unsigned long long w_loc = W.cnt[kCntLocated], w_lst = W.cnt[kCntLocSteps];
   if (lane == 0) {
     if (w_rays) atomicAdd(&S.stats->rays, w_rays);
     if (w_steps) atomicAdd(&S.stats->steps, w_steps);
     if (w_side) atomicAdd(&S.stats->side_tests, w_side);
-    if (w_fb) atomicAdd(&S.stats->exact_fallbacks, w_fb);
+    if (w_fb) atomicAdd(&S.stats->exact_fallbacks, (unsigned long long)w_fb);
     if (w_inv) atomicAdd(&S.stats->invalid_rays, w_inv);
-    if (w_lim) atomicAdd(&S.stats->walk_limit_rays, w_lim);
+    if (w_limit) atomicAdd(&S.stats->walk_limit_rays, (unsigned long long)w_limit);
     if (w_loc) atomicAdd(&S.stats->located, w_loc);
     if (w_lst) atomicAdd(&S.stats->locate_steps, w_lst);
   }
