@@ -296,7 +296,7 @@ def run_config4(args, torch, cct, sg, dev):
     from paper_2112_05570_gb300 import autotune
 
     t0 = time.perf_counter()
-    work = config4_scenes()
+    work = config4_scenes(n_scenes=args.scenes)
     build_s = time.perf_counter() - t0
     scenes = [cct.Scene.from_triangulation(tri, sg.D) for segs, tri, r, _ in work]
     stream = torch.cuda.current_stream(dev)
@@ -308,6 +308,16 @@ def run_config4(args, torch, cct, sg, dev):
                       torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.float32, device=dev),
                       torch.empty(n, dtype=torch.int32, device=dev)))
     total = sum(len(w[2]) for w in work)
+    if args.profile:
+        # profiling mode: the default launch configuration, one warm-up launch
+        # and one launch a profiler captures; no timing, no JSON
+        b = cct.Batch(scenes, len(items), 0)
+        b.stage(items)
+        b.enqueue(stream)
+        b.enqueue(stream)
+        torch.cuda.synchronize(dev)
+        b.free()
+        return work, scenes, None
     out = {}
     for name, flags in (("filtered", 0), ("exact", cct.CCT_TRACE_EXACT_ONLY)):
         b = cct.Batch(scenes, len(items), flags)
@@ -336,7 +346,7 @@ def run_config4(args, torch, cct, sg, dev):
             "config": {"workload": "config4-512-scenes-100..200k-segments-1k..1M-rays", "scenes": len(scenes),
                        "segments_total": int(sum(w[0].shape[0] for w in work)),
                        "triangles_total": int(sum(w[1].n_tri for w in work)), "rays_per_step": total,
-                       "table_bytes_total": int(sum(w[1].n_tri for w in work)) * 32,
+                       "scene_device_bytes_total": int(sum(sc.info()[0] for sc in scenes)),
                        "build_s": build_s, "launch": "one persistent batched kernel, CUDA-graph replay"},
             "batched": out, "plain_512_launches": {"rays_per_s": total / (ms_plain * 1e-3), "ms": ms_plain},
             "gpu_launches": args.steps}
@@ -421,6 +431,59 @@ def run_config3(args, torch, cct, sg, dev):
     print(json.dumps(line))
 
 
+def run_profile_kernels(args, torch, cct, sg, dev):
+    """Profiling mode: every kernel of the library on one config-2 scene
+    (2^23 isotropic rays, larger than L2 with their results): the locate
+    kernel, the binned trace (locate, histogram, three scan passes, scatter,
+    sorted walk), the split and fused walks, the kd-tree and BVH baselines,
+    a four-item batched launch over the same scene and the gather peak; each
+    twice (warm-up, then the launch a profiler captures).  Prints the
+    CUDA-event time of the second launch of each call."""
+    name = args.families.split(",")[0]
+    segs = family_segments(name)
+    cdt, ref, tri = sg.pipeline(segs, SCENE_SEED + FAMILIES.index(name), sweeps=4)
+    n = 1 << 23
+    r = sg.rays_isotropic(tri, n, 100 + FAMILIES.index(name))
+    d = [torch.from_numpy(getattr(r, k)).to(dev) for k in ("ox", "oy", "dx", "dy")]
+    start = torch.from_numpy(r.start).to(dev)
+    hit = torch.empty(n, dtype=torch.int32, device=dev)
+    t = torch.empty(n, dtype=torch.float32, device=dev)
+    steps = torch.empty(n, dtype=torch.int32, device=dev)
+    loc = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    scene = cct.Scene.from_triangulation(tri, sg.D)
+    bvh = cct.Bvh(sg.bvh(segs, 1.0))
+    kd = cct.KdTree(sg.kdtree(segs, 1.0), sg.D)
+    q = n // 4
+    items = [(0, d[0][k * q:(k + 1) * q], d[1][k * q:(k + 1) * q], d[2][k * q:(k + 1) * q],
+              d[3][k * q:(k + 1) * q], None, hit[k * q:(k + 1) * q], t[k * q:(k + 1) * q], steps[k * q:(k + 1) * q])
+             for k in range(4)]
+    batch = cct.Batch([scene], max_items=4)
+    batch.stage(items)
+    calls = {
+        "locate_kernel": lambda: cct.cct_locate(scene.handle, d[0], d[1], loc, stream),
+        "binned_trace": lambda: cct.cct_trace(scene.handle, *d, None, hit, t, steps, cct.CCT_TRACE_BIN, stream),
+        "split_trace": lambda: cct.cct_trace(scene.handle, *d, None, hit, t, steps, cct.CCT_TRACE_SPLIT_LOCATE,
+                                             stream),
+        "fused_trace": lambda: cct.cct_trace(scene.handle, *d, None, hit, t, steps, 0, stream),
+        "given_trace": lambda: cct.cct_trace(scene.handle, *d, start, hit, t, steps, 0, stream),
+        "kd_trace": lambda: kd.trace(*d, stream),
+        "bvh_trace": lambda: bvh.trace(*d, stream),
+        "batched_4_items": lambda: batch.enqueue(stream),
+    }
+    out = {}
+    for label, fn in calls.items():
+        fn()
+        out[label] = _time_loop(torch, dev, stream, fn, 1)
+    ms, bps = cct.cct_measure_gather(tri.n_tri * 32, 1 << 27, 1, stream)
+    out["gather_kernel"] = ms
+    print(json.dumps({"profile_kernels_ms": out, "scene": name, "rays": n, "triangles": tri.n_tri,
+                      "gather_peak_gbs": bps / 1e9}))
+    for o in (batch, bvh, kd, scene):
+        o.free()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,10 +497,16 @@ def main():
                          "batched launch; 5: the continuous-batching server")
     ap.add_argument("--profile", action="store_true",
                     help="profiling mode: per scene, 2 warm-up traces, then one trace with start cells given and "
-                         "one with the fused locate; no timing, no JSON")
+                         "one with the fused locate; no timing, no JSON.  With --config 4: one warm-up and one "
+                         "profiled batched launch at the default launch configuration")
     ap.add_argument("--seed-densities", default="",
                     help="with --profile: also time the fused locate with these seed-grid densities (k: 2^k cells "
                          "per triangle), e.g. 1,2,3,4")
+    ap.add_argument("--scenes", type=int, default=512,
+                    help="--config 4: number of scenes (512 is the workload; fewer for profiling runs)")
+    ap.add_argument("--profile-kernels", action="store_true",
+                    help="profiling mode: every kernel of the library, twice each, on the first of --families "
+                         "(2^23 rays); CUDA-event times of the second launches, no JSON bench line")
     ap.add_argument("--families", default=",".join(FAMILIES),
                     help="comma-separated scene families (profiling runs)")
     args = ap.parse_args()
@@ -463,6 +532,8 @@ def main():
     _build.build()
     import scenegen as sg
 
+    if args.profile_kernels:
+        return run_profile_kernels(args, torch, cct, sg, dev)
     if args.config != "2":
         fn = {"3": run_config3, "4": run_config4, "5": run_config5}[args.config]
         fn(args, torch, cct, sg, dev)

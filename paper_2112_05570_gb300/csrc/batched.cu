@@ -69,15 +69,16 @@ struct BatchStacks {
   int4 d_a[kBStack];  // parked: ox word, oy word, kx word, ky word
   int4 d_b[kBStack];  // parked: ray index, final record << 2 | exit edge, steps or status, item
   int pf[5][32];      // the next batch's ray inputs (ox, oy, dx, dy, start), copied in while the warp walks
+  int l_idx[2][32], l_item[2][32];  // the walk slots' ray indices and items (read when they park)
   unsigned cnt[kBCounters];
   unsigned long long steps, sides;
 };
 
-// One walk slot (see walk.cu), plus the item of its ray and its scene's
-// half-edge table.
+// One walk slot (see walk.cu), plus its scene's half-edge table; its ray
+// index and item wait in shared memory until it parks.
 struct BSlot {
   const int4* he;
-  int ox, oy, kx, ky, h, ns, id, item;
+  int ox, oy, kx, ky, h, ns;
   bool act, dn;
 };
 
@@ -85,8 +86,11 @@ struct BSlot {
 // until that limit; a ray that needed more than its own scene's limit
 // becomes a walk-limit ray when its result is written, exactly as if it had
 // stopped at its own limit.
+// 72 registers per thread (no spills): at the compiler's own choice (83) the
+// kernel holds 24 warps per SM and ran 13 % slower on 512 scenes; at 64 it
+// spills and ran 13 % slower.  72 x 512 threads still fits one block per SM.
 template <bool kExact>
-__global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev* __restrict__ scenes,
+__global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes,
                                                                  const BatchHeader* __restrict__ hdr,
                                                                  const BatchItemDev* __restrict__ items,
                                                                  int refill_min, int max_steps,
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
   unsigned n_fb = 0;  // this lane's int64 fallbacks
   BSlot sl[2];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) sl[q] = BSlot{nullptr, 0, 0, 0, 0, 0, 0, 0, 0, false, false};
+  for (int q = 0; q < 2; ++q) sl[q] = BSlot{nullptr, 0, 0, 0, 0, 0, 0, false, false};
   if (lane < kBCounters) W.cnt[lane] = 0;
   if (lane == 0) W.steps = W.sides = 0;
   __syncwarp();
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
           if (sl[q].dn) {
             const int k = n_done + __popc(dm & lt);
             W.d_a[k] = make_int4(sl[q].ox, sl[q].oy, sl[q].kx, sl[q].ky);
-            W.d_b[k] = make_int4(sl[q].id, sl[q].h, sl[q].ns, sl[q].item);
+            W.d_b[k] = make_int4(W.l_idx[q][lane], sl[q].h, sl[q].ns, W.l_item[q][lane]);
             sl[q].dn = false;
           }
           n_done += __popc(dm);
@@ -375,8 +379,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_kernel(const SceneDev*
           sl[q].kx = a.z;
           sl[q].ky = a.w;
           sl[q].h = b.x;
-          sl[q].id = b.y;
-          sl[q].item = b.z;
+          W.l_idx[q][lane] = b.y;
+          W.l_item[q][lane] = b.z;
           sl[q].he = scenes[b.w].he;
           sl[q].ns = 1;
           sl[q].act = true;
