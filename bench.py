@@ -7,8 +7,9 @@ misalignment stress), and Gaussian-clustered random segments -- six scenes of
 about 30,000 segments, each with its annealed triangulation and 2^24 isotropic
 rays (origins uniform on the integer grid, angles uniform).  One step = the
 whole query path on one batch: for every scene, locate (Sec. 5.2) + walk
-(Sec. 5.1) of its 2^24 rays through ``cct_trace``, start cells found on the
-GPU.  Inputs (6 x 2^24 rays, 2 GB with results) are larger than L2; the
+(Sec. 5.1) of its 2^24 rays, start cells found on the GPU, in one batched
+launch over the six scenes (``cct_batch_enqueue`` replayed from a CUDA graph);
+the same step as six plain ``cct_trace`` launches is reported beside it.  Inputs (6 x 2^24 rays, 2 GB with results) are larger than L2; the
 2-4 MB triangle tables stay L2-resident as acceleration structures do.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
@@ -186,8 +187,8 @@ def _time_loop(torch, dev, stream, fn, k):
     return e0.elapsed_time(e1) / k
 
 
-TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "walk_kernel_fused_locate_dram_six_scenes.md")
-TRAFFIC_SOURCES = ("paper_2112_05570_gb300/csrc/walk.cu", "paper_2112_05570_gb300/csrc/cct_internal.cuh",
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "batch_kernel_six_scenes_dram.md")
+TRAFFIC_SOURCES = ("paper_2112_05570_gb300/csrc/batched.cu", "paper_2112_05570_gb300/csrc/cct_internal.cuh",
                    "paper_2112_05570_gb300/csrc/scene.cu")
 
 
@@ -202,8 +203,9 @@ def kernel_sources_sha256() -> str:
 
 
 def captured_traffic():
-    """DRAM bytes per launch of the fused walk kernel from the committed ncu
-    summary, or None when the kernel sources changed since that capture."""
+    """DRAM bytes per launch of the timed step's kernel (batch_kernel over the
+    six scenes) from the committed ncu summary, or None when the kernel
+    sources changed since that capture."""
     try:
         text = open(TRAFFIC_SUMMARY).read()
     except OSError:
@@ -218,7 +220,7 @@ def captured_traffic():
         return None, "ncu summary unreadable"
     if sha != kernel_sources_sha256():
         return None, "kernel changed since the ncu capture"
-    return b, "DRAM read+write bytes per launch, mean over the six scenes, from " + os.path.basename(TRAFFIC_SUMMARY)
+    return b, "DRAM read+write bytes per launch from " + os.path.basename(TRAFFIC_SUMMARY)
 
 
 TUNE_PARAMS = (0.25, 0.5, 1.0, 2.0, 4.0)
@@ -502,6 +504,9 @@ def main():
     ap.add_argument("--seed-densities", default="",
                     help="with --profile: also time the fused locate with these seed-grid densities (k: 2^k cells "
                          "per triangle), e.g. 1,2,3,4")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="profiling mode: the timed step's batched launch over the six scenes at a fixed "
+                         "configuration, twice (warm-up, captured); no timing, no JSON")
     ap.add_argument("--scenes", type=int, default=512,
                     help="--config 4: number of scenes (512 is the workload; fewer for profiling runs)")
     ap.add_argument("--profile-kernels", action="store_true",
@@ -556,6 +561,21 @@ def main():
         cct.cct_trace(sc["scene"].handle, d["ox"], d["oy"], d["dx"], d["dy"], start, hit, t, steps, flags,
                       stream if s is None else s)
 
+    if args.profile_step:
+        # the timed step's launch at a fixed configuration (exact-only predicates, 64 threads,
+        # refill 16, chunk 512): one warm-up and one launch a profiler captures
+        outs = [(torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.float32, device=dev),
+                 torch.empty(n, dtype=torch.int32, device=dev)) for _ in scenes]
+        items = [(k, sc["d"]["ox"], sc["d"]["oy"], sc["d"]["dx"], sc["d"]["dy"], None, *outs[k])
+                 for k, sc in enumerate(scenes)]
+        b = cct.Batch([sc["scene"] for sc in scenes], len(items), cct.CCT_TRACE_EXACT_ONLY)
+        b.set_tuning({"block_threads": 64, "refill_min": 16, "chunk": 512})
+        b.stage(items)
+        b.enqueue(stream)
+        b.enqueue(stream)
+        torch.cuda.synchronize(dev)
+        b.free()
+        return 0
     if args.profile:
         # per scene: 2 warm-up traces, then start cells given / fused locate, each
         # with the fp32 filter and exact-only; CUDA-event times of 3 more of each
@@ -627,39 +647,50 @@ def main():
         for sc in scenes:
             sc["scene"].set_tuning({"trace_flags": cct.CCT_TRACE_BIN if path == "bin" else 0})
     flags = 0
-    # our kernels per step: the fused locate+walk; locate and walk (split);
-    # or locate, histogram, three scan passes, scatter and walk (binned)
-    kernels_per_step = sum(7 if sc["scene"].tuning()["trace_flags"] & cct.CCT_TRACE_BIN else
-                           2 if sc["scene"].tuning()["trace_flags"] & cct.CCT_TRACE_SPLIT_LOCATE else 1
-                           for sc in scenes)
     tried = tuned
 
+    # ---- the timed step: one batched launch (cct_batch_enqueue, replayed from a CUDA graph) walks
+    # the rays of all six scenes, start cells found on the GPU; one launch per step also hides the
+    # drain at the end of each scene's walk (a few long rays stepping alone) behind the others'
+    # work.  Launch configuration (block size, refill threshold, chunk, fp32-filtered or exact-only
+    # predicates) from the autotuner.
+    outs = [(torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.float32, device=dev),
+             torch.empty(n, dtype=torch.int32, device=dev)) for _ in scenes]
+    items = [(k, sc["d"]["ox"], sc["d"]["oy"], sc["d"]["dx"], sc["d"]["dy"], None, *outs[k])
+             for k, sc in enumerate(scenes)]
+    batch, btune = None, None
+    for label, bflags in (("filtered", 0), ("exact", cct.CCT_TRACE_EXACT_ONLY)):
+        b = cct.Batch([sc["scene"] for sc in scenes], len(items), bflags)
+        res = autotune.tune_batch(b, items)
+        if btune is None or res["ms"] < btune["ms"]:
+            if batch is not None:
+                batch.free()
+            batch, btune = b, dict(res, predicates=label)
+        else:
+            b.free()
+    batch.stage(items)
+    batch.capture()
     for _ in range(max(3, args.warmup)):
-        step(flags)
+        batch.replay()
     torch.cuda.synchronize(dev)
-    for sc in scenes:
-        sc["scene"].stats(reset=True)
+    batch.stats(reset=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    # per-launch events on the launching stream bracket each scene's trace
-    # (one fused locate+walk kernel per scene on the plain path)
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in scenes]
-          for _ in range(args.steps)]
+    # per-launch events on the launching stream bracket each replay (one batch_kernel launch)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(dev.index) as clk:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for k in range(args.steps):
-            for sc, (a, b) in zip(scenes, ev[k]):
-                a.record(stream)
-                trace(sc, None, flags)
-                b.record(stream)
+            ev[k][0].record(stream)
+            batch.replay()
+            ev[k][1].record(stream)
         e1.record(stream)
         e1.synchronize()
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.steps
-    scene_ms = [sum(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)) / args.steps
-                for i in range(len(scenes))]
+    launch_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     if dist:
         dist.barrier()
         m = torch.tensor([ms], device=dev)
@@ -667,31 +698,43 @@ def main():
         ms = float(m.item())
     rays_per_step = n * len(scenes)
     value = rays_per_step * world / (ms * 1e-3)
-    tot = {"rays": 0, "steps": 0, "side_tests": 0, "exact_fallbacks": 0, "located": 0, "locate_steps": 0}
-    timed_stats = []
-    for sc in scenes:
-        st = sc["scene"].stats(reset=True)
-        timed_stats.append(st)
-        for k in tot:
-            tot[k] += st[k]
+    tot = batch.stats(reset=True)
+    # the results of the timed launches equal the plain per-scene trace's (one scene, every ray)
+    chk = scenes[len(scenes) // 2]
+    trace(chk, None, 0)
+    torch.cuda.synchronize(dev)
+    o = outs[len(scenes) // 2]
+    if not (torch.equal(o[0], hit) and torch.equal(o[2], steps)):
+        raise RuntimeError("batched results differ from the plain trace")
 
-    # ---- roofline of the timed kernel (fused locate + walk): algorithmic bytes
-    # per launch over its event-timed duration, against the random-sector
-    # gather peak measured over a table of the scene's size
-    alg_bytes_tot, alg_over_peak, timed_ms_tot = 0.0, 0.0, 0.0
+    # ---- the same step as six plain launches (one cct_trace per scene, each at its own tuned
+    # configuration), for comparison; per-scene counters weight the roofline's peak
+    for _ in range(2):
+        step(flags)
+    torch.cuda.synchronize(dev)
+    for sc in scenes:
+        sc["scene"].stats(reset=True)
+    k_plain = max(3, args.steps // 4)
+    plain_ms = _time_loop(torch, dev, stream, lambda: step(flags), k_plain)
+    plain_stats = [sc["scene"].stats(reset=True) for sc in scenes]
+
+    # ---- roofline of the timed kernel (batch_kernel): algorithmic bytes per launch over its
+    # event-timed duration, against the random-sector gather peak measured over tables of the
+    # scenes' sizes (weighted by each scene's share of the bytes)
+    def alg_bytes(st, reps):
+        # distinct record reads: locate triangles + walk triangles - 1 (the start triangle
+        # serves both); 4 B seed cell; 16 B ray in, 12 B out
+        return (32.0 * (st["steps"] + st["locate_steps"] - st["located"]) + 4.0 * st["located"]
+                + 28.0 * st["rays"]) / reps
+
     gather_bps = {}
+    share_over_peak = 0.0
+    plain_alg = [alg_bytes(st, k_plain) for st in plain_stats]
     for i, sc in enumerate(scenes):
-        st = timed_stats[i]
-        reps = args.steps
-        # distinct record reads: locate triangles + walk triangles - 1 (the
-        # start triangle serves both); 4 B seed cell; 16 B ray in, 12 B out
-        alg = (32.0 * (st["steps"] + st["locate_steps"] - st["located"]) + 4.0 * st["located"]
-               + 28.0 * st["rays"]) / reps
         _, bps = cct.cct_measure_gather(sc["tri"].n_tri * 32, 1 << 27, 5, stream)
         gather_bps[sc["name"]] = bps
-        alg_bytes_tot += alg
-        alg_over_peak += alg / bps
-        timed_ms_tot += scene_ms[i]
+        share_over_peak += plain_alg[i] / sum(plain_alg) / bps
+    alg_per_launch = alg_bytes(tot, args.steps)
 
     # ---- per scene: the walk kernel alone (start cells given); CDT vs annealed steps
     per = {}
@@ -725,9 +768,8 @@ def main():
                            "length_annealed_over_cdt": sc["tri"].length(True) / sc["cdt"].length(True),
                            "length_refined_over_cdt": sc["ref"].length(True) / sc["cdt"].length(True),
                            "walk_l2_frac": (alg / (wms * 1e-3)) / bps, "gather_peak_gbs": bps / 1e9}
-    n_launch = len(scenes)
-    achieved = alg_bytes_tot / (timed_ms_tot * 1e-3) / 1e9
-    l2_peak = alg_bytes_tot / alg_over_peak / 1e9  # byte-weighted gather peak over the scenes' table sizes
+    achieved = alg_per_launch / (launch_ms * 1e-3) / 1e9
+    l2_peak = 1.0 / share_over_peak / 1e9  # byte-weighted gather peak over the scenes' table sizes
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = json.load(open(peaks_path)).get("hbm_gbs") if os.path.exists(peaks_path) else None
     hbm_src = "MEASURED_PEAKS.json (measured)" if hbm_peak else "fallback 6800 GB/s"
@@ -735,9 +777,8 @@ def main():
     traffic, traffic_note = captured_traffic()
     roofline = {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
                 "traffic": traffic, "traffic_note": traffic_note,
-                "kernel": "walk_kernel with the fused locate (the timed step's only kernel), one launch per scene",
-                "launch_ms_mean": timed_ms_tot / n_launch,
-                "algorithmic_bytes_per_launch_mean": alg_bytes_tot / n_launch,
+                "kernel": "batch_kernel (the timed step's only kernel): one launch per step over the six scenes",
+                "launch_ms_mean": launch_ms, "algorithmic_bytes_per_launch_mean": alg_per_launch,
                 "peak_source": "measured live: random 32-byte sector gathers over tables of each scene's size "
                                "(cct_measure_gather), weighted by each scene's bytes",
                 "bytes_model": "32 B per distinct triangle record read (walk steps + locate steps - 1 per ray) + "
@@ -810,11 +851,17 @@ def main():
 
     line = {"metric": "closest-hit rays/s", "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64+fp32-filter", "data": "synthetic",
+            "vs_baseline": None, "dtype": "int64" if btune["predicates"] == "exact" else "int64+fp32-filter",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "families": list(FAMILIES), "segments_per_scene": N_SEGMENTS,
-                       "rays_per_step": rays_per_step, "path": path, "tuning": tried,
+                       "rays_per_step": rays_per_step,
+                       "launch": "one batched launch per step over the six scenes (CUDA-graph replay)",
+                       "batch_tuning": dict(btune["tuning"], predicates=btune["predicates"]),
                        "l2": "inputs larger than L2 (6 x 2^24 rays + results, 2 GB); triangle tables L2-resident",
                        "parallelism": f"replicas x{world}"},
+            "plain_per_scene": {"rays_per_s": rays_per_step * world / (plain_ms * 1e-3), "ms_per_step": plain_ms,
+                                "launch": "one cct_trace per scene, each at its own autotuned configuration",
+                                "path": path, "tuning": tried},
             "steps_per_ray": tot["steps"] / max(1, tot["rays"]),
             "kd_ops_per_ray": float(np.mean([p["kd"]["ops_per_ray"] for p in per.values()])),
             "bvh_ops_per_ray": float(np.mean([p["bvh"]["ops_per_ray"] for p in per.values()])),
@@ -822,7 +869,7 @@ def main():
             "fallback_rate": tot["exact_fallbacks"] / max(1, tot["side_tests"]),
             "locate_steps_per_ray": tot["locate_steps"] / max(1, tot["located"]),
             "per_scene": per, "roofline": roofline, "e2e": e2e,
-            "gpu_launches": kernels_per_step * args.steps}
+            "gpu_launches": args.steps}
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample_n, dt = cpu_oracle_rate(work)
         line["cpu_baseline"] = {"value": rate, "unit": "rays/s", "cores": cores, "kind": "oracle",
