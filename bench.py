@@ -433,6 +433,83 @@ def run_config3(args, torch, cct, sg, dev):
     print(json.dumps(line))
 
 
+LINES_N = (1, 3, 10, 30, 100, 300, 1000)
+
+
+def run_lines(args, torch, cct, sg, dev):
+    """The `lines' scenes of Sec. 4.2 / 6.1: length factors 0.1, 1, 3 x orientations
+    uniform, mostly vertical, mostly diagonal x N = 1..1000 lines, two scenes each;
+    2^16 isotropic rays per scene with known start cells (the paper's setting).
+    Operations per ray, as in Sec. 5.4: triangles visited by the walk on the
+    annealed, optimally refined and unrefined triangulations; BVH AABB + segment
+    tests; roped kd-tree leaves + ideal rope steps + distinct segments tested
+    (each structure's cost parameter chosen per scene by the fewest operations).
+    All on the GPU; the three structures' hit ids are checked equal."""
+    stream = torch.cuda.current_stream(dev)
+    n_rays = 1 << 16
+    table = {}
+    t0 = time.perf_counter()
+    for factor in (0.1, 1.0, 3.0):
+        for orient in ("uniform", "vertical", "diagonal"):
+            rows = {}
+            for N in LINES_N:
+                acc = {"segments": [], "walk": [], "walk_refined": [], "walk_cdt": [], "kd": [], "bvh": [],
+                       "kd_leaves": [], "kd_rope": [], "kd_prims": [], "bvh_aabb": [], "bvh_prims": []}
+                for rep in range(2):
+                    seed = 7000 + 97 * rep + N
+                    segs = sg.lines(N, seed, factor, orient)
+                    cdt, ref, tri = sg.pipeline(segs, seed, sweeps=4)
+                    r = sg.rays_isotropic(tri, n_rays, seed + 1)
+                    d = [torch.from_numpy(getattr(r, k)).to(dev) for k in ("ox", "oy", "dx", "dy")]
+                    start = torch.from_numpy(r.start).to(dev)
+                    hits = []
+                    for key, tr in (("walk", tri), ("walk_refined", ref), ("walk_cdt", cdt)):
+                        # start cells are caller triangle ids of the triangulation the rays were made for
+                        sc = cct.Scene.from_triangulation(tr, sg.D)
+                        st = start if tr is tri else None
+                        h, _, stp = sc.trace(*d, st)
+                        # rays made for the annealed triangulation may start on an edge of the
+                        # others (rare; reported invalid there): mean over valid rays
+                        stp = stp[stp > 0].to(torch.float64)
+                        acc[key].append(float(stp.mean()))
+                        if tr is tri:
+                            hits.append(h)
+                        sc.free()
+                    best = {}
+                    for kind in ("bvh", "kd"):
+                        for prm in TUNE_PARAMS:
+                            host = sg.bvh(segs, prm) if kind == "bvh" else sg.kdtree(segs, prm)
+                            g = cct.Bvh(host) if kind == "bvh" else cct.KdTree(host, sg.D)
+                            h, _, ops = g.trace(*d, stream)
+                            ops = ops.to(torch.float64)
+                            if kind == "bvh":
+                                parts = (float(ops[:, 0].mean()), float(ops[:, 1].mean()))
+                            else:
+                                parts = (float(ops[:, 0].mean()), float(ops[:, 4].mean()), float(ops[:, 3].mean()))
+                            if kind not in best or sum(parts) < sum(best[kind][0]):
+                                best[kind] = (parts, h)
+                            g.free()
+                        hits.append(best[kind][1])
+                    if not all(torch.equal(hits[0], h) for h in hits[1:]):
+                        raise RuntimeError(f"lines {factor} {orient} {N}: hit ids differ between structures")
+                    acc["segments"].append(int(segs.shape[0]))
+                    acc["bvh"].append(sum(best["bvh"][0]))
+                    acc["bvh_aabb"].append(best["bvh"][0][0])
+                    acc["bvh_prims"].append(best["bvh"][0][1])
+                    acc["kd"].append(sum(best["kd"][0]))
+                    acc["kd_leaves"].append(best["kd"][0][0])
+                    acc["kd_rope"].append(best["kd"][0][1])
+                    acc["kd_prims"].append(best["kd"][0][2])
+                rows[str(N)] = {k: float(np.mean(v)) for k, v in acc.items()}
+            table[f"factor{factor:g}/{orient}"] = rows
+    line = {"metric": "operations per ray vs N (lines scenes)", "value": None, "unit": "ops/ray",
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "lines-scenes-factor0.1,1,3-uniform,vertical,diagonal-N1..1000-2^16-rays",
+                       "rays_per_scene": n_rays, "scenes_per_point": 2, "build_and_trace_s": time.perf_counter() - t0},
+            "by_scene": table}
+    print(json.dumps(line))
+
+
 def run_profile_kernels(args, torch, cct, sg, dev):
     """Profiling mode: every kernel of the library on one config-2 scene
     (2^23 isotropic rays, larger than L2 with their results): the locate
@@ -494,9 +571,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--flags", default="auto", help="auto | plain | bin")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="2", choices=["2", "3", "4", "5"],
+    ap.add_argument("--config", default="2", choices=["2", "3", "4", "5", "lines"],
                     help="2 (default): the six config-2 scene families; 3: scaling in N; 4: 512 scenes in one "
-                         "batched launch; 5: the continuous-batching server")
+                         "batched launch; 5: the continuous-batching server; lines: operations per ray vs N on "
+                         "the paper's lines scenes (walk, kd-tree, BVH)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling mode: per scene, 2 warm-up traces, then one trace with start cells given and "
                          "one with the fused locate; no timing, no JSON.  With --config 4: one warm-up and one "
@@ -540,7 +618,7 @@ def main():
     if args.profile_kernels:
         return run_profile_kernels(args, torch, cct, sg, dev)
     if args.config != "2":
-        fn = {"3": run_config3, "4": run_config4, "5": run_config5}[args.config]
+        fn = {"3": run_config3, "4": run_config4, "5": run_config5, "lines": run_lines}[args.config]
         fn(args, torch, cct, sg, dev)
         return 0
     fams = tuple(f for f in args.families.split(",") if f) if args.profile else FAMILIES

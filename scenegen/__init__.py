@@ -50,6 +50,8 @@ def _load():
     L.sg_gen_random_segments.argtypes = [i64, u64, i32, dbl, dbl, dbl, dbl, vp, i64]
     L.sg_gen_clustered.restype = i64
     L.sg_gen_clustered.argtypes = [i64, u64, i32, dbl, dbl, dbl, i32, dbl, vp, i64]
+    L.sg_gen_lines.restype = i64
+    L.sg_gen_lines.argtypes = [i64, u64, i32, dbl, i32, dbl, dbl, vp, i64]
     L.sg_gen_circles.restype = i64
     L.sg_gen_circles.argtypes = [i64, u64, i32, i32, i32, vp, i64]
     L.sg_gen_dash_grid.restype = i64
@@ -132,6 +134,22 @@ def clustered(n: int, seed: int, n_clusters=32, sigma=0.02, len_lo=0.005, len_hi
     L = _load()
     out = np.zeros((n, 4), np.int32)
     m = L.sg_gen_clustered(n, seed, D, len_lo, len_hi, length_scale(n), n_clusters, sigma, _ptr(out), n)
+    return out[:m].copy()
+
+
+LINE_ORIENTATIONS = {"uniform": 0, "vertical": 1, "diagonal": 2}
+
+
+def lines(n: int, seed: int, factor: float = 1.0, orientation: str = "uniform", spread_deg: float = 10.0,
+          margin: float = 0.01) -> np.ndarray:
+    """The paper's `lines' scenes (Sec. 4.2): up to n pairwise-disjoint segments
+    of length min(0.95, factor * 0.95 / sqrt(n)) of the domain side; orientation
+    uniform, mostly vertical or mostly diagonal (normal spread of spread_deg
+    degrees).  Dense scenes (factor 3, large n) may hold fewer than n."""
+    L = _load()
+    out = np.zeros((max(1, n), 4), np.int32)
+    m = L.sg_gen_lines(n, seed, D, float(factor), LINE_ORIENTATIONS[orientation], float(spread_deg), float(margin),
+                       _ptr(out), n)
     return out[:m].copy()
 
 

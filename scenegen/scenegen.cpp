@@ -1235,6 +1235,47 @@ int64_t sg_gen_clustered(int64_t n, uint64_t seed, int32_t D, double len_lo, dou
   return gen_segments(n, seed, D, len_lo, len_hi, scale, 0.01, n_clusters, sigma, out, cap);
 }
 
+// The `lines' scenes of Sec. 4.2: n pairwise-disjoint segments of one length,
+// min(0.95, factor * 0.95 / sqrt(n)) * D, centres uniform, endpoints at least
+// margin * D from the border; orientation 0 = uniform in [0, pi), 1 = mostly
+// vertical (90 degrees + a normal spread), 2 = mostly diagonal (45 degrees +
+// a normal spread), spread in degrees.  Dense scenes may hold fewer than n:
+// returns the number written.
+int64_t sg_gen_lines(int64_t n, uint64_t seed, int32_t D, double factor, int32_t orientation, double spread_deg,
+                     double margin, int32_t* out, int64_t cap) {
+  Rng rng(seed, 0x11E5);
+  const double L = std::min(0.95, factor * 0.95 / std::sqrt((double)std::max<int64_t>(1, n))) * D;
+  SegGrid grid(D, std::max(L, (double)D / 4096.0));
+  const double lo = margin * D, hi = (1.0 - margin) * D;
+  const double deg = 3.141592653589793 / 180.0;
+  int64_t cnt = 0, tries = 0;
+  const int64_t max_tries = std::max<int64_t>(2000 * n, 100000);
+  while (cnt < n && cnt < cap && tries < max_tries) {
+    ++tries;
+    double th;
+    if (orientation == 1)
+      th = (90.0 + spread_deg * rng.normal()) * deg;
+    else if (orientation == 2)
+      th = (45.0 + spread_deg * rng.normal()) * deg;
+    else
+      th = 3.141592653589793 * rng.uni();
+    const double hx = 0.5 * L * std::cos(th), hy = 0.5 * L * std::sin(th);
+    const double cx = lo + std::fabs(hx) + (hi - lo - 2 * std::fabs(hx)) * rng.uni();
+    const double cy = lo + std::fabs(hy) + (hi - lo - 2 * std::fabs(hy)) * rng.uni();
+    Pt a{rnd_coord(cx - hx), rnd_coord(cy - hy)}, b{rnd_coord(cx + hx), rnd_coord(cy + hy)};
+    if (a == b) continue;
+    if (a.x < lo || a.x > hi || a.y < lo || a.y > hi || b.x < lo || b.x > hi || b.y < lo || b.y > hi) continue;
+    if (grid.touches(a, b)) continue;
+    grid.add(a, b);
+    out[4 * cnt + 0] = a.x;
+    out[4 * cnt + 1] = a.y;
+    out[4 * cnt + 2] = b.x;
+    out[4 * cnt + 3] = b.y;
+    ++cnt;
+  }
+  return cnt;
+}
+
 // Disjoint polygonal circles with sides uniform in [min_sides, max_sides],
 // until about n_target segments.  Fill: the discs cover about 30% of the domain.
 int64_t sg_gen_circles(int64_t n_target, uint64_t seed, int32_t D, int32_t min_sides, int32_t max_sides,
