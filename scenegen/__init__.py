@@ -75,7 +75,7 @@ def _load():
     L.sg_tri_length.restype = ctypes.c_float
     L.sg_tri_length.argtypes = [vp, i32]
     L.sg_anneal.restype = i64
-    L.sg_anneal.argtypes = [vp, u64, dbl, dbl, dbl]
+    L.sg_anneal.argtypes = [vp, u64, dbl, dbl, dbl, dbl]
     L.sg_rays_isotropic.restype = i64
     L.sg_rays_isotropic.argtypes = [vp, i64, u64, vp, vp, vp, vp, vp, i32]
     L.sg_rays_pinhole.restype = i64
@@ -239,14 +239,17 @@ def cdt(segs: np.ndarray) -> Triangulation:
     return _export(h, segs, "cdt")
 
 
-def anneal(tri: Triangulation, seed: int, sweeps=20.0, T0=0.02, T1=1e-4) -> Triangulation:
-    """A copy of ``tri`` annealed over edge flips: greedy flips to shorter
-    diagonals, then simulated annealing with temperature T0 -> T1 (units of the
-    domain side, as the paper's unit-square schedule, Sec. 3.3), then greedy
-    flips again; the shorter of (greedy only, annealed) is kept."""
+def anneal(tri: Triangulation, seed: int, sweeps=20.0, T0=0.02, T1=1e-4, moves=1.0) -> Triangulation:
+    """A copy of ``tri`` annealed: greedy flips to shorter diagonals, then
+    simulated annealing with temperature T0 -> T1 (units of the domain side,
+    as the paper's unit-square schedule, Sec. 3.3) over edge flips (Sec. 3.2.7)
+    and, with weight ``moves`` (0: flips only), moves of Steiner vertices --
+    free ones on the lattice, those inside a segment along it (Sec. 3.2's
+    P1 and P3) -- then greedy flips again; the shorter of (greedy only,
+    annealed) is kept."""
     L = _load()
     h = L.sg_tri_copy(tri._h)
-    L.sg_anneal(h, seed, float(sweeps), float(T0) * D, float(T1) * D)
+    L.sg_anneal(h, seed, float(sweeps), float(T0) * D, float(T1) * D, float(moves))
     return _export(h, tri.segs, "annealed")
 
 

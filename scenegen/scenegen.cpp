@@ -765,17 +765,144 @@ static int64_t greedy_flips(Triangulation& tr) {
   return flips;
 }
 
-// Simulated annealing over edge flips (Sec. 3.2.7) with Metropolis acceptance
-// (Sec. 3.1) and an exponential temperature schedule (Sec. 3.3).  The energy is
-// the total edge length; lengths and differences are fp32.
-static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double T0, double T1) {
+// Vertex classes for the vertex perturbations: 0 fixed (hull vertices, segment
+// endpoints, vertices shared by several segments), 1 free Steiner vertex (no
+// incident constrained edge: moves anywhere on the lattice, Sec. 3.2.2's P1),
+// 2 Steiner vertex inside one segment (its two constrained edges carry the same
+// segment and are collinear: moves along the segment, P3); dir = the
+// segment's primitive lattice step, nb = its two neighbours along it.
+struct VertexClasses {
+  std::vector<int8_t> kind;
+  std::vector<Pt> dir;
+  std::vector<std::pair<int32_t, int32_t>> nb;
+  int64_t movable = 0;
+};
+
+static int64_t gcd64(int64_t a, int64_t b) {
+  a = a < 0 ? -a : a;
+  b = b < 0 ? -b : b;
+  while (b) {
+    int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+static void classify_vertices(const Triangulation& tr, VertexClasses& vc) {
+  const int nv = (int)tr.P.size();
+  vc.kind.assign(nv, 0);
+  vc.dir.assign(nv, Pt{0, 0});
+  vc.nb.assign(nv, {-1, -1});
+  vc.movable = 0;
+  std::vector<std::pair<int32_t, int32_t>> ce;  // (other vertex, segment) of incident constrained edges
+  for (int v = 0; v < nv; ++v) {
+    const Pt& p = tr.P[v];
+    if (p.x <= 0 || p.y <= 0 || p.x >= tr.D || p.y >= tr.D) continue;
+    ce.clear();
+    tr.for_fan(v, [&](int t, int k) {
+      const Tri& x = tr.T[t];
+      // edge (k+2)%3 joins v and vertex (k+1)%3; each incident edge is seen once this way
+      if (x.c[(k + 2) % 3] >= 0) ce.push_back({x.v[(k + 1) % 3], x.c[(k + 2) % 3]});
+      return false;
+    });
+    if (ce.empty()) {
+      vc.kind[v] = 1;
+      ++vc.movable;
+      continue;
+    }
+    if (ce.size() != 2 || ce[0].second != ce[1].second) continue;
+    const Pt &a = tr.P[ce[0].first], &b = tr.P[ce[1].first];
+    if (orient(a, b, p) != 0) continue;
+    const int64_t dot = (int64_t)(a.x - p.x) * (b.x - p.x) + (int64_t)(a.y - p.y) * (b.y - p.y);
+    if (dot >= 0) continue;  // not between its neighbours
+    const int64_t dx = (int64_t)b.x - a.x, dy = (int64_t)b.y - a.y, g = gcd64(dx, dy);
+    vc.kind[v] = 2;
+    vc.dir[v] = Pt{(int32_t)(dx / g), (int32_t)(dy / g)};
+    vc.nb[v] = {ce[0].first, ce[1].first};
+    ++vc.movable;
+  }
+}
+
+// Proposes moving vertex v to q: true (and the change of the total edge
+// length in *delta) if every triangle of v's star stays strictly CCW.
+static bool vertex_move_delta(const Triangulation& tr, int v, const Pt& q, float* delta) {
+  const Pt& p = tr.P[v];
+  bool ok = true;
+  float d = 0.f;
+  tr.for_fan(v, [&](int t, int k) {
+    const Tri& x = tr.T[t];
+    const Pt &a = tr.P[x.v[(k + 1) % 3]], &b = tr.P[x.v[(k + 2) % 3]];
+    if (orient(q, a, b) <= 0) {
+      ok = false;
+      return true;
+    }
+    d += edge_len(q, a) - edge_len(p, a);  // edge (v, a): once per star triangle
+    return false;
+  });
+  *delta = d;
+  return ok;
+}
+
+// Simulated annealing (Sec. 3.1-3.3) over edge flips (Sec. 3.2.7) and, when
+// moves > 0, vertex perturbations (P1 for free Steiner vertices, P3 along the
+// segment for Steiner vertices inside a segment) with Metropolis acceptance
+// and an exponential temperature schedule.  The energy is the total edge
+// length; lengths and differences are fp32.  A vertex proposal is drawn with
+// probability moves * (movable vertices / vertices); its step is normal with
+// a scale that shrinks with the temperature, from 0.3 to 0.02 of the
+// vertex's shortest incident edge (along the segment: of the nearer
+// neighbour's distance), rounded to the lattice.
+static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double T0, double T1, double moves) {
   Rng rng(seed, 0xA77);
   int64_t n_half = (int64_t)tr.T.size() * 3;
   int64_t K = (int64_t)(sweeps * (double)n_half);
   if (K <= 0) return;
+  VertexClasses vc;
+  double p_move = 0.0;
+  std::vector<int32_t> movable;
+  if (moves > 0) {
+    classify_vertices(tr, vc);
+    for (int v = 0; v < (int)vc.kind.size(); ++v)
+      if (vc.kind[v]) movable.push_back(v);
+    p_move = movable.empty() ? 0.0 : moves * (double)movable.size() / (double)tr.P.size();
+  }
   double lt0 = std::log(T0), lt1 = std::log(T1);
   for (int64_t k = 0; k < K; ++k) {
-    float temp = (float)std::exp(lt0 + (lt1 - lt0) * ((double)k / (double)K));
+    const double frac_k = (double)k / (double)K;
+    float temp = (float)std::exp(lt0 + (lt1 - lt0) * frac_k);
+    if (p_move > 0 && rng.uni() < p_move) {
+      const int v = movable[rng.below((uint32_t)movable.size())];
+      const Pt p = tr.P[v];
+      const double scale = 0.02 + 0.28 * std::sqrt(temp / T0);
+      Pt q;
+      if (vc.kind[v] == 1) {
+        float lmin = 3.0e38f;
+        tr.for_fan(v, [&](int t, int kk) {
+          lmin = std::min(lmin, edge_len(p, tr.P[tr.T[t].v[(kk + 1) % 3]]));
+          return false;
+        });
+        const double sd = scale * lmin;
+        q = Pt{(int32_t)(p.x + std::llround(sd * rng.normal())), (int32_t)(p.y + std::llround(sd * rng.normal()))};
+        if (q.x <= 0 || q.y <= 0 || q.x >= tr.D || q.y >= tr.D) continue;
+      } else {
+        const Pt dir = vc.dir[v];
+        const Pt &a = tr.P[vc.nb[v].first], &b = tr.P[vc.nb[v].second];
+        const double step = std::sqrt((double)len2(Pt{0, 0}, dir));
+        const double near = std::min(std::sqrt((double)len2(a, p)), std::sqrt((double)len2(b, p)));
+        int64_t m = std::llround(scale * near / step * rng.normal());
+        if (m == 0) m = rng.uni() < 0.5 ? -1 : 1;
+        q = Pt{(int32_t)(p.x + m * dir.x), (int32_t)(p.y + m * dir.y)};
+        // strictly between its two neighbours on the segment
+        const int64_t da = (int64_t)(a.x - q.x) * (b.x - q.x) + (int64_t)(a.y - q.y) * (b.y - q.y);
+        if (da >= 0) continue;
+      }
+      if (q == p) continue;
+      float delta;
+      if (!vertex_move_delta(tr, v, q, &delta)) continue;
+      if (delta <= 0.f || (float)rng.uni() < std::exp(-delta / temp)) tr.P[v] = q;
+      continue;
+    }
     int t = (int)rng.below((uint32_t)tr.T.size());
     int i = (int)rng.below(3);
     if (tr.T[t].c[i] >= 0 || tr.T[t].n[i] < 0) continue;
@@ -1422,16 +1549,17 @@ float sg_tri_length(void* h, int32_t interior_only) {
   return (float)((Triangulation*)h)->total_length(interior_only != 0);
 }
 
-// Anneal in place: greedy flips, then simulated annealing over flips from
-// temperature T0 to T1 (grid units) for `sweeps` proposals per half-edge, then
-// greedy flips again.  Keeps whichever of (greedy-only, annealed) is shorter.
+// Anneal in place: greedy flips, then simulated annealing (over flips, and
+// vertex perturbations with weight `moves`, see anneal_flips) from temperature
+// T0 to T1 (grid units) for `sweeps` proposals per half-edge, then greedy
+// flips again.  Keeps whichever of (greedy-only, annealed) is shorter.
 // Returns the number of greedy flips of the kept result.
-int64_t sg_anneal(void* h, uint64_t seed, double sweeps, double T0, double T1) {
+int64_t sg_anneal(void* h, uint64_t seed, double sweeps, double T0, double T1, double moves) {
   auto* tr = (Triangulation*)h;
   Triangulation g = *tr;
   int64_t f0 = greedy_flips(g);
   float lg = (float)g.total_length(false);
-  anneal_flips(*tr, seed, sweeps, T0, T1);
+  anneal_flips(*tr, seed, sweeps, T0, T1, moves);
   int64_t f1 = greedy_flips(*tr);
   float la = (float)tr->total_length(false);
   if (la > lg) {

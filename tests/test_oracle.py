@@ -417,3 +417,29 @@ def test_lattice_fixture_valid_and_walk_matches_bruteforce(lattice):
     hb, tb = oracle.closest_bruteforce(tri.segs, px[ok], py[ok], dx[ok], dy[ok])
     assert np.array_equal(h[ok], hb)
     assert (s[~ok] == -1).all() and (s[ok] >= 1).all()
+
+
+def test_vertex_moves_keep_the_scene_and_shorten():
+    """Annealing with vertex perturbations (free Steiner vertices on the
+    lattice, Steiner vertices inside a segment along it): the result is a valid
+    triangulation of the same segments (every segment still covered by
+    constrained edges, no other edge constrained), the segment endpoints and
+    the hull stay where they were, it is no longer than flips alone on a scene
+    with Steiner vertices, and the walk on it equals the brute force."""
+    segs = sg.circles(3000, 21)
+    ref = sg.refine_optimal(sg.cdt(segs))
+    flips = sg.anneal(ref, 21, sweeps=4, moves=0.0)
+    moved = sg.anneal(ref, 21, sweeps=4, moves=1.0)
+    assert oracle.check_triangulation(moved, sg.D) == 0
+    assert oracle.interior_length(moved) < oracle.interior_length(flips)
+    # segment endpoints and hull corners are among the vertices, unmoved
+    pts = set(zip(moved.vx.tolist(), moved.vy.tolist()))
+    for x0, y0, x1, y1 in segs.tolist():
+        assert (x0, y0) in pts and (x1, y1) in pts
+    assert {(0, 0), (sg.D, 0), (sg.D, sg.D), (0, sg.D)} <= pts
+    # some Steiner vertex did move (the refined CDT's vertex set is not kept)
+    assert pts != set(zip(ref.vx.tolist(), ref.vy.tolist()))
+    r = sg.rays_isotropic(moved, 4000, 22)
+    hb, tb = oracle.closest_bruteforce(segs, r.ox, r.oy, r.dx, r.dy)
+    hw, tw, sw = oracle.walk(moved, r.ox, r.oy, r.dx, r.dy, r.start)
+    assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
