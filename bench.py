@@ -585,6 +585,9 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="profiling mode: the timed step's batched launch over the six scenes at a fixed "
                          "configuration, twice (warm-up, captured); no timing, no JSON")
+    ap.add_argument("--profile-rays", type=int, default=24,
+                    help="with --profile-step: 2^k rays per scene (24 is the workload; fewer for captures that "
+                         "save and restore device memory many times)")
     ap.add_argument("--scenes", type=int, default=512,
                     help="--config 4: number of scenes (512 is the workload; fewer for profiling runs)")
     ap.add_argument("--profile-kernels", action="store_true",
@@ -622,7 +625,8 @@ def main():
         fn(args, torch, cct, sg, dev)
         return 0
     fams = tuple(f for f in args.families.split(",") if f) if args.profile else FAMILIES
-    work = build_workload(families=fams, with_refined=True)
+    n_build = min(N_RAYS, 1 << args.profile_rays) if args.profile_step else N_RAYS
+    work = build_workload(n_rays=n_build, families=fams, with_refined=True)
     stream = torch.cuda.current_stream(dev)
     n = N_RAYS
     hit = torch.empty(n, dtype=torch.int32, device=dev)
@@ -642,9 +646,10 @@ def main():
     if args.profile_step:
         # the timed step's launch at a fixed configuration (exact-only predicates, 64 threads,
         # refill 16, chunk 512): one warm-up and one launch a profiler captures
-        outs = [(torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.float32, device=dev),
-                 torch.empty(n, dtype=torch.int32, device=dev)) for _ in scenes]
-        items = [(k, sc["d"]["ox"], sc["d"]["oy"], sc["d"]["dx"], sc["d"]["dy"], None, *outs[k])
+        m = min(n, 1 << args.profile_rays)
+        outs = [(torch.empty(m, dtype=torch.int32, device=dev), torch.empty(m, dtype=torch.float32, device=dev),
+                 torch.empty(m, dtype=torch.int32, device=dev)) for _ in scenes]
+        items = [(k, sc["d"]["ox"][:m], sc["d"]["oy"][:m], sc["d"]["dx"][:m], sc["d"]["dy"][:m], None, *outs[k])
                  for k, sc in enumerate(scenes)]
         b = cct.Batch([sc["scene"] for sc in scenes], len(items), cct.CCT_TRACE_EXACT_ONLY)
         b.set_tuning({"block_threads": 64, "refill_min": 16, "chunk": 512})

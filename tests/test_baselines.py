@@ -181,3 +181,44 @@ def test_gpu_baselines_config2_scale(family):
         else:
             assert np.array_equal(ops, eops)
         g.free()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("factor,orientation,n", [(3.0, "diagonal", 30), (1.0, "vertical", 300),
+                                                  (0.1, "uniform", 1000)])
+def test_gpu_lines_scenes_walk_kd_bvh_equal_oracle(factor, orientation, n):
+    """The lines scenes (Sec. 4.2): the walk (start cells given and located),
+    the kd-tree and the BVH on the GPU give the oracle's hits, steps and
+    operation counts; the diagonal case is the one whose best kd-tree is a
+    single leaf (Sec. 6.1)."""
+    torch, cct = _gpu()
+    segs = sg.lines(n, 31, factor, orientation)
+    tri = sg.pipeline(segs, 31, sweeps=2)[2]
+    r = sg.rays_isotropic(tri, 50_000, 32)
+    rays = (r.ox, r.oy, r.dx, r.dy)
+    hw, tw, sw = oracle.walk(tri, *rays, r.start)
+    hb, tb = oracle.closest_bruteforce(segs, *rays)
+    assert np.array_equal(hw, hb) and np.array_equal(tw, tb)
+    scene = cct.Scene.from_triangulation(tri, sg.D)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in rays]
+    for start in (torch.from_numpy(r.start).cuda(), None):
+        h, t, s = scene.trace(*d, start)
+        torch.cuda.synchronize()
+        assert np.array_equal(h.cpu().numpy(), hw) and np.array_equal(s.cpu().numpy(), sw)
+        t = t.cpu().numpy()
+        fin = np.isfinite(tw)
+        assert np.array_equal(np.isfinite(t), fin) and np.all(np.abs(t[fin] - tw[fin]) <= 1e-6 * np.abs(tw[fin]))
+    scene.free()
+    for name, s, tr in (("bvh", sg.bvh(segs, 1.0), oracle.bvh_trace), ("kd", sg.kdtree(segs, 1.0), oracle.kd_trace)):
+        eh, et, eops = tr(s, *rays)
+        assert np.array_equal(eh, hw)
+        g = cct.Bvh(s) if name == "bvh" else cct.KdTree(s, sg.D)
+        h, t, ops = _run_gpu(torch, g, rays)
+        assert np.array_equal(h, eh)
+        if name == "kd":
+            ok = ops[:, 5] == 0
+            assert ok.mean() > 0.999
+            assert np.array_equal(ops[ok, :5], eops[ok, :5])
+        else:
+            assert np.array_equal(ops, eops)
+        g.free()
