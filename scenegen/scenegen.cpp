@@ -765,12 +765,13 @@ static int64_t greedy_flips(Triangulation& tr) {
   return flips;
 }
 
-// Vertex classes for the vertex perturbations: 0 fixed (hull vertices, segment
-// endpoints, vertices shared by several segments), 1 free Steiner vertex (no
-// incident constrained edge: moves anywhere on the lattice, Sec. 3.2.2's P1),
-// 2 Steiner vertex inside one segment (its two constrained edges carry the same
-// segment and are collinear: moves along the segment, P3); dir = the
-// segment's primitive lattice step, nb = its two neighbours along it.
+// Vertex classes for the vertex perturbation (Sec. 3.2.2): 0 fixed (hull
+// vertices, segment endpoints, vertices shared by several segments), 1 free
+// Steiner vertex (no incident constrained edge: two degrees of freedom), 2
+// Steiner vertex inside one segment (its two constrained edges carry the same
+// segment and are collinear: the displacement is projected onto the segment,
+// Sec. 3.2.1); dir = the segment's primitive lattice step, nb = its two
+// neighbours along it.
 struct VertexClasses {
   std::vector<int8_t> kind;
   std::vector<Pt> dir;
@@ -844,21 +845,69 @@ static bool vertex_move_delta(const Triangulation& tr, int v, const Pt& q, float
   return ok;
 }
 
+// The vertex perturbation of Sec. 3.2.2, p -> p + lambda eta xi: xi a point
+// uniform in the unit disk with its radius multiplied by a Pareto factor
+// (pdf alpha / x^(alpha + 1), alpha = 1/2, x > 1: heavy-tailed), eta the
+// square root of the area of the vertex's star, lambda adapted to keep the
+// acceptance rate near 23 % (its own value per vertex class).  The result is
+// rounded to the integer lattice (after projection onto the segment for a
+// vertex inside one), which keeps every predicate of the walk exact.
+struct VertexMover {
+  double lambda[3] = {0.0, 0.1, 0.1};
+  int64_t tried[3] = {0, 0, 0}, accepted[3] = {0, 0, 0};
+
+  bool propose(const Triangulation& tr, const VertexClasses& vc, int v, Rng& rng, Pt& q) const {
+    const Pt p = tr.P[v];
+    double area2 = 0.0;
+    tr.for_fan(v, [&](int t, int) {
+      const Tri& x = tr.T[t];
+      area2 += (double)orient(tr.P[x.v[0]], tr.P[x.v[1]], tr.P[x.v[2]]);
+      return false;
+    });
+    const double eta = std::sqrt(0.5 * area2);
+    const double r = std::sqrt(rng.uni()), th = 6.283185307179586 * rng.uni();
+    const double pareto = std::pow(1.0 - rng.uni(), -2.0);  // alpha = 1/2
+    double ex = lambda[vc.kind[v]] * eta * r * pareto * std::cos(th);
+    double ey = lambda[vc.kind[v]] * eta * r * pareto * std::sin(th);
+    if (!(std::fabs(ex) < 4.0 * tr.D && std::fabs(ey) < 4.0 * tr.D)) return false;
+    if (vc.kind[v] == 1) {
+      q = Pt{(int32_t)(p.x + std::llround(ex)), (int32_t)(p.y + std::llround(ey))};
+      return q.x > 0 && q.y > 0 && q.x < tr.D && q.y < tr.D && !(q == p);
+    }
+    // inside a segment: project onto it, whole lattice steps, strictly between its neighbours
+    const Pt dir = vc.dir[v];
+    const int64_t m = std::llround((ex * dir.x + ey * dir.y) / (double)len2(Pt{0, 0}, dir));
+    if (m == 0) return false;
+    q = Pt{(int32_t)(p.x + m * dir.x), (int32_t)(p.y + m * dir.y)};
+    const Pt &a = tr.P[vc.nb[v].first], &b = tr.P[vc.nb[v].second];
+    return (int64_t)(a.x - q.x) * (b.x - q.x) + (int64_t)(a.y - q.y) * (b.y - q.y) < 0;
+  }
+
+  void record(int kind, bool acc) {
+    ++tried[kind];
+    accepted[kind] += acc;
+    if (tried[kind] == 256) {  // steer towards 23 % acceptance
+      const double rate = (double)accepted[kind] / 256.0;
+      lambda[kind] *= std::exp(2.0 * (rate - 0.23));
+      lambda[kind] = std::min(10.0, std::max(1e-6, lambda[kind]));
+      tried[kind] = accepted[kind] = 0;
+    }
+  }
+};
+
 // Simulated annealing (Sec. 3.1-3.3) over edge flips (Sec. 3.2.7) and, when
-// moves > 0, vertex perturbations (P1 for free Steiner vertices, P3 along the
-// segment for Steiner vertices inside a segment) with Metropolis acceptance
-// and an exponential temperature schedule.  The energy is the total edge
-// length; lengths and differences are fp32.  A vertex proposal is drawn with
-// probability moves * (movable vertices / vertices); its step is normal with
-// a scale that shrinks with the temperature, from 0.3 to 0.02 of the
-// vertex's shortest incident edge (along the segment: of the nearer
-// neighbour's distance), rounded to the lattice.
+// moves > 0, the vertex perturbation of Sec. 3.2.2 on Steiner vertices (see
+// VertexMover), with Metropolis acceptance and an exponential temperature
+// schedule.  The energy is the total edge length; lengths and differences are
+// fp32.  A vertex proposal is drawn with probability
+// moves * (movable vertices / vertices).
 static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double T0, double T1, double moves) {
   Rng rng(seed, 0xA77);
   int64_t n_half = (int64_t)tr.T.size() * 3;
   int64_t K = (int64_t)(sweeps * (double)n_half);
   if (K <= 0) return;
   VertexClasses vc;
+  VertexMover mover;
   double p_move = 0.0;
   std::vector<int32_t> movable;
   if (moves > 0) {
@@ -869,38 +918,18 @@ static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double
   }
   double lt0 = std::log(T0), lt1 = std::log(T1);
   for (int64_t k = 0; k < K; ++k) {
-    const double frac_k = (double)k / (double)K;
-    float temp = (float)std::exp(lt0 + (lt1 - lt0) * frac_k);
+    float temp = (float)std::exp(lt0 + (lt1 - lt0) * ((double)k / (double)K));
     if (p_move > 0 && rng.uni() < p_move) {
       const int v = movable[rng.below((uint32_t)movable.size())];
-      const Pt p = tr.P[v];
-      const double scale = 0.02 + 0.28 * std::sqrt(temp / T0);
       Pt q;
-      if (vc.kind[v] == 1) {
-        float lmin = 3.0e38f;
-        tr.for_fan(v, [&](int t, int kk) {
-          lmin = std::min(lmin, edge_len(p, tr.P[tr.T[t].v[(kk + 1) % 3]]));
-          return false;
-        });
-        const double sd = scale * lmin;
-        q = Pt{(int32_t)(p.x + std::llround(sd * rng.normal())), (int32_t)(p.y + std::llround(sd * rng.normal()))};
-        if (q.x <= 0 || q.y <= 0 || q.x >= tr.D || q.y >= tr.D) continue;
-      } else {
-        const Pt dir = vc.dir[v];
-        const Pt &a = tr.P[vc.nb[v].first], &b = tr.P[vc.nb[v].second];
-        const double step = std::sqrt((double)len2(Pt{0, 0}, dir));
-        const double near = std::min(std::sqrt((double)len2(a, p)), std::sqrt((double)len2(b, p)));
-        int64_t m = std::llround(scale * near / step * rng.normal());
-        if (m == 0) m = rng.uni() < 0.5 ? -1 : 1;
-        q = Pt{(int32_t)(p.x + m * dir.x), (int32_t)(p.y + m * dir.y)};
-        // strictly between its two neighbours on the segment
-        const int64_t da = (int64_t)(a.x - q.x) * (b.x - q.x) + (int64_t)(a.y - q.y) * (b.y - q.y);
-        if (da >= 0) continue;
-      }
-      if (q == p) continue;
       float delta;
-      if (!vertex_move_delta(tr, v, q, &delta)) continue;
-      if (delta <= 0.f || (float)rng.uni() < std::exp(-delta / temp)) tr.P[v] = q;
+      bool acc = false;
+      if (mover.propose(tr, vc, v, rng, q) && vertex_move_delta(tr, v, q, &delta) &&
+          (delta <= 0.f || (float)rng.uni() < std::exp(-delta / temp))) {
+        tr.P[v] = q;
+        acc = true;
+      }
+      mover.record(vc.kind[v], acc);
       continue;
     }
     int t = (int)rng.below((uint32_t)tr.T.size());
