@@ -138,7 +138,9 @@ typedef struct {
  * ranges, strictly CCW triangles, neighbour symmetry, equal labels on both
  * sides, hull edges on the square's sides, sum of areas = D^2.  Reorders the
  * triangles along a Hilbert curve (unless CCT_LOAD_NO_REORDER), packs one
- * 32-byte record per triangle and builds the locate seed grid (Sec. 5.2).
+ * 32-byte record per triangle (coordinates and neighbours) and three 16-byte
+ * half-edge records (one per entry edge: the apex and the two candidate exits,
+ * all a walk step reads) and builds the locate seed grid (Sec. 5.2).
  * Waits for its upload on `stream`.  *out receives the handle.
  * Errors: CCT_ERR_INVALID_ARGUMENT, CCT_ERR_BAD_TRIANGULATION,
  * CCT_ERR_OUT_OF_MEMORY, CCT_ERR_CUDA, CCT_ERR_NO_DEVICE. */
