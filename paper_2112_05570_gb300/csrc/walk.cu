@@ -28,6 +28,7 @@
 //            compute hit id and t, write the results.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "cct_internal.cuh"
 
@@ -444,15 +445,21 @@ static cudaError_t launch_walk_t(const SceneDev& S, const RaySrc& R, const cct_t
   auto k = walk_kernel<kExact, kSrc>;
   const int threads = tu.block_threads;
   const size_t smem = sizeof(WarpStacks<pf_rows<kSrc>()>) * (size_t)(threads / 32);
-  static bool configured = false;  // per instantiation; setting it twice is harmless
-  if (!configured) {
-    // the stacks of 16 warps exceed the default 48 KB of dynamic shared
-    // memory.  The shared/L1 split is left to the driver: a maximal shared
-    // carveout measured 1.5x slower (the L1 also holds the loads in flight).
-    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(sizeof(WarpStacks<pf_rows<kSrc>()>) * (kWalkMaxThreads / 32)));
-    if (e != cudaSuccess) return e;
-    configured = true;
+  {
+    // once per instantiation and device (function attributes belong to each
+    // device's context; `dev` is current): the stacks of 16 warps exceed the
+    // default 48 KB of dynamic shared memory.  The shared/L1 split is left to
+    // the driver: a maximal shared carveout measured 1.5x slower (the L1 also
+    // holds the loads in flight).
+    static std::mutex mu;
+    static uint64_t configured = 0;  // bit d: done on device d (d < 64; others every call)
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || !((configured >> dev) & 1u)) {
+      const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(sizeof(WarpStacks<pf_rows<kSrc>()>) * (kWalkMaxThreads / 32)));
+      if (e != cudaSuccess) return e;
+      if (dev >= 0 && dev < 64) configured |= 1ull << dev;
+    }
   }
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess || per_sm < 1)
