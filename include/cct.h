@@ -54,6 +54,7 @@ extern "C" {
 #define CCT_ERR_CUDA -4                /* a CUDA runtime call failed */
 #define CCT_ERR_WALK_LIMIT -5          /* reported by cct_get_stats' counters only */
 #define CCT_ERR_NO_DEVICE -6           /* no usable CUDA device */
+#define CCT_ERR_IO -7                  /* cct_scene_load_file: file missing, unreadable or malformed */
 
 /* Per-ray status, written to d_steps instead of a step count. */
 #define CCT_RAY_INVALID -1    /* direction off the 2^-22 grid, |component| > 1, zero, or the
@@ -145,6 +146,18 @@ typedef struct {
  * Errors: CCT_ERR_INVALID_ARGUMENT, CCT_ERR_BAD_TRIANGULATION,
  * CCT_ERR_OUT_OF_MEMORY, CCT_ERR_CUDA, CCT_ERR_NO_DEVICE. */
 int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* stream, cct_scene* out);
+
+/* cct_scene_load from a file holding the triangulation (the offline build of
+ * Sec. 4 writes it once; queries load it).  Layout, little-endian: the 8
+ * bytes "CCTTRI1" + NUL; int32 n_vert, n_tri, n_seg, domain; then the int32
+ * arrays of cct_tri_desc in order: vx[n_vert], vy[n_vert], tri_v[3 n_tri],
+ * tri_nb[3 n_tri], tri_seg[3 n_tri].  The header and the file size are checked
+ * before anything is allocated; the arrays are then validated by
+ * cct_scene_load.  Errors: CCT_ERR_INVALID_ARGUMENT (null argument), CCT_ERR_IO
+ * (cannot open or read, wrong magic, counts out of range, size not matching
+ * the counts), then those of cct_scene_load. */
+#define CCT_FILE_MAGIC "CCTTRI1"
+int cct_scene_load_file(const char* path, uint32_t flags, void* stream, cct_scene* out);
 
 /* Releases a scene's device memory.  The caller guarantees no work using it
  * is pending.  NULL is accepted. */

@@ -19,6 +19,7 @@ CCT_ERR_OUT_OF_MEMORY = -3
 CCT_ERR_CUDA = -4
 CCT_ERR_WALK_LIMIT = -5
 CCT_ERR_NO_DEVICE = -6
+CCT_ERR_IO = -7
 CCT_RAY_INVALID = -1
 CCT_RAY_WALK_LIMIT = -2
 CCT_LOAD_NO_REORDER = 1
@@ -97,6 +98,8 @@ def lib() -> ctypes.CDLL:
     L.cct_scene_load.argtypes = [ctypes.POINTER(_TriDesc), u32, vp, ctypes.POINTER(vp)]
     L.cct_scene_free.restype = ctypes.c_int
     L.cct_scene_free.argtypes = [vp]
+    L.cct_scene_load_file.restype = ctypes.c_int
+    L.cct_scene_load_file.argtypes = [ctypes.c_char_p, u32, vp, ctypes.POINTER(vp)]
     L.cct_scene_info.restype = ctypes.c_int
     L.cct_scene_info.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i32)]
     L.cct_locate.restype = ctypes.c_int
@@ -190,6 +193,14 @@ def cct_scene_load(vx, vy, tri_v, tri_nb, tri_seg, n_seg: int, domain: int, flag
                  *[ctypes.c_void_p(a.ctypes.data) for a in arrs])
     h = ctypes.c_void_p()
     _check(lib().cct_scene_load(ctypes.byref(d), flags, _stream_ptr(stream), ctypes.byref(h)), "cct_scene_load")
+    return h.value
+
+
+def cct_scene_load_file(path: str, flags: int = 0, stream=None) -> int:
+    """Load a triangulation file (include/cct.h for the layout); returns the scene handle."""
+    h = ctypes.c_void_p()
+    _check(lib().cct_scene_load_file(os.fsencode(path), flags, _stream_ptr(stream), ctypes.byref(h)),
+           "cct_scene_load_file")
     return h.value
 
 
@@ -291,6 +302,14 @@ class Scene:
     def from_triangulation(cls, tri, domain: int, flags: int = 0, stream=None) -> "Scene":
         n_seg = int(np.asarray(tri.segs).reshape(-1, 4).shape[0])
         return cls(tri.vx, tri.vy, tri.tri_v, tri.tri_nb, tri.tri_seg, n_seg, domain, flags, stream)
+
+    @classmethod
+    def from_file(cls, path: str, flags: int = 0, stream=None) -> "Scene":
+        """A scene loaded by cct_scene_load_file."""
+        self = cls.__new__(cls)
+        self.handle = cct_scene_load_file(path, flags, stream)
+        self.n_tri = cct_scene_info(self.handle)[1]
+        return self
 
     def trace(self, ox, oy, dx, dy, start=None, flags: int = 0, stream=None, out=None):
         """Closest hits of the rays (device tensors): (hit, t, steps) tensors."""

@@ -14,6 +14,7 @@
 //      perturbed: see seed_point in cct_internal.cuh), found by exact walks.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -321,6 +322,46 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
   }
 }
 
+extern "C" int cct_scene_load_file(const char* path, uint32_t flags, void* stream_v, cct_scene* out) {
+  if (!path || !out) return CCT_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return CCT_ERR_IO;
+  struct Closer {
+    FILE* f;
+    ~Closer() { std::fclose(f); }
+  } closer{f};
+  char magic[8];
+  int32_t hdr[4];
+  if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, CCT_FILE_MAGIC, 8) != 0) return CCT_ERR_IO;
+  if (std::fread(hdr, sizeof(int32_t), 4, f) != 4) return CCT_ERR_IO;
+  const int64_t nv = hdr[0], nt = hdr[1], ns = hdr[2], D = hdr[3];
+  if (nv < 3 || nt < 1 || nt >= (1ll << 29) || ns < 0 || D < 1 || D > (1 << 20)) return CCT_ERR_IO;
+  // the size must match the counts exactly before anything is allocated
+  const int64_t body = 4ll * (2 * nv + 9 * nt);
+  if (std::fseek(f, 0, SEEK_END) != 0) return CCT_ERR_IO;
+  const long long size = std::ftell(f);
+  if (size != 8 + 16 + body || std::fseek(f, 24, SEEK_SET) != 0) return CCT_ERR_IO;
+  try {
+    std::vector<int32_t> vx(nv), vy(nv), tv(3 * nt), tn(3 * nt), ts(3 * nt);
+    for (auto* v : {&vx, &vy, &tv, &tn, &ts})
+      if (std::fread(v->data(), sizeof(int32_t), v->size(), f) != v->size()) return CCT_ERR_IO;
+    cct_tri_desc d{};
+    d.n_vert = (int32_t)nv;
+    d.n_tri = (int32_t)nt;
+    d.n_seg = (int32_t)ns;
+    d.domain = (int32_t)D;
+    d.vx = vx.data();
+    d.vy = vy.data();
+    d.tri_v = tv.data();
+    d.tri_nb = tn.data();
+    d.tri_seg = ts.data();
+    return cct_scene_load(&d, flags, stream_v, out);
+  } catch (const std::bad_alloc&) {
+    return CCT_ERR_OUT_OF_MEMORY;
+  }
+}
+
 extern "C" int cct_scene_free(cct_scene s) {
   if (!s) return CCT_OK;
   int rc = CCT_OK;
@@ -371,6 +412,7 @@ extern "C" const char* cct_error_string(int code) {
     case CCT_ERR_CUDA: return "CUDA runtime error";
     case CCT_ERR_WALK_LIMIT: return "walk step limit exceeded";
     case CCT_ERR_NO_DEVICE: return "no CUDA device";
+    case CCT_ERR_IO: return "scene file missing, unreadable or malformed";
     default: return "unknown status";
   }
 }

@@ -208,6 +208,19 @@ class Triangulation:
     def length(self, interior_only=False) -> float:
         return float(_load().sg_tri_length(self._h, 1 if interior_only else 0))
 
+    def save(self, path: str, domain: int = None) -> None:
+        """Writes the triangulation in the file layout that cct_scene_load_file
+        reads: the 8 bytes "CCTTRI1" + NUL, int32 n_vert, n_tri, n_seg, domain,
+        then vx, vy, tri_v, tri_nb, tri_seg as little-endian int32."""
+        d = D if domain is None else int(domain)
+        n_seg = int(np.asarray(self.segs).reshape(-1, 4).shape[0])
+        hdr = np.array([self.n_vert, self.n_tri, n_seg, d], "<i4")
+        with open(path, "wb") as f:
+            f.write(b"CCTTRI1\0")
+            f.write(hdr.tobytes())
+            for a in (self.vx, self.vy, self.tri_v, self.tri_nb, self.tri_seg):
+                f.write(np.ascontiguousarray(a, "<i4").tobytes())
+
     def __del__(self):
         if self._h and _lib is not None:
             _lib.sg_tri_free(self._h)

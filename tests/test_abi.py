@@ -102,3 +102,55 @@ def test_valid_triangulation_passes_validation_without_gpu():
     with pytest.raises(cct.CctError) as e:
         cct.Scene.from_triangulation(t, sg.D)
     assert e.value.code == cct.CCT_ERR_NO_DEVICE
+
+
+def test_scene_file_round_trip_and_malformed_files(tmp_path):
+    """cct_scene_load_file: a file written by the offline build gets past the
+    header checks and validation (and loads where a GPU is present); a missing
+    file, a wrong magic, counts out of range, a size that does not match the
+    counts and a truncated array are CCT_ERR_IO; corrupt arrays are
+    CCT_ERR_BAD_TRIANGULATION (the validation of cct_scene_load)."""
+    import torch
+
+    t = _tri()
+    good = tmp_path / "scene.cct"
+    t.save(str(good))
+    raw = good.read_bytes()
+    assert raw[:8] == b"CCTTRI1\0"
+    hdr = np.frombuffer(raw[8:24], "<i4")
+    assert list(hdr) == [t.n_vert, t.n_tri, t.segs.shape[0], sg.D]
+    assert len(raw) == 24 + 4 * (2 * t.n_vert + 9 * t.n_tri)
+    if torch.cuda.is_available():
+        s = cct.Scene.from_file(str(good))
+        assert s.n_tri == t.n_tri
+        s.free()
+    else:
+        with pytest.raises(cct.CctError) as e:
+            cct.cct_scene_load_file(str(good))
+        assert e.value.code == cct.CCT_ERR_NO_DEVICE
+
+    def expect(data, code, name):
+        p = tmp_path / name
+        p.write_bytes(data)
+        with pytest.raises(cct.CctError) as e:
+            cct.cct_scene_load_file(str(p))
+        assert e.value.code == code, name
+
+    with pytest.raises(cct.CctError) as e:
+        cct.cct_scene_load_file(str(tmp_path / "missing.cct"))
+    assert e.value.code == cct.CCT_ERR_IO
+    expect(b"CCTTRI2\0" + raw[8:], cct.CCT_ERR_IO, "magic")
+    expect(raw[:-4], cct.CCT_ERR_IO, "truncated")
+    expect(raw + b"\0\0\0\0", cct.CCT_ERR_IO, "trailing")
+    bad = bytearray(raw)
+    bad[12:16] = np.array([1 << 29], "<i4").tobytes()  # n_tri out of range
+    expect(bytes(bad), cct.CCT_ERR_IO, "count")
+    bad = bytearray(raw)
+    bad[8:12] = np.array([t.n_vert + 1], "<i4").tobytes()  # size no longer matches
+    expect(bytes(bad), cct.CCT_ERR_IO, "size")
+    # a neighbour index out of range: the arrays reach cct_scene_load's checks
+    off = 24 + 4 * (2 * t.n_vert + 3 * t.n_tri)  # start of tri_nb
+    bad = bytearray(raw)
+    bad[off:off + 4] = np.array([t.n_tri + 7], "<i4").tobytes()
+    expect(bytes(bad), cct.CCT_ERR_BAD_TRIANGULATION, "arrays")
+    assert "file" in cct.cct_error_string(cct.CCT_ERR_IO)

@@ -304,3 +304,18 @@ def test_results_independent_of_tuning(cct, scenes):
     with pytest.raises(cct.CctError):
         scene.set_tuning({"block_threads": 33})
     scene.free()
+
+
+def test_scene_from_file_traces_identically(cct, scenes, tmp_path):
+    """A scene loaded by cct_scene_load_file gives the same results as one
+    loaded from the arrays (and as the oracle)."""
+    kind, seed, tri = scenes[1]
+    path = tmp_path / "scene.cct"
+    tri.save(str(path))
+    r = sg.rays_isotropic(tri, 20000, 91)
+    exp = oracle.walk(tri, r.ox, r.oy, r.dx, r.dy, r.start)
+    from_file = cct.Scene.from_file(str(path))
+    assert from_file.n_tri == tri.n_tri
+    for start in (r.start, None):
+        _assert_parity(_trace(from_file, r.ox, r.oy, r.dx, r.dy, start), exp)
+    from_file.free()
