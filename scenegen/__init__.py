@@ -256,10 +256,10 @@ def anneal(tri: Triangulation, seed: int, sweeps=20.0, T0=0.02, T1=1e-4, moves=1
     """A copy of ``tri`` annealed: greedy flips to shorter diagonals, then
     simulated annealing with temperature T0 -> T1 (units of the domain side,
     as the paper's unit-square schedule, Sec. 3.3) over edge flips (Sec. 3.2.7)
-    and, with weight ``moves`` (0: flips only), the single-vertex perturbation
-    of Sec. 3.2.2 on Steiner vertices -- free ones on the lattice, those inside
-    a segment along it -- then greedy flips again; the shorter of (greedy only,
-    annealed) is kept."""
+    and, with weight ``moves`` (0: flips only), the vertex perturbation and
+    resampling of Sec. 3.2.2 and 3.2.4 on Steiner vertices -- free ones on the
+    lattice, those inside a segment along it -- then greedy flips again; the
+    shorter of (greedy only, annealed) is kept."""
     L = _load()
     h = L.sg_tri_copy(tri._h)
     L.sg_anneal(h, seed, float(sweeps), float(T0) * D, float(T1) * D, float(moves))

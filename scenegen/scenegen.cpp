@@ -883,6 +883,53 @@ struct VertexMover {
     return (int64_t)(a.x - q.x) * (b.x - q.x) + (int64_t)(a.y - q.y) * (b.y - q.y) < 0;
   }
 
+  // The resampling of Sec. 3.2.4: a new position uniform (by area) in the
+  // triangles around the vertex (for a vertex inside a segment: a lattice
+  // point uniform between its two neighbours along it), rounded to the lattice.
+  bool resample(const Triangulation& tr, const VertexClasses& vc, int v, Rng& rng, Pt& q) const {
+    const Pt p = tr.P[v];
+    if (vc.kind[v] == 2) {
+      const Pt dir = vc.dir[v];
+      const Pt &a = tr.P[vc.nb[v].first], &b = tr.P[vc.nb[v].second];
+      const int64_t sx = dir.x != 0 ? dir.x : dir.y;
+      const int64_t ma = ((int64_t)(dir.x != 0 ? a.x - p.x : a.y - p.y)) / sx;  // a = p + ma dir
+      const int64_t mb = ((int64_t)(dir.x != 0 ? b.x - p.x : b.y - p.y)) / sx;
+      const int64_t lo = std::min(ma, mb) + 1, hi = std::max(ma, mb) - 1;  // strictly between
+      if (hi < lo) return false;
+      const int64_t m = lo + (int64_t)(rng.uni() * (double)(hi - lo + 1));
+      if (m == 0 || m > hi) return false;
+      q = Pt{(int32_t)(p.x + m * dir.x), (int32_t)(p.y + m * dir.y)};
+      return true;
+    }
+    double total = 0.0;
+    tr.for_fan(v, [&](int t, int k) {
+      const Tri& x = tr.T[t];
+      total += (double)orient(p, tr.P[x.v[(k + 1) % 3]], tr.P[x.v[(k + 2) % 3]]);
+      return false;
+    });
+    double pick = rng.uni() * total;
+    bool done = false;
+    tr.for_fan(v, [&](int t, int k) {
+      const Tri& x = tr.T[t];
+      const Pt &a = tr.P[x.v[(k + 1) % 3]], &b = tr.P[x.v[(k + 2) % 3]];
+      const double w = (double)orient(p, a, b);
+      if (pick > w) {
+        pick -= w;
+        return false;
+      }
+      double r1 = rng.uni(), r2 = rng.uni();
+      if (r1 + r2 > 1.0) {
+        r1 = 1.0 - r1;
+        r2 = 1.0 - r2;
+      }
+      q = Pt{(int32_t)std::llround(p.x + r1 * (a.x - p.x) + r2 * (b.x - p.x)),
+             (int32_t)std::llround(p.y + r1 * (a.y - p.y) + r2 * (b.y - p.y))};
+      done = true;
+      return true;
+    });
+    return done && !(q == p) && q.x > 0 && q.y > 0 && q.x < tr.D && q.y < tr.D;
+  }
+
   void record(int kind, bool acc) {
     ++tried[kind];
     accepted[kind] += acc;
@@ -896,9 +943,9 @@ struct VertexMover {
 };
 
 // Simulated annealing (Sec. 3.1-3.3) over edge flips (Sec. 3.2.7) and, when
-// moves > 0, the vertex perturbation of Sec. 3.2.2 on Steiner vertices (see
-// VertexMover), with Metropolis acceptance and an exponential temperature
-// schedule.  The energy is the total edge length; lengths and differences are
+// moves > 0, the vertex perturbations of Sec. 3.2.2 and 3.2.4 on Steiner
+// vertices (see VertexMover), with Metropolis acceptance and an exponential
+// temperature schedule.  The energy is the total edge length; lengths and differences are
 // fp32.  A vertex proposal is drawn with probability
 // moves * (movable vertices / vertices).
 static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double T0, double T1, double moves) {
@@ -924,12 +971,15 @@ static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double
       Pt q;
       float delta;
       bool acc = false;
-      if (mover.propose(tr, vc, v, rng, q) && vertex_move_delta(tr, v, q, &delta) &&
+      // the two vertex strategies share the vertex proposals equally (Sec. 3.3)
+      const bool resample = rng.uni() < 0.5;
+      const bool proposed = resample ? mover.resample(tr, vc, v, rng, q) : mover.propose(tr, vc, v, rng, q);
+      if (proposed && vertex_move_delta(tr, v, q, &delta) &&
           (delta <= 0.f || (float)rng.uni() < std::exp(-delta / temp))) {
         tr.P[v] = q;
         acc = true;
       }
-      mover.record(vc.kind[v], acc);
+      if (!resample) mover.record(vc.kind[v], acc);  // lambda steers the Sec. 3.2.2 move only
       continue;
     }
     int t = (int)rng.below((uint32_t)tr.T.size());
