@@ -140,6 +140,26 @@ def cpu_oracle_rate(work, seconds_target=12.0):
     return n2 * len(work) / dt, threads, n2, dt
 
 
+def job_step_ms(dist, ms: float, device=None) -> float:
+    """The job's time per step under N replicas: every rank times its own steps,
+    then the slowest rank's time is the job's (barrier + all-reduce MAX; no
+    collective touches the ray data).  Without a process group: ms."""
+    if dist is None:
+        return ms
+    import torch
+
+    dist.barrier()
+    m = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(m.item())
+
+
+def job_rays_per_s(rays_per_step_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput of N replicas (weak scaling: every rank walks its own
+    full workload per step) over the job's step time."""
+    return rays_per_step_per_rank * world / (ms * 1e-3)
+
+
 def run_reference(args):
     """The baseline arm: the CPU oracle, as it stands, on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -774,13 +794,9 @@ def main():
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.steps
     launch_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    if dist:
-        dist.barrier()
-        m = torch.tensor([ms], device=dev)
-        dist.all_reduce(m, op=dist.ReduceOp.MAX)
-        ms = float(m.item())
+    ms = job_step_ms(dist, ms, dev)
     rays_per_step = n * len(scenes)
-    value = rays_per_step * world / (ms * 1e-3)
+    value = job_rays_per_s(rays_per_step, world, ms)
     tot = batch.stats(reset=True)
     # the results of the timed launches equal the plain per-scene trace's (one scene, every ray)
     chk = scenes[len(scenes) // 2]
