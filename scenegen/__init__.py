@@ -75,7 +75,7 @@ def _load():
     L.sg_tri_length.restype = ctypes.c_float
     L.sg_tri_length.argtypes = [vp, i32]
     L.sg_anneal.restype = i64
-    L.sg_anneal.argtypes = [vp, u64, dbl, dbl, dbl, dbl]
+    L.sg_anneal.argtypes = [vp, u64, dbl, dbl, dbl, dbl, dbl]
     L.sg_rays_isotropic.restype = i64
     L.sg_rays_isotropic.argtypes = [vp, i64, u64, vp, vp, vp, vp, vp, i32]
     L.sg_rays_pinhole.restype = i64
@@ -252,17 +252,19 @@ def cdt(segs: np.ndarray) -> Triangulation:
     return _export(h, segs, "cdt")
 
 
-def anneal(tri: Triangulation, seed: int, sweeps=20.0, T0=0.02, T1=1e-4, moves=1.0) -> Triangulation:
+def anneal(tri: Triangulation, seed: int, sweeps=20.0, T0=0.02, T1=1e-4, moves=1.0, collapse=0.5) -> Triangulation:
     """A copy of ``tri`` annealed: greedy flips to shorter diagonals, then
     simulated annealing with temperature T0 -> T1 (units of the domain side,
     as the paper's unit-square schedule, Sec. 3.3) over edge flips (Sec. 3.2.7)
     and, with weight ``moves`` (0: flips only), the vertex perturbation and
     resampling of Sec. 3.2.2 and 3.2.4 on Steiner vertices -- free ones on the
-    lattice, those inside a segment along it -- then greedy flips again; the
-    shorter of (greedy only, annealed) is kept."""
+    lattice, those inside a segment along it -- of which a share ``collapse``
+    instead merges the vertex into a neighbour (contraction, Sec. 3.2.6 /
+    3.4.1, as a discrete edge collapse); then greedy flips again; the shorter
+    of (greedy only, annealed) is kept."""
     L = _load()
     h = L.sg_tri_copy(tri._h)
-    L.sg_anneal(h, seed, float(sweeps), float(T0) * D, float(T1) * D, float(moves))
+    L.sg_anneal(h, seed, float(sweeps), float(T0) * D, float(T1) * D, float(moves), float(collapse))
     return _export(h, tri.segs, "annealed")
 
 

@@ -942,13 +942,142 @@ struct VertexMover {
   }
 };
 
+// Contraction, in the discrete form this exact-lattice build allows (the
+// paper contracts fuzzily: vertices first move onto one another under the
+// objective of Sec. 2.2, Sec. 3.2.6, and are merged afterwards, Sec. 3.4.1):
+// Steiner vertex v is merged into its neighbour u, deleting the two triangles
+// on edge (u, v).  A free Steiner vertex may merge into any neighbour, one
+// inside a segment only into a neighbour along that segment (so the segment
+// stays covered).  Valid iff the links of u and v share exactly the two apexes
+// (the topology stays a triangulation) and every triangle of v's star, with v
+// replaced by u, stays strictly CCW (exact).  *delta = the change of the total
+// edge length.  Triangles and vertices are only marked dead (v[0] = -1,
+// vtri = -1); compact_dead renumbers at the end.
+static bool collapse_delta(const Triangulation& tr, int v, int u, int& t1, int& t2, float* delta) {
+  int i1;
+  if (!tr.find_edge(v, u, t1, i1)) return false;
+  t2 = tr.T[t1].n[i1];
+  if (t2 < 0) return false;
+  const int a = tr.T[t1].v[i1], b = tr.T[t2].v[tr.nb_edge(t2, t1)];
+  // link condition
+  std::vector<int32_t> lv, lu;
+  tr.for_fan(v, [&](int t, int k) {
+    lv.push_back(tr.T[t].v[(k + 1) % 3]);
+    lv.push_back(tr.T[t].v[(k + 2) % 3]);
+    return false;
+  });
+  tr.for_fan(u, [&](int t, int k) {
+    lu.push_back(tr.T[t].v[(k + 1) % 3]);
+    lu.push_back(tr.T[t].v[(k + 2) % 3]);
+    return false;
+  });
+  std::sort(lv.begin(), lv.end());
+  lv.erase(std::unique(lv.begin(), lv.end()), lv.end());
+  std::sort(lu.begin(), lu.end());
+  lu.erase(std::unique(lu.begin(), lu.end()), lu.end());
+  int shared = 0;
+  for (int32_t x : lv)
+    if (x != u && std::binary_search(lu.begin(), lu.end(), x)) {
+      if (x != a && x != b) return false;
+      ++shared;
+    }
+  if (shared != 2) return false;
+  const Pt &pv = tr.P[v], &pu = tr.P[u];
+  bool ok = true;
+  float d = -edge_len(pv, pu);
+  tr.for_fan(v, [&](int t, int k) {
+    const Tri& x = tr.T[t];
+    const int p = x.v[(k + 1) % 3], q = x.v[(k + 2) % 3];
+    // edge (v, p) once per star triangle: removed if p is an apex, else moved to u
+    d += (p == a || p == b) ? -edge_len(pv, tr.P[p]) : (p == u ? 0.f : edge_len(pu, tr.P[p]) - edge_len(pv, tr.P[p]));
+    if (t == t1 || t == t2) return false;
+    if (orient(pu, tr.P[p], tr.P[q]) <= 0) {
+      ok = false;
+      return true;
+    }
+    return false;
+  });
+  *delta = d;
+  return ok;
+}
+
+static void do_collapse(Triangulation& tr, int v, int u, int t1, int t2) {
+  // v's star, collected before any neighbour pointer changes
+  std::vector<int> star;
+  tr.for_fan(v, [&](int t, int) {
+    star.push_back(t);
+    return false;
+  });
+  // the outer neighbours of t1 / t2 across their edges at v and at u become
+  // neighbours of each other across the merged edge (u, apex)
+  for (int t : {t1, t2}) {
+    const Tri x = tr.T[t];
+    const int kv = Triangulation::idx_of(x, v), ku = Triangulation::idx_of(x, u);
+    const int n_v = x.n[ku], n_u = x.n[kv];  // across the edge at v (opposite u) / at u (opposite v)
+    const int c_u = x.c[kv];
+    if (n_v >= 0) {
+      const int e = tr.nb_edge(n_v, t);
+      tr.T[n_v].n[e] = n_u;
+      tr.T[n_v].c[e] = c_u;
+    }
+    if (n_u >= 0) {
+      const int e = tr.nb_edge(n_u, t);
+      tr.T[n_u].n[e] = n_v;
+    }
+    const int apex = x.v[3 - kv - ku];
+    tr.vtri[apex] = n_v >= 0 ? n_v : n_u;
+    tr.vtri[u] = n_v >= 0 ? n_v : n_u;
+  }
+  // every other triangle of v's star takes u in v's place
+  for (int t : star) {
+    if (t == t1 || t == t2) continue;
+    const int k = Triangulation::idx_of(tr.T[t], v);
+    tr.T[t].v[k] = u;
+    tr.vtri[u] = t;
+  }
+  tr.T[t1].v[0] = -1;
+  tr.T[t2].v[0] = -1;
+  tr.vtri[v] = -1;
+}
+
+// Drops dead triangles and vertices and renumbers the rest.
+static void compact_dead(Triangulation& tr) {
+  std::vector<int32_t> tmap(tr.T.size(), -1), vmap(tr.P.size(), -1);
+  std::vector<Tri> T2;
+  std::vector<Pt> P2;
+  for (size_t v = 0; v < tr.P.size(); ++v)
+    if (tr.vtri[v] >= 0) {
+      vmap[v] = (int32_t)P2.size();
+      P2.push_back(tr.P[v]);
+    }
+  for (size_t t = 0; t < tr.T.size(); ++t)
+    if (tr.T[t].v[0] >= 0) {
+      tmap[t] = (int32_t)T2.size();
+      T2.push_back(tr.T[t]);
+    }
+  if (T2.size() == tr.T.size()) return;
+  std::vector<int32_t> vtri2(P2.size(), 0);
+  for (size_t t = 0; t < T2.size(); ++t)
+    for (int i = 0; i < 3; ++i) {
+      T2[t].v[i] = vmap[T2[t].v[i]];
+      if (T2[t].n[i] >= 0) T2[t].n[i] = tmap[T2[t].n[i]];
+      vtri2[T2[t].v[i]] = (int32_t)t;
+    }
+  tr.T.swap(T2);
+  tr.P.swap(P2);
+  tr.vtri.swap(vtri2);
+  tr.last = 0;
+}
+
 // Simulated annealing (Sec. 3.1-3.3) over edge flips (Sec. 3.2.7) and, when
 // moves > 0, the vertex perturbations of Sec. 3.2.2 and 3.2.4 on Steiner
 // vertices (see VertexMover), with Metropolis acceptance and an exponential
 // temperature schedule.  The energy is the total edge length; lengths and differences are
 // fp32.  A vertex proposal is drawn with probability
 // moves * (movable vertices / vertices).
-static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double T0, double T1, double moves) {
+static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double T0, double T1, double moves,
+                         double collapse) {
+  int64_t n_collapsed = 0;
   Rng rng(seed, 0xA77);
   int64_t n_half = (int64_t)tr.T.size() * 3;
   int64_t K = (int64_t)(sweeps * (double)n_half);
@@ -968,9 +1097,48 @@ static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double
     float temp = (float)std::exp(lt0 + (lt1 - lt0) * ((double)k / (double)K));
     if (p_move > 0 && rng.uni() < p_move) {
       const int v = movable[rng.below((uint32_t)movable.size())];
+      if (tr.vtri[v] < 0) continue;  // merged away
       Pt q;
       float delta;
       bool acc = false;
+      if (collapse > 0 && rng.uni() < collapse) {
+        // merge v into a neighbour: any for a free vertex, one along its segment otherwise
+        int u = -1;
+        if (vc.kind[v] == 2) {
+          u = rng.uni() < 0.5 ? vc.nb[v].first : vc.nb[v].second;
+        } else {
+          int deg = 0;
+          tr.for_fan(v, [&](int, int) {
+            ++deg;
+            return false;
+          });
+          int pick = (int)rng.below((uint32_t)deg);
+          tr.for_fan(v, [&](int t, int kk) {
+            if (pick-- == 0) {
+              u = tr.T[t].v[(kk + 1) % 3];
+              return true;
+            }
+            return false;
+          });
+        }
+        int t1, t2;
+        if (u >= 0 && collapse_delta(tr, v, u, t1, t2, &delta) &&
+            (delta <= 0.f || (float)rng.uni() < std::exp(-delta / temp))) {
+          if (vc.kind[v] == 2) {
+            // the segment neighbours of v now neighbour each other
+            const int w = vc.nb[v].first == u ? vc.nb[v].second : vc.nb[v].first;
+            for (int x : {u, w})
+              if (x >= 0 && vc.kind[x] == 2) {
+                if (vc.nb[x].first == v) vc.nb[x].first = (x == u ? w : u);
+                if (vc.nb[x].second == v) vc.nb[x].second = (x == u ? w : u);
+              }
+          }
+          do_collapse(tr, v, u, t1, t2);
+          vc.kind[v] = 0;
+          ++n_collapsed;
+        }
+        continue;
+      }
       // the two vertex strategies share the vertex proposals equally (Sec. 3.3)
       const bool resample = rng.uni() < 0.5;
       const bool proposed = resample ? mover.resample(tr, vc, v, rng, q) : mover.propose(tr, vc, v, rng, q);
@@ -984,7 +1152,7 @@ static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double
     }
     int t = (int)rng.below((uint32_t)tr.T.size());
     int i = (int)rng.below(3);
-    if (tr.T[t].c[i] >= 0 || tr.T[t].n[i] < 0) continue;
+    if (tr.T[t].v[0] < 0 || tr.T[t].c[i] >= 0 || tr.T[t].n[i] < 0) continue;
     int x, y;
     if (!tr.strictly_convex(t, i, x, y)) continue;
     const Pt& q = tr.P[tr.T[t].v[(i + 1) % 3]];
@@ -992,6 +1160,7 @@ static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double
     float delta = edge_len(tr.P[x], tr.P[y]) - edge_len(q, r);
     if (delta <= 0.f || (float)rng.uni() < std::exp(-delta / temp)) tr.flip(t, i);
   }
+  if (n_collapsed > 0) compact_dead(tr);
 }
 
 // ---------------------------------------------------------------- rays
@@ -1633,12 +1802,12 @@ float sg_tri_length(void* h, int32_t interior_only) {
 // T0 to T1 (grid units) for `sweeps` proposals per half-edge, then greedy
 // flips again.  Keeps whichever of (greedy-only, annealed) is shorter.
 // Returns the number of greedy flips of the kept result.
-int64_t sg_anneal(void* h, uint64_t seed, double sweeps, double T0, double T1, double moves) {
+int64_t sg_anneal(void* h, uint64_t seed, double sweeps, double T0, double T1, double moves, double collapse) {
   auto* tr = (Triangulation*)h;
   Triangulation g = *tr;
   int64_t f0 = greedy_flips(g);
   float lg = (float)g.total_length(false);
-  anneal_flips(*tr, seed, sweeps, T0, T1, moves);
+  anneal_flips(*tr, seed, sweeps, T0, T1, moves, collapse);
   int64_t f1 = greedy_flips(*tr);
   float la = (float)tr->total_length(false);
   if (la > lg) {

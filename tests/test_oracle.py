@@ -443,3 +443,27 @@ def test_vertex_moves_keep_the_scene_and_shorten():
     hb, tb = oracle.closest_bruteforce(segs, r.ox, r.oy, r.dx, r.dy)
     hw, tw, sw = oracle.walk(moved, r.ox, r.oy, r.dx, r.dy, r.start)
     assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
+
+
+def test_contraction_removes_steiner_vertices_and_keeps_the_scene():
+    """The discrete contraction (a Steiner vertex merged into a neighbour, the
+    two triangles on their edge deleted): still a valid triangulation of the
+    same segments (Euler count, coverage, orientation, neighbours), with fewer
+    vertices and no longer than without contraction, and the walk on it equals
+    the brute force, steps included."""
+    segs = sg.circles(3000, 23)
+    ref = sg.refine_optimal(sg.cdt(segs))
+    kept = sg.anneal(ref, 23, sweeps=4, collapse=0.0)
+    merged = sg.anneal(ref, 23, sweeps=4, collapse=0.5)
+    assert oracle.check_triangulation(merged, sg.D) == 0
+    assert merged.n_vert < kept.n_vert and merged.n_tri < kept.n_tri
+    assert oracle.interior_length(merged) < oracle.interior_length(kept)
+    pts = set(zip(merged.vx.tolist(), merged.vy.tolist()))
+    for x0, y0, x1, y1 in segs.tolist():
+        assert (x0, y0) in pts and (x1, y1) in pts
+    r = sg.rays_isotropic(merged, 4000, 24)
+    hb, tb = oracle.closest_bruteforce(segs, r.ox, r.oy, r.dx, r.dy)
+    hw, tw, sw = oracle.walk(merged, r.ox, r.oy, r.dx, r.dy, r.start)
+    assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
+    assert np.array_equal(sw[:500], oracle.steps_bruteforce(merged, r.ox[:500], r.oy[:500], r.dx[:500], r.dy[:500],
+                                                             hb[:500]))
