@@ -935,8 +935,28 @@ def main():
         e2e_step()
     torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / k_e2e
+    # the same pipeline's copies alone (no walk): the copy-bound ceiling of the end-to-end rate on this machine
+    def copies_only():
+        for i, (sc, lo) in enumerate(pieces):
+            b = i % n_buf
+            m = min(piece, n - lo)
+            with torch.cuda.stream(h2d_s):
+                for k in dbuf[b]:
+                    dbuf[b][k][:m].copy_(sc["pin"][k][lo:lo + m], non_blocking=True)
+            with torch.cuda.stream(d2h_s):
+                for host, dv in zip(sc["pin_out"], obuf[b]):
+                    host[lo:lo + m].copy_(dv[:m], non_blocking=True)
+
+    copies_only()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        copies_only()
+    torch.cuda.synchronize(dev)
+    copy_s = (time.perf_counter() - t0) / k_e2e
     e2e = {"value": rays_per_step * world / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": 16 * rays_per_step,
            "d2h_bytes_per_step": 12 * rays_per_step,
+           "copies_only_rays_per_s": rays_per_step * world / copy_s,
            "pipeline": "per scene: pinned host->device copy, cct_trace, device->host copy on three streams, "
                        "two device buffer sets; the copies of neighbouring scenes (also across steps) overlap each "
                        "walk; one host wait after the timed steps"}
