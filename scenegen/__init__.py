@@ -82,6 +82,8 @@ def _load():
     L.sg_rays_pinhole.argtypes = [vp, i64, i64, dbl, u64, vp, vp, vp, vp, vp, i32]
     L.sg_refine.restype = i64
     L.sg_refine.argtypes = [vp, dbl, dbl, i64]
+    L.sg_subdivide.restype = i64
+    L.sg_subdivide.argtypes = [vp]
     L.sg_refine_optimal.restype = vp
     L.sg_refine_optimal.argtypes = [vp, vp, i32, vp, i32, i64, i32, P(dbl), P(dbl)]
     L.sg_bvh_build.restype = vp
@@ -266,6 +268,18 @@ def anneal(tri: Triangulation, seed: int, sweeps=20.0, T0=0.02, T1=1e-4, moves=1
     h = L.sg_tri_copy(tri._h)
     L.sg_anneal(h, seed, float(sweeps), float(T0) * D, float(T1) * D, float(moves), float(collapse))
     return _export(h, tri.segs, "annealed")
+
+
+def subdivide(tri: Triangulation) -> Triangulation:
+    """A copy of ``tri`` with the lattice midpoint of every interior edge
+    inserted (the 1 -> 4 subdivision of Sec. 3.5.2 on the lattice; constrained
+    edges split along their segment), made constrained-Delaunay again."""
+    L = _load()
+    h = L.sg_tri_copy(tri._h)
+    if L.sg_subdivide(h) < 0:
+        L.sg_tri_free(h)
+        raise RuntimeError("subdivision failed")
+    return _export(h, tri.segs, "subdivided")
 
 
 def refine(tri: Triangulation, min_angle_deg: float = 20.0, max_area: float = 0.0,

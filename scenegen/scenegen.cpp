@@ -1963,6 +1963,34 @@ extern "C" {
 // Quality refinement of a CDT in place (see refine above): min_angle_deg (0 =
 // none), max_area (0 = none, grid units^2), at most max_insert new vertices.
 // Returns the number of vertices inserted, or -1 on a construction failure.
+// The 1 -> 4 subdivision of Sec. 3.5.2, on the lattice: the midpoint of every
+// interior edge that has a lattice midpoint is inserted (a constrained edge's
+// midpoint splits it, keeping its segment), then the triangulation is made
+// constrained-Delaunay again by flips; hull edges are not split.  The
+// optimiser then moves, flips and contracts the new vertices (Sec. 3.5.3).
+// Returns the number of vertices inserted.
+int64_t sg_subdivide(void* h) {
+  auto* tr = (Triangulation*)h;
+  std::vector<Pt> mids;
+  for (int t = 0; t < (int)tr->T.size(); ++t)
+    for (int i = 0; i < 3; ++i) {
+      const int u = tr->T[t].n[i];
+      if (u < t) continue;  // each interior edge once; hull edges (u < 0) skipped
+      const Pt& p = tr->P[tr->T[t].v[(i + 1) % 3]];
+      const Pt& q = tr->P[tr->T[t].v[(i + 2) % 3]];
+      if (((p.x + q.x) & 1) || ((p.y + q.y) & 1)) continue;
+      mids.push_back(Pt{(p.x + q.x) / 2, (p.y + q.y) / 2});
+    }
+  int64_t inserted = 0;
+  for (const Pt& m : mids) {
+    const size_t nv = tr->P.size();
+    const int v = tr->insert_point(m);
+    if (tr->status < 0) return -1;
+    if (v >= 0 && (size_t)v >= nv) ++inserted;
+  }
+  return inserted;
+}
+
 int64_t sg_refine(void* h, double min_angle_deg, double max_area, int64_t max_insert) {
   auto* tr = (Triangulation*)h;
   int64_t n = refine(*tr, min_angle_deg, max_area, max_insert);

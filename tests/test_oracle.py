@@ -467,3 +467,47 @@ def test_contraction_removes_steiner_vertices_and_keeps_the_scene():
     assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
     assert np.array_equal(sw[:500], oracle.steps_bruteforce(merged, r.ox[:500], r.oy[:500], r.dx[:500], r.dy[:500],
                                                              hb[:500]))
+
+
+def test_subdivision_splits_edges_and_keeps_the_scene():
+    """The 1 -> 4 subdivision (Sec. 3.5.2 on the lattice): every interior edge
+    with a lattice midpoint gains that vertex, constrained edges are split
+    along their segment, the result is a valid triangulation of the same
+    segments, annealing it keeps it valid, and the walk on both equals the
+    brute force."""
+    segs = sg.random_segments(300, 31)
+    base = sg.anneal(sg.refine_optimal(sg.cdt(segs)), 31, sweeps=2)
+    sub = sg.subdivide(base)
+    assert oracle.check_triangulation(sub, sg.D) == 0
+    pts = set(zip(sub.vx.tolist(), sub.vy.tolist()))
+    for t in range(base.n_tri):
+        for i in range(3):
+            u = base.tri_nb[t, i]
+            if u < 0:
+                continue
+            p, q = base.tri_v[t, (i + 1) % 3], base.tri_v[t, (i + 2) % 3]
+            mx, my = int(base.vx[p]) + int(base.vx[q]), int(base.vy[p]) + int(base.vy[q])
+            if mx % 2 == 0 and my % 2 == 0:
+                assert (mx // 2, my // 2) in pts
+    assert sub.n_vert > base.n_vert and sub.n_tri > base.n_tri
+    # constrained midpoints are vertices of constrained edges of the same segment
+    for t in range(base.n_tri):
+        for i in range(3):
+            s = base.tri_seg[t, i]
+            if s < 0:
+                continue
+            p, q = base.tri_v[t, (i + 1) % 3], base.tri_v[t, (i + 2) % 3]
+            mx, my = int(base.vx[p]) + int(base.vx[q]), int(base.vy[p]) + int(base.vy[q])
+            if mx % 2 or my % 2:
+                continue
+            m = int(np.argwhere((sub.vx == mx // 2) & (sub.vy == my // 2))[0, 0])
+            inc = np.argwhere(sub.tri_v == m)
+            labels = {int(sub.tri_seg[tt, k]) for tt, vi in inc for k in range(3) if k != vi}
+            assert s in labels
+    again = sg.anneal(sub, 32, sweeps=2)
+    assert oracle.check_triangulation(again, sg.D) == 0
+    for tri in (sub, again):
+        r = sg.rays_isotropic(tri, 2000, 33)
+        hb, tb = oracle.closest_bruteforce(segs, r.ox, r.oy, r.dx, r.dy)
+        hw, tw, _ = oracle.walk(tri, r.ox, r.oy, r.dx, r.dy, r.start)
+        assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
