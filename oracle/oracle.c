@@ -901,4 +901,332 @@ int oracle_kd_trace(int32_t n_nodes, const int32_t* axis, const int32_t* split, 
   return 0;
 }
 
+/* ------------------------------------------------------------------ secondary rays */
+/* Sec. 5.2: a secondary ray starts where its parent hit the geometry, and the
+ * final triangle of the parent's walk is its start triangle.  The paper fixes
+ * nothing else; readings used here (and by the GPU path):
+ *   - the secondary ray is the mirror image of its parent about the hit
+ *     segment;
+ *   - its origin is the parent's exact hit point moved onto the hit
+ *     constrained edge (a -> b) of the final triangle (a right of the parent
+ *     ray, b left of it or on its line): P' = a + (i / 2^32) (b - a) with
+ *     i = round(2^32 mu) (halves up) clamped to [1, 2^32 - 1], mu the exact
+ *     parameter of the hit point on that edge.  P' lies exactly on the edge,
+ *     strictly between its endpoints, so its coordinates are multiples of
+ *     2^-32: origins are held as X = 2^32 x, Y = 2^32 y (int64);
+ *   - its direction is k' = 2 (k.u) u / |u|^2 - k rounded componentwise to
+ *     integers (halves up) and clamped to [-2^22, 2^22], u = b - a; when k'
+ *     does not point strictly back to the parent's side of the segment (the
+ *     sign of u x k' must be opposite to that of u x k) the path ends;
+ *   - every ray of the path, the first included, follows the rules of the
+ *     primary rays (side rule, hit, tie order), with the origin in 2^-32
+ *     units.  A path of a primary ray has up to 1 + n_bounce rays; it ends at
+ *     a miss, an invalid primary ray, a walk limit or a grazing reflection.
+ * Records of a path: entry b * n + r for ray b of path r.  steps: as for the
+ * walk; -3 = no ray (the path ended before this bounce), with hit -1, t NaN,
+ * origin 0 and direction 0. */
+#define BNC_NONE (-3)
+static const i128 QONE = (i128)1 << 32;
+
+/* 2^32 * (k x (v - P)) = kx (vy 2^32 - Y) - ky (vx 2^32 - X), exact (|.| < 2^76) */
+static int side_q(int64_t kx, int64_t ky, int64_t X, int64_t Y, int64_t vx, int64_t vy) {
+  i128 v = (i128)kx * ((i128)vy * QONE - Y) - (i128)ky * ((i128)vx * QONE - X);
+  return v >= 0 ? ORC_SIDE_L : ORC_SIDE_R;
+}
+
+/* t = cross(b - a, a - P) / cross(b - a, d) = 2^22 num / (2^32 den), den > 0 */
+typedef struct {
+  i128 num;
+  i128 den;
+} qratio;
+
+static qratio seg_param_q(int64_t kx, int64_t ky, int64_t X, int64_t Y, int64_t ax, int64_t ay, int64_t bx,
+                          int64_t by) {
+  qratio r;
+  int64_t ex = bx - ax, ey = by - ay;
+  r.num = (i128)ex * ((i128)ay * QONE - Y) - (i128)ey * ((i128)ax * QONE - X);
+  r.den = (i128)ex * ky - (i128)ey * kx;
+  if (r.den < 0) {
+    r.num = -r.num;
+    r.den = -r.den;
+  }
+  return r;
+}
+
+static int qratio_cmp(qratio a, qratio b) { /* |num| < 2^75, den < 2^45: products < 2^120 */
+  i128 l = a.num * b.den, r = b.num * a.den;
+  return (l > r) - (l < r);
+}
+
+static float qratio_to_t(qratio r) { return (float)((double)r.num / (double)r.den * 0x1p-10); }
+
+static i128 floordiv(i128 n, i128 d) { /* d > 0 */
+  i128 q = n / d;
+  if (n % d != 0 && n < 0) q -= 1;
+  return q;
+}
+
+/* The origin of the secondary ray on the hit edge (a -> b). */
+static void snap_origin(int64_t kx, int64_t ky, int64_t X, int64_t Y, int64_t ax, int64_t ay, int64_t bx,
+                        int64_t by, int64_t* X2, int64_t* Y2) {
+  int64_t ex = bx - ax, ey = by - ay;
+  /* mu = cross(k, P - a) / cross(k, b - a); 2^32 mu = num / den */
+  i128 num = (i128)kx * ((i128)Y - (i128)ay * QONE) - (i128)ky * ((i128)X - (i128)ax * QONE);
+  i128 den = (i128)kx * ey - (i128)ky * ex;
+  if (den < 0) {
+    num = -num;
+    den = -den;
+  }
+  i128 i = floordiv(2 * num + den, 2 * den);
+  if (i < 1) i = 1;
+  if (i > QONE - 1) i = QONE - 1;
+#if ORACLE_MUTANT == 6 /* planted: measures the parameter from the wrong endpoint */
+  *X2 = (int64_t)((i128)bx * QONE - i * ex);
+  *Y2 = (int64_t)((i128)by * QONE - i * ey);
+#else
+  *X2 = (int64_t)((i128)ax * QONE + i * ex);
+  *Y2 = (int64_t)((i128)ay * QONE + i * ey);
+#endif
+}
+
+/* Mirror direction about u; returns 0 when it does not point strictly back. */
+static int reflect_dir(int64_t kx, int64_t ky, int64_t ux, int64_t uy, int64_t* rx, int64_t* ry) {
+  const i128 ku = (i128)kx * ux + (i128)ky * uy, uu = (i128)ux * ux + (i128)uy * uy;
+#if ORACLE_MUTANT == 5 /* planted: adds the incoming direction instead of subtracting it */
+  const i128 nx = 2 * ku * ux + uu * kx, ny = 2 * ku * uy + uu * ky;
+#else
+  const i128 nx = 2 * ku * ux - uu * kx, ny = 2 * ku * uy - uu * ky;
+#endif
+  i128 qx = floordiv(2 * nx + uu, 2 * uu), qy = floordiv(2 * ny + uu, 2 * uu);
+  const i128 lim = (i128)1 << 22;
+  if (qx > lim) qx = lim;
+  if (qx < -lim) qx = -lim;
+  if (qy > lim) qy = lim;
+  if (qy < -lim) qy = -lim;
+  *rx = (int64_t)qx;
+  *ry = (int64_t)qy;
+  const i128 c0 = (i128)ux * ky - (i128)uy * kx, c1 = (i128)ux * qy - (i128)uy * qx;
+  return (c0 > 0 && c1 < 0) || (c0 < 0 && c1 > 0);
+}
+
+typedef struct {
+  int64_t n_tri, n_seg;
+  const int32_t *vx, *vy, *tri_v, *tri_nb, *tri_seg, *seg;
+  int64_t n;
+  const int32_t *ox, *oy;
+  const float *dx, *dy;
+  const int32_t* start;
+  int32_t n_bounce;
+  int32_t *hit, *steps;
+  float* t;
+  int64_t *org_x, *org_y;
+  float *dir_x, *dir_y;
+  int64_t max_steps;
+} bounce_ctx;
+
+static void bounce_clear(const bounce_ctx* c, int64_t r) {
+  for (int b = 0; b <= c->n_bounce; ++b) {
+    int64_t k = (int64_t)b * c->n + r;
+    c->hit[k] = -1;
+    c->t[k] = NAN;
+    if (c->steps) c->steps[k] = BNC_NONE;
+    c->org_x[k] = c->org_y[k] = 0;
+    c->dir_x[k] = c->dir_y[k] = 0.0f;
+  }
+}
+
+static void bounce_origin(const bounce_ctx* c, int64_t k, int64_t X, int64_t Y, int64_t kx, int64_t ky) {
+  c->org_x[k] = X;
+  c->org_y[k] = Y;
+  c->dir_x[k] = (float)kx * 0x1p-22f;
+  c->dir_y[k] = (float)ky * 0x1p-22f;
+}
+
+/* Whether the primary ray r is valid: direction on the grid and non-zero,
+ * origin inside the domain's range; its k. */
+static int bounce_primary(const bounce_ctx* c, int64_t r, int64_t* kx, int64_t* ky) {
+  return dir_to_int(c->dx[r], kx) && dir_to_int(c->dy[r], ky) && (*kx != 0 || *ky != 0) && c->ox[r] >= 0 &&
+         c->oy[r] >= 0;
+}
+
+/* The walk path: every ray of the path walks from the final triangle of the
+ * previous one (Sec. 5.1 in each triangle, the start cell of Sec. 5.2). */
+static void bounce_walk_range(void* p, int64_t lo, int64_t hi) {
+  const bounce_ctx* c = (const bounce_ctx*)p;
+  walk_ctx w; /* only for strictly_inside */
+  memset(&w, 0, sizeof w);
+  w.vx = c->vx;
+  w.vy = c->vy;
+  w.tri_v = c->tri_v;
+  for (int64_t r = lo; r < hi; ++r) {
+    bounce_clear(c, r);
+    int64_t kx, ky;
+    int64_t T = c->start[r];
+    if (!bounce_primary(c, r, &kx, &ky) || T < 0 || T >= c->n_tri || !strictly_inside(&w, T, c->ox[r], c->oy[r])) {
+      c->steps[r] = -1;
+      continue;
+    }
+    int64_t X = (int64_t)c->ox[r] << 32, Y = (int64_t)c->oy[r] << 32;
+    for (int b = 0; b <= c->n_bounce; ++b) {
+      const int64_t k = (int64_t)b * c->n + r;
+      bounce_origin(c, k, X, Y, kx, ky);
+      int64_t steps = 0;
+      int more = 0;
+      for (;;) {
+        ++steps;
+        if (steps > c->max_steps) {
+          c->steps[k] = -2;
+          break;
+        }
+        int e = -1;
+        for (int i = 0; i < 3; ++i) {
+          int32_t a = c->tri_v[3 * T + (i + 1) % 3], bb = c->tri_v[3 * T + (i + 2) % 3];
+          if (side_q(kx, ky, X, Y, c->vx[a], c->vy[a]) == ORC_SIDE_R &&
+              side_q(kx, ky, X, Y, c->vx[bb], c->vy[bb]) == ORC_SIDE_L) {
+            e = i;
+            break;
+          }
+        }
+        if (e < 0) { /* cannot happen: the origin is inside T or on its entry edge */
+          c->steps[k] = -1;
+          break;
+        }
+        const int32_t seg = c->tri_seg[3 * T + e], nb = c->tri_nb[3 * T + e];
+        if (seg >= 0) {
+          const int32_t a = c->tri_v[3 * T + (e + 1) % 3], bb = c->tri_v[3 * T + (e + 2) % 3];
+          const int64_t ax = c->vx[a], ay = c->vy[a], bx = c->vx[bb], by = c->vy[bb];
+          c->hit[k] = seg;
+          c->t[k] = qratio_to_t(seg_param_q(kx, ky, X, Y, ax, ay, bx, by));
+          c->steps[k] = (int32_t)steps;
+          if (b < c->n_bounce) {
+            int64_t X2, Y2, kx2, ky2;
+            snap_origin(kx, ky, X, Y, ax, ay, bx, by, &X2, &Y2);
+            if (reflect_dir(kx, ky, bx - ax, by - ay, &kx2, &ky2)) {
+              X = X2;
+              Y = Y2;
+              kx = kx2;
+              ky = ky2;
+              more = 1; /* T stays: the next ray starts in the final triangle */
+            }
+          }
+          break;
+        }
+        if (nb < 0) {
+          c->t[k] = INFINITY;
+          c->steps[k] = (int32_t)steps;
+          break;
+        }
+        T = nb;
+      }
+      if (!more) break;
+    }
+  }
+}
+
+/* Closest segment of the ray (P, k), P in 2^-32 units; -1 for none.  As
+ * closest_segment, with the exact arithmetic widened. */
+static int32_t closest_segment_q(const int32_t* seg, int64_t n_seg, int64_t X, int64_t Y, int64_t kx, int64_t ky,
+                                 qratio* best_t) {
+  int32_t best = -1;
+  qratio bt = {0, 1};
+  int64_t bux = 0, buy = 0;
+  for (int64_t s = 0; s < n_seg; ++s) {
+    int64_t ax = seg[4 * s], ay = seg[4 * s + 1], bx = seg[4 * s + 2], by = seg[4 * s + 3];
+    int sa = side_q(kx, ky, X, Y, ax, ay), sb = side_q(kx, ky, X, Y, bx, by);
+    if (sa == sb) continue;
+    qratio r = seg_param_q(kx, ky, X, Y, ax, ay, bx, by);
+    if (r.num <= 0) continue;
+    int64_t wx = sa == ORC_SIDE_R ? ax : bx, wy = sa == ORC_SIDE_R ? ay : by;
+    int c = best < 0 ? -1 : qratio_cmp(r, bt);
+    if (c == 0) {
+      int64_t pvx = (wx == ax && wy == ay) ? bx : ax, pvy = (wx == ax && wy == ay) ? by : ay;
+      c = tie_cmp(kx, ky, wx - pvx, wy - pvy, bux - pvx, buy - pvy);
+    }
+    if (c < 0) {
+      best = (int32_t)s;
+      bt = r;
+      bux = wx;
+      buy = wy;
+    }
+  }
+  *best_t = bt;
+  return best;
+}
+
+/* The same paths by brute force: each ray's closest hit over all segments,
+ * the hit constrained edge found by scanning every edge labelled with the hit
+ * segment (the one whose endpoints lie on opposite sides of the ray). */
+static void bounce_bf_range(void* p, int64_t lo, int64_t hi) {
+  const bounce_ctx* c = (const bounce_ctx*)p;
+  for (int64_t r = lo; r < hi; ++r) {
+    bounce_clear(c, r);
+    int64_t kx, ky;
+    if (!bounce_primary(c, r, &kx, &ky)) continue;
+    int64_t X = (int64_t)c->ox[r] << 32, Y = (int64_t)c->oy[r] << 32;
+    for (int b = 0; b <= c->n_bounce; ++b) {
+      const int64_t k = (int64_t)b * c->n + r;
+      bounce_origin(c, k, X, Y, kx, ky);
+      qratio bt;
+      const int32_t s = closest_segment_q(c->seg, c->n_seg, X, Y, kx, ky, &bt);
+      if (s < 0) {
+        c->t[k] = INFINITY;
+        break;
+      }
+      c->hit[k] = s;
+      c->t[k] = qratio_to_t(bt);
+      if (b == c->n_bounce) break;
+      int64_t ax = 0, ay = 0, bx = 0, by = 0;
+      int found = 0;
+      for (int64_t q = 0; q < 3 * c->n_tri && !found; ++q) {
+        if (c->tri_seg[q] != s) continue;
+        const int64_t T = q / 3, i = q % 3;
+        const int32_t u = c->tri_v[3 * T + (i + 1) % 3], v = c->tri_v[3 * T + (i + 2) % 3];
+        const int su = side_q(kx, ky, X, Y, c->vx[u], c->vy[u]), sv = side_q(kx, ky, X, Y, c->vx[v], c->vy[v]);
+        if (su == sv) continue;
+        const int32_t ra = su == ORC_SIDE_R ? u : v, lb = su == ORC_SIDE_R ? v : u;
+        ax = c->vx[ra];
+        ay = c->vy[ra];
+        bx = c->vx[lb];
+        by = c->vy[lb];
+        found = 1;
+      }
+      if (!found) break; /* cannot happen for a triangulation that covers the segments */
+      int64_t X2, Y2, kx2, ky2;
+      snap_origin(kx, ky, X, Y, ax, ay, bx, by, &X2, &Y2);
+      if (!reflect_dir(kx, ky, bx - ax, by - ay, &kx2, &ky2)) break;
+      X = X2;
+      Y = Y2;
+      kx = kx2;
+      ky = ky2;
+    }
+  }
+}
+
+/* Mirror paths of n primary rays with up to n_bounce secondary rays each, by
+ * walks chained through their final triangles.  Outputs (1 + n_bounce) * n
+ * entries, entry b * n + r: hit, t, steps as oracle_walk plus -3 (no ray),
+ * origin (2^-32 units) and direction of each ray of the path. */
+int oracle_bounce_walk(int64_t n_tri, const int32_t* vx, const int32_t* vy, const int32_t* tri_v,
+                       const int32_t* tri_nb, const int32_t* tri_seg, int64_t n, const int32_t* ox,
+                       const int32_t* oy, const float* dx, const float* dy, const int32_t* start, int32_t n_bounce,
+                       int32_t* hit, float* t, int32_t* steps, int64_t* org_x, int64_t* org_y, float* dir_x,
+                       float* dir_y, int64_t max_steps, int32_t n_threads) {
+  bounce_ctx c = {n_tri, 0, vx, vy, tri_v, tri_nb, tri_seg, NULL, n, ox, oy, dx, dy, start, n_bounce,
+                  hit, steps, t, org_x, org_y, dir_x, dir_y, max_steps};
+  run_parallel(bounce_walk_range, &c, n, n_threads);
+  return 0;
+}
+
+/* The same paths by brute force over the segments (no steps). */
+int oracle_bounce_bruteforce(int64_t n_tri, const int32_t* vx, const int32_t* vy, const int32_t* tri_v,
+                             const int32_t* tri_seg, int64_t n_seg, const int32_t* seg, int64_t n,
+                             const int32_t* ox, const int32_t* oy, const float* dx, const float* dy,
+                             int32_t n_bounce, int32_t* hit, float* t, int64_t* org_x, int64_t* org_y,
+                             float* dir_x, float* dir_y, int32_t n_threads) {
+  bounce_ctx c = {n_tri, n_seg, vx, vy, tri_v, NULL, tri_seg, seg, n, ox, oy, dx, dy, NULL, n_bounce,
+                  hit, NULL, t, org_x, org_y, dir_x, dir_y, 0};
+  run_parallel(bounce_bf_range, &c, n, n_threads);
+  return 0;
+}
+
 int32_t oracle_mutant(void) { return ORACLE_MUTANT; }

@@ -181,6 +181,19 @@ def ring_of_circles(n_target: int) -> np.ndarray:
     return out[:m].copy()
 
 
+def room(n_obstacles: int, seed: int, wall_margin: float = 0.005) -> np.ndarray:
+    """A closed square room (four wall segments sharing their corners,
+    wall_margin of the domain side from the border) around n_obstacles random
+    segments (``random_segments``, 1% from the border, so inside the walls):
+    mirror paths inside it end only by grazing or at the bounce limit."""
+    m = int(round(wall_margin * D))
+    walls = np.array([[m, m, D - m, m], [D - m, m, D - m, D - m], [D - m, D - m, m, D - m], [m, D - m, m, m]],
+                     np.int32)
+    if n_obstacles <= 0:
+        return walls
+    return np.concatenate([walls, random_segments(n_obstacles, seed)]).astype(np.int32)
+
+
 # ----------------------------------------------------------------------------- triangulations
 @dataclass
 class Triangulation:

@@ -311,7 +311,7 @@ def test_crofton_through_walk():
     assert abs(crossings.mean() - pred) <= 5.0 * sd + 0.05
 
 
-@pytest.mark.parametrize("mutant", list(range(1, oracle.N_MUTANTS + 1)))
+@pytest.mark.parametrize("mutant", oracle.PRIMARY_MUTANTS)
 def test_planted_mutations_are_caught(mutant):
     """Each planted mistake in the oracle (wrong sign, on-line side flipped,
     hits behind the origin accepted, entry edge taken for the exit) makes at

@@ -1,0 +1,229 @@
+"""Pins of the oracle's secondary rays (Sec. 5.2: a secondary ray starts where
+its parent hit a segment, in the final triangle of the parent's walk; here the
+mirror image of the parent).  The walk-chained paths are checked against the
+same paths by brute force over all segments, and both against closed forms:
+parallel mirrors, a 45-degree mirror, perpendicular incidence, the snapped
+origin's exact position, and the reflected direction's length."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+
+D = sg.D
+Q = 1 << 32
+NONE = oracle.BOUNCE_NONE
+
+
+def _locate(tri, ox, oy):
+    st = oracle.locate_bruteforce(tri, ox, oy)
+    assert (st >= 0).all(), "test origins must lie strictly inside a triangle"
+    return st
+
+
+def _rays(ox, oy, kx, ky):
+    ox, oy = np.asarray(ox, np.int32), np.asarray(oy, np.int32)
+    dx = (np.asarray(kx, np.float64) / 2 ** 22).astype(np.float32)
+    dy = (np.asarray(ky, np.float64) / 2 ** 22).astype(np.float32)
+    return ox, oy, dx, dy
+
+
+def _k(d):
+    return int(round(float(d) * 2 ** 22))
+
+
+def _equal_paths(W, B):
+    for key in ("hit", "org_x", "org_y", "dir_x", "dir_y"):
+        assert np.array_equal(W[key], B[key]), key
+    assert np.array_equal(W["t"], B["t"], equal_nan=True)
+
+
+def _path_ok(W, nb):
+    """Record structure: once a path ends, every later entry is 'no ray';
+    a path continues only after a hit."""
+    st, hit = W["steps"], W["hit"]
+    for b in range(1, nb + 1):
+        cont = st[b] != NONE
+        assert (hit[b - 1][cont] >= 0).all()
+        assert (st[b - 1][cont] > 0).all()
+        assert (st[b][st[b - 1] == NONE] == NONE).all()
+
+
+@pytest.mark.parametrize("scene", ["random", "room", "circles"])
+def test_bounce_walk_equals_bruteforce(scene):
+    """Walks chained through their final triangles give, ray by ray and
+    bounce by bounce, the paths found by brute force over all segments (hit,
+    t, snapped origin, mirror direction); the first ray of each path is the
+    primary walk of oracle.walk."""
+    if scene == "random":
+        segs = sg.random_segments(200, 5)
+    elif scene == "room":
+        segs = sg.room(150, 6)
+    else:
+        segs = sg.circles(3000, 7)
+    for tri in (sg.cdt(segs), sg.anneal(sg.refine_optimal(sg.cdt(segs)), 8, sweeps=2)):
+        r = sg.rays_isotropic(tri, 3000, 9)
+        nb = 8
+        W = oracle.bounce_walk(tri, r.ox, r.oy, r.dx, r.dy, r.start, nb)
+        B = oracle.bounce_bruteforce(tri, r.ox, r.oy, r.dx, r.dy, nb)
+        _equal_paths(W, B)
+        _path_ok(W, nb)
+        h, t, s = oracle.walk(tri, r.ox, r.oy, r.dx, r.dy, r.start)
+        assert np.array_equal(W["hit"][0], h) and np.array_equal(W["steps"][0], s)
+        assert np.array_equal(W["t"][0], t, equal_nan=True)
+        assert np.array_equal(W["org_x"][0], r.ox.astype(np.int64) << 32)
+        if scene == "room":
+            # closed room: most paths use every bounce
+            assert (W["steps"][nb] > 0).mean() > 0.5
+        assert (W["steps"][1] > 0).sum() > 300
+
+
+def _mirrors(y1=400_000, y2=600_000, m=1000):
+    return np.array([[m, y1, D - m, y1], [D - m, y2, m, y2]], np.int32)
+
+
+@pytest.mark.parametrize("refined", [False, True])
+def test_parallel_mirrors_closed_form(refined):
+    """Between two horizontal mirrors y = y1, y2 the path alternates between
+    them, the direction's vertical component flips exactly, every origin after
+    the first lies exactly on a mirror, each secondary ray's t is
+    (y2 - y1) / |d_y|, and the origins follow the exact zig-zag within the
+    snapping error."""
+    y1, y2 = 400_000, 600_000
+    segs = _mirrors(y1, y2)
+    tri = sg.cdt(segs)
+    if refined:
+        tri = sg.anneal(sg.refine_optimal(tri), 3, sweeps=2)
+    rng = np.random.default_rng(11)
+    n, nb = 64, 8
+    th = np.deg2rad(rng.uniform(78, 102, n)) * np.where(rng.random(n) < 0.5, 1, -1)
+    kx = np.array([_k(np.cos(a)) for a in th])
+    ky = np.array([_k(np.sin(a)) for a in th])
+    ox = rng.integers(480_000, 560_000, n)
+    oy = rng.integers(450_000, 550_000, n) | 1
+    ox, oy, dx, dy = _rays(ox, oy, kx, ky)
+    st = _locate(tri, ox, oy)
+    W = oracle.bounce_walk(tri, ox, oy, dx, dy, st, nb)
+    _equal_paths(W, oracle.bounce_bruteforce(tri, ox, oy, dx, dy, nb))
+    for i in range(n):
+        up = ky[i] > 0
+        x_exact = Fraction(int(ox[i]))
+        y_prev = int(oy[i])
+        for b in range(nb + 1):
+            assert W["steps"][b, i] > 0
+            sign = 1 if (b % 2 == 0) == up else -1
+            assert W["dir_x"][b, i] == dx[i] and W["dir_y"][b, i] == np.float32(sign * abs(dy[i]))
+            target = y2 if sign > 0 else y1
+            assert W["hit"][b, i] == (1 if sign > 0 else 0)
+            dist = abs(target - y_prev)
+            t_exact = Fraction(dist * 2 ** 22, abs(int(ky[i])))
+            assert abs(Fraction(float(W["t"][b, i])) - t_exact) <= t_exact * Fraction(1, 2 ** 23)
+            if b > 0:
+                assert W["org_y"][b, i] == y_prev * Q
+                err = abs(Fraction(int(W["org_x"][b, i]), Q) - x_exact)
+                assert err <= Fraction(b * (D - 2000), Q)
+            x_exact += t_exact * Fraction(int(kx[i]), 2 ** 22)
+            y_prev = target
+
+
+def test_diagonal_mirror_swaps_the_direction():
+    """A mirror along (1, 1) maps k = (kx, ky) to (ky, kx) exactly."""
+    segs = np.array([[300_000, 300_000, 700_000, 700_000]], np.int32)
+    tri = sg.cdt(segs)
+    rng = np.random.default_rng(12)
+    n = 400
+    ox = rng.integers(420_000, 620_000, n)
+    oy = ox - rng.integers(20_000, 100_000, n)
+    th = rng.uniform(0, 2 * np.pi, n)
+    kx = np.array([_k(np.cos(a)) for a in th])
+    ky = np.array([_k(np.sin(a)) for a in th])
+    ox, oy, dx, dy = _rays(ox, oy, kx, ky)
+    W = oracle.bounce_walk(tri, ox, oy, dx, dy, _locate(tri, ox, oy), 1)
+    on = W["hit"][0] == 0
+    assert on.sum() > 50
+    assert np.array_equal(W["dir_x"][1][on], dy[on]) and np.array_equal(W["dir_y"][1][on], dx[on])
+    # the mirror image travels away from the mirror: no second hit on it
+    assert (W["hit"][1][on] == -1).all()
+
+
+def test_perpendicular_incidence_returns_along_the_ray():
+    """A ray meeting a mirror at right angles comes back along itself (k' =
+    -k exactly) and then hits what the reversed primary ray hits, at the sum
+    of the two distances."""
+    segs = np.concatenate([_mirrors(), sg.random_segments(60, 13)[:, :]])
+    segs = segs[(np.minimum(segs[:, 1], segs[:, 3]) > 620_000) | (np.maximum(segs[:, 1], segs[:, 3]) < 380_000)
+                | (np.arange(len(segs)) < 2)]
+    tri = sg.cdt(segs)
+    n = 64
+    rng = np.random.default_rng(14)
+    ox = rng.integers(5000, D - 5000, n)
+    oy = rng.integers(410_000, 590_000, n) | 1
+    k = 1 << 22
+    ky = np.where(rng.random(n) < 0.5, k, -k)
+    ox, oy, dx, dy = _rays(ox, oy, np.zeros(n, int), ky)
+    W = oracle.bounce_walk(tri, ox, oy, dx, dy, _locate(tri, ox, oy), 2)
+    assert np.array_equal(W["dir_y"][1], -dy) and (W["dir_x"][1] == 0).all()
+    hb, tb = oracle.closest_bruteforce(segs, ox, oy, -dx, -dy)
+    assert np.array_equal(W["hit"][1], hb)
+    np.testing.assert_allclose(W["t"][1], W["t"][0] + tb, rtol=1e-6)
+    # the snapped origin: a dyadic parameter of the mirror, within |e| / 2 units of 2^-32
+    assert (np.abs(W["org_x"][1] - ox.astype(np.int64) * Q) <= (D - 2000) // 2).all()
+
+
+def test_snapped_origins_lie_on_the_hit_segment():
+    """Each secondary origin lies exactly on the hit segment, strictly between
+    its endpoints, within |segment| 2^-32 of the exact hit point of its
+    parent; the reflected direction keeps the length of k within rounding."""
+    segs = sg.room(100, 15)
+    tri = sg.anneal(sg.refine_optimal(sg.cdt(segs)), 15, sweeps=2)
+    r = sg.rays_isotropic(tri, 400, 16)
+    nb = 6
+    W = oracle.bounce_walk(tri, r.ox, r.oy, r.dx, r.dy, r.start, nb)
+    checked = 0
+    for b in range(nb):
+        for i in np.nonzero(W["steps"][b + 1] > 0)[0]:
+            s = int(W["hit"][b, i])
+            ax, ay, bx, by = (int(v) for v in segs[s])
+            X, Y = Fraction(int(W["org_x"][b, i]), Q), Fraction(int(W["org_y"][b, i]), Q)
+            kx, ky = _k(W["dir_x"][b, i]), _k(W["dir_y"][b, i])
+            ex, ey = bx - ax, by - ay
+            t = Fraction(ex * (ay - Y) - ey * (ax - X)) / Fraction(ex * ky - ey * kx)
+            hx, hy = X + t * kx, Y + t * ky  # exact hit point (t in units of k)
+            X2, Y2 = Fraction(int(W["org_x"][b + 1, i]), Q), Fraction(int(W["org_y"][b + 1, i]), Q)
+            assert ex * (Y2 - ay) - ey * (X2 - ax) == 0
+            lam = ((X2 - ax) * ex + (Y2 - ay) * ey) / (ex * ex + ey * ey)
+            assert 0 < lam < 1
+            bound = Fraction(ex * ex + ey * ey) / Fraction(Q * Q)
+            assert (X2 - hx) ** 2 + (Y2 - hy) ** 2 <= bound
+            k2x, k2y = _k(W["dir_x"][b + 1, i]), _k(W["dir_y"][b + 1, i])
+            assert abs(np.hypot(k2x, k2y) - np.hypot(kx, ky)) <= 1.0
+            # the mirror image points back to the parent's side
+            assert (ex * ky - ey * kx) * (ex * k2y - ey * k2x) < 0
+            checked += 1
+    assert checked > 500
+
+
+@pytest.mark.parametrize("mutant", oracle.BOUNCE_MUTANTS)
+def test_planted_bounce_mutations_are_caught(mutant):
+    """Each planted mistake in the secondary-ray construction (the incoming
+    direction added instead of subtracted; the snapped parameter measured from
+    the wrong endpoint) fails a closed-form pin."""
+    failed = []
+    for fn in (test_parallel_mirrors_closed_form, test_snapped_origins_lie_on_the_hit_segment):
+        real = oracle._libs.get(0)
+        try:
+            oracle._libs[0] = oracle._load(mutant)
+            if fn is test_parallel_mirrors_closed_form:
+                fn(False)
+            else:
+                fn()
+        except AssertionError:
+            failed.append(fn.__name__)
+        finally:
+            if real is not None:
+                oracle._libs[0] = real
+            else:
+                oracle._libs.pop(0, None)
+    assert failed
