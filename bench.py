@@ -140,6 +140,22 @@ def cpu_oracle_rate(work, seconds_target=12.0):
     return n2 * len(work) / dt, threads, n2, dt
 
 
+def cpu_oracle_bounce_rate(work, n=1 << 15):
+    """Oracle mirror paths (8 bounces, given start cells) on all host cores over
+    the first n rays of every scene: walked rays per second."""
+    import oracle
+
+    threads = os.cpu_count() or 1
+    walked = 0
+    t0 = time.perf_counter()
+    for w in work:
+        tri, r = w[3], w[4]
+        p = oracle.bounce_walk(tri, r.ox[:n], r.oy[:n], r.dx[:n], r.dy[:n], r.start[:n], N_BOUNCE, n_threads=threads)
+        walked += int((p["steps"] != oracle.BOUNCE_NONE).sum())
+    dt = time.perf_counter() - t0
+    return walked / dt, threads, n, dt
+
+
 def job_step_ms(dist, ms: float, device=None) -> float:
     """The job's time per step under N replicas: every rank times its own steps,
     then the slowest rank's time is the job's (barrier + all-reduce MAX; no
@@ -287,6 +303,52 @@ def comparison_structures(torch, cct, sg, sc, dev, stream, n_timed):
 
 
 # ---------------------------------------------------------------------------------------------- configs 3-5
+N_BOUNCE = 8
+N_BOUNCE_RAYS = 1 << 22
+
+
+def secondary_rays(torch, cct, scenes, dev, stream, gather_bps, k_rep):
+    """Mirror paths (cct_trace_bounces: each secondary ray starts in the final
+    triangle of its parent's walk, Sec. 5.2) of the first 2^22 rays of each
+    scene with up to 8 bounces; event-timed per scene.  The primary records
+    are checked against cct_trace's results."""
+    out, tot_ms, tot_rays, tot_steps, tot_bytes_over_peak = {}, 0.0, 0, 0, 0.0
+    for sc in scenes:
+        d = sc["d"]
+        m = N_BOUNCE_RAYS
+        args = (d["ox"][:m], d["oy"][:m], d["dx"][:m], d["dy"][:m], N_BOUNCE)
+        res = sc["scene"].trace_bounces(*args, start=d["start"][:m], stream=stream, with_rays=False)
+        h, _, s_ = sc["scene"].trace(d["ox"][:m], d["oy"][:m], d["dx"][:m], d["dy"][:m], d["start"][:m],
+                                     stream=stream)
+        torch.cuda.synchronize(dev)
+        if not (torch.equal(res["hit"][0], h) and torch.equal(res["steps"][0], s_)):
+            raise RuntimeError("primary records of the mirror paths differ from cct_trace")
+        full = float((res["steps"][N_BOUNCE] > 0).float().mean())
+        sc["scene"].stats(reset=True)
+        ms = _time_loop(torch, dev, stream,
+                        lambda sc=sc: sc["scene"].trace_bounces(*args, start=d["start"][:m], stream=stream,
+                                                                with_rays=False), k_rep)
+        st = sc["scene"].stats(reset=True)
+        rays, steps = st["rays"] / k_rep, st["steps"] / k_rep
+        # 32 B per triangle visited, 20 B per primary ray in, 12 B per record out
+        alg = 32.0 * steps + 20.0 * m + 12.0 * m * (N_BOUNCE + 1)
+        bps = gather_bps[sc["name"]]
+        out[sc["name"]] = {"ms": ms, "walked_rays_per_s": rays / (ms * 1e-3), "steps_per_walked_ray": steps / rays,
+                           "walked_rays_per_path": rays / m, "paths_using_every_bounce": full,
+                           "gather_frac": alg / (ms * 1e-3) / bps}
+        tot_ms += ms
+        tot_rays += rays
+        tot_steps += steps
+        tot_bytes_over_peak += alg / bps
+    return {"n_bounce": N_BOUNCE, "primary_rays_per_scene": N_BOUNCE_RAYS,
+            "walked_rays_per_s": tot_rays / (tot_ms * 1e-3), "steps_per_walked_ray": tot_steps / tot_rays,
+            "gather_frac": tot_bytes_over_peak / (tot_ms * 1e-3),
+            "kernel": "bounce_kernel: one path per lane, exact int64 side tests on 2^-32 origins",
+            "reading": "mirror reflection about the hit segment; origin snapped onto the hit edge at a 2^-32 "
+                       "parameter; start cell = the parent's final triangle (no locate)",
+            "per_scene": out}
+
+
 def _parallel(fn, items, workers=None):
     from concurrent.futures import ThreadPoolExecutor
 
@@ -867,6 +929,7 @@ def main():
                            "length_annealed_over_cdt": sc["tri"].length(True) / sc["cdt"].length(True),
                            "length_refined_over_cdt": sc["ref"].length(True) / sc["cdt"].length(True),
                            "walk_l2_frac": (alg / (wms * 1e-3)) / bps, "gather_peak_gbs": bps / 1e9}
+    secondary = secondary_rays(torch, cct, scenes, dev, stream, gather_bps, max(3, args.steps // 10))
     achieved = alg_per_launch / (launch_ms * 1e-3) / 1e9
     l2_peak = 1.0 / share_over_peak / 1e9  # byte-weighted gather peak over the scenes' table sizes
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -987,13 +1050,17 @@ def main():
             "walk_steps_per_ray_mean_over_scenes": float(np.mean([p["steps_per_ray"] for p in per.values()])),
             "fallback_rate": tot["exact_fallbacks"] / max(1, tot["side_tests"]),
             "locate_steps_per_ray": tot["locate_steps"] / max(1, tot["located"]),
-            "per_scene": per, "roofline": roofline, "e2e": e2e,
+            "per_scene": per, "roofline": roofline, "e2e": e2e, "secondary_rays": secondary,
             "gpu_launches": args.steps}
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample_n, dt = cpu_oracle_rate(work)
         line["cpu_baseline"] = {"value": rate, "unit": "rays/s", "cores": cores, "kind": "oracle",
                                 "sample": f"oracle walk from given start cells over the first {sample_n} rays of "
                                           f"each of the {len(work)} scenes ({dt:.1f} s wall)"}
+        brate, bcores, bn, bdt = cpu_oracle_bounce_rate(work)
+        secondary["cpu_oracle"] = {"value": brate, "unit": "walked rays/s", "cores": bcores, "kind": "oracle",
+                                   "sample": f"oracle mirror paths ({N_BOUNCE} bounces) of the first {bn} rays of "
+                                             f"each of the {len(work)} scenes ({bdt:.1f} s wall)"}
     if rank == 0:
         line["clocks"] = clk.summary()
         print(json.dumps(line))

@@ -60,6 +60,7 @@ extern "C" {
 #define CCT_RAY_INVALID -1    /* direction off the 2^-22 grid, |component| > 1, zero, or the
                                  start triangle does not strictly contain the origin */
 #define CCT_RAY_WALK_LIMIT -2 /* more than n_tri + 8 steps (only on a corrupt triangulation) */
+#define CCT_RAY_NONE -3       /* cct_trace_bounces: no ray at this bounce (the path ended before it) */
 
 /* ------------------------------------------------------------------ flags */
 /* cct_scene_load */
@@ -222,6 +223,45 @@ int cct_trace(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy, const f
 int cct_trace_noalloc(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy, const float* d_dx,
                       const float* d_dy, const int32_t* d_start_tri, int64_t n, int32_t* d_hit_seg, float* d_t,
                       int32_t* d_steps, uint32_t flags, void* stream);
+
+/* Mirror paths of n primary rays (Sec. 5.2: a secondary ray starts where its
+ * parent hit the geometry, and the final triangle of the parent's walk is its
+ * start triangle, so secondary rays need no locate).  Each primary ray (inputs
+ * and start cells as cct_trace; d_start_tri NULL = located first) is followed
+ * by up to n_bounce secondary rays, each the mirror image of its parent about
+ * the hit segment:
+ *   origin     the parent's exact hit point moved onto the hit constrained
+ *              edge (a -> b) of the final triangle (a right of the parent ray,
+ *              b left or on its line): a + (i / 2^32)(b - a),
+ *              i = round(2^32 mu) (halves up) clamped to [1, 2^32 - 1], mu the
+ *              exact parameter of the hit point on the edge;
+ *   direction  k' = 2 (k.u) u / |u|^2 - k for k = 2^22 d and u = b - a,
+ *              rounded to integers (halves up), clamped to [-2^22, 2^22],
+ *              then d' = k' / 2^22;
+ *   walk       Sec. 5.1 from that triangle, entered through the hit edge; the
+ *              side rule, hit rule and tie order of cct_trace apply with the
+ *              origin in units of 2^-32 (all decisions exact).
+ * A path ends at a miss, an invalid primary ray, a walk limit, after n_bounce
+ * secondary rays, or when k' does not point strictly back to the parent's side
+ * of the segment (a grazing reflection).
+ * Outputs (device, (1 + n_bounce) * n entries, entry b * n + r for ray b of
+ * path r; b = 0 is the primary ray): d_hit_seg, d_t, d_steps as cct_trace, and
+ * CCT_RAY_NONE in d_steps (hit -1, t NaN) where the path ended earlier.
+ * Optional outputs (NULL: not written): d_org_x, d_org_y = the ray's origin in
+ * units of 2^-32 (int64; 0 where there is no ray or the primary ray is
+ * invalid), d_dir_x, d_dir_y = its direction (0 likewise).
+ * Launch: blocks of 256 threads, one path per lane; the scene tuning's chunk
+ * applies.  flags: 0 or CCT_TRACE_EXACT_ONLY (every decision is exact here).  Scratch
+ * (a work counter, located start cells) comes from the stream-ordered
+ * allocator on `stream`.  n = 0 is a no-op.
+ * Errors: CCT_ERR_INVALID_ARGUMENT (n < 0, n_bounce outside
+ * [0, CCT_MAX_BOUNCES], other flags, a null required pointer),
+ * CCT_ERR_OUT_OF_MEMORY, CCT_ERR_CUDA. */
+#define CCT_MAX_BOUNCES 1024
+int cct_trace_bounces(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy, const float* d_dx,
+                      const float* d_dy, const int32_t* d_start_tri, int64_t n, int32_t n_bounce, int32_t* d_hit_seg,
+                      float* d_t, int32_t* d_steps, int64_t* d_org_x, int64_t* d_org_y, float* d_dir_x,
+                      float* d_dir_y, uint32_t flags, void* stream);
 
 /* Copies the scene's counters to *out after waiting for `stream`; reset != 0
  * zeroes them afterwards.  Errors: CCT_ERR_INVALID_ARGUMENT, CCT_ERR_CUDA. */

@@ -22,6 +22,8 @@ CCT_ERR_NO_DEVICE = -6
 CCT_ERR_IO = -7
 CCT_RAY_INVALID = -1
 CCT_RAY_WALK_LIMIT = -2
+CCT_RAY_NONE = -3
+CCT_MAX_BOUNCES = 1024
 CCT_LOAD_NO_REORDER = 1
 CCT_LOAD_NO_VALIDATE = 2
 
@@ -136,6 +138,8 @@ def lib() -> ctypes.CDLL:
     L.cct_kdtree_free.argtypes = [vp]
     L.cct_trace_kdtree.restype = ctypes.c_int
     L.cct_trace_kdtree.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    L.cct_trace_bounces.restype = ctypes.c_int
+    L.cct_trace_bounces.argtypes = [vp, vp, vp, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, u32, vp]
     L.cct_trace_noalloc.restype = ctypes.c_int
     L.cct_trace_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, u32, vp]
     L.cct_get_stats.restype = ctypes.c_int
@@ -270,6 +274,30 @@ def cct_trace_noalloc(scene: int, ox, oy, dx, dy, start, hit, t, steps, flags: i
                                    _stream_ptr(stream)), "cct_trace_noalloc")
 
 
+def cct_trace_bounces(scene: int, ox, oy, dx, dy, start, n_bounce: int, hit, t, steps, org_x=None, org_y=None,
+                      dir_x=None, dir_y=None, flags: int = 0, stream=None) -> None:
+    """Mirror paths (include/cct.h): outputs hold (1 + n_bounce) * n entries,
+    entry b * n + r for ray b of path r; org_*, dir_* are optional."""
+    import torch
+
+    n = ox.numel()
+    for a in (oy, dx, dy) + ((start,) if start is not None else ()):
+        if a.numel() != n:
+            raise ValueError("all ray tensors must have the same length")
+    m = (int(n_bounce) + 1) * n
+    for a in (hit, t, steps, org_x, org_y, dir_x, dir_y):
+        if a is not None and a.numel() != m:
+            raise ValueError("result tensors must hold (1 + n_bounce) * n entries")
+    _check(lib().cct_trace_bounces(ctypes.c_void_p(scene), _dev(ox, torch.int32, "ox"), _dev(oy, torch.int32, "oy"),
+                                   _dev(dx, torch.float32, "dx"), _dev(dy, torch.float32, "dy"),
+                                   _dev(start, torch.int32, "start"), n, int(n_bounce),
+                                   _dev(hit, torch.int32, "hit"), _dev(t, torch.float32, "t"),
+                                   _dev(steps, torch.int32, "steps"), _dev(org_x, torch.int64, "org_x"),
+                                   _dev(org_y, torch.int64, "org_y"), _dev(dir_x, torch.float32, "dir_x"),
+                                   _dev(dir_y, torch.float32, "dir_y"), flags, _stream_ptr(stream)),
+           "cct_trace_bounces")
+
+
 def cct_get_stats(scene: int, reset: bool = False, stream=None) -> dict:
     s = _Stats()
     _check(lib().cct_get_stats(ctypes.c_void_p(scene), ctypes.byref(s), 1 if reset else 0, _stream_ptr(stream)),
@@ -321,6 +349,26 @@ class Scene:
                    torch.empty(n, dtype=torch.float32, device=ox.device),
                    torch.empty(n, dtype=torch.int32, device=ox.device))
         cct_trace(self.handle, ox, oy, dx, dy, start, out[0], out[1], out[2], flags, stream)
+        return out
+
+    def trace_bounces(self, ox, oy, dx, dy, n_bounce: int, start=None, flags: int = 0, stream=None,
+                      with_rays: bool = True):
+        """Mirror paths: dict of (1 + n_bounce, n) tensors hit, t, steps (and
+        org_x, org_y, dir_x, dir_y when with_rays)."""
+        import torch
+
+        n, dev = ox.numel(), ox.device
+        shape = (int(n_bounce) + 1, n)
+        out = dict(hit=torch.empty(shape, dtype=torch.int32, device=dev),
+                   t=torch.empty(shape, dtype=torch.float32, device=dev),
+                   steps=torch.empty(shape, dtype=torch.int32, device=dev))
+        if with_rays:
+            out.update(org_x=torch.empty(shape, dtype=torch.int64, device=dev),
+                       org_y=torch.empty(shape, dtype=torch.int64, device=dev),
+                       dir_x=torch.empty(shape, dtype=torch.float32, device=dev),
+                       dir_y=torch.empty(shape, dtype=torch.float32, device=dev))
+        cct_trace_bounces(self.handle, ox, oy, dx, dy, start, n_bounce, out["hit"], out["t"], out["steps"],
+                          out.get("org_x"), out.get("org_y"), out.get("dir_x"), out.get("dir_y"), flags, stream)
         return out
 
     def locate(self, ox, oy, stream=None):
