@@ -19,6 +19,9 @@
 // (A(v) is an integer): one exact int64 product pair and a compare per step,
 // with ch computed once per ray of the path.  For a primary ray ch is
 // kx oy - ky ox and the test is the walk kernel's.  No fp32 filter is needed.
+// The snapped parameter and the mirror direction are exact quotients whose
+// remainders are small: they are found in int64 arithmetic modulo 2^64 from
+// fp32 estimates (floordiv_mod); only t's numerator is formed in 128 bits.
 //
 // One path per lane.  A lane whose ray left its triangle through a hull or
 // constrained edge waits (pending) until kBounceServeMin lanes of the warp are
@@ -75,31 +78,44 @@ __device__ __forceinline__ float i128_to_float(i128 v) {
   return neg ? -f : f;
 }
 
-// floor(num / den) for den > 0.  Each fp32 estimate of the remaining
-// quotient is within 2^-21 relative plus 1: with |num / den| < 2^41 two
-// estimates (kTwo) leave it within 2 of the quotient, with |num / den| < 2^24
-// one does; exact int128 corrections finish.
-template <bool kTwo>
-__device__ __forceinline__ long long floordiv_exact(i128 num, long long den, float fd) {
-  long long q = __float2ll_rd(__fdiv_rn(i128_to_float(num), fd));
-  i128 r = num - (i128)q * den;
-  if (kTwo) {
-    q += __float2ll_rd(__fdiv_rn(i128_to_float(r), fd));
-    r = num - (i128)q * den;
+// floor(m / d) for d > 0 when the quotient is known to lie in [lo, hi]
+// (|lo|, |hi| < 2^40), m is given modulo 2^64 (mm) and approximately (mf, an
+// fp32 value whose error divided by d is below 2^40).  The first estimate is
+// clamped to [lo, hi], so its remainder m - q d is below 2^63 in magnitude and
+// equals its value modulo 2^64; each further estimate of the remaining
+// quotient is within 2^-21 relative plus 1, so after two of them the quotient
+// is within 2 and exact int64 corrections finish.
+__device__ __forceinline__ long long floordiv_mod(unsigned long long mm, float mf, long long d, long long lo,
+                                                 long long hi) {
+  const float rd = __frcp_rn(__ll2float_rn(d));
+  long long q = __float2ll_rd(__fmul_rn(mf, rd));
+  q = q < lo ? lo : (q > hi ? hi : q);
+  long long r = (long long)(mm - (unsigned long long)q * (unsigned long long)d);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    q += __float2ll_rd(__fmul_rn(__ll2float_rn(r), rd));
+    r = (long long)(mm - (unsigned long long)q * (unsigned long long)d);
   }
   while (r < 0) {
     --q;
-    r += den;
+    r += d;
   }
-  while (r >= den) {
+  while (r >= d) {
     ++q;
-    r -= den;
+    r -= d;
   }
   return q;
 }
 
-// ceil(c / 2^32) = -floor(-c / 2^32) (arithmetic shift = floor)
-__device__ __forceinline__ long long ceil_q(i128 c) { return -(long long)((-c) >> 32); }
+// ceil((kx Y - ky X) / 2^32) from the 32-bit halves of X and Y (no 128-bit
+// product): with X = Xh 2^32 + Xl, the value is (kx Yh - ky Xh) + ceil(B / 2^32),
+// B = kx Yl - ky Xl (|B| < 2^55).
+__device__ __forceinline__ long long ceil_cross_q(int kx, int ky, long long X, long long Y) {
+  const long long Xh = X >> 32, Yh = Y >> 32;
+  const long long Xl = X & 0xffffffffll, Yl = Y & 0xffffffffll;
+  const long long B = (long long)kx * Yl - (long long)ky * Xl;
+  return ((long long)kx * Yh - (long long)ky * Xh) - ((-B) >> 32);
+}
 
 // Four blocks per SM (64 registers, no spills): 1.07-1.17x faster than the
 // compiler's 76 registers at three blocks (more warps to hide the gathers).
@@ -142,6 +158,7 @@ __global__ void __launch_bounds__(kBounceThreads, 4) bounce_kernel(SceneDev S, B
   // neighbour word is w (< 0): a miss, or a hit that may start the next ray.
   auto finish = [&](int T, int e, int32_t w) {
     c_steps += (unsigned)ns;
+    c_sides += (unsigned)ns + (b == 0 ? 2u : 0u);  // one side per triangle, three in a primary's first
     if (w == -1) {
       record(b, -1, __int_as_float(0x7f800000), ns, true);
       end_path(b + 1);
@@ -151,8 +168,9 @@ __global__ void __launch_bounds__(kBounceThreads, 4) bounce_kernel(SceneDev S, B
     const int ia = (e == 2) ? 0 : e + 1, ib = (e == 0) ? 2 : e - 1;
     const long long ax = vx_of(r, ia), ay = vy_of(r, ia), bx = vx_of(r, ib), by = vy_of(r, ib);
     const long long ex = bx - ax, ey = by - ay;
+    const long long Rx = X - (ax << 32), Ry = Y - (ay << 32);  // P - a in units of 2^-32
     // t = cross(e, a - P) / cross(e, d) = 2^22 num / (2^32 den)
-    i128 num = ((i128)(ex * ay - ey * ax) << 32) - ((i128)ex * Y - (i128)ey * X);
+    i128 num = (i128)ey * Rx - (i128)ex * Ry;
     long long den = ex * ky - ey * kx;
     if (den < 0) {
       num = -num;
@@ -164,23 +182,27 @@ __global__ void __launch_bounds__(kBounceThreads, 4) bounce_kernel(SceneDev S, B
       act = false;
       return;
     }
-    // the next origin on the edge: 2^32 mu = (C - 2^32 A(a)) / (A(b) - A(a))
-    const long long Aa = (long long)kx * ay - (long long)ky * ax, Ab = (long long)kx * by - (long long)ky * bx;
-    i128 nmu = ((i128)kx * Y - (i128)ky * X) - ((i128)Aa << 32);
-    long long dmu = Ab - Aa;
-    if (dmu < 0) {
-      nmu = -nmu;
-      dmu = -dmu;
-    }
-    long long i = floordiv_exact<true>(2 * nmu + dmu, 2 * dmu, __ll2float_rn(2 * dmu));
+    // the next origin on the edge: 2^32 mu = N / Dd, N = k x (P - a) in units of
+    // 2^-32 (|N| < 2^75), Dd = k x (b - a) > 0; i = floor((2 N + Dd) / (2 Dd)) in [0, 2^32]
+    const long long Dd = (long long)kx * ey - (long long)ky * ex;
+    const unsigned long long Nm = (unsigned long long)(long long)kx * (unsigned long long)Ry -
+                                  (unsigned long long)(long long)ky * (unsigned long long)Rx;
+    const float Nf = __fmaf_rn((float)kx, __ll2float_rn(Ry), -__fmul_rn((float)ky, __ll2float_rn(Rx)));
+    long long i = floordiv_mod(2ull * Nm + (unsigned long long)Dd, __fmaf_rn(2.0f, Nf, __ll2float_rn(Dd)), 2 * Dd, 0,
+                               kQ);
     i = i < 1 ? 1 : (i > kQ - 1 ? kQ - 1 : i);
-    // mirror direction about u = b - a
+    // mirror direction about u = b - a: k' = floor((2 n + uu) / (2 uu)), n = 2 (k.u) u - uu k,
+    // |k'| <= 2^22.5
     const long long ku = (long long)kx * ex + (long long)ky * ey, uu = ex * ex + ey * ey;
-    const i128 nx = 2 * (i128)ku * ex - (i128)uu * kx, ny = 2 * (i128)ku * ey - (i128)uu * ky;
-    const float fuu = __ll2float_rn(2 * uu);
-    long long k2x = floordiv_exact<false>(2 * nx + uu, 2 * uu, fuu);
-    long long k2y = floordiv_exact<false>(2 * ny + uu, 2 * uu, fuu);
+    const float kuf = __ll2float_rn(ku), uuf = __ll2float_rn(uu);
+    const unsigned long long ku2 = 2ull * (unsigned long long)ku, uum = (unsigned long long)uu;
+    const unsigned long long mxm = 2ull * (ku2 * (unsigned long long)ex - uum * (unsigned long long)(long long)kx) + uum;
+    const unsigned long long mym = 2ull * (ku2 * (unsigned long long)ey - uum * (unsigned long long)(long long)ky) + uum;
+    const float mxf = __fmaf_rn(2.0f, __fmaf_rn(2.0f * kuf, (float)ex, -__fmul_rn(uuf, (float)kx)), uuf);
+    const float myf = __fmaf_rn(2.0f, __fmaf_rn(2.0f * kuf, (float)ey, -__fmul_rn(uuf, (float)ky)), uuf);
     constexpr long long kLim = 1ll << 22;
+    long long k2x = floordiv_mod(mxm, mxf, 2 * uu, -2 * kLim, 2 * kLim);
+    long long k2y = floordiv_mod(mym, myf, 2 * uu, -2 * kLim, 2 * kLim);
     k2x = k2x > kLim ? kLim : (k2x < -kLim ? -kLim : k2x);
     k2y = k2y > kLim ? kLim : (k2y < -kLim ? -kLim : k2y);
     const long long c0 = ex * ky - ey * kx, c1 = ex * k2y - ey * k2x;
@@ -192,7 +214,7 @@ __global__ void __launch_bounds__(kBounceThreads, 4) bounce_kernel(SceneDev S, B
     Y = (ay << 32) + i * ey;
     kx = (int)k2x;
     ky = (int)k2y;
-    ch = ceil_q((i128)kx * Y - (i128)ky * X);
+    ch = ceil_cross_q(kx, ky, X, Y);
     ++b;
     ns = 0;
     h = 3 * T + e;  // enter T again through the hit edge
@@ -234,7 +256,6 @@ __global__ void __launch_bounds__(kBounceThreads, 4) bounce_kernel(SceneDev S, B
     const bool s2 = (long long)kx * vy_of(r, 2) - (long long)ky * vx_of(r, 2) >= ch;
     const int e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
     const int32_t w = nb_of(r, e);
-    c_sides += 3;
     ns = 1;
     act = true;
     if (w >= 0) {
@@ -287,12 +308,12 @@ __global__ void __launch_bounds__(kBounceThreads, 4) bounce_kernel(SceneDev S, B
       const int4 q = load_he(he_tab + h);
       const bool sc = (long long)kx * coord_of_word(q.y) - (long long)ky * coord_of_word(q.x) >= ch;
       ++ns;
-      ++c_sides;
       const int32_t w = sc ? q.z : q.w;
       if (w >= 0 && ns < max_steps) {
         h = w;
       } else if (w >= 0) {
         ++c_lim;
+        c_sides += (unsigned)ns + (b == 0 ? 2u : 0u);
         record(b, -1, __int_as_float(0x7fc00000), CCT_RAY_WALK_LIMIT, true);
         end_path(b + 1);
       } else {
