@@ -32,6 +32,7 @@
 // path across bounces: the next ray continues from 3 T + e in registers.
 #include <algorithm>
 
+#include "bounce_arith.cuh"
 #include "cct_internal.cuh"
 
 namespace cct {
@@ -44,7 +45,6 @@ constexpr int kBounceThreads = 256;
 // a closed room and a dash grid at 8 bounces (3.4x faster than serving every
 // finished ray at once).
 constexpr int kBounceServeMin = 24;
-constexpr long long kQ = 1ll << 32;
 
 typedef __int128 i128;
 
@@ -76,45 +76,6 @@ __device__ __forceinline__ float i128_to_float(i128 v) {
   const unsigned long long hi = (unsigned long long)(m >> 64), lo = (unsigned long long)m;
   const float f = hi ? __fmaf_rn(__ull2float_rn(hi), 18446744073709551616.0f, __ull2float_rn(lo)) : __ull2float_rn(lo);
   return neg ? -f : f;
-}
-
-// floor(m / d) for d > 0 when the quotient is known to lie in [lo, hi]
-// (|lo|, |hi| < 2^40), m is given modulo 2^64 (mm) and approximately (mf, an
-// fp32 value whose error divided by d is below 2^40).  The first estimate is
-// clamped to [lo, hi], so its remainder m - q d is below 2^63 in magnitude and
-// equals its value modulo 2^64; each further estimate of the remaining
-// quotient is within 2^-21 relative plus 1, so after two of them the quotient
-// is within 2 and exact int64 corrections finish.
-__device__ __forceinline__ long long floordiv_mod(unsigned long long mm, float mf, long long d, long long lo,
-                                                 long long hi) {
-  const float rd = __frcp_rn(__ll2float_rn(d));
-  long long q = __float2ll_rd(__fmul_rn(mf, rd));
-  q = q < lo ? lo : (q > hi ? hi : q);
-  long long r = (long long)(mm - (unsigned long long)q * (unsigned long long)d);
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    q += __float2ll_rd(__fmul_rn(__ll2float_rn(r), rd));
-    r = (long long)(mm - (unsigned long long)q * (unsigned long long)d);
-  }
-  while (r < 0) {
-    --q;
-    r += d;
-  }
-  while (r >= d) {
-    ++q;
-    r -= d;
-  }
-  return q;
-}
-
-// ceil((kx Y - ky X) / 2^32) from the 32-bit halves of X and Y (no 128-bit
-// product): with X = Xh 2^32 + Xl, the value is (kx Yh - ky Xh) + ceil(B / 2^32),
-// B = kx Yl - ky Xl (|B| < 2^55).
-__device__ __forceinline__ long long ceil_cross_q(int kx, int ky, long long X, long long Y) {
-  const long long Xh = X >> 32, Yh = Y >> 32;
-  const long long Xl = X & 0xffffffffll, Yl = Y & 0xffffffffll;
-  const long long B = (long long)kx * Yl - (long long)ky * Xl;
-  return ((long long)kx * Yh - (long long)ky * Xh) - ((-B) >> 32);
 }
 
 // Four blocks per SM (64 registers, no spills): 1.07-1.17x faster than the
@@ -182,39 +143,18 @@ __global__ void __launch_bounds__(kBounceThreads, 4) bounce_kernel(SceneDev S, B
       act = false;
       return;
     }
-    // the next origin on the edge: 2^32 mu = N / Dd, N = k x (P - a) in units of
-    // 2^-32 (|N| < 2^75), Dd = k x (b - a) > 0; i = floor((2 N + Dd) / (2 Dd)) in [0, 2^32]
-    const long long Dd = (long long)kx * ey - (long long)ky * ex;
-    const unsigned long long Nm = (unsigned long long)(long long)kx * (unsigned long long)Ry -
-                                  (unsigned long long)(long long)ky * (unsigned long long)Rx;
-    const float Nf = __fmaf_rn((float)kx, __ll2float_rn(Ry), -__fmul_rn((float)ky, __ll2float_rn(Rx)));
-    long long i = floordiv_mod(2ull * Nm + (unsigned long long)Dd, __fmaf_rn(2.0f, Nf, __ll2float_rn(Dd)), 2 * Dd, 0,
-                               kQ);
-    i = i < 1 ? 1 : (i > kQ - 1 ? kQ - 1 : i);
-    // mirror direction about u = b - a: k' = floor((2 n + uu) / (2 uu)), n = 2 (k.u) u - uu k,
-    // |k'| <= 2^22.5
-    const long long ku = (long long)kx * ex + (long long)ky * ey, uu = ex * ex + ey * ey;
-    const float kuf = __ll2float_rn(ku), uuf = __ll2float_rn(uu);
-    const unsigned long long ku2 = 2ull * (unsigned long long)ku, uum = (unsigned long long)uu;
-    const unsigned long long mxm = 2ull * (ku2 * (unsigned long long)ex - uum * (unsigned long long)(long long)kx) + uum;
-    const unsigned long long mym = 2ull * (ku2 * (unsigned long long)ey - uum * (unsigned long long)(long long)ky) + uum;
-    const float mxf = __fmaf_rn(2.0f, __fmaf_rn(2.0f * kuf, (float)ex, -__fmul_rn(uuf, (float)kx)), uuf);
-    const float myf = __fmaf_rn(2.0f, __fmaf_rn(2.0f * kuf, (float)ey, -__fmul_rn(uuf, (float)ky)), uuf);
-    constexpr long long kLim = 1ll << 22;
-    long long k2x = floordiv_mod(mxm, mxf, 2 * uu, -2 * kLim, 2 * kLim);
-    long long k2y = floordiv_mod(mym, myf, 2 * uu, -2 * kLim, 2 * kLim);
-    k2x = k2x > kLim ? kLim : (k2x < -kLim ? -kLim : k2x);
-    k2y = k2y > kLim ? kLim : (k2y < -kLim ? -kLim : k2y);
-    const long long c0 = ex * ky - ey * kx, c1 = ex * k2y - ey * k2x;
-    if (!((c0 > 0 && c1 < 0) || (c0 < 0 && c1 > 0))) {
+    // the next origin on the edge and the mirror direction
+    const long long i = bounce::snap_param(kx, ky, Rx, Ry, ex, ey);
+    int k2x, k2y;
+    if (!bounce::mirror_dir(kx, ky, ex, ey, k2x, k2y)) {
       end_path(b + 1);
       return;
     }
     X = (ax << 32) + i * ex;
     Y = (ay << 32) + i * ey;
-    kx = (int)k2x;
-    ky = (int)k2y;
-    ch = ceil_cross_q(kx, ky, X, Y);
+    kx = k2x;
+    ky = k2y;
+    ch = bounce::ceil_cross_q(kx, ky, X, Y);
     ++b;
     ns = 0;
     h = 3 * T + e;  // enter T again through the hit edge
