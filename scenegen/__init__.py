@@ -84,6 +84,8 @@ def _load():
     L.sg_refine.argtypes = [vp, dbl, dbl, i64]
     L.sg_subdivide.restype = i64
     L.sg_subdivide.argtypes = [vp]
+    L.sg_fuzzy_objective.restype = None
+    L.sg_fuzzy_objective.argtypes = [vp, dbl, dbl, dbl, dbl, dbl, ctypes.c_int32, vp, vp]
     L.sg_refine_optimal.restype = vp
     L.sg_refine_optimal.argtypes = [vp, vp, i32, vp, i32, i64, i32, P(dbl), P(dbl)]
     L.sg_bvh_build.restype = vp
@@ -281,6 +283,26 @@ def anneal(tri: Triangulation, seed: int, sweeps=20.0, T0=0.02, T1=1e-4, moves=1
     h = L.sg_tri_copy(tri._h)
     L.sg_anneal(h, seed, float(sweeps), float(T0) * D, float(T1) * D, float(moves), float(collapse))
     return _export(h, tri.segs, "annealed")
+
+
+FUZZY_DELTA = 1.0 + float(np.cos(np.deg2rad(179.0)))  # Sec. 2.2.3: the angle penalty acts above 179 degrees
+
+
+def fuzzy_objective(tri: Triangulation, eps: float, delta: float = FUZZY_DELTA, eps0: float = 1e-10,
+                    mu_angle: float = 1.0, mu_len: float = 10.0, polish: bool = False, per_edge: bool = False):
+    """The objective f of Sec. 2.2 in unit-square units: dict with f, w_contr
+    (the edge-length sum with fuzzy contraction at length scale eps), angle and
+    length (the two penalty sums), and with per_edge the weight w(e) of every
+    edge as an (n_tri, 3) array (edge i of triangle t, opposite vertex i)."""
+    L = _load()
+    terms = np.zeros(4, np.float64)
+    w = np.zeros((tri.n_tri, 3), np.float64) if per_edge else None
+    L.sg_fuzzy_objective(tri._h, float(eps), float(delta), float(eps0), float(mu_angle), float(mu_len),
+                         1 if polish else 0, _ptr(terms), _ptr(w) if per_edge else None)
+    out = dict(f=float(terms[0]), w_contr=float(terms[1]), angle=float(terms[2]), length=float(terms[3]))
+    if per_edge:
+        out["w"] = w
+    return out
 
 
 def subdivide(tri: Triangulation) -> Triangulation:

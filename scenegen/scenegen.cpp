@@ -1163,6 +1163,149 @@ static void anneal_flips(Triangulation& tr, uint64_t seed, double sweeps, double
   if (n_collapsed > 0) compact_dead(tr);
 }
 
+// ---------------------------------------------------------------- fuzzy objective (Sec. 2.2)
+// f = W_contr + mu_angle Pi_angle + mu_len Pi_len in unit-square units (lengths / D):
+//   W_contr = sum_e w(e) |e|,  w(e) = P M(P),  P = prod of c(e') over the other edges e' of the
+//   (one or two) triangles of e,  c(e') = 1/2 + min(1, |e'| / eps) / 2 for a contractible edge, else 1;
+//   M(x) = 0 below 1/4, 4x - 1 on [1/4, 1/2], 1 above (the correction for multiply merged edges).
+//   The printed weight is M(P) alone; the text's worked example (an isolated contraction gives the
+//   two merging edges 1/2 each, a doubly merged edge 0, and M "not counting" multiply contracted
+//   edges) holds for w = P M(P), the reading used here.
+//   Pi_angle = sum over the three angles of every triangle of max(0, -1 + delta - cos) / delta
+//   (angles near 180 degrees); when polishing (fixed topology, w = 1) max(0, cos - 1 + delta) / delta
+//   (angles near 0 degrees) instead.  Pi_len = sum_e max(0, eps0 - |e|) / eps0.
+struct FuzzyParams {
+  double eps, delta, eps0, mu_angle, mu_len;
+  int polish;
+};
+
+// Contractibility of edge i of triangle t (Sec. 2.2.2).  By degrees of freedom: a free vertex
+// merges into any vertex; two vertices without freedom (segment endpoints and junctions, the
+// hull's vertices) never merge; a Steiner vertex inside a segment merges only along its segment
+// (the edge is then a constrained edge of that segment).  By planarity: a common neighbour of the
+// two endpoints that is not an apex of the edge's triangles (a nontrivial 1-hop connection) forbids
+// it unless that neighbour lies within eps of an apex, or an apex lies within eps of both endpoints
+// (the whole triangle contracts to one point, so the triangles joining the neighbour to the two
+// endpoints through that apex degenerate instead of overlapping: the case of the text's example of
+// three contracted edges, which the distance rule alone would forbid).  The conditioning and flat-triangle checks of
+// the paper are left to the exact validity test of the actual contraction (exact predicates cannot
+// be broken by thin triangles).
+static bool fuzzy_contractible(const Triangulation& tr, const VertexClasses& vc, double eps_lattice, int t,
+                               int i) {
+  const Tri& x = tr.T[t];
+  const int p = x.v[(i + 1) % 3], q = x.v[(i + 2) % 3];
+  const int kp = vc.kind[p], kq = vc.kind[q];
+  if (kp != 1 && kq != 1) {
+    if (kp == 0 && kq == 0) return false;
+    if (x.c[i] < 0) return false;  // both constrained: only along their own segment
+  }
+  const int a = x.v[i], n = x.n[i];
+  const int b = n >= 0 ? tr.T[n].v[tr.nb_edge(n, t)] : -1;
+  int np = 0;
+  int nbp[64];
+  bool overflow = false;
+  tr.for_fan(p, [&](int tt, int k) {
+    for (int s = 1; s <= 2; ++s) {
+      const int w = tr.T[tt].v[(k + s) % 3];
+      bool seen = false;
+      for (int j = 0; j < np; ++j) seen |= nbp[j] == w;
+      if (!seen) {
+        if (np == 64) {
+          overflow = true;
+          return true;
+        }
+        nbp[np++] = w;
+      }
+    }
+    return false;
+  });
+  if (overflow) return false;
+  const double e2 = eps_lattice * eps_lattice;
+  const Pt &pp = tr.P[p], &pq = tr.P[q];
+  const bool a_in = (double)len2(tr.P[a], pp) < e2 && (double)len2(tr.P[a], pq) < e2;
+  const bool b_in = b >= 0 && (double)len2(tr.P[b], pp) < e2 && (double)len2(tr.P[b], pq) < e2;
+  if (a_in || b_in) return true;
+  bool ok = true;
+  tr.for_fan(q, [&](int tt, int k) {
+    for (int s = 1; s <= 2; ++s) {
+      const int w = tr.T[tt].v[(k + s) % 3];
+      if (w == p || w == a || w == b) continue;
+      bool common = false;
+      for (int j = 0; j < np; ++j) common |= nbp[j] == w;
+      if (!common) continue;
+      const double da = (double)len2(tr.P[w], tr.P[a]), db = b >= 0 ? (double)len2(tr.P[w], tr.P[b]) : 1e300;
+      if (da >= e2 && db >= e2) {
+        ok = false;
+        return true;
+      }
+    }
+    return false;
+  });
+  return ok;
+}
+
+static inline double multi_merge(double x) { return x < 0.25 ? 0.0 : (x <= 0.5 ? 4.0 * x - 1.0 : 1.0); }
+
+static inline double angle_penalty(double c, const FuzzyParams& fp) {
+  return fp.polish ? std::max(0.0, c - 1.0 + fp.delta) / fp.delta : std::max(0.0, -1.0 + fp.delta - c) / fp.delta;
+}
+
+// The three angle cosines of triangle t.
+static void tri_cosines(const Triangulation& tr, int t, double cs[3]) {
+  for (int k = 0; k < 3; ++k) {
+    const Pt &a = tr.P[tr.T[t].v[k]], &b = tr.P[tr.T[t].v[(k + 1) % 3]], &c = tr.P[tr.T[t].v[(k + 2) % 3]];
+    const double ux = (double)b.x - a.x, uy = (double)b.y - a.y, vx = (double)c.x - a.x, vy = (double)c.y - a.y;
+    cs[k] = (ux * vx + uy * vy) / std::sqrt((ux * ux + uy * uy) * (vx * vx + vy * vy));
+  }
+}
+
+// f and its three terms; w_out (optional, 3 per triangle) receives every edge's weight w(e).
+static void fuzzy_objective(const Triangulation& tr, const FuzzyParams& fp, double terms[4], double* w_out) {
+  VertexClasses vc;
+  classify_vertices(tr, vc);
+  const size_t nt = tr.T.size();
+  const double D = (double)tr.D, eps_lat = fp.eps * D;
+  std::vector<double> len(3 * nt), cw(3 * nt);
+  for (size_t t = 0; t < nt; ++t)
+    for (int i = 0; i < 3; ++i) {
+      const int n = tr.T[t].n[i];
+      if (n >= 0 && (size_t)n < t) {  // the other side holds it
+        const int j = tr.nb_edge(n, (int)t);
+        len[3 * t + i] = len[3 * n + j];
+        cw[3 * t + i] = cw[3 * n + j];
+        continue;
+      }
+      const Pt &p = tr.P[tr.T[t].v[(i + 1) % 3]], &q = tr.P[tr.T[t].v[(i + 2) % 3]];
+      len[3 * t + i] = std::sqrt((double)len2(p, q)) / D;
+      cw[3 * t + i] = (fp.polish || !fuzzy_contractible(tr, vc, eps_lat, (int)t, i))
+                          ? 1.0
+                          : 0.5 + std::min(1.0, len[3 * t + i] / fp.eps) / 2.0;
+    }
+  double W = 0, PA = 0, PL = 0;
+  for (size_t t = 0; t < nt; ++t) {
+    for (int i = 0; i < 3; ++i) {
+      const int n = tr.T[t].n[i];
+      double P = cw[3 * t + (i + 1) % 3] * cw[3 * t + (i + 2) % 3];
+      if (n >= 0) {
+        const int j = tr.nb_edge(n, (int)t);
+        P *= cw[3 * n + (j + 1) % 3] * cw[3 * n + (j + 2) % 3];
+      }
+      const double w = fp.polish ? 1.0 : P * multi_merge(P);
+      if (w_out) w_out[3 * t + i] = w;
+      if (n >= 0 && (size_t)n < t) continue;  // each edge once
+      W += w * len[3 * t + i];
+      PL += std::max(0.0, fp.eps0 - len[3 * t + i]) / fp.eps0;
+    }
+    double cs[3];
+    tri_cosines(tr, (int)t, cs);
+    for (int k = 0; k < 3; ++k) PA += angle_penalty(cs[k], fp);
+  }
+  terms[0] = W + fp.mu_angle * PA + fp.mu_len * PL;
+  terms[1] = W;
+  terms[2] = PA;
+  terms[3] = PL;
+}
+
 // ---------------------------------------------------------------- rays
 struct SeedGrid {
   int G = 1;
@@ -1802,6 +1945,14 @@ float sg_tri_length(void* h, int32_t interior_only) {
 // T0 to T1 (grid units) for `sweeps` proposals per half-edge, then greedy
 // flips again.  Keeps whichever of (greedy-only, annealed) is shorter.
 // Returns the number of greedy flips of the kept result.
+// The fuzzy objective of Sec. 2.2 (see fuzzy_objective): terms = {f, W_contr, Pi_angle, Pi_len};
+// w (optional, 3 per triangle) = each edge's weight.
+void sg_fuzzy_objective(void* h, double eps, double delta, double eps0, double mu_angle, double mu_len,
+                        int32_t polish, double* terms, double* w) {
+  FuzzyParams fp{eps, delta, eps0, mu_angle, mu_len, polish};
+  fuzzy_objective(*(Triangulation*)h, fp, terms, w);
+}
+
 int64_t sg_anneal(void* h, uint64_t seed, double sweeps, double T0, double T1, double moves, double collapse) {
   auto* tr = (Triangulation*)h;
   Triangulation g = *tr;

@@ -1,0 +1,153 @@
+"""Pins of the fuzzy objective of Sec. 2.2 (scenegen.fuzzy_objective): the
+paper's worked example of fuzzy contraction (tests/golden/
+fuzzy_contraction_figure.json), the planarity and degree-of-freedom rules of
+contractibility, and closed forms (no contraction: plain length)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+
+D = sg.D
+HERE = os.path.dirname(os.path.abspath(__file__))
+FIG = json.load(open(os.path.join(HERE, "golden", "fuzzy_contraction_figure.json")))
+
+
+def _from_triangles(points, tris, segs=None, constrained=()):
+    """Triangulation from named points (lattice) and CCW triangles; neighbours by edge matching."""
+    names = list(points)
+    idx = {n: i for i, n in enumerate(names)}
+    vx = np.array([points[n][0] for n in names], np.int32)
+    vy = np.array([points[n][1] for n in names], np.int32)
+    tv = np.array([[idx[a] for a in t] for t in tris], np.int32)
+    nt = len(tris)
+    tn = np.full((nt, 3), -1, np.int32)
+    ts = np.full((nt, 3), -1, np.int32)
+    where = {}
+    for t in range(nt):
+        for i in range(3):
+            a, b = tv[t, (i + 1) % 3], tv[t, (i + 2) % 3]
+            where[(a, b)] = (t, i)
+    for (a, b), (t, i) in where.items():
+        if (b, a) in where:
+            tn[t, i] = where[(b, a)][0]
+    for s, (a, b) in enumerate(constrained):
+        for key in ((idx[a], idx[b]), (idx[b], idx[a])):
+            if key in where:
+                t, i = where[key]
+                ts[t, i] = s
+    segs = np.zeros((0, 4), np.int32) if segs is None else np.asarray(segs, np.int32)
+    return sg.from_arrays(vx, vy, tv, tn, ts, segs), idx
+
+
+def _edge_weight(tri, w, idx, a, b):
+    ia, ib = idx[a], idx[b]
+    for t in range(tri.n_tri):
+        for i in range(3):
+            if {tri.tri_v[t, (i + 1) % 3], tri.tri_v[t, (i + 2) % 3]} == {ia, ib}:
+                return w[t, i]
+    raise KeyError((a, b))
+
+
+def _lattice(case, shrink_units=4.0):
+    """The figure's configuration on the lattice (square [-1, 1]^2 -> [0, 2^20]^2), the inner
+    vertices pulled towards the contracted point so that contracted edges are a few units long."""
+    h = D / 2
+    cx, cy = FIG["contracted_point"]
+    C = (round((cx + 1) * h), round((cy + 1) * h))
+    pts = {k: (round((x + 1) * h), round((y + 1) * h)) for k, (x, y) in FIG["corners"].items()}
+    for k, (x, y) in FIG[case]["inner"].items():
+        pts[k] = (C[0] + round((x - cx) * shrink_units / 0.1 / 1), C[1] + round((y - cy) * shrink_units / 0.1 / 1))
+    return pts, C
+
+
+def _contracted_state_length(C):
+    c = np.array(C, np.float64) / D
+    corners = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], np.float64)
+    return 4.0 + float(np.linalg.norm(corners - c, axis=1).sum())
+
+
+@pytest.mark.parametrize("case", ["one_contracted_edge", "three_contracted_edges"])
+def test_figure_worked_example(case):
+    """The caption's weights: merging edges 1/2, the doubly merged edge 0, the
+    contracted edges 0; the weighted sum equals the length of the contracted
+    state (perimeter + four spokes) for both representations."""
+    pts, C = _lattice(case)
+    tri, idx = _from_triangles(pts, FIG[case]["triangles"])
+    assert oracle.check_triangulation(tri, D) == 0
+    eps = 0.05
+    r = sg.fuzzy_objective(tri, eps, per_edge=True)
+    for name, want in FIG[case]["expected_weight"].items():
+        a, b = name.split("-")
+        got = _edge_weight(tri, r["w"], idx, a, b)
+        assert abs(got - want) < 2e-3, (case, name, got, want)
+    assert abs(r["w_contr"] - _contracted_state_length(C)) < 2e-3
+    assert r["angle"] == 0.0 and r["length"] == 0.0
+    # without fuzzy contraction (eps -> 0) the weight is the plain length
+    plain = sg.fuzzy_objective(tri, 1e-12)
+    assert abs(plain["w_contr"] - tri.length(False) / D) < 1e-6 * plain["w_contr"]  # tri.length sums in fp32
+
+
+def test_one_hop_connection_blocks_contraction():
+    """A short edge A-B whose endpoints share a third neighbour H that is not
+    an apex of its triangles (a nontrivial 1-hop connection), with both apexes
+    farther than eps, is not contractible, so its neighbours keep weight 1;
+    with H within eps of an apex it is, and they drop to 1/2."""
+    pts = {"BL": (0, 0), "BR": (D, 0), "TR": (D, D), "TL": (0, D), "A": (500000, 500000), "B": (500010, 500000),
+           "H": (500005, 700000), "I": (500005, 560000)}
+    tris = [["A", "B", "I"], ["B", "H", "I"], ["H", "A", "I"], ["BL", "BR", "A"], ["A", "BR", "B"],
+            ["B", "BR", "TR"], ["B", "TR", "H"], ["H", "TR", "TL"], ["A", "H", "TL"], ["A", "TL", "BL"]]
+    tri, idx = _from_triangles(pts, tris)
+    assert oracle.check_triangulation(tri, D) == 0
+    w = sg.fuzzy_objective(tri, 0.05, per_edge=True)["w"]
+    assert _edge_weight(tri, w, idx, "A", "BR") == 1.0  # A-B incontractible (H is 0.13 from I)
+    w = sg.fuzzy_objective(tri, 0.5, per_edge=True)["w"]
+    assert abs(_edge_weight(tri, w, idx, "A", "BR") - 0.5) < 1e-4  # H within eps of the apex I
+
+
+def test_fixed_vertices_never_merge_and_free_ones_do():
+    """A short segment (both endpoints fixed) is incontractible: the edges
+    around it keep weight 1; the same short edge between two free vertices
+    lowers them to 1/2."""
+    h = D // 2
+    pts = {"BL": (0, 0), "BR": (D, 0), "TR": (D, D), "TL": (0, D), "P": (h, h), "Q": (h + 6, h + 2)}
+    tris = [["BL", "BR", "P"], ["P", "BR", "Q"], ["Q", "BR", "TR"], ["Q", "TR", "TL"], ["P", "Q", "TL"],
+            ["BL", "P", "TL"]]
+    seg = [[h, h, h + 6, h + 2]]
+    fixed, idx = _from_triangles(pts, tris, segs=seg, constrained=[("P", "Q")])
+    free, _ = _from_triangles(pts, tris)
+    assert oracle.check_triangulation(fixed, D) == 0 and oracle.check_triangulation(free, D) == 0
+    wf = sg.fuzzy_objective(fixed, 0.05, per_edge=True)["w"]
+    wr = sg.fuzzy_objective(free, 0.05, per_edge=True)["w"]
+    for a, b in (("P", "BR"), ("Q", "BR"), ("P", "TL"), ("Q", "TL")):
+        assert _edge_weight(fixed, wf, idx, a, b) == 1.0
+        assert abs(_edge_weight(free, wr, idx, a, b) - 0.5) < 1e-4
+
+
+def test_polish_mode_and_penalties():
+    """Polishing: every weight 1 (plain length) and the sharp-angle penalty;
+    the obtuse-angle penalty counts angles above 179 degrees; the length
+    penalty counts edges shorter than eps0."""
+    segs = sg.random_segments(100, 3)
+    tri = sg.pipeline(segs, 3, sweeps=1)[2]
+    p = sg.fuzzy_objective(tri, 0.05, polish=True)
+    assert abs(p["w_contr"] - tri.length(False) / D) < 1e-6 * p["w_contr"]
+    # a triangle with an angle of about 179.5 degrees: the obtuse penalty is about 1/2 of its ramp
+    import math
+    a = math.radians(0.25)
+    L = 400000
+    pts = {"BL": (0, 0), "BR": (D, 0), "TR": (D, D), "TL": (0, D),
+           "M": (D // 2, D // 2 + round(L * math.tan(a))), "L": (D // 2 - L, D // 2), "R": (D // 2 + L, D // 2)}
+    tris = [["L", "R", "M"], ["BL", "BR", "L"], ["L", "BR", "R"], ["R", "BR", "TR"], ["R", "TR", "M"],
+            ["M", "TR", "TL"], ["L", "M", "TL"], ["BL", "L", "TL"]]
+    t2, _ = _from_triangles(pts, tris)
+    assert oracle.check_triangulation(t2, D) == 0
+    r = sg.fuzzy_objective(t2, 0.05)
+    cosM = -math.cos(2 * a)
+    want = max(0.0, -1 + sg.FUZZY_DELTA - cosM) / sg.FUZZY_DELTA
+    assert 0.3 < want < 0.9 and abs(r["angle"] - want) < 0.02
+    r = sg.fuzzy_objective(t2, 0.05, eps0=0.5)
+    assert r["length"] > 0  # edges shorter than half the side
