@@ -84,6 +84,10 @@ def _load():
     L.sg_refine.argtypes = [vp, dbl, dbl, i64]
     L.sg_subdivide.restype = i64
     L.sg_subdivide.argtypes = [vp]
+    L.sg_anneal_fuzzy.restype = i64
+    L.sg_anneal_fuzzy.argtypes = [vp, ctypes.c_uint64, dbl, dbl, dbl, dbl, dbl, dbl]
+    L.sg_contract_short_edges.restype = i64
+    L.sg_contract_short_edges.argtypes = [vp, dbl]
     L.sg_fuzzy_objective.restype = None
     L.sg_fuzzy_objective.argtypes = [vp, dbl, dbl, dbl, dbl, dbl, ctypes.c_int32, vp, vp]
     L.sg_refine_optimal.restype = vp
@@ -303,6 +307,30 @@ def fuzzy_objective(tri: Triangulation, eps: float, delta: float = FUZZY_DELTA, 
     if per_edge:
         out["w"] = w
     return out
+
+
+def anneal_fuzzy(tri: Triangulation, seed: int, sweeps: float = 20.0, T0: float = 0.02, T1: float = 1e-4,
+                 eps_a: float = 0.05, eps_b: float = 1e-4, moves: float = 1.0):
+    """A copy of ``tri`` annealed on the fuzzy objective (Sec. 2.2, 3.3: T and
+    the contraction length eps decrease exponentially together, unit-square
+    units), then with every contractible edge shorter than eps_b contracted
+    (Sec. 3.4).  Returns (triangulation, contractions)."""
+    L = _load()
+    h = L.sg_tri_copy(tri._h)
+    n = L.sg_anneal_fuzzy(h, int(seed), float(sweeps), float(T0), float(T1), float(eps_a), float(eps_b),
+                          float(moves))
+    return _export(h, tri.segs, "fuzzy"), int(n)
+
+
+def fuzzy_pipeline(segs: np.ndarray, seed: int, sweeps: float = 20.0, polish_sweeps: float = 10.0,
+                   eps_a: float = 0.05, eps_b: float = 1e-4, T0: float = 0.02, T1: float = 1e-4):
+    """The optimisation of Sec. 3 with fuzzy contraction: the optimally
+    refined CDT, fuzzy annealing and contraction (anneal_fuzzy), then a
+    polishing anneal without contraction (edge flips and vertex moves on the
+    plain length, Sec. 3.4) and greedy flips.  Returns (refined CDT, result)."""
+    r = refine_optimal(cdt(segs))
+    f, _ = anneal_fuzzy(r, seed, sweeps, T0, T1, eps_a, eps_b)
+    return r, anneal(f, seed + 1, sweeps=polish_sweeps, T0=T1 * 10, T1=T1, moves=1.0, collapse=0.0)
 
 
 def subdivide(tri: Triangulation) -> Triangulation:

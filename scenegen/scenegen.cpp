@@ -1306,6 +1306,270 @@ static void fuzzy_objective(const Triangulation& tr, const FuzzyParams& fp, doub
   terms[3] = PL;
 }
 
+// The fuzzy objective over a region: every edge of the given triangles once, with its weight from
+// the current state, plus those triangles' angle penalties.  c values are memoised per edge for one
+// evaluation.  A proposal's energy change is the region's energy after minus before, for a region
+// that holds every edge whose weight the proposal can change (see anneal_fuzzy).
+struct FuzzyLocal {
+  const Triangulation& tr;
+  const VertexClasses& vc;
+  const FuzzyParams& fp;
+  std::vector<std::pair<uint64_t, double>> memo;
+  std::vector<uint64_t> seen;
+
+  FuzzyLocal(const Triangulation& t, const VertexClasses& v, const FuzzyParams& f) : tr(t), vc(v), fp(f) {}
+  static uint64_t key(int p, int q) {
+    return p < q ? ((uint64_t)(uint32_t)p << 32) | (uint32_t)q : ((uint64_t)(uint32_t)q << 32) | (uint32_t)p;
+  }
+  double len(int t, int i) const {
+    const Tri& x = tr.T[t];
+    return std::sqrt((double)len2(tr.P[x.v[(i + 1) % 3]], tr.P[x.v[(i + 2) % 3]])) / (double)tr.D;
+  }
+  double c(int t, int i) {
+    if (fp.polish) return 1.0;
+    const Tri& x = tr.T[t];
+    const uint64_t k = key(x.v[(i + 1) % 3], x.v[(i + 2) % 3]);
+    for (const auto& m : memo)
+      if (m.first == k) return m.second;
+    const double v = fuzzy_contractible(tr, vc, fp.eps * (double)tr.D, t, i)
+                         ? 0.5 + std::min(1.0, len(t, i) / fp.eps) / 2.0
+                         : 1.0;
+    memo.push_back({k, v});
+    return v;
+  }
+  double w(int t, int i) {
+    if (fp.polish) return 1.0;
+    double P = c(t, (i + 1) % 3) * c(t, (i + 2) % 3);
+    const int n = tr.T[t].n[i];
+    if (n >= 0) {
+      const int j = tr.nb_edge(n, t);
+      P *= c(n, (j + 1) % 3) * c(n, (j + 2) % 3);
+    }
+    return P * multi_merge(P);
+  }
+  double energy(const std::vector<int>& tris) {
+    memo.clear();
+    seen.clear();
+    double E = 0.0;
+    for (int t : tris)
+      for (int i = 0; i < 3; ++i) {
+        const Tri& x = tr.T[t];
+        const uint64_t k = key(x.v[(i + 1) % 3], x.v[(i + 2) % 3]);
+        if (std::find(seen.begin(), seen.end(), k) != seen.end()) continue;
+        seen.push_back(k);
+        const double l = len(t, i);
+        E += w(t, i) * l + fp.mu_len * std::max(0.0, fp.eps0 - l) / fp.eps0;
+      }
+    for (int t : tris) {
+      double cs[3];
+      tri_cosines(tr, t, cs);
+      for (int k = 0; k < 3; ++k) E += fp.mu_angle * angle_penalty(cs[k], fp);
+    }
+    return E;
+  }
+};
+
+static void add_star(const Triangulation& tr, int v, std::vector<int>& out) {
+  tr.for_fan(v, [&](int t, int) {
+    out.push_back(t);
+    return false;
+  });
+}
+static void sort_unique(std::vector<int>& v) {
+  std::sort(v.begin(), v.end());
+  v.erase(std::unique(v.begin(), v.end()), v.end());
+}
+
+// "Contraction to a neighbour" (Sec. 3.2): v is resampled within distance eps of a random neighbour u
+// (a Steiner vertex inside a segment: along the segment, towards itself, from a segment neighbour).
+static bool propose_to_neighbour(const Triangulation& tr, const VertexClasses& vc, int v, double eps_lat, Rng& rng,
+                                 Pt& q) {
+  if (vc.kind[v] == 2) {
+    const int u = rng.uni() < 0.5 ? vc.nb[v].first : vc.nb[v].second;
+    const Pt &pu = tr.P[u], &pv = tr.P[v], dir = vc.dir[v];
+    const int64_t sx = dir.x != 0 ? dir.x : dir.y;
+    const int64_t mv = ((int64_t)(dir.x != 0 ? pv.x - pu.x : pv.y - pu.y)) / sx;  // v = u + mv dir
+    const int64_t other = vc.nb[v].first == u ? vc.nb[v].second : vc.nb[v].first;
+    const Pt& pw = tr.P[other];
+    const int64_t mw = ((int64_t)(dir.x != 0 ? pw.x - pu.x : pw.y - pu.y)) / sx;  // w = u + mw dir
+    const double step = std::sqrt((double)dir.x * dir.x + (double)dir.y * dir.y);
+    const int64_t reach = std::max<int64_t>(1, (int64_t)(eps_lat / step));
+    const int64_t sgn_w = mw > 0 ? 1 : -1;
+    const int64_t lim = std::min<int64_t>(reach, std::llabs(mw) - 1);
+    if (lim < 1) return false;
+    const int64_t m = sgn_w * (1 + (int64_t)(rng.uni() * (double)lim));
+    if (m == mv) return false;
+    q = Pt{(int32_t)(pu.x + m * dir.x), (int32_t)(pu.y + m * dir.y)};
+    return true;
+  }
+  int deg = 0;
+  tr.for_fan(v, [&](int, int) {
+    ++deg;
+    return false;
+  });
+  int pick = (int)rng.below((uint32_t)deg), u = -1;
+  tr.for_fan(v, [&](int t, int k) {
+    if (pick-- == 0) {
+      u = tr.T[t].v[(k + 1) % 3];
+      return true;
+    }
+    return false;
+  });
+  if (u < 0) return false;
+  const double r = eps_lat * std::sqrt(rng.uni()), a = 6.283185307179586 * rng.uni();
+  const Pt& pu = tr.P[u];
+  q = Pt{(int32_t)std::llround(pu.x + r * std::cos(a)), (int32_t)std::llround(pu.y + r * std::sin(a))};
+  return q.x > 0 && q.y > 0 && q.x < tr.D && q.y < tr.D && !(q == tr.P[v]);
+}
+
+// Simulated annealing on the fuzzy objective f (Sec. 2.2, 3.1-3.3): T and eps decrease
+// exponentially together (T0 -> T1, eps_a -> eps_b, unit-square units); proposals are the vertex
+// perturbation and resampling of Sec. 3.2.2 / 3.2.4, the contraction to a neighbour, and edge flips,
+// with Metropolis acceptance on the exact change of f over a region that holds every edge whose
+// weight the proposal can change: for a vertex move the triangles of the stars of the vertex and of
+// its neighbours (lengths and contractibility distances change at the vertex; an edge's weight reads
+// the c of the edges of its own triangles); for a flip the stars of the quadrilateral's four vertices
+// (their neighbour sets change, hence the 1-hop test of every edge at them).
+static void anneal_fuzzy(Triangulation& tr, uint64_t seed, double sweeps, double T0, double T1, double eps_a,
+                         double eps_b, double moves) {
+  Rng rng(seed, 0xF022);
+  VertexClasses vc;
+  classify_vertices(tr, vc);
+  std::vector<int32_t> movable;
+  for (int v = 0; v < (int)vc.kind.size(); ++v)
+    if (vc.kind[v]) movable.push_back(v);
+  const double p_move = movable.empty() ? 0.0 : moves * (double)movable.size() / (double)tr.P.size();
+  FuzzyParams fp{eps_a, 1.0 + std::cos(179.0 * 3.14159265358979323846 / 180.0), 1e-10, 1.0, 10.0, 0};
+  FuzzyLocal loc(tr, vc, fp);
+  VertexMover mover;
+  const int64_t K = (int64_t)(sweeps * (double)tr.T.size() * 3.0);
+  const double lt0 = std::log(T0), lt1 = std::log(T1), le0 = std::log(eps_a), le1 = std::log(eps_b);
+  std::vector<int> region;
+  for (int64_t k = 0; k < K; ++k) {
+    const double fr = (double)k / (double)K;
+    const double temp = std::exp(lt0 + (lt1 - lt0) * fr);
+    fp.eps = std::exp(le0 + (le1 - le0) * fr);
+    if (p_move > 0 && rng.uni() < p_move) {
+      const int v = movable[rng.below((uint32_t)movable.size())];
+      Pt q;
+      const double u3 = rng.uni();
+      const int kind = u3 < 1.0 / 3 ? 0 : (u3 < 2.0 / 3 ? 1 : 2);
+      const bool ok = kind == 0   ? mover.propose(tr, vc, v, rng, q)
+                      : kind == 1 ? mover.resample(tr, vc, v, rng, q)
+                                  : propose_to_neighbour(tr, vc, v, fp.eps * (double)tr.D, rng, q);
+      float dl;
+      bool acc = false;
+      if (ok && vertex_move_delta(tr, v, q, &dl)) {
+        region.clear();
+        add_star(tr, v, region);
+        tr.for_fan(v, [&](int t, int kk) {
+          add_star(tr, tr.T[t].v[(kk + 1) % 3], region);
+          return false;
+        });
+        sort_unique(region);
+        const double e0 = loc.energy(region);
+        const Pt old = tr.P[v];
+        tr.P[v] = q;
+        const double d = loc.energy(region) - e0;
+        if (d <= 0.0 || rng.uni() < std::exp(-d / temp)) {
+          acc = true;
+        } else {
+          tr.P[v] = old;
+        }
+      }
+      if (kind == 0) mover.record(vc.kind[v], acc);
+      continue;
+    }
+    const int t = (int)rng.below((uint32_t)tr.T.size()), i = (int)rng.below(3);
+    if (tr.T[t].c[i] >= 0 || tr.T[t].n[i] < 0) continue;
+    int x, y;
+    if (!tr.strictly_convex(t, i, x, y)) continue;
+    const int qv = tr.T[t].v[(i + 1) % 3], rv = tr.T[t].v[(i + 2) % 3];
+    region.clear();
+    for (int w : {qv, rv, x, y}) add_star(tr, w, region);
+    sort_unique(region);
+    const double e0 = loc.energy(region);
+    tr.flip(t, i);
+    const double d = loc.energy(region) - e0;
+    if (d <= 0.0 || rng.uni() < std::exp(-d / temp)) continue;
+    int t2, i2;
+    if (tr.find_edge(x, y, t2, i2)) tr.flip(t2, i2);  // undo: the quadrilateral's other diagonal
+  }
+}
+
+// Turns the fuzzy topology into a true one (Sec. 3.4): while some contractible edge is shorter than
+// eps (unit-square units), the shortest is contracted by a discrete collapse of its less constrained
+// endpoint into the other (a free vertex into anything, a segment's Steiner vertex along its segment;
+// both directions tried for two free vertices); an edge whose collapse would fold the triangulation is
+// skipped (temporarily incontractible).  Returns the number of contractions.
+static int64_t contract_short_edges(Triangulation& tr, double eps) {
+  int64_t done = 0;
+  const double eps_lat = eps * (double)tr.D;
+  for (int round = 0; round < 64; ++round) {
+    VertexClasses vc;
+    classify_vertices(tr, vc);
+    std::vector<std::pair<double, std::pair<int, int>>> cand;
+    for (int t = 0; t < (int)tr.T.size(); ++t) {
+      if (tr.T[t].v[0] < 0) continue;
+      for (int i = 0; i < 3; ++i) {
+        const int n = tr.T[t].n[i];
+        if (n >= 0 && n < t) continue;
+        const Tri& x = tr.T[t];
+        const int p = x.v[(i + 1) % 3], q = x.v[(i + 2) % 3];
+        const double l = std::sqrt((double)len2(tr.P[p], tr.P[q]));
+        if (l >= eps_lat || !fuzzy_contractible(tr, vc, eps_lat, t, i)) continue;
+        cand.push_back({l, {p, q}});
+      }
+    }
+    if (cand.empty()) break;
+    std::sort(cand.begin(), cand.end());
+    std::vector<char> touched(tr.P.size(), 0);
+    int64_t this_round = 0;
+    for (const auto& cd : cand) {
+      const int p = cd.second.first, q = cd.second.second;
+      if (touched[p] || touched[q] || tr.vtri[p] < 0 || tr.vtri[q] < 0) continue;
+      // the vertex that moves: the one with more freedom
+      int order[2][2] = {{p, q}, {q, p}};
+      int n_try = 0;
+      const int kp = vc.kind[p], kq = vc.kind[q];
+      int tries[2][2];
+      if (kp == 1 && kq == 1) {
+        tries[0][0] = p, tries[0][1] = q, tries[1][0] = q, tries[1][1] = p;
+        n_try = 2;
+      } else if (kp == 1 || (kp == 2 && kq == 0)) {
+        tries[0][0] = p, tries[0][1] = q;
+        n_try = 1;
+      } else if (kq == 1 || (kq == 2 && kp == 0)) {
+        tries[0][0] = q, tries[0][1] = p;
+        n_try = 1;
+      } else if (kp == 2 && kq == 2) {
+        tries[0][0] = p, tries[0][1] = q, tries[1][0] = q, tries[1][1] = p;
+        n_try = 2;
+      }
+      (void)order;
+      for (int k = 0; k < n_try; ++k) {
+        const int v = tries[k][0], u = tries[k][1];
+        int t1, t2;
+        float dl;
+        if (!collapse_delta(tr, v, u, t1, t2, &dl)) continue;
+        // mark the neighbourhood: its classification is stale until the next round
+        tr.for_fan(v, [&](int t, int kk) {
+          for (int s = 0; s < 3; ++s) touched[tr.T[t].v[s]] = 1;
+          (void)kk;
+          return false;
+        });
+        do_collapse(tr, v, u, t1, t2);
+        ++this_round;
+        break;
+      }
+    }
+    done += this_round;
+    if (this_round == 0) break;
+    compact_dead(tr);  // the next round classifies every vertex: none may be dead
+  }
+  return done;
+}
+
 // ---------------------------------------------------------------- rays
 struct SeedGrid {
   int G = 1;
@@ -1952,6 +2216,18 @@ void sg_fuzzy_objective(void* h, double eps, double delta, double eps0, double m
   FuzzyParams fp{eps, delta, eps0, mu_angle, mu_len, polish};
   fuzzy_objective(*(Triangulation*)h, fp, terms, w);
 }
+
+// Fuzzy annealing (anneal_fuzzy) followed by the contraction of edges shorter than eps_b
+// (contract_short_edges); returns the number of contractions.
+int64_t sg_anneal_fuzzy(void* h, uint64_t seed, double sweeps, double T0, double T1, double eps_a, double eps_b,
+                        double moves) {
+  auto* tr = (Triangulation*)h;
+  anneal_fuzzy(*tr, seed, sweeps, T0, T1, eps_a, eps_b, moves);
+  return contract_short_edges(*tr, eps_b);
+}
+
+// Contraction alone (contract_short_edges).
+int64_t sg_contract_short_edges(void* h, double eps) { return contract_short_edges(*(Triangulation*)h, eps); }
 
 int64_t sg_anneal(void* h, uint64_t seed, double sweeps, double T0, double T1, double moves, double collapse) {
   auto* tr = (Triangulation*)h;

@@ -151,3 +151,29 @@ def test_polish_mode_and_penalties():
     assert 0.3 < want < 0.9 and abs(r["angle"] - want) < 0.02
     r = sg.fuzzy_objective(t2, 0.05, eps0=0.5)
     assert r["length"] > 0  # edges shorter than half the side
+
+
+def test_fuzzy_annealing_and_contraction_keep_the_scene():
+    """Annealing on the fuzzy objective (Sec. 3.3) and the contraction of
+    short edges (Sec. 3.4) on a subdivided triangulation: a valid
+    triangulation of the same segments with fewer vertices, on which the walk
+    equals the brute force; after contraction no contractible edge shorter
+    than eps_b is left whose collapse would keep the triangulation valid."""
+    segs = sg.random_segments(120, 41)
+    tri = sg.subdivide(sg.refine_optimal(sg.cdt(segs)))
+    out, n = sg.anneal_fuzzy(tri, 41, sweeps=5, eps_b=2e-4)
+    assert n > 0 and out.n_vert == tri.n_vert - n
+    assert oracle.check_triangulation(out, D) == 0
+    pts = set(zip(out.vx.tolist(), out.vy.tolist()))
+    for x0, y0, x1, y1 in segs.tolist():
+        assert (x0, y0) in pts and (x1, y1) in pts
+    r = sg.rays_isotropic(out, 3000, 42)
+    hb, tb = oracle.closest_bruteforce(segs, r.ox, r.oy, r.dx, r.dy)
+    hw, tw, _ = oracle.walk(out, r.ox, r.oy, r.dx, r.dy, r.start)
+    assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
+    # a second contraction pass at the same length finds nothing more to do
+    again, n2 = sg.anneal_fuzzy(out, 43, sweeps=0.0, eps_b=2e-4)
+    assert n2 == 0 and again.n_vert == out.n_vert
+    # the fuzzy objective at a small contraction length is the plain length of the result
+    fz = sg.fuzzy_objective(out, 1e-12)
+    assert abs(fz["w_contr"] - out.length(False) / D) < 1e-6 * fz["w_contr"]
