@@ -140,7 +140,7 @@ def cpu_oracle_rate(work, seconds_target=12.0):
     return n2 * len(work) / dt, threads, n2, dt
 
 
-def cpu_oracle_bounce_rate(work, n=1 << 15):
+def cpu_oracle_bounce_rate(work, n=1 << 20):
     """Oracle mirror paths (8 bounces, given start cells) on all host cores over
     the first n rays of every scene: walked rays per second."""
     import oracle

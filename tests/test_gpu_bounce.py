@@ -166,3 +166,35 @@ def test_parallel_mirrors_long_paths(cct):
         assert (got["steps"][nb] > 0).mean() > 0.9
     finally:
         scene.free()
+
+
+@pytest.mark.parametrize("family", ["circles", "dash45"])
+def test_bench_size_paths_sampled(cct, family):
+    """The bench's secondary-ray workload at full size (the bench's scene,
+    2^22 paths, up to 8 bounces, start cells given): 4096 randomly sampled
+    paths equal the oracle's chained walks; every path's record structure is
+    consistent (a path continues only after a hit) and the counters count every
+    walked ray."""
+    import bench
+
+    k = bench.FAMILIES.index(family)
+    segs = bench.family_segments(family)
+    tri = sg.pipeline(segs, bench.SCENE_SEED + k, sweeps=4)[2]
+    r = sg.rays_isotropic(tri, bench.N_BOUNCE_RAYS, 100 + k)
+    scene = cct.Scene.from_triangulation(tri, sg.D)
+    try:
+        nb = bench.N_BOUNCE
+        scene.stats(reset=True)
+        got = _gpu_paths(scene, r, nb)
+        st = scene.stats(reset=True)
+        idx = np.sort(np.random.default_rng(50 + k).choice(r.ox.size, 4096, replace=False))
+        exp = oracle.bounce_walk(tri, r.ox[idx], r.oy[idx], r.dx[idx], r.dy[idx], r.start[idx], nb)
+        _assert_paths({key: v[:, idx] for key, v in got.items()}, exp)
+        steps, hit = got["steps"], got["hit"]
+        for b in range(1, nb + 1):
+            cont = steps[b] != NONE
+            assert (hit[b - 1][cont] >= 0).all() and (steps[b - 1][cont] > 0).all()
+        assert st["rays"] == int((steps != NONE).sum())
+        assert st["steps"] == int(steps[steps > 0].sum())
+    finally:
+        scene.free()
