@@ -313,6 +313,16 @@ def secondary_rays(torch, cct, scenes, dev, stream, gather_bps, k_rep):
     scene with up to 8 bounces; event-timed per scene.  The primary records
     are checked against cct_trace's results."""
     out, tot_ms, tot_rays, tot_steps, tot_bytes_over_peak = {}, 0.0, 0, 0, 0.0
+    diffuse, d_ms, d_rays, d_steps = {}, 0.0, 0, 0
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    # diffuse bounces: directions cosine-weighted about the normal, given in each hit edge's
+    # frame as (c, s) = (sin theta, cos theta), theta = asin(2 u - 1), on the 2^-22 grid
+    u = torch.rand((N_BOUNCE, N_BOUNCE_RAYS), generator=gen, device=dev, dtype=torch.float64)
+    th = torch.asin(2.0 * u - 1.0)
+    frame = torch.stack([torch.round(torch.sin(th) * 2.0 ** 22), torch.round(torch.cos(th) * 2.0 ** 22)], -1)
+    frame = (frame / 2.0 ** 22).to(torch.float32).contiguous()
+    del u, th
     for sc in scenes:
         d = sc["d"]
         m = N_BOUNCE_RAYS
@@ -340,10 +350,22 @@ def secondary_rays(torch, cct, scenes, dev, stream, gather_bps, k_rep):
         tot_rays += rays
         tot_steps += steps
         tot_bytes_over_peak += alg / bps
+        ms_d = _time_loop(torch, dev, stream,
+                          lambda sc=sc: sc["scene"].trace_bounces(*args, start=d["start"][:m], stream=stream,
+                                                                  with_rays=False, frame=frame), k_rep)
+        st = sc["scene"].stats(reset=True)
+        diffuse[sc["name"]] = {"ms": ms_d, "walked_rays_per_s": st["rays"] / k_rep / (ms_d * 1e-3),
+                               "steps_per_walked_ray": st["steps"] / max(1, st["rays"])}
+        d_ms += ms_d
+        d_rays += st["rays"] / k_rep
+        d_steps += st["steps"] / k_rep
     return {"n_bounce": N_BOUNCE, "primary_rays_per_scene": N_BOUNCE_RAYS,
             "walked_rays_per_s": tot_rays / (tot_ms * 1e-3), "steps_per_walked_ray": tot_steps / tot_rays,
             "gather_frac": tot_bytes_over_peak / (tot_ms * 1e-3),
             "kernel": "bounce_kernel: one path per lane, exact int64 side tests on 2^-32 origins",
+            "diffuse": {"walked_rays_per_s": d_rays / (d_ms * 1e-3), "steps_per_walked_ray": d_steps / d_rays,
+                        "directions": "cosine-weighted about the normal, given in each hit edge's frame "
+                                      "(d_frame of cct_trace_bounces)", "per_scene": diffuse},
             "reading": "mirror reflection about the hit segment; origin snapped onto the hit edge at a 2^-32 "
                        "parameter; start cell = the parent's final triangle (no locate)",
             "per_scene": out}

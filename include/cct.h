@@ -229,7 +229,8 @@ int cct_trace_noalloc(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy,
  * start triangle, so secondary rays need no locate).  Each primary ray (inputs
  * and start cells as cct_trace; d_start_tri NULL = located first) is followed
  * by up to n_bounce secondary rays, each the mirror image of its parent about
- * the hit segment:
+ * the hit segment (or, with d_frame, a direction the caller gives in the hit
+ * edge's frame):
  *   origin     the parent's exact hit point moved onto the hit constrained
  *              edge (a -> b) of the final triangle (a right of the parent ray,
  *              b left or on its line): a + (i / 2^32)(b - a),
@@ -237,7 +238,14 @@ int cct_trace_noalloc(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy,
  *              exact parameter of the hit point on the edge;
  *   direction  k' = 2 (k.u) u / |u|^2 - k for k = 2^22 d and u = b - a,
  *              rounded to integers (halves up), clamped to [-2^22, 2^22],
- *              then d' = k' / 2^22;
+ *              then d' = k' / 2^22;  with d_frame (device, 2 * n_bounce * n
+ *              floats, the pair (c, s) of ray b >= 1 of path r at
+ *              2 ((b - 1) n + r)): k' = 2^22 (c u + s m) / |u| rounded to
+ *              integers (halves up, decided exactly) and clamped, m = (-u_y, u_x)
+ *              the normal on the parent's side; c and s must lie on the
+ *              2^-22 grid with |c|, |s| <= 1 and s > 0, else that ray is
+ *              CCT_RAY_INVALID and the path ends (a diffuse or glossy bounce
+ *              samples (c, s) without knowing which segment is hit);
  *   walk       Sec. 5.1 from that triangle, entered through the hit edge; the
  *              side rule, hit rule and tie order of cct_trace apply with the
  *              origin in units of 2^-32 (all decisions exact).
@@ -259,7 +267,8 @@ int cct_trace_noalloc(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy,
  * CCT_ERR_OUT_OF_MEMORY, CCT_ERR_CUDA. */
 #define CCT_MAX_BOUNCES 1024
 int cct_trace_bounces(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy, const float* d_dx,
-                      const float* d_dy, const int32_t* d_start_tri, int64_t n, int32_t n_bounce, int32_t* d_hit_seg,
+                      const float* d_dy, const int32_t* d_start_tri, int64_t n, int32_t n_bounce,
+                      const float* d_frame, int32_t* d_hit_seg,
                       float* d_t, int32_t* d_steps, int64_t* d_org_x, int64_t* d_org_y, float* d_dir_x,
                       float* d_dir_y, uint32_t flags, void* stream);
 

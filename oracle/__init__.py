@@ -25,9 +25,9 @@ _libs: dict[int, ctypes.CDLL] = {}
 # failure bits of check_triangulation
 BAD_INDEX, NOT_CCW, AREA, NB_ASYM, HULL, EULER, CONSTRAINT_ASYM, COVERAGE, NOT_DELAUNAY = (
     1, 2, 4, 8, 16, 32, 64, 128, 256)
-N_MUTANTS = 6
+N_MUTANTS = 7
 PRIMARY_MUTANTS = (1, 2, 3, 4)  # planted in the primary-ray predicates and walk
-BOUNCE_MUTANTS = (5, 6)  # planted in the secondary-ray construction
+BOUNCE_MUTANTS = (5, 6, 7)  # planted in the secondary-ray construction
 BOUNCE_NONE = -3  # steps of a path entry with no ray
 
 
@@ -74,10 +74,10 @@ def _load(mutant: int = 0) -> ctypes.CDLL:
     L.oracle_kd_trace.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, i32]
     L.oracle_bounce_walk.restype = ctypes.c_int
     L.oracle_bounce_walk.argtypes = [i64, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp,
-                                     vp, i64, i32]
+                                     vp, i64, vp, i32]
     L.oracle_bounce_bruteforce.restype = ctypes.c_int
     L.oracle_bounce_bruteforce.argtypes = [i64, vp, vp, vp, vp, i64, vp, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp,
-                                           vp, vp, i32]
+                                           vp, vp, vp, i32]
     L.oracle_mutant.restype = i32
     _libs[mutant] = L
     return L
@@ -157,10 +157,21 @@ def _bounce_shape(out, n, n_bounce):
     return {k: v.reshape(n_bounce + 1, n) for k, v in out.items()}
 
 
-def bounce_walk(tri, ox, oy, dx, dy, start, n_bounce, max_steps=None, n_threads=None, mutant=0):
+def _frame(frame, n, n_bounce):
+    if frame is None:
+        return None
+    f = _c(frame, np.float32).reshape(-1)
+    if f.size != 2 * n * n_bounce:
+        raise ValueError("frame must hold (c, s) for n_bounce x n secondary rays")
+    return f
+
+
+def bounce_walk(tri, ox, oy, dx, dy, start, n_bounce, max_steps=None, n_threads=None, mutant=0, frame=None):
     """Mirror paths (Sec. 5.2: each secondary ray starts in the final triangle
     of its parent's walk): dict of (1 + n_bounce, n) arrays hit, t, steps,
-    org_x, org_y (origins in 2^-32 units), dir_x, dir_y."""
+    org_x, org_y (origins in 2^-32 units), dir_x, dir_y.  frame (optional,
+    (n_bounce, n, 2) float32): each secondary ray's direction (c, s) in the
+    frame of its parent's hit edge instead of the mirror image."""
     L = _load(mutant)
     vx, vy = _c(tri.vx, np.int32), _c(tri.vy, np.int32)
     tv, tn, ts = _c(tri.tri_v, np.int32), _c(tri.tri_nb, np.int32), _c(tri.tri_seg, np.int32)
@@ -170,13 +181,14 @@ def bounce_walk(tri, ox, oy, dx, dy, start, n_bounce, max_steps=None, n_threads=
     nt = tv.size // 3
     o = _bounce_out(n, n_bounce, True)
     ms = nt + 8 if max_steps is None else int(max_steps)
+    fr = _frame(frame, n, n_bounce)
     L.oracle_bounce_walk(nt, _p(vx), _p(vy), _p(tv), _p(tn), _p(ts), n, _p(ox), _p(oy), _p(dx), _p(dy), _p(start),
                          int(n_bounce), _p(o["hit"]), _p(o["t"]), _p(o["steps"]), _p(o["org_x"]), _p(o["org_y"]),
-                         _p(o["dir_x"]), _p(o["dir_y"]), ms, _nthreads(n_threads))
+                         _p(o["dir_x"]), _p(o["dir_y"]), ms, _p(fr) if fr is not None else None, _nthreads(n_threads))
     return _bounce_shape(o, n, n_bounce)
 
 
-def bounce_bruteforce(tri, ox, oy, dx, dy, n_bounce, n_threads=None, mutant=0):
+def bounce_bruteforce(tri, ox, oy, dx, dy, n_bounce, n_threads=None, mutant=0, frame=None):
     """The same mirror paths by brute force over all segments (hit edges found
     by scanning the constrained edges): dict as bounce_walk without steps."""
     L = _load(mutant)
@@ -186,9 +198,11 @@ def bounce_bruteforce(tri, ox, oy, dx, dy, n_bounce, n_threads=None, mutant=0):
     ox, oy, dx, dy = _c(ox, np.int32), _c(oy, np.int32), _c(dx, np.float32), _c(dy, np.float32)
     n = ox.size
     o = _bounce_out(n, n_bounce, False)
+    fr = _frame(frame, n, n_bounce)
     L.oracle_bounce_bruteforce(tv.size // 3, _p(vx), _p(vy), _p(tv), _p(ts), segs.shape[0], _p(segs), n, _p(ox),
                                _p(oy), _p(dx), _p(dy), int(n_bounce), _p(o["hit"]), _p(o["t"]), _p(o["org_x"]),
-                               _p(o["org_y"]), _p(o["dir_x"]), _p(o["dir_y"]), _nthreads(n_threads))
+                               _p(o["org_y"]), _p(o["dir_x"]), _p(o["dir_y"]), _p(fr) if fr is not None else None,
+                               _nthreads(n_threads))
     return _bounce_shape(o, n, n_bounce)
 
 

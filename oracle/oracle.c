@@ -918,6 +918,12 @@ int oracle_kd_trace(int32_t n_nodes, const int32_t* axis, const int32_t* split, 
  *     integers (halves up) and clamped to [-2^22, 2^22], u = b - a; when k'
  *     does not point strictly back to the parent's side of the segment (the
  *     sign of u x k' must be opposite to that of u x k) the path ends;
+ *   - or, when the caller gives it, the direction (c, s) in the hit edge's
+ *     frame: d' = c u/|u| + s n, n the unit normal of u pointing back to the
+ *     parent's side, c and s on the 2^-22 grid with |c|, |s| <= 1 and s > 0
+ *     (else the ray is invalid); k' = 2^22 d' rounded componentwise (halves
+ *     up, an exact comparison with the square root) and clamped to 2^22, then
+ *     the same test;
  *   - every ray of the path, the first included, follows the rules of the
  *     primary rays (side rule, hit, tie order), with the origin in 2^-32
  *     units.  A path of a primary ray has up to 1 + n_bounce rays; it ends at
@@ -1009,6 +1015,42 @@ static int reflect_dir(int64_t kx, int64_t ky, int64_t ux, int64_t uy, int64_t* 
   return (c0 > 0 && c1 < 0) || (c0 < 0 && c1 > 0);
 }
 
+/* is a < b sqrt(m), exactly (m >= 0; |a| < 2^62, |b| sqrt(m) < 2^62) */
+static int lt_sqrt(i128 a, i128 b, i128 m) {
+  if (b >= 0) return a < 0 || a * a < b * b * m;
+  return a < 0 && a * a > b * b * m;
+}
+
+/* round(n / sqrt(m)) with halves up: the q with (2q - 1) sqrt(m) <= 2n < (2q + 1) sqrt(m) */
+static int64_t round_div_sqrt(int64_t n, int64_t m) {
+  int64_t q = (int64_t)floor((double)n / sqrt((double)m) + 0.5);
+  while (!lt_sqrt(2 * (i128)n, 2 * (i128)q + 1, m)) ++q;
+  while (lt_sqrt(2 * (i128)n, 2 * (i128)q - 1, m)) --q;
+  return q;
+}
+
+/* The direction (c, s) in the frame of the hit edge u = b - a (a right of the
+ * parent ray k, b left): k' = round(2^22 (c u + s n) / |u|) with n = (-u_y, u_x),
+ * the normal on the parent's side.  Returns -1 if (c, s) is not a valid frame
+ * direction, 0 if k' does not point strictly back, 1 otherwise. */
+static int frame_dir(float c, float s, int64_t kx, int64_t ky, int64_t ux, int64_t uy, int64_t* rx, int64_t* ry) {
+  int64_t kc, ks;
+  if (!dir_to_int(c, &kc) || !dir_to_int(s, &ks) || ks <= 0) return -1;
+  const int64_t m = ux * ux + uy * uy;
+#if ORACLE_MUTANT == 7 /* planted: the normal on the far side */
+  int64_t qx = round_div_sqrt(kc * ux + ks * uy, m), qy = round_div_sqrt(kc * uy - ks * ux, m);
+#else
+  int64_t qx = round_div_sqrt(kc * ux - ks * uy, m), qy = round_div_sqrt(kc * uy + ks * ux, m);
+#endif
+  const int64_t lim = (int64_t)1 << 22;
+  qx = qx > lim ? lim : (qx < -lim ? -lim : qx);
+  qy = qy > lim ? lim : (qy < -lim ? -lim : qy);
+  *rx = qx;
+  *ry = qy;
+  const i128 c0 = (i128)ux * ky - (i128)uy * kx, c1 = (i128)ux * qy - (i128)uy * qx;
+  return (c0 > 0 && c1 < 0) || (c0 < 0 && c1 > 0);
+}
+
 typedef struct {
   int64_t n_tri, n_seg;
   const int32_t *vx, *vy, *tri_v, *tri_nb, *tri_seg, *seg;
@@ -1022,7 +1064,17 @@ typedef struct {
   int64_t *org_x, *org_y;
   float *dir_x, *dir_y;
   int64_t max_steps;
+  const float* frame; /* optional: (c, s) of ray b >= 1 of path r at 2 ((b - 1) n + r) */
 } bounce_ctx;
+
+/* The next ray's direction after ray b of path r hit edge (a -> b) (u): 1 = go on,
+ * 0 = the path ends, -1 = ray b + 1 is invalid (a caller's frame direction). */
+static int next_dir(const bounce_ctx* c, int b, int64_t r, int64_t kx, int64_t ky, int64_t ux, int64_t uy,
+                    int64_t* rx, int64_t* ry) {
+  if (!c->frame) return reflect_dir(kx, ky, ux, uy, rx, ry);
+  const int64_t k = 2 * ((int64_t)b * c->n + r);
+  return frame_dir(c->frame[k], c->frame[k + 1], kx, ky, ux, uy, rx, ry);
+}
 
 static void bounce_clear(const bounce_ctx* c, int64_t r) {
   for (int b = 0; b <= c->n_bounce; ++b) {
@@ -1101,12 +1153,15 @@ static void bounce_walk_range(void* p, int64_t lo, int64_t hi) {
           if (b < c->n_bounce) {
             int64_t X2, Y2, kx2, ky2;
             snap_origin(kx, ky, X, Y, ax, ay, bx, by, &X2, &Y2);
-            if (reflect_dir(kx, ky, bx - ax, by - ay, &kx2, &ky2)) {
+            const int nd = next_dir(c, b, r, kx, ky, bx - ax, by - ay, &kx2, &ky2);
+            if (nd > 0) {
               X = X2;
               Y = Y2;
               kx = kx2;
               ky = ky2;
               more = 1; /* T stays: the next ray starts in the final triangle */
+            } else if (nd < 0) {
+              c->steps[(int64_t)(b + 1) * c->n + r] = -1; /* invalid frame direction */
             }
           }
           break;
@@ -1193,7 +1248,7 @@ static void bounce_bf_range(void* p, int64_t lo, int64_t hi) {
       if (!found) break; /* cannot happen for a triangulation that covers the segments */
       int64_t X2, Y2, kx2, ky2;
       snap_origin(kx, ky, X, Y, ax, ay, bx, by, &X2, &Y2);
-      if (!reflect_dir(kx, ky, bx - ax, by - ay, &kx2, &ky2)) break;
+      if (next_dir(c, b, r, kx, ky, bx - ax, by - ay, &kx2, &ky2) <= 0) break;
       X = X2;
       Y = Y2;
       kx = kx2;
@@ -1205,14 +1260,16 @@ static void bounce_bf_range(void* p, int64_t lo, int64_t hi) {
 /* Mirror paths of n primary rays with up to n_bounce secondary rays each, by
  * walks chained through their final triangles.  Outputs (1 + n_bounce) * n
  * entries, entry b * n + r: hit, t, steps as oracle_walk plus -3 (no ray),
- * origin (2^-32 units) and direction of each ray of the path. */
+ * origin (2^-32 units) and direction of each ray of the path.  frame
+ * (optional): the caller's directions in the hit edges' frames instead of
+ * mirror images; an invalid one gives steps -1 at its ray. */
 int oracle_bounce_walk(int64_t n_tri, const int32_t* vx, const int32_t* vy, const int32_t* tri_v,
                        const int32_t* tri_nb, const int32_t* tri_seg, int64_t n, const int32_t* ox,
                        const int32_t* oy, const float* dx, const float* dy, const int32_t* start, int32_t n_bounce,
                        int32_t* hit, float* t, int32_t* steps, int64_t* org_x, int64_t* org_y, float* dir_x,
-                       float* dir_y, int64_t max_steps, int32_t n_threads) {
+                       float* dir_y, int64_t max_steps, const float* frame, int32_t n_threads) {
   bounce_ctx c = {n_tri, 0, vx, vy, tri_v, tri_nb, tri_seg, NULL, n, ox, oy, dx, dy, start, n_bounce,
-                  hit, steps, t, org_x, org_y, dir_x, dir_y, max_steps};
+                  hit, steps, t, org_x, org_y, dir_x, dir_y, max_steps, frame};
   run_parallel(bounce_walk_range, &c, n, n_threads);
   return 0;
 }
@@ -1222,9 +1279,9 @@ int oracle_bounce_bruteforce(int64_t n_tri, const int32_t* vx, const int32_t* vy
                              const int32_t* tri_seg, int64_t n_seg, const int32_t* seg, int64_t n,
                              const int32_t* ox, const int32_t* oy, const float* dx, const float* dy,
                              int32_t n_bounce, int32_t* hit, float* t, int64_t* org_x, int64_t* org_y,
-                             float* dir_x, float* dir_y, int32_t n_threads) {
+                             float* dir_x, float* dir_y, const float* frame, int32_t n_threads) {
   bounce_ctx c = {n_tri, n_seg, vx, vy, tri_v, NULL, tri_seg, seg, n, ox, oy, dx, dy, NULL, n_bounce,
-                  hit, NULL, t, org_x, org_y, dir_x, dir_y, 0};
+                  hit, NULL, t, org_x, org_y, dir_x, dir_y, 0, frame};
   run_parallel(bounce_bf_range, &c, n, n_threads);
   return 0;
 }

@@ -139,7 +139,7 @@ def lib() -> ctypes.CDLL:
     L.cct_trace_kdtree.restype = ctypes.c_int
     L.cct_trace_kdtree.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp, vp]
     L.cct_trace_bounces.restype = ctypes.c_int
-    L.cct_trace_bounces.argtypes = [vp, vp, vp, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, u32, vp]
+    L.cct_trace_bounces.argtypes = [vp, vp, vp, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, u32, vp]
     L.cct_trace_noalloc.restype = ctypes.c_int
     L.cct_trace_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, u32, vp]
     L.cct_get_stats.restype = ctypes.c_int
@@ -275,9 +275,11 @@ def cct_trace_noalloc(scene: int, ox, oy, dx, dy, start, hit, t, steps, flags: i
 
 
 def cct_trace_bounces(scene: int, ox, oy, dx, dy, start, n_bounce: int, hit, t, steps, org_x=None, org_y=None,
-                      dir_x=None, dir_y=None, flags: int = 0, stream=None) -> None:
+                      dir_x=None, dir_y=None, flags: int = 0, stream=None, frame=None) -> None:
     """Mirror paths (include/cct.h): outputs hold (1 + n_bounce) * n entries,
-    entry b * n + r for ray b of path r; org_*, dir_* are optional."""
+    entry b * n + r for ray b of path r; org_*, dir_* are optional; frame
+    (optional, 2 * n_bounce * n floats): the secondary rays' directions (c, s)
+    in their hit edges' frames instead of mirror images."""
     import torch
 
     n = ox.numel()
@@ -285,13 +287,15 @@ def cct_trace_bounces(scene: int, ox, oy, dx, dy, start, n_bounce: int, hit, t, 
         if a.numel() != n:
             raise ValueError("all ray tensors must have the same length")
     m = (int(n_bounce) + 1) * n
+    if frame is not None and frame.numel() != 2 * int(n_bounce) * n:
+        raise ValueError("frame must hold 2 * n_bounce * n floats")
     for a in (hit, t, steps, org_x, org_y, dir_x, dir_y):
         if a is not None and a.numel() != m:
             raise ValueError("result tensors must hold (1 + n_bounce) * n entries")
     _check(lib().cct_trace_bounces(ctypes.c_void_p(scene), _dev(ox, torch.int32, "ox"), _dev(oy, torch.int32, "oy"),
                                    _dev(dx, torch.float32, "dx"), _dev(dy, torch.float32, "dy"),
                                    _dev(start, torch.int32, "start"), n, int(n_bounce),
-                                   _dev(hit, torch.int32, "hit"), _dev(t, torch.float32, "t"),
+                                   _dev(frame, torch.float32, "frame"), _dev(hit, torch.int32, "hit"), _dev(t, torch.float32, "t"),
                                    _dev(steps, torch.int32, "steps"), _dev(org_x, torch.int64, "org_x"),
                                    _dev(org_y, torch.int64, "org_y"), _dev(dir_x, torch.float32, "dir_x"),
                                    _dev(dir_y, torch.float32, "dir_y"), flags, _stream_ptr(stream)),
@@ -352,9 +356,11 @@ class Scene:
         return out
 
     def trace_bounces(self, ox, oy, dx, dy, n_bounce: int, start=None, flags: int = 0, stream=None,
-                      with_rays: bool = True):
+                      with_rays: bool = True, frame=None):
         """Mirror paths: dict of (1 + n_bounce, n) tensors hit, t, steps (and
-        org_x, org_y, dir_x, dir_y when with_rays)."""
+        org_x, org_y, dir_x, dir_y when with_rays); frame (optional, a
+        (n_bounce, n, 2) float32 device tensor): the secondary rays' directions
+        in their hit edges' frames."""
         import torch
 
         n, dev = ox.numel(), ox.device
@@ -368,7 +374,8 @@ class Scene:
                        dir_x=torch.empty(shape, dtype=torch.float32, device=dev),
                        dir_y=torch.empty(shape, dtype=torch.float32, device=dev))
         cct_trace_bounces(self.handle, ox, oy, dx, dy, start, n_bounce, out["hit"], out["t"], out["steps"],
-                          out.get("org_x"), out.get("org_y"), out.get("dir_x"), out.get("dir_y"), flags, stream)
+                          out.get("org_x"), out.get("org_y"), out.get("dir_x"), out.get("dir_y"), flags, stream,
+                          frame)
         return out
 
     def locate(self, ox, oy, stream=None):

@@ -4,7 +4,8 @@
 //
 // A path starts as a primary ray (lattice origin, start triangle given or
 // located) and continues with up to n_bounce secondary rays, each the mirror
-// image of its parent about the hit segment.  A secondary ray starts on the
+// image of its parent about the hit segment (or takes the caller's direction
+// in the frame of the hit edge).  A secondary ray starts on the
 // hit constrained edge (a -> b) of its parent's final triangle T, at
 // P' = a + (i / 2^32) (b - a) with i = round(2^32 mu) (halves up) clamped to
 // [1, 2^32 - 1], mu the exact parameter of the hit point on that edge; it
@@ -62,7 +63,8 @@ struct BounceArgs {
   int32_t* hit;
   float* t;
   int32_t* steps;
-  int64_t* org_x;  // optional outputs (NULL: not written)
+  const float* frame;  // optional: (c, s) of ray b >= 1 of path i at 2 ((b - 1) n_total + off + i)
+  int64_t* org_x;     // optional outputs (NULL: not written)
   int64_t* org_y;
   float* dir_x;
   float* dir_y;
@@ -80,6 +82,9 @@ __device__ __forceinline__ float i128_to_float(i128 v) {
 
 // Four blocks per SM (64 registers, no spills): 1.07-1.17x faster than the
 // compiler's 76 registers at three blocks (more warps to hide the gathers).
+// kFrame: the secondary directions come from A.frame (a separate instantiation
+// keeps the mirror paths free of that code's register pressure: 4-5 % faster).
+template <bool kFrame>
 __global__ void __launch_bounds__(kBounceThreads, 4) bounce_kernel(SceneDev S, BounceArgs A,
                                                                 unsigned long long* __restrict__ counter) {
   constexpr unsigned FULL = 0xffffffffu;
@@ -143,10 +148,25 @@ __global__ void __launch_bounds__(kBounceThreads, 4) bounce_kernel(SceneDev S, B
       act = false;
       return;
     }
-    // the next origin on the edge and the mirror direction
+    // the next origin on the edge; the mirror direction, or the caller's in the edge's frame
     const long long i = bounce::snap_param(kx, ky, Rx, Ry, ex, ey);
     int k2x, k2y;
-    if (!bounce::mirror_dir(kx, ky, ex, ey, k2x, k2y)) {
+    bool back;
+    if (kFrame) {
+      const long long fi = 2 * ((long long)b * A.n_total + A.off + id);
+      int kc, ks;
+      if (!dir_to_k(A.frame[fi], kc) || !dir_to_k(A.frame[fi + 1], ks) || ks <= 0) {
+        record(b + 1, -1, __int_as_float(0x7fc00000), CCT_RAY_INVALID, false);  // an invalid secondary ray
+        end_path(b + 2);
+        ++c_inv;
+        ++c_rays;
+        return;
+      }
+      back = bounce::frame_dir(kc, ks, kx, ky, ex, ey, k2x, k2y);
+    } else {
+      back = bounce::mirror_dir(kx, ky, ex, ey, k2x, k2y);
+    }
+    if (!back) {
       end_path(b + 1);
       return;
     }
@@ -287,7 +307,8 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 using namespace cct;
 
 extern "C" int cct_trace_bounces(cct_scene scene, const int32_t* ox, const int32_t* oy, const float* dx,
-                                 const float* dy, const int32_t* start, int64_t n, int32_t n_bounce, int32_t* hit,
+                                 const float* dy, const int32_t* start, int64_t n, int32_t n_bounce,
+                                 const float* frame, int32_t* hit,
                                  float* t, int32_t* steps, int64_t* org_x, int64_t* org_y, float* dir_x,
                                  float* dir_y, uint32_t flags, void* stream_v) {
   if (!scene || n < 0 || n_bounce < 0 || n_bounce > CCT_MAX_BOUNCES || (flags & ~CCT_TRACE_EXACT_ONLY) != 0)
@@ -309,9 +330,9 @@ extern "C" int cct_trace_bounces(cct_scene scene, const int32_t* ox, const int32
     return CCT_ERR_OUT_OF_MEMORY;
   }
   unsigned long long* counter = (unsigned long long*)sc.base;
+  auto kern = frame ? bounce_kernel<true> : bounce_kernel<false>;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bounce_kernel, kBounceThreads, 0) != cudaSuccess ||
-      per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBounceThreads, 0) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   for (int64_t off = 0; off < n; off += kMaxLaunch) {
     const int64_t m = std::min<int64_t>(kMaxLaunch, n - off);
@@ -325,11 +346,11 @@ extern "C" int cct_trace_bounces(cct_scene scene, const int32_t* ox, const int32
       st_user = false;
     }
     BounceArgs A{ox + off, oy + off, dx + off, dy + off, st, st_user ? 1 : 0, (int32_t)m, n_bounce, n, off,
-                 hit, t, steps, org_x, org_y, dir_x, dir_y, std::max(32, tu.chunk)};
+                 hit, t, steps, frame, org_x, org_y, dir_x, dir_y, std::max(32, tu.chunk)};
     const long long want = (m + kBounceThreads - 1) / kBounceThreads;
     long long grid = std::min<long long>((long long)sm_count(scene->device) * per_sm, want);
     if (grid < 1) grid = 1;
-    bounce_kernel<<<(unsigned)grid, kBounceThreads, 0, stream>>>(S, A, counter);
+    kern<<<(unsigned)grid, kBounceThreads, 0, stream>>>(S, A, counter);
     if (cudaGetLastError() != cudaSuccess) return CCT_ERR_CUDA;
   }
   return CCT_OK;

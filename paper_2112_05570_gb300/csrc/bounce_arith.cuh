@@ -1,6 +1,6 @@
 // Exact integer arithmetic of a secondary ray's start (the snapped origin
-// parameter and the mirror direction), shared by bounce_kernel and its CPU
-// check.  Host builds use the IEEE operations the device intrinsics compute
+// parameter, the mirror direction or the caller's direction in the hit edge's
+// frame), shared by bounce_kernel and its CPU check.  Host builds use the IEEE operations the device intrinsics compute
 // (round to nearest; floor for the float -> int64 conversion).
 #pragma once
 
@@ -16,6 +16,8 @@ __device__ __forceinline__ float ll2f(long long v) { return __ll2float_rn(v); }
 __device__ __forceinline__ long long f2ll_rd(float x) { return __float2ll_rd(x); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float sqrt_rn(float x) { return __fsqrt_rn(x); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
 #define CCT_BX __device__ __forceinline__
 #else
 inline float rcp_rn(float x) {
@@ -29,6 +31,11 @@ inline float mul_rn(float a, float b) {
   return r;
 }
 inline float fma_rn(float a, float b, float c) { return fmaf(a, b, c); }
+inline float sqrt_rn(float x) { return sqrtf(x); }
+inline float div_rn(float a, float b) {
+  volatile float r = a / b;
+  return r;
+}
 #define CCT_BX inline
 #endif
 
@@ -101,6 +108,38 @@ CCT_BX bool mirror_dir(int kx, int ky, long long ex, long long ey, int& k2x_out,
   const float myf = fma_rn(2.0f, fma_rn(2.0f * kuf, (float)ey, -mul_rn(uuf, (float)ky)), uuf);
   long long k2x = floordiv_mod(mxm, mxf, 2 * uu, -2 * kKLim, 2 * kKLim);
   long long k2y = floordiv_mod(mym, myf, 2 * uu, -2 * kKLim, 2 * kKLim);
+  k2x = k2x > kKLim ? kKLim : (k2x < -kKLim ? -kKLim : k2x);
+  k2y = k2y > kKLim ? kKLim : (k2y < -kKLim ? -kKLim : k2y);
+  k2x_out = (int)k2x;
+  k2y_out = (int)k2y;
+  const long long c0 = ex * ky - ey * kx, c1 = ex * k2y - ey * k2x;
+  return (c0 > 0 && c1 < 0) || (c0 < 0 && c1 > 0);
+}
+
+// Whether a < b sqrt(m), exactly (m >= 0, |a| < 2^62, |b| sqrt(m) < 2^62).
+CCT_BX bool lt_sqrt(long long a, long long b, long long m) {
+  const __int128 a2 = (__int128)a * a, b2m = (__int128)b * b * m;
+  if (b >= 0) return a < 0 || a2 < b2m;
+  return a < 0 && a2 > b2m;
+}
+
+// round(n / sqrt(m)) with halves up (m >= 1, |n / sqrt(m)| < 2^40): the q with
+// (2q - 1) sqrt(m) <= 2n < (2q + 1) sqrt(m), from an fp32 estimate and exact steps.
+CCT_BX long long round_div_sqrt(long long n, long long m) {
+  long long q = f2ll_rd(div_rn(ll2f(n), sqrt_rn(ll2f(m))) + 0.5f);
+  while (!lt_sqrt(2 * n, 2 * q + 1, m)) ++q;
+  while (lt_sqrt(2 * n, 2 * q - 1, m)) --q;
+  return q;
+}
+
+// The caller's direction (kc, ks) = 2^22 (c, s) in the frame of the hit edge
+// u = (ex, ey) (a right of the parent ray k, b left): k' = round(2^22 (c u + s n) / |u|),
+// n = (-u_y, u_x) (the normal on the parent's side), clamped to [-2^22, 2^22].
+// Returns whether k' points strictly back to the parent's side (as mirror_dir).
+CCT_BX bool frame_dir(int kc, int ks, int kx, int ky, long long ex, long long ey, int& k2x_out, int& k2y_out) {
+  const long long m = ex * ex + ey * ey;
+  long long k2x = round_div_sqrt((long long)kc * ex - (long long)ks * ey, m);
+  long long k2y = round_div_sqrt((long long)kc * ey + (long long)ks * ex, m);
   k2x = k2x > kKLim ? kKLim : (k2x < -kKLim ? -kKLim : k2x);
   k2y = k2y > kKLim ? kKLim : (k2y < -kKLim ? -kKLim : k2y);
   k2x_out = (int)k2x;

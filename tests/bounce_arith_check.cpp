@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <random>
+#include <string>
 
 #include "bounce_arith.cuh"
 
@@ -23,7 +24,43 @@ static i128 floordiv128(i128 n, i128 d) {
   return q;
 }
 
+// "round <count> <seed>": prints n m round_div_sqrt(n, m) for random and
+// adversarial pairs (perfect squares, halves, extreme magnitudes), one per line.
+static int round_mode(long long count, unsigned long long seed) {
+  std::mt19937_64 g(seed);
+  auto rnd = [&](long long lo, long long hi) { return lo + (long long)(g() % (unsigned long long)(hi - lo + 1)); };
+  for (long long k = 0; k < count; ++k) {
+    long long m, n;
+    switch (k % 4) {
+      case 0:  // a frame computation's range: |n| < 2^43, m = |u|^2 < 2^41
+        m = rnd(1, 1ll << 41);
+        n = rnd(-(1ll << 43), 1ll << 43);
+        break;
+      case 1: {  // perfect squares with exact halves
+        const long long r = rnd(1, 1 << 20);
+        m = r * r;
+        n = (2 * rnd(-(1ll << 21), 1ll << 21) + 1) * r / 2;
+        if ((r & 1) == 0) n = (2 * rnd(-(1ll << 21), 1ll << 21) + 1) * (r / 2);
+        break;
+      }
+      case 2:  // small values
+        m = rnd(1, 50);
+        n = rnd(-200, 200);
+        break;
+      default: {  // near a half: n ~ (q + 1/2) sqrt(m)
+        m = rnd(2, 1ll << 41);
+        const double q = (double)rnd(-(1 << 22), 1 << 22) + 0.5;
+        n = llround(q * sqrt((double)m));
+      }
+    }
+    printf("%lld %lld %lld\n", n, m, round_div_sqrt(n, m));
+  }
+  return 0;
+}
+
 int main(int argc, char** argv) {
+  if (argc > 1 && std::string(argv[1]) == "round")
+    return round_mode(argc > 2 ? atoll(argv[2]) : 100000, argc > 3 ? strtoull(argv[3], nullptr, 10) : 1);
   const long long cases = argc > 1 ? atoll(argv[1]) : 1000000;
   std::mt19937_64 g(argc > 2 ? strtoull(argv[2], nullptr, 10) : 1);
   const long long D = 1 << 20;

@@ -198,3 +198,51 @@ def test_bench_size_paths_sampled(cct, family):
         assert st["steps"] == int(steps[steps > 0].sum())
     finally:
         scene.free()
+
+
+def _frames(seed, n, nb):
+    """Frame directions (c, s) for secondary rays: mostly valid, some grazing,
+    some invalid (s = 0, a component off the 2^-22 grid)."""
+    rng = np.random.default_rng(seed)
+    th = rng.uniform(0.02, np.pi - 0.02, (nb, n))
+    th = np.where(rng.random((nb, n)) < 0.03, rng.choice([1e-7, np.pi - 1e-7], (nb, n)), th)
+    c = np.round(np.cos(th) * 2 ** 22) / 2 ** 22
+    s = np.maximum(np.round(np.sin(th) * 2 ** 22), 0) / 2 ** 22
+    fr = np.stack([c, s], -1).astype(np.float32)
+    bad = rng.random((nb, n))
+    fr[..., 1][bad < 0.01] = 0.0
+    fr[..., 0][(bad >= 0.01) & (bad < 0.02)] = np.float32(0.1)
+    return fr
+
+
+@pytest.mark.parametrize("name,gen", _scene_cases()[1:3], ids=[c[0] for c in _scene_cases()[1:3]])
+def test_frame_direction_paths_equal_oracle(cct, name, gen):
+    """Secondary rays with the caller's directions in the hit edges' frames
+    (diffuse-style bounces, some grazing, some invalid): bit-exact against the
+    oracle's chained walks, start cells given and located; the counters count
+    every walked ray, the invalid secondary ones included."""
+    segs = gen()
+    tri = sg.pipeline(segs, 71, sweeps=2)[2]
+    scene = cct.Scene.from_triangulation(tri, sg.D)
+    try:
+        r = sg.rays_isotropic(tri, 20_000 + 33, 72)
+        nb = 6
+        fr = _frames(73, r.ox.size, nb)
+        exp = oracle.bounce_walk(tri, r.ox, r.oy, r.dx, r.dy, r.start, nb, frame=fr)
+        assert (exp["steps"][1:] == -1).sum() > 100 and (exp["steps"][nb] > 0).sum() > 1000
+        scene.stats(reset=True)
+        out = scene.trace_bounces(_dev(r.ox), _dev(r.oy), _dev(r.dx), _dev(r.dy), nb, start=_dev(r.start),
+                                  frame=_dev(fr))
+        torch.cuda.synchronize()
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+        _assert_paths(got, exp)
+        st = scene.stats(reset=True)
+        assert st["rays"] == int((exp["steps"] != NONE).sum())
+        assert st["invalid_rays"] == int((exp["steps"] == -1).sum())
+        out = scene.trace_bounces(_dev(r.ox), _dev(r.oy), _dev(r.dx), _dev(r.dy), nb, frame=_dev(fr))
+        torch.cuda.synchronize()
+        _assert_paths({k: v.cpu().numpy() for k, v in out.items()}, exp)
+        with pytest.raises(ValueError):
+            scene.trace_bounces(_dev(r.ox), _dev(r.oy), _dev(r.dx), _dev(r.dy), nb, frame=_dev(fr[:-1]))
+    finally:
+        scene.free()

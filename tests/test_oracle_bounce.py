@@ -209,9 +209,11 @@ def test_snapped_origins_lie_on_the_hit_segment():
 def test_planted_bounce_mutations_are_caught(mutant):
     """Each planted mistake in the secondary-ray construction (the incoming
     direction added instead of subtracted; the snapped parameter measured from
-    the wrong endpoint) fails a closed-form pin."""
+    the wrong endpoint; the frame's normal on the far side) fails a
+    closed-form pin."""
     failed = []
-    for fn in (test_parallel_mirrors_closed_form, test_snapped_origins_lie_on_the_hit_segment):
+    for fn in (test_parallel_mirrors_closed_form, test_snapped_origins_lie_on_the_hit_segment,
+               test_frame_directions_on_parallel_mirrors_closed_form):
         real = oracle._libs.get(0)
         try:
             oracle._libs[0] = oracle._load(mutant)
@@ -227,3 +229,72 @@ def test_planted_bounce_mutations_are_caught(mutant):
             else:
                 oracle._libs.pop(0, None)
     assert failed
+
+
+def _frames(rng, n, nb, grazing=0.0):
+    """Random frame directions (c, s): s > 0, |(c, s)| <= 1, on the 2^-22 grid."""
+    th = rng.uniform(0.02, np.pi - 0.02, (nb, n))
+    if grazing:
+        th = np.where(rng.random((nb, n)) < grazing, rng.choice([1e-7, np.pi - 1e-7], (nb, n)), th)
+    c = np.round(np.cos(th) * 2 ** 22) / 2 ** 22
+    s = np.maximum(np.round(np.sin(th) * 2 ** 22), 0) / 2 ** 22
+    return np.stack([c, s], -1).astype(np.float32)
+
+
+@pytest.mark.parametrize("scene", ["room", "circles"])
+def test_frame_directions_walk_equals_bruteforce(scene):
+    """Secondary rays with the caller's directions in the hit edges' frames:
+    the chained walks equal the brute-force paths; every secondary direction
+    points back to its parent's side."""
+    segs = sg.room(150, 61) if scene == "room" else sg.circles(3000, 62)
+    tri = sg.anneal(sg.refine_optimal(sg.cdt(segs)), 63, sweeps=2)
+    r = sg.rays_isotropic(tri, 3000, 64)
+    nb = 6
+    fr = _frames(np.random.default_rng(65), r.ox.size, nb, grazing=0.05)
+    W = oracle.bounce_walk(tri, r.ox, r.oy, r.dx, r.dy, r.start, nb, frame=fr)
+    B = oracle.bounce_bruteforce(tri, r.ox, r.oy, r.dx, r.dy, nb, frame=fr)
+    _equal_paths(W, B)
+    assert (W["steps"][nb] > 0).sum() > 200
+    # the invalid frame direction case: s = 0 (along the edge) makes the next ray invalid
+    bad = fr.copy()
+    bad[0, :, 1] = 0.0
+    Wb = oracle.bounce_walk(tri, r.ox, r.oy, r.dx, r.dy, r.start, nb, frame=bad)
+    hit0 = W["hit"][0] >= 0
+    assert (Wb["steps"][1][hit0] == -1).all() and (Wb["steps"][2:][:, hit0] == NONE).all()
+
+
+def test_frame_directions_on_parallel_mirrors_closed_form():
+    """On horizontal mirrors the frame is axis-aligned: the direction (c, s)
+    becomes exactly (+-c, s) or (-c, -s) in grid units (the normal points back
+    to the parent's side), each secondary ray travels y2 - y1 with
+    t = (y2 - y1) / s, and a perpendicular direction (0, 1) leaves straight
+    back."""
+    y1, y2 = 400_000, 600_000
+    segs = _mirrors(y1, y2)
+    tri = sg.cdt(segs)
+    rng = np.random.default_rng(66)
+    n, nb = 64, 6
+    ox = rng.integers(480_000, 560_000, n)
+    oy = rng.integers(450_000, 550_000, n) | 1
+    ky = np.where(rng.random(n) < 0.5, 1, -1) * (1 << 22)
+    ox, oy, dx, dy = _rays(ox, oy, np.zeros(n, int), ky)
+    st = _locate(tri, ox, oy)
+    th = rng.uniform(np.deg2rad(86), np.deg2rad(94), (nb, n))
+    fr = np.stack([np.round(np.cos(th) * 2 ** 22) / 2 ** 22, np.round(np.sin(th) * 2 ** 22) / 2 ** 22], -1)
+    fr = fr.astype(np.float32)
+    W = oracle.bounce_walk(tri, ox, oy, dx, dy, st, nb, frame=fr)
+    _equal_paths(W, oracle.bounce_bruteforce(tri, ox, oy, dx, dy, nb, frame=fr))
+    # mirror 0 (y1) runs +x, mirror 1 (y2) runs -x: u = (+-1, 0) * length
+    for i in range(n):
+        for b in range(1, nb + 1):
+            assert W["steps"][b, i] > 0
+            on_top = W["hit"][b - 1, i] == 1  # parent hit the upper mirror: u points -x, normal -y
+            c, s = float(fr[b - 1, i, 0]), float(fr[b - 1, i, 1])
+            ex_dx, ex_dy = (-c, -s) if on_top else (c, s)
+            assert W["dir_x"][b, i] == np.float32(ex_dx) and W["dir_y"][b, i] == np.float32(ex_dy)
+            t_exact = Fraction(y2 - y1) / Fraction(abs(float(W["dir_y"][b, i])))
+            assert abs(Fraction(float(W["t"][b, i])) - t_exact) <= t_exact * Fraction(1, 2 ** 23)
+    perp = np.zeros_like(fr)
+    perp[..., 1] = 1.0
+    Wp = oracle.bounce_walk(tri, ox, oy, dx, dy, st, nb, frame=perp)
+    assert np.array_equal(Wp["dir_y"][1], -dy) and (Wp["dir_x"][1] == 0).all()
