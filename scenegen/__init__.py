@@ -273,6 +273,66 @@ def cdt(segs: np.ndarray) -> Triangulation:
     return _export(h, segs, "cdt")
 
 
+def load(path: str, segs: np.ndarray) -> Triangulation:
+    """A triangulation written by Triangulation.save (the layout cct_scene_load_file
+    reads), with the scene segments it was built for; checks the header, the
+    size and the domain."""
+    raw = open(path, "rb").read()
+    if raw[:8] != b"CCTTRI1\0" or len(raw) < 24:
+        raise ValueError(f"{path}: not a triangulation file")
+    nv, nt, ns, dom = (int(x) for x in np.frombuffer(raw[8:24], "<i4"))
+    if len(raw) != 24 + 4 * (2 * nv + 9 * nt) or dom != D or ns != np.asarray(segs).reshape(-1, 4).shape[0]:
+        raise ValueError(f"{path}: size, domain or segment count does not match")
+    a = np.frombuffer(raw[24:], "<i4")
+    vx, vy = a[:nv].copy(), a[nv:2 * nv].copy()
+    tv = a[2 * nv:2 * nv + 3 * nt].reshape(nt, 3).copy()
+    tn = a[2 * nv + 3 * nt:2 * nv + 6 * nt].reshape(nt, 3).copy()
+    ts = a[2 * nv + 6 * nt:].reshape(nt, 3).copy()
+    return from_arrays(vx, vy, tv, tn, ts, segs, kind="loaded")
+
+
+def anneal_resumable(tri: Triangulation, seed: int, checkpoint: str, sweeps: float = 20.0, chunks: int = 8,
+                     T0: float = 0.02, T1: float = 1e-4, moves: float = 1.0, collapse: float = 0.5,
+                     stop_after: int = None) -> Triangulation:
+    """``anneal`` in ``chunks`` pieces of the exponential schedule T0 -> T1
+    (piece k: sweeps / chunks sweeps from T0 (T1/T0)^(k/chunks) to
+    T0 (T1/T0)^((k+1)/chunks), seed + k), checkpointing after each piece: the
+    triangulation file ``checkpoint`` (replaced atomically) and a sidecar
+    ``checkpoint + ".json"`` with the pieces done and the parameters.  A call
+    with the same parameters and an existing checkpoint resumes after its last
+    piece, so an interrupted run ends with the result of an uninterrupted one.
+    stop_after (testing): return after that many pieces of this call."""
+    import json
+    import os
+
+    params = dict(seed=int(seed), sweeps=float(sweeps), chunks=int(chunks), T0=float(T0), T1=float(T1),
+                  moves=float(moves), collapse=float(collapse), n_vert=tri.n_vert, n_tri=tri.n_tri)
+    side = checkpoint + ".json"
+    start, cur = 0, tri
+    if os.path.exists(side) and os.path.exists(checkpoint):
+        st = json.load(open(side))
+        if st.get("params") == params:
+            start, cur = int(st["done"]), load(checkpoint, tri.segs)
+    ran = 0
+    for k in range(start, chunks):
+        if stop_after is not None and ran >= stop_after:
+            return cur
+        ta = T0 * (T1 / T0) ** (k / chunks)
+        tb = T0 * (T1 / T0) ** ((k + 1) / chunks)
+        cur = anneal(cur, seed + k, sweeps=sweeps / chunks, T0=ta, T1=tb, moves=moves, collapse=collapse)
+        tmp = checkpoint + ".tmp"
+        cur.save(tmp)
+        os.replace(tmp, checkpoint)
+        # go on from the file's state, as a resumed run does (the in-memory
+        # vertex-to-triangle map of a fresh import decides fan orders)
+        cur = load(checkpoint, tri.segs)
+        with open(side + ".tmp", "w") as f:
+            json.dump({"done": k + 1, "params": params}, f)
+        os.replace(side + ".tmp", side)
+        ran += 1
+    return cur
+
+
 def anneal(tri: Triangulation, seed: int, sweeps=20.0, T0=0.02, T1=1e-4, moves=1.0, collapse=0.5) -> Triangulation:
     """A copy of ``tri`` annealed: greedy flips to shorter diagonals, then
     simulated annealing with temperature T0 -> T1 (units of the domain side,

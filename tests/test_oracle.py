@@ -511,3 +511,26 @@ def test_subdivision_splits_edges_and_keeps_the_scene():
         hb, tb = oracle.closest_bruteforce(segs, r.ox, r.oy, r.dx, r.dy)
         hw, tw, _ = oracle.walk(tri, r.ox, r.oy, r.dx, r.dy, r.start)
         assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
+
+
+def test_annealer_checkpoint_resume(tmp_path):
+    """The annealer checkpoints its triangulation after each piece of its
+    schedule (a file cct_scene_load_file reads): a run stopped after three
+    pieces and resumed from the checkpoint ends with exactly the triangulation
+    of an uninterrupted run, which is valid and keeps the scene; a checkpoint
+    of other parameters is not resumed."""
+    segs = sg.circles(1500, 81)
+    ref = sg.refine_optimal(sg.cdt(segs))
+    full = sg.anneal_resumable(ref, 81, str(tmp_path / "a.cct"), sweeps=4, chunks=6)
+    part = sg.anneal_resumable(ref, 81, str(tmp_path / "b.cct"), sweeps=4, chunks=6, stop_after=3)
+    assert json.load(open(tmp_path / "b.cct.json"))["done"] == 3
+    resumed = sg.anneal_resumable(ref, 81, str(tmp_path / "b.cct"), sweeps=4, chunks=6)
+    for k in ("vx", "vy", "tri_v", "tri_nb", "tri_seg"):
+        assert np.array_equal(getattr(full, k), getattr(resumed, k)), k
+    assert oracle.check_triangulation(resumed, sg.D) == 0
+    assert oracle.interior_length(resumed) < oracle.interior_length(ref)
+    loaded = sg.load(str(tmp_path / "b.cct"), segs)
+    assert np.array_equal(loaded.tri_v, resumed.tri_v)
+    # other parameters: the checkpoint is ignored and the run starts over
+    other = sg.anneal_resumable(ref, 82, str(tmp_path / "b.cct"), sweeps=4, chunks=6, stop_after=1)
+    assert json.load(open(tmp_path / "b.cct.json"))["done"] == 1 and other.n_tri > 0
