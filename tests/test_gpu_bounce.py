@@ -246,3 +246,35 @@ def test_frame_direction_paths_equal_oracle(cct, name, gen):
             scene.trace_bounces(_dev(r.ox), _dev(r.oy), _dev(r.dx), _dev(r.dy), nb, frame=_dev(fr[:-1]))
     finally:
         scene.free()
+
+
+def test_walk_limit_on_corrupt_triangulation(cct):
+    """Mirror paths in a triangulation whose triangle 0 names itself as every
+    neighbour (loaded without validation): the primary rays starting in it stop
+    at the step limit with CCT_RAY_WALK_LIMIT, the rest of each path is 'no
+    ray', and the kernel returns instead of hanging."""
+    K = 1 << 22
+    segs = sg.random_segments(200, 1)
+    tri = sg.cdt(segs)
+    tn = tri.tri_nb.copy()
+    ts = tri.tri_seg.copy()
+    tn[0] = [0, 0, 0]
+    ts[0] = [-1, -1, -1]
+    vx, vy = tri.vx[tri.tri_v[0]].astype(np.int64), tri.vy[tri.tri_v[0]].astype(np.int64)
+    n = 64
+    ox = np.full(n, int(vx.sum() // 3), np.int32)
+    oy = np.full(n, int(vy.sum() // 3), np.int32)
+    assert oracle.locate_bruteforce(tri, ox[:1], oy[:1])[0] == 0
+    th = np.linspace(0, 2 * np.pi, n, endpoint=False)
+    dx = (np.rint(np.cos(th) * K) / K).astype(np.float32)
+    dy = (np.rint(np.sin(th) * K) / K).astype(np.float32)
+    scene = cct.Scene(tri.vx, tri.vy, tri.tri_v, tn, ts, tri.segs.shape[0], sg.D,
+                      flags=cct.CCT_LOAD_NO_VALIDATE | cct.CCT_LOAD_NO_REORDER)
+    try:
+        r = sg.Rays(ox=ox, oy=oy, dx=dx, dy=dy, start=np.zeros(n, np.int32))
+        got = _gpu_paths(scene, r, 3)
+        assert (got["steps"][0] == cct.CCT_RAY_WALK_LIMIT).all() and (got["hit"][0] == -1).all()
+        assert (got["steps"][1:] == NONE).all()
+        assert scene.stats()["walk_limit_rays"] == n
+    finally:
+        scene.free()
