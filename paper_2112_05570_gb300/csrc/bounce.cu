@@ -80,12 +80,14 @@ __device__ __forceinline__ float i128_to_float(i128 v) {
   return neg ? -f : f;
 }
 
-// Four blocks per SM (64 registers, no spills): 1.07-1.17x faster than the
-// compiler's 76 registers at three blocks (more warps to hide the gathers).
-// kFrame: the secondary directions come from A.frame (a separate instantiation
-// keeps the mirror paths free of that code's register pressure: 4-5 % faster).
+// Mirror paths: four blocks per SM (64 registers, no spills), 1.07-1.17x faster
+// than the compiler's 76 registers at three blocks (more warps to hide the
+// gathers).  kFrame: the secondary directions come from A.frame; a separate
+// instantiation keeps the mirror paths free of that code's register pressure
+// (4-5 % faster), and it runs at three blocks (80 registers): at four it
+// spilled and ran 1.14-1.28x slower.
 template <bool kFrame>
-__global__ void __launch_bounds__(kBounceThreads, 4) bounce_kernel(SceneDev S, BounceArgs A,
+__global__ void __launch_bounds__(kBounceThreads, kFrame ? 3 : 4) bounce_kernel(SceneDev S, BounceArgs A,
                                                                 unsigned long long* __restrict__ counter) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
