@@ -449,8 +449,8 @@ static cudaError_t launch_walk_t(const SceneDev& S, const RaySrc& R, const cct_t
     // once per instantiation and device (function attributes belong to each
     // device's context; `dev` is current): the stacks of 16 warps exceed the
     // default 48 KB of dynamic shared memory.  The shared/L1 split is left to
-    // the driver: a maximal shared carveout measured 1.5x slower (the L1 also
-    // holds the loads in flight).
+    // the CUDA runtime's choice: a maximal shared carveout measured 1.5x
+    // slower (the L1 also holds the loads in flight).
     static std::mutex mu;
     static uint64_t configured = 0;  // bit d: done on device d (d < 64; others every call)
     std::lock_guard<std::mutex> lk(mu);
