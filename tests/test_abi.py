@@ -87,6 +87,17 @@ def test_load_argument_errors():
     assert L.cct_trace(None, None, None, None, None, None, 0, None, None, None, 0, None) == cct.CCT_ERR_INVALID_ARGUMENT
     assert L.cct_locate(None, None, None, 0, None, None) == cct.CCT_ERR_INVALID_ARGUMENT
     assert L.cct_scene_free(None) == cct.CCT_OK
+    # cct_trace_bounces: a null scene, n < 0, n_bounce outside [0, CCT_MAX_BOUNCES], other flags
+    args = [None, None, None, None, None, None, 0, 0, None, None, None, None, None, None, None, None, 0, None]
+    assert L.cct_trace_bounces(*args) == cct.CCT_ERR_INVALID_ARGUMENT
+    fake = ctypes.c_void_p(1)  # never dereferenced: the checks come first
+    for n, nb, fl in ((-1, 0, 0), (1, -1, 0), (1, cct.CCT_MAX_BOUNCES + 1, 0), (1, 2, cct.CCT_TRACE_BIN)):
+        a = list(args)
+        a[0], a[6], a[7], a[16] = fake, n, nb, fl
+        assert L.cct_trace_bounces(*a) == cct.CCT_ERR_INVALID_ARGUMENT, (n, nb, fl)
+    a = list(args)
+    a[0] = fake
+    assert L.cct_trace_bounces(*a) == cct.CCT_OK  # n = 0: a no-op before any pointer is read
 
 
 def test_valid_triangulation_passes_validation_without_gpu():
