@@ -1422,9 +1422,22 @@ static bool propose_to_neighbour(const Triangulation& tr, const VertexClasses& v
   return q.x > 0 && q.y > 0 && q.x < tr.D && q.y < tr.D && !(q == tr.P[v]);
 }
 
+// Whether vertex v (at position q) has a neighbour closer than r (lattice units).
+static bool has_neighbour_within(const Triangulation& tr, int v, const Pt& q, double r) {
+  const double r2 = r * r;
+  return tr.for_fan(v, [&](int t, int k) { return (double)len2(q, tr.P[tr.T[t].v[(k + 1) % 3]]) < r2; });
+}
+
 // Simulated annealing on the fuzzy objective f (Sec. 2.2, 3.1-3.3): T and eps decrease
-// exponentially together (T0 -> T1, eps_a -> eps_b, unit-square units); proposals are the vertex
-// perturbation and resampling of Sec. 3.2.2 / 3.2.4, the contraction to a neighbour, and edge flips,
+// exponentially together (T0 -> T1, eps_a -> eps_b, unit-square units); proposals are edge flips
+// and, in equal shares, the vertex perturbation (Sec. 3.2.2), the perturbation of a group of
+// contracted vertices (Sec. 3.2.3: the free vertices within d ~ U[eps/2, 5 eps] of a central one move
+// together by one heavy-tailed step scaled by the root of their stars' area), the resampling within
+// the neighbouring triangles (Sec. 3.2.4), the swap of a contracted edge (Sec. 3.2.5: a vertex with a
+// neighbour closer than l ~ U[0.2 eps, 2 eps] resampled in the disk of radius l about a random
+// neighbour) and the contraction to a neighbour (Sec. 3.2.6: an uncontracted vertex resampled within
+// eps of a random neighbour, a contracted one by the resampling of Sec. 3.2.4 kept only if it leaves
+// every neighbour),
 // with Metropolis acceptance on the exact change of f over a region that holds every edge whose
 // weight the proposal can change: for a vertex move the triangles of the stars of the vertex and of
 // its neighbours (lengths and contractibility distances change at the vertex; an edge's weight reads
@@ -1444,38 +1457,95 @@ static void anneal_fuzzy(Triangulation& tr, uint64_t seed, double sweeps, double
   VertexMover mover;
   const int64_t K = (int64_t)(sweeps * (double)tr.T.size() * 3.0);
   const double lt0 = std::log(T0), lt1 = std::log(T1), le0 = std::log(eps_a), le1 = std::log(eps_b);
-  std::vector<int> region;
+  std::vector<int> region, group;
+  std::vector<Pt> newpos, oldpos;
   for (int64_t k = 0; k < K; ++k) {
     const double fr = (double)k / (double)K;
     const double temp = std::exp(lt0 + (lt1 - lt0) * fr);
     fp.eps = std::exp(le0 + (le1 - le0) * fr);
     if (p_move > 0 && rng.uni() < p_move) {
       const int v = movable[rng.below((uint32_t)movable.size())];
+      const double eps_lat = fp.eps * (double)tr.D;
+      const int kind = (int)rng.below(5);  // 3.2.2, 3.2.3, 3.2.4, 3.2.5, 3.2.6
+      // the vertices that move and their new positions
+      group.clear();
+      newpos.clear();
+      bool ok = false;
       Pt q;
-      const double u3 = rng.uni();
-      const int kind = u3 < 1.0 / 3 ? 0 : (u3 < 2.0 / 3 ? 1 : 2);
-      const bool ok = kind == 0   ? mover.propose(tr, vc, v, rng, q)
-                      : kind == 1 ? mover.resample(tr, vc, v, rng, q)
-                                  : propose_to_neighbour(tr, vc, v, fp.eps * (double)tr.D, rng, q);
-      float dl;
-      bool acc = false;
-      if (ok && vertex_move_delta(tr, v, q, &dl)) {
+      if (kind == 0) {
+        ok = mover.propose(tr, vc, v, rng, q);
+      } else if (kind == 2) {
+        ok = mover.resample(tr, vc, v, rng, q);
+      } else if (kind == 3) {
+        const double l = eps_lat * (0.2 + 1.8 * rng.uni());
+        if (vc.kind[v] == 1 && has_neighbour_within(tr, v, tr.P[v], l)) ok = propose_to_neighbour(tr, vc, v, l, rng, q);
+      } else if (kind == 4) {
+        // contract an uncontracted vertex onto a random neighbour (within eps of it), or uncontract a
+        // contracted one by the resampling of Sec. 3.2.4, kept only if it leaves every neighbour
+        if (!has_neighbour_within(tr, v, tr.P[v], eps_lat))
+          ok = propose_to_neighbour(tr, vc, v, eps_lat, rng, q) && has_neighbour_within(tr, v, q, eps_lat);
+        else
+          ok = mover.resample(tr, vc, v, rng, q) && !has_neighbour_within(tr, v, q, eps_lat);
+      } else if (vc.kind[v] == 1) {
+        // the group: free vertices within d of v, found through the triangulation's edges
+        const double d = eps_lat * (0.5 + 4.5 * rng.uni()), d2 = d * d;
+        group.push_back(v);
+        for (size_t g = 0; g < group.size() && group.size() < 64; ++g)
+          tr.for_fan(group[g], [&](int t, int kk) {
+            const int u = tr.T[t].v[(kk + 1) % 3];
+            if (vc.kind[u] == 1 && (double)len2(tr.P[u], tr.P[v]) <= d2 &&
+                std::find(group.begin(), group.end(), u) == group.end())
+              group.push_back(u);
+            return false;
+          });
         region.clear();
-        add_star(tr, v, region);
-        tr.for_fan(v, [&](int t, int kk) {
-          add_star(tr, tr.T[t].v[(kk + 1) % 3], region);
-          return false;
-        });
+        for (int u : group) add_star(tr, u, region);
+        sort_unique(region);
+        double area2 = 0.0;
+        for (int t : region) area2 += (double)orient(tr.P[tr.T[t].v[0]], tr.P[tr.T[t].v[1]], tr.P[tr.T[t].v[2]]);
+        const double eta = std::sqrt(0.5 * area2), r = std::sqrt(rng.uni()), th = 6.283185307179586 * rng.uni();
+        const double step = mover.lambda[1] * eta * r * std::pow(1.0 - rng.uni(), -2.0);
+        const int64_t sx = std::llround(step * std::cos(th)), sy = std::llround(step * std::sin(th));
+        ok = (sx != 0 || sy != 0) && std::llabs(sx) < tr.D && std::llabs(sy) < tr.D;
+        for (int u : group) {
+          const Pt pu{(int32_t)(tr.P[u].x + sx), (int32_t)(tr.P[u].y + sy)};
+          ok = ok && pu.x > 0 && pu.y > 0 && pu.x < tr.D && pu.y < tr.D;
+          newpos.push_back(pu);
+        }
+      }
+      if (group.empty() && ok) {
+        group.push_back(v);
+        newpos.push_back(q);
+      }
+      bool acc = false;
+      if (ok) {
+        region.clear();
+        for (int u : group) {
+          add_star(tr, u, region);
+          tr.for_fan(u, [&](int t, int kk) {
+            add_star(tr, tr.T[t].v[(kk + 1) % 3], region);
+            return false;
+          });
+        }
         sort_unique(region);
         const double e0 = loc.energy(region);
-        const Pt old = tr.P[v];
-        tr.P[v] = q;
-        const double d = loc.energy(region) - e0;
-        if (d <= 0.0 || rng.uni() < std::exp(-d / temp)) {
-          acc = true;
-        } else {
-          tr.P[v] = old;
+        oldpos.clear();
+        for (size_t g = 0; g < group.size(); ++g) {
+          oldpos.push_back(tr.P[group[g]]);
+          tr.P[group[g]] = newpos[g];
         }
+        // every triangle around a moved vertex stays strictly CCW
+        bool valid = true;
+        for (int u : group)
+          valid = valid && !tr.for_fan(u, [&](int t, int) {
+            return orient(tr.P[tr.T[t].v[0]], tr.P[tr.T[t].v[1]], tr.P[tr.T[t].v[2]]) <= 0;
+          });
+        if (valid) {
+          const double dlt = loc.energy(region) - e0;
+          acc = dlt <= 0.0 || rng.uni() < std::exp(-dlt / temp);
+        }
+        if (!acc)
+          for (size_t g = 0; g < group.size(); ++g) tr.P[group[g]] = oldpos[g];
       }
       if (kind == 0) mover.record(vc.kind[v], acc);
       continue;
