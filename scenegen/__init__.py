@@ -383,14 +383,30 @@ def anneal_fuzzy(tri: Triangulation, seed: int, sweeps: float = 20.0, T0: float 
 
 
 def fuzzy_pipeline(segs: np.ndarray, seed: int, sweeps: float = 20.0, polish_sweeps: float = 10.0,
-                   eps_a: float = 0.05, eps_b: float = 1e-4, T0: float = 0.02, T1: float = 1e-4):
+                   eps_a: float = 0.05, eps_b: float = 1e-4, T0: float = 0.02, T1: float = 1e-4,
+                   max_rounds: int = 6):
     """The optimisation of Sec. 3 with fuzzy contraction: the optimally
-    refined CDT, fuzzy annealing and contraction (anneal_fuzzy), then a
+    refined CDT and fuzzy annealing with the contraction of edges shorter than
+    eps_b (anneal_fuzzy), then the contract-and-polish loop of Sec. 3.4: a
     polishing anneal without contraction (edge flips and vertex moves on the
-    plain length, Sec. 3.4) and greedy flips.  Returns (refined CDT, result)."""
+    plain length) and greedy flips, after which the contraction length is
+    doubled and the triangulation contracted and polished again, until the
+    total length stops decreasing (at most max_rounds).  Returns (refined CDT,
+    the shortest triangulation of the loop)."""
     r = refine_optimal(cdt(segs))
-    f, _ = anneal_fuzzy(r, seed, sweeps, T0, T1, eps_a, eps_b)
-    return r, anneal(f, seed + 1, sweeps=polish_sweeps, T0=T1 * 10, T1=T1, moves=1.0, collapse=0.0)
+    cur, _ = anneal_fuzzy(r, seed, sweeps, T0, T1, eps_a, eps_b)
+    best = anneal(cur, seed + 1, sweeps=polish_sweeps, T0=T1 * 10, T1=T1, moves=1.0, collapse=0.0)
+    eps = eps_b
+    for k in range(1, max_rounds):
+        eps *= 2.0
+        nxt, n = anneal_fuzzy(best, seed + 1 + k, 0.0, T0, T1, eps, eps)  # contraction only
+        if n == 0:
+            continue
+        nxt = anneal(nxt, seed + 1 + k, sweeps=polish_sweeps, T0=T1 * 10, T1=T1, moves=1.0, collapse=0.0)
+        if nxt.length(True) >= best.length(True):
+            break
+        best = nxt
+    return r, best
 
 
 def subdivide(tri: Triangulation) -> Triangulation:

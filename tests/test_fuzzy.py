@@ -177,3 +177,18 @@ def test_fuzzy_annealing_and_contraction_keep_the_scene():
     # the fuzzy objective at a small contraction length is the plain length of the result
     fz = sg.fuzzy_objective(out, 1e-12)
     assert abs(fz["w_contr"] - out.length(False) / D) < 1e-6 * fz["w_contr"]
+
+
+def test_fuzzy_pipeline_contract_and_polish():
+    """The full optimisation with fuzzy contraction (Sec. 3: fuzzy annealing,
+    contraction, then the contract-and-polish loop of Sec. 3.4): a valid
+    triangulation of the same segments, shorter than the optimally refined
+    CDT, on which the walk equals the brute force."""
+    segs = sg.circles(600, 91)
+    ref, out = sg.fuzzy_pipeline(segs, 91, sweeps=3, polish_sweeps=3)
+    assert oracle.check_triangulation(out, D) == 0
+    assert oracle.interior_length(out) < oracle.interior_length(ref)
+    r = sg.rays_isotropic(out, 3000, 92)
+    hb, tb = oracle.closest_bruteforce(segs, r.ox, r.oy, r.dx, r.dy)
+    hw, tw, _ = oracle.walk(out, r.ox, r.oy, r.dx, r.dy, r.start)
+    assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
