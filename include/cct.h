@@ -256,8 +256,8 @@ int cct_trace_noalloc(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy,
  * path r; b = 0 is the primary ray): d_hit_seg, d_t, d_steps as cct_trace, and
  * CCT_RAY_NONE in d_steps (hit -1, t NaN) where the path ended earlier.
  * Optional outputs (NULL: not written): d_org_x, d_org_y = the ray's origin in
- * units of 2^-32 (int64; 0 where there is no ray or the primary ray is
- * invalid), d_dir_x, d_dir_y = its direction (0 likewise).
+ * units of 2^-32 (int64; 0 where there is no ray or the ray is invalid),
+ * d_dir_x, d_dir_y = its direction (0 likewise).
  * Launch: blocks of 256 threads, one path per lane; the scene tuning's chunk
  * applies.  flags: 0 or CCT_TRACE_EXACT_ONLY (every decision is exact here).  Scratch
  * (a work counter, located start cells) comes from the stream-ordered
