@@ -382,19 +382,13 @@ def anneal_fuzzy(tri: Triangulation, seed: int, sweeps: float = 20.0, T0: float 
     return _export(h, tri.segs, "fuzzy"), int(n)
 
 
-def fuzzy_pipeline(segs: np.ndarray, seed: int, sweeps: float = 20.0, polish_sweeps: float = 10.0,
-                   eps_a: float = 0.05, eps_b: float = 1e-4, T0: float = 0.02, T1: float = 1e-4,
-                   max_rounds: int = 6):
-    """The optimisation of Sec. 3 with fuzzy contraction: the optimally
-    refined CDT and fuzzy annealing with the contraction of edges shorter than
-    eps_b (anneal_fuzzy), then the contract-and-polish loop of Sec. 3.4: a
-    polishing anneal without contraction (edge flips and vertex moves on the
-    plain length) and greedy flips, after which the contraction length is
-    doubled and the triangulation contracted and polished again, until the
-    total length stops decreasing (at most max_rounds).  Returns (refined CDT,
-    the shortest triangulation of the loop)."""
-    r = refine_optimal(cdt(segs))
-    cur, _ = anneal_fuzzy(r, seed, sweeps, T0, T1, eps_a, eps_b)
+def _optimise_and_contract(tri: Triangulation, seed: int, sweeps: float, polish_sweeps: float, eps_a: float,
+                           eps_b: float, T0: float, T1: float, max_rounds: int) -> Triangulation:
+    """Fuzzy annealing with the contraction of edges shorter than eps_b, then
+    the contract-and-polish loop of Sec. 3.4 (polish without contraction and
+    greedy flips; the contraction length doubled per round until the total
+    length stops decreasing)."""
+    cur, _ = anneal_fuzzy(tri, seed, sweeps, T0, T1, eps_a, eps_b)
     best = anneal(cur, seed + 1, sweeps=polish_sweeps, T0=T1 * 10, T1=T1, moves=1.0, collapse=0.0)
     eps = eps_b
     for k in range(1, max_rounds):
@@ -406,6 +400,24 @@ def fuzzy_pipeline(segs: np.ndarray, seed: int, sweeps: float = 20.0, polish_swe
         if nxt.length(True) >= best.length(True):
             break
         best = nxt
+    return best
+
+
+def fuzzy_pipeline(segs: np.ndarray, seed: int, sweeps: float = 20.0, polish_sweeps: float = 10.0,
+                   eps_a: float = 0.05, eps_b: float = 1e-4, T0: float = 0.02, T1: float = 1e-4,
+                   max_rounds: int = 6, subdivisions: int = 0):
+    """The optimisation of Sec. 3 with fuzzy contraction (the full pipeline of
+    Sec. 3.5.3): the optimally refined CDT through optimisation and
+    contraction (_optimise_and_contract), then, ``subdivisions`` times, a 1 -> 4
+    subdivision of the result through the same process again, keeping the
+    shortest triangulation.  Returns (refined CDT, result)."""
+    r = refine_optimal(cdt(segs))
+    args = (sweeps, polish_sweeps, eps_a, eps_b, T0, T1, max_rounds)
+    best = _optimise_and_contract(r, seed, *args)
+    for k in range(subdivisions):
+        nxt = _optimise_and_contract(subdivide(best), seed + 100 * (k + 1), *args)
+        if nxt.length(True) < best.length(True):
+            best = nxt
     return r, best
 
 

@@ -181,11 +181,12 @@ def test_fuzzy_annealing_and_contraction_keep_the_scene():
 
 def test_fuzzy_pipeline_contract_and_polish():
     """The full optimisation with fuzzy contraction (Sec. 3: fuzzy annealing,
-    contraction, then the contract-and-polish loop of Sec. 3.4): a valid
+    contraction, the contract-and-polish loop of Sec. 3.4, and a second round
+    after a 1 -> 4 subdivision, Sec. 3.5.3): a valid
     triangulation of the same segments, shorter than the optimally refined
     CDT, on which the walk equals the brute force."""
     segs = sg.circles(600, 91)
-    ref, out = sg.fuzzy_pipeline(segs, 91, sweeps=3, polish_sweeps=3)
+    ref, out = sg.fuzzy_pipeline(segs, 91, sweeps=3, polish_sweeps=3, subdivisions=1)
     assert oracle.check_triangulation(out, D) == 0
     assert oracle.interior_length(out) < oracle.interior_length(ref)
     r = sg.rays_isotropic(out, 3000, 92)
