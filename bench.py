@@ -1024,7 +1024,7 @@ def main():
         e2e_step()
     torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / k_e2e
-    # the same pipeline's copies alone (no walk): the copy-bound ceiling of the end-to-end rate on this machine
+    # the same pipeline's copies alone (no walk): a reference for the copy-bound rate (it varies between runs)
     def copies_only():
         for i, (sc, lo) in enumerate(pieces):
             b = i % n_buf
