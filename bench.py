@@ -494,6 +494,60 @@ def run_config5(args, torch, cct, sg, dev):
     print(json.dumps(line))
 
 
+def run_config1(args, torch, cct, sg, dev):
+    """The tiny plain case: 200 random non-crossing segments (CDT and
+    annealed), 65,536 isotropic rays, four seeds; per triangulation the walk
+    from given start cells and the fused locate + walk (CUDA events), steps per
+    ray; as the CPU baseline, the oracle walk and the all-segment brute force
+    timed on the host cores (the brute force is timed here only).  (Their
+    parity with the oracle is a test: tests/test_gpu_walk.py.)"""
+    import oracle
+
+    n = 1 << 16
+    stream = torch.cuda.current_stream(dev)
+    hit = torch.empty(n, dtype=torch.int32, device=dev)
+    t = torch.empty(n, dtype=torch.float32, device=dev)
+    steps = torch.empty(n, dtype=torch.int32, device=dev)
+    out = {}
+    threads = os.cpu_count() or 1
+    for seed in (1, 2, 3, 4):
+        segs = sg.random_segments(200, seed)
+        cdt, _, ann = sg.pipeline(segs, seed, sweeps=20)
+        for kind, tri in (("cdt", cdt), ("annealed", ann)):
+            r = sg.rays_isotropic(tri, n, 10 + seed)
+            d = [torch.from_numpy(getattr(r, k)).to(dev) for k in ("ox", "oy", "dx", "dy", "start")]
+            sc = cct.Scene.from_triangulation(tri, sg.D)
+            res = {}
+            sc.stats(reset=True)
+            for label, st in (("given", d[4]), ("locate", None)):
+                fn = lambda st=st: cct.cct_trace(sc.handle, *d[:4], st, hit, t, steps, 0, stream)
+                for _ in range(3):
+                    fn()
+                ms = _time_loop(torch, dev, stream, fn, max(10, args.steps))
+                res[f"{label}_rays_per_s"] = n / (ms * 1e-3)
+            st = sc.stats(reset=True)
+            res.update(steps_per_ray=st["steps"] / max(1, st["rays"]), triangles=tri.n_tri)
+            # the CPU baseline: the oracle's walk and brute force, timed
+            oracle.walk(tri, r.ox[:1024], r.oy[:1024], r.dx[:1024], r.dy[:1024], r.start[:1024], n_threads=threads)
+            t0 = time.perf_counter()
+            oracle.walk(tri, r.ox, r.oy, r.dx, r.dy, r.start, n_threads=threads)
+            t1 = time.perf_counter()
+            oracle.closest_bruteforce(segs, r.ox, r.oy, r.dx, r.dy, n_threads=threads)
+            t2 = time.perf_counter()
+            res["cpu_baseline"] = {"oracle_walk_rays_per_s": n / (t1 - t0),
+                                   "oracle_bruteforce_rays_per_s": n / (t2 - t1), "cores": threads}
+            out[f"seed{seed}/{kind}"] = res
+            sc.free()
+    mean = lambda key, kind: float(np.mean([v[key] for k, v in out.items() if k.endswith(kind)]))
+    print(json.dumps({"config": "1: 200 random segments, 65,536 isotropic rays, four seeds", "per_scene": out,
+                      "steps_per_ray": {"cdt": mean("steps_per_ray", "cdt"),
+                                        "annealed": mean("steps_per_ray", "annealed")},
+                      "given_rays_per_s": mean("given_rays_per_s", "annealed"),
+                      "locate_rays_per_s": mean("locate_rays_per_s", "annealed"), "cpu_cores": threads,
+                      "note": "65,536 rays are a few microseconds of GPU work: the rates are launch-bound"}))
+    return 0
+
+
 def run_config3(args, torch, cct, sg, dev):
     """Ring of circles, N = 1e3 .. 1e6 in a fixed domain; 2^26 isotropic rays and
     4096 pinhole fans of 4096 rays; start cells from the GPU locate."""
@@ -679,8 +733,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--flags", default="auto", help="auto | plain | bin")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="2", choices=["2", "3", "4", "5", "lines"],
-                    help="2 (default): the six config-2 scene families; 3: scaling in N; 4: 512 scenes in one "
+    ap.add_argument("--config", default="2", choices=["1", "2", "3", "4", "5", "lines"],
+                    help="2 (default): the six config-2 scene families; 1: the tiny plain case (200 segments, "
+                         "65,536 rays, with the oracle's rates); 3: scaling in N; 4: 512 scenes in one "
                          "batched launch; 5: the continuous-batching server; lines: operations per ray vs N on "
                          "the paper's lines scenes (walk, kd-tree, BVH)")
     ap.add_argument("--profile", action="store_true",
@@ -729,7 +784,7 @@ def main():
     if args.profile_kernels:
         return run_profile_kernels(args, torch, cct, sg, dev)
     if args.config != "2":
-        fn = {"3": run_config3, "4": run_config4, "5": run_config5, "lines": run_lines}[args.config]
+        fn = {"1": run_config1, "3": run_config3, "4": run_config4, "5": run_config5, "lines": run_lines}[args.config]
         fn(args, torch, cct, sg, dev)
         return 0
     fams = tuple(f for f in args.families.split(",") if f) if args.profile else FAMILIES
