@@ -136,7 +136,7 @@ def tune_batch(batch: "cct.Batch", items, reps: int = 3) -> dict:
     stream = torch.cuda.current_stream()
     best, best_ms, tried = None, float("inf"), {}
     for bt in KNOBS["block_threads"]:
-        for rm in (1, 8, 16):
+        for rm in (8, 16, 24, 32):
             for ch in KNOBS["chunk"]:
                 tu = {"block_threads": bt, "refill_min": rm, "chunk": ch}
                 batch.set_tuning(tu)
