@@ -319,3 +319,24 @@ def test_scene_from_file_traces_identically(cct, scenes, tmp_path):
     for start in (r.start, None):
         _assert_parity(_trace(from_file, r.ox, r.oy, r.dx, r.dy, start), exp)
     from_file.free()
+
+
+@pytest.mark.parametrize("N", [100_000, 1_000_000])
+def test_config3_ring_of_circles_sampled(cct, N):
+    """The scaling workload (ring of circles in a fixed domain, built as the
+    scaling run builds it) at 10^5 and 10^6 segments, where the tables outgrow
+    L2: 2^22 isotropic rays and 1024 pinhole fans of 4096 rays, start cells from
+    the fused locate and with binning; 4096 sampled rays of each equal the
+    oracle (start cells from the CPU)."""
+    segs = sg.ring_of_circles(N)
+    tri = sg.pipeline(segs, 3, sweeps=1)[2]
+    scene = cct.Scene.from_triangulation(tri, sg.D)
+    try:
+        for name, r in (("iso", sg.rays_isotropic(tri, 1 << 22, 11)), ("fans", sg.rays_pinhole(tri, 1024, 4096, 12))):
+            idx = np.sort(np.random.default_rng(13).choice(len(r), 4096, replace=False))
+            exp = oracle.walk(tri, r.ox[idx], r.oy[idx], r.dx[idx], r.dy[idx], r.start[idx])
+            for flags in (0, cct.CCT_TRACE_BIN):
+                h, t, s = _trace(scene, r.ox, r.oy, r.dx, r.dy, None, flags)
+                _assert_parity((h[idx], t[idx], s[idx]), exp)
+    finally:
+        scene.free()
