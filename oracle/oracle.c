@@ -14,6 +14,9 @@
  *     one exit-edge determination (Sec. 5.4);
  *   - the step count by brute force (1 + interior edges crossed before the hit);
  *   - point location by scanning all triangles (Sec. 5.2's start triangle);
+ *   - paths of secondary rays that start in the final triangle of their
+ *     parent's walk (Sec. 5.2), walk-chained and by brute force (see the
+ *     section "secondary rays" for the readings);
  *   - triangulation invariants and the Cauchy-Crofton line statistic that ties
  *     edge length to traversal cost (Sec. 1.4).
  *
@@ -29,7 +32,10 @@
  * All hit / step decisions are exact integer arithmetic (int64, int128); t is
  * reported as the fp32 rounding of num/den computed in fp64 (both exact in fp64).
  * parity pinned: see tests/test_oracle.py (brute force vs walk vs step count,
- * golden worked examples, Crofton identity, planted mutations).
+ * golden worked examples, Crofton identity, planted mutations) and
+ * tests/test_oracle_bounce.py (secondary rays: brute force vs chained walks,
+ * closed forms on parallel and 45-degree mirrors, exact snapped origins,
+ * planted mutations).
  */
 #include <math.h>
 #include <pthread.h>
