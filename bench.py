@@ -673,8 +673,8 @@ def run_profile_kernels(args, torch, cct, sg, dev):
     (2^23 isotropic rays, larger than L2 with their results): the locate
     kernel, the binned trace (locate, histogram, three scan passes, scatter,
     sorted walk), the split and fused walks, the kd-tree and BVH baselines,
-    a four-item batched launch over the same scene, mirror paths of 2^21 of
-    the rays with 8 bounces and the gather peak; each
+    a four-item batched launch over the same scene, mirror and diffuse paths
+    of 2^21 of the rays with 8 bounces and the gather peak; each
     twice (warm-up, then the launch a profiler captures).  Prints the
     CUDA-event time of the second launch of each call."""
     name = args.families.split(",")[0]
@@ -699,6 +699,11 @@ def run_profile_kernels(args, torch, cct, sg, dev):
     batch = cct.Batch([scene], max_items=4)
     batch.stage(items)
     nb_rays = 1 << 21  # mirror paths: 2^21 primary rays, up to 8 bounces (9 records each)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    th = torch.asin(2.0 * torch.rand((N_BOUNCE, nb_rays), generator=gen, device=dev, dtype=torch.float64) - 1.0)
+    frame = (torch.stack([torch.round(torch.sin(th) * 2.0 ** 22), torch.round(torch.cos(th) * 2.0 ** 22)], -1)
+             / 2.0 ** 22).to(torch.float32).contiguous()  # diffuse bounces (cosine-weighted, in the hit edges' frames)
     calls = {
         "locate_kernel": lambda: cct.cct_locate(scene.handle, d[0], d[1], loc, stream),
         "binned_trace": lambda: cct.cct_trace(scene.handle, *d, None, hit, t, steps, cct.CCT_TRACE_BIN, stream),
@@ -711,6 +716,9 @@ def run_profile_kernels(args, torch, cct, sg, dev):
         "batched_4_items": lambda: batch.enqueue(stream),
         "bounce_8": lambda: scene.trace_bounces(d[0][:nb_rays], d[1][:nb_rays], d[2][:nb_rays], d[3][:nb_rays],
                                                 N_BOUNCE, start=start[:nb_rays], stream=stream, with_rays=False),
+        "bounce_8_diffuse": lambda: scene.trace_bounces(d[0][:nb_rays], d[1][:nb_rays], d[2][:nb_rays],
+                                                        d[3][:nb_rays], N_BOUNCE, start=start[:nb_rays], stream=stream,
+                                                        with_rays=False, frame=frame),
     }
     out = {}
     for label, fn in calls.items():
