@@ -165,3 +165,17 @@ def test_scene_file_round_trip_and_malformed_files(tmp_path):
     bad[off:off + 4] = np.array([t.n_tri + 7], "<i4").tobytes()
     expect(bytes(bad), cct.CCT_ERR_BAD_TRIANGULATION, "arrays")
     assert "file" in cct.cct_error_string(cct.CCT_ERR_IO)
+
+
+def test_binding_constants_match_the_header():
+    """Every integer constant include/cct.h defines (status codes, per-ray
+    statuses, load and trace flags, limits) has the same value in the Python
+    binding."""
+    txt = open(os.path.join(ROOT, "include", "cct.h")).read()
+    defs = dict(re.findall(r"^#define (CCT_[A-Z0-9_]+) \(?([-0-9<> ]+?)u?\)?\s*(?:/\*|$)", txt, re.M))
+    defs = {k: eval(v.replace("u", "")) for k, v in defs.items() if k != "CCT_H"}  # noqa: S307 (integer literals)
+    assert {"CCT_OK", "CCT_ERR_IO", "CCT_RAY_NONE", "CCT_MAX_BOUNCES", "CCT_TRACE_BIN",
+            "CCT_NOALLOC_MAX_RAYS"} <= set(defs)
+    for name, value in defs.items():
+        assert getattr(cct, name) == value, name
+    assert cct.CCT_LOAD_SEED_DENSITY(3) == (3 + 1) << 8
