@@ -59,3 +59,18 @@ def test_two_replicas_time_and_throughput():
 def test_single_process_is_identity():
     assert bench.job_step_ms(None, 3.5) == 3.5
     assert bench.job_rays_per_s(10, 1, 2.0) == pytest.approx(5000.0)
+
+
+def test_roofline_object_schema():
+    """The bench's roofline object: bound hbm against the measured HBM copy
+    peak (achieved / peak = frac), the traffic figure, and the stricter
+    live random-gather peak beside it."""
+    import bench
+
+    r = bench.make_roofline(5000.0, 9000.0, 6775.3, "MEASURED_PEAKS.json hbm_gbs (of measured)", 4.47e9, "note",
+                            5.8, 3.1e10)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6775.3
+    assert abs(r["frac"] - 5000.0 / 6775.3) < 1e-12 and r["traffic"] == 4.47e9
+    assert abs(r["l2_gather"]["frac"] - 5000.0 / 9000.0) < 1e-12
+    for key in ("achieved", "peak", "unit", "frac", "traffic", "bound"):
+        assert key in r
