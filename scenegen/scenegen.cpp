@@ -1314,10 +1314,17 @@ struct FuzzyLocal {
   const Triangulation& tr;
   const VertexClasses& vc;
   const FuzzyParams& fp;
-  std::vector<std::pair<uint64_t, double>> memo;
-  std::vector<uint64_t> seen;
+  // open-addressing tables keyed by edge (cleared per evaluation through a generation stamp):
+  // the memoised c of an edge, and the edges already summed
+  static constexpr int kBits = 12, kSize = 1 << kBits;
+  std::vector<uint64_t> key_c, key_s;
+  std::vector<uint32_t> gen_c, gen_s;
+  std::vector<double> val_c;
+  uint32_t gen = 0;
 
-  FuzzyLocal(const Triangulation& t, const VertexClasses& v, const FuzzyParams& f) : tr(t), vc(v), fp(f) {}
+  FuzzyLocal(const Triangulation& t, const VertexClasses& v, const FuzzyParams& f)
+      : tr(t), vc(v), fp(f), key_c(kSize), key_s(kSize), gen_c(kSize, 0), gen_s(kSize, 0), val_c(kSize) {}
+  static uint32_t slot(uint64_t k) { return (uint32_t)((k * 0x9E3779B97F4A7C15ull) >> (64 - kBits)); }
   static uint64_t key(int p, int q) {
     return p < q ? ((uint64_t)(uint32_t)p << 32) | (uint32_t)q : ((uint64_t)(uint32_t)q << 32) | (uint32_t)p;
   }
@@ -1329,13 +1336,29 @@ struct FuzzyLocal {
     if (fp.polish) return 1.0;
     const Tri& x = tr.T[t];
     const uint64_t k = key(x.v[(i + 1) % 3], x.v[(i + 2) % 3]);
-    for (const auto& m : memo)
-      if (m.first == k) return m.second;
+    uint32_t h = slot(k);
+    while (gen_c[h] == gen) {
+      if (key_c[h] == k) return val_c[h];
+      h = (h + 1) & (kSize - 1);
+    }
     const double v = fuzzy_contractible(tr, vc, fp.eps * (double)tr.D, t, i)
                          ? 0.5 + std::min(1.0, len(t, i) / fp.eps) / 2.0
                          : 1.0;
-    memo.push_back({k, v});
+    gen_c[h] = gen;
+    key_c[h] = k;
+    val_c[h] = v;
     return v;
+  }
+  // whether edge k was summed already in this evaluation (and mark it)
+  bool seen_before(uint64_t k) {
+    uint32_t h = slot(k);
+    while (gen_s[h] == gen) {
+      if (key_s[h] == k) return true;
+      h = (h + 1) & (kSize - 1);
+    }
+    gen_s[h] = gen;
+    key_s[h] = k;
+    return false;
   }
   double w(int t, int i) {
     if (fp.polish) return 1.0;
@@ -1348,15 +1371,17 @@ struct FuzzyLocal {
     return P * multi_merge(P);
   }
   double energy(const std::vector<int>& tris) {
-    memo.clear();
-    seen.clear();
+    if (++gen == 0) {  // the stamp wrapped: clear the tables
+      std::fill(gen_c.begin(), gen_c.end(), 0);
+      std::fill(gen_s.begin(), gen_s.end(), 0);
+      gen = 1;
+    }
     double E = 0.0;
     for (int t : tris)
       for (int i = 0; i < 3; ++i) {
         const Tri& x = tr.T[t];
         const uint64_t k = key(x.v[(i + 1) % 3], x.v[(i + 2) % 3]);
-        if (std::find(seen.begin(), seen.end(), k) != seen.end()) continue;
-        seen.push_back(k);
+        if (seen_before(k)) continue;
         const double l = len(t, i);
         E += w(t, i) * l + fp.mu_len * std::max(0.0, fp.eps0 - l) / fp.eps0;
       }
