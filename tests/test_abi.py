@@ -1,6 +1,7 @@
 """C-ABI library checks that need no GPU: libcct.so loads, exports every symbol
 include/cct.h declares, and its host-side validation returns status codes."""
 import ctypes
+import json
 import os
 import re
 
@@ -179,3 +180,34 @@ def test_binding_constants_match_the_header():
     for name, value in defs.items():
         assert getattr(cct, name) == value, name
     assert cct.CCT_LOAD_SEED_DENSITY(3) == (3 + 1) << 8
+
+
+def test_offline_build_command(tmp_path):
+    """python -m scenegen build writes a triangulation file (with its segments)
+    that reads back valid and passes cct_scene_load_file's header checks; the
+    checkpointed build resumes to the same file."""
+    import subprocess
+    import sys
+
+    import oracle
+
+    out = str(tmp_path / "s.cct")
+    cmd = [sys.executable, "-m", "scenegen", "build", "--family", "circles", "--n", "800", "--seed", "3",
+           "--sweeps", "2", "--checkpoint", str(tmp_path / "ck.cct"), "--out", out]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, check=True)
+    rep = json.loads(r.stdout.strip().splitlines()[-1])
+    assert rep["triangles"] > 0 and rep["interior_length_over_cdt"] < 1.0
+    segs = np.load(out + ".segs.npy")
+    tri = sg.load(out, segs)
+    assert oracle.check_triangulation(tri, sg.D) == 0
+    info = subprocess.run([sys.executable, "-m", "scenegen", "info", out], cwd=ROOT, capture_output=True, text=True,
+                          check=True)
+    assert json.loads(info.stdout)["triangles"] == tri.n_tri
+    again = subprocess.run(cmd[:-1] + [str(tmp_path / "t.cct")], cwd=ROOT, capture_output=True, text=True, check=True)
+    assert open(str(tmp_path / "t.cct"), "rb").read() == open(out, "rb").read()
+    import torch
+
+    if not torch.cuda.is_available():
+        with pytest.raises(cct.CctError) as e:
+            cct.cct_scene_load_file(out)
+        assert e.value.code == cct.CCT_ERR_NO_DEVICE  # past the header and size checks
