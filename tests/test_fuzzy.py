@@ -193,3 +193,38 @@ def test_fuzzy_pipeline_contract_and_polish():
     hb, tb = oracle.closest_bruteforce(segs, r.ox, r.oy, r.dx, r.dy)
     hw, tw, _ = oracle.walk(out, r.ox, r.oy, r.dx, r.dy, r.start)
     assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
+
+
+def test_contraction_along_a_segment_and_fixed_vertices():
+    """The contraction of short edges (Sec. 3.4): a Steiner vertex inside a
+    segment, a few units from the segment's endpoint, merges into the endpoint
+    along the segment (the segment stays covered by constrained edges and the
+    walk equals the brute force); a short segment between two fixed vertices
+    is never contracted."""
+    h = D // 2
+    # segment A-B with a Steiner vertex S 3 units from A; a short fixed segment P-Q elsewhere
+    pts = {"BL": (0, 0), "BR": (D, 0), "TR": (D, D), "TL": (0, D),
+           "A": (h - 200_000, h), "S": (h - 199_997, h), "B": (h + 200_000, h),
+           "P": (h, h + 300_000), "Q": (h + 5, h + 300_001)}
+    tris = [["BL", "BR", "A"], ["A", "BR", "S"], ["S", "BR", "B"], ["B", "BR", "TR"], ["B", "TR", "Q"],
+            ["Q", "TR", "TL"], ["P", "Q", "TL"], ["A", "S", "P"], ["S", "B", "P"], ["B", "Q", "P"],
+            ["A", "P", "TL"], ["BL", "A", "TL"]]
+    segs = [[h - 200_000, h, h + 200_000, h], [h, h + 300_000, h + 5, h + 300_001]]
+    tri, idx = _from_triangles(pts, tris, segs=segs, constrained=[("A", "S"), ("P", "Q")])
+    # S-B carries segment 0 too
+    ts = tri.tri_seg.copy()
+    for t in range(tri.n_tri):
+        for i in range(3):
+            if {tri.tri_v[t, (i + 1) % 3], tri.tri_v[t, (i + 2) % 3]} == {idx["S"], idx["B"]}:
+                ts[t, i] = 0
+    tri = sg.from_arrays(tri.vx, tri.vy, tri.tri_v, tri.tri_nb, ts, np.asarray(segs, np.int32))
+    assert oracle.check_triangulation(tri, D) == 0
+    out, n = sg.anneal_fuzzy(tri, 5, sweeps=0.0, eps_b=1e-4)  # contraction only: edges < 105 units
+    assert n == 1 and out.n_vert == tri.n_vert - 1
+    assert oracle.check_triangulation(out, D) == 0
+    pts_out = set(zip(out.vx.tolist(), out.vy.tolist()))
+    assert pts["S"] not in pts_out and pts["A"] in pts_out and pts["P"] in pts_out and pts["Q"] in pts_out
+    r = sg.rays_isotropic(out, 4000, 6)
+    hb, tb = oracle.closest_bruteforce(np.asarray(segs, np.int32), r.ox, r.oy, r.dx, r.dy)
+    hw, tw, _ = oracle.walk(out, r.ox, r.oy, r.dx, r.dy, r.start)
+    assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
