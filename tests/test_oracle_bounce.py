@@ -298,3 +298,60 @@ def test_frame_directions_on_parallel_mirrors_closed_form():
     perp[..., 1] = 1.0
     Wp = oracle.bounce_walk(tri, ox, oy, dx, dy, st, nb, frame=perp)
     assert np.array_equal(Wp["dir_y"][1], -dy) and (Wp["dir_x"][1] == 0).all()
+
+
+def _two_mirror_room(split_top: bool):
+    """Lower mirror y = 100000 and upper mirror y = 500000 (x from 100000 to
+    900000); the upper one either one segment with a Steiner vertex at x =
+    500000 (split_top) or two collinear segments meeting there."""
+    import test_fuzzy as tf
+
+    pts = {"BL": (0, 0), "BR": (D, 0), "TR": (D, D), "TL": (0, D),
+           "L0": (100_000, 100_000), "L1": (900_000, 100_000),
+           "U0": (100_000, 500_000), "UM": (500_000, 500_000), "U1": (900_000, 500_000)}
+    tris = [["BL", "BR", "L1"], ["BL", "L1", "L0"], ["BL", "L0", "U0"], ["BL", "U0", "TL"],
+            ["L1", "BR", "U1"], ["BR", "TR", "U1"], ["U1", "TR", "TL"], ["UM", "U1", "TL"], ["U0", "UM", "TL"],
+            ["L0", "L1", "UM"], ["L0", "UM", "U0"], ["L1", "U1", "UM"]]
+    if split_top:
+        segs = [[100_000, 100_000, 900_000, 100_000], [100_000, 500_000, 900_000, 500_000]]
+        cons = [("L0", "L1"), ("U0", "UM"), ("UM", "U1")]
+        labels = {("L0", "L1"): 0, ("U0", "UM"): 1, ("UM", "U1"): 1}
+    else:
+        segs = [[100_000, 100_000, 900_000, 100_000], [100_000, 500_000, 500_000, 500_000],
+                [500_000, 500_000, 900_000, 500_000]]
+        cons = [("L0", "L1"), ("U0", "UM"), ("UM", "U1")]
+        labels = {("L0", "L1"): 0, ("U0", "UM"): 1, ("UM", "U1"): 2}
+    tri, idx = tf._from_triangles(pts, tris, segs=segs, constrained=cons)
+    ts = tri.tri_seg.copy()
+    for t in range(tri.n_tri):
+        for i in range(3):
+            e = {tri.tri_v[t, (i + 1) % 3], tri.tri_v[t, (i + 2) % 3]}
+            for (a, b), lab in labels.items():
+                if e == {idx[a], idx[b]}:
+                    ts[t, i] = lab
+    tri = sg.from_arrays(tri.vx, tri.vy, tri.tri_v, tri.tri_nb, ts, np.asarray(segs, np.int32))
+    assert oracle.check_triangulation(tri, D) == 0
+    return tri, np.asarray(segs, np.int32)
+
+
+@pytest.mark.parametrize("split_top", [True, False])
+def test_secondary_ray_from_a_vertex_hit(split_top):
+    """A ray straight up through the vertex (500000, 500000) of the upper
+    mirror: the ray, shifted infinitesimally to its right, hits the part of the
+    mirror on its right (the sub-edge towards x = 900000, or the right-hand
+    segment when two segments meet there); the secondary origin is snapped to
+    i = 2^32 - 1 on that edge, just right of the vertex, and the mirror image
+    goes straight down to the lower mirror at t = 400000.  Walk = brute force."""
+    tri, segs = _two_mirror_room(split_top)
+    ox, oy, dx, dy = _rays([500_000], [300_001], [0], [1 << 22])
+    st = _locate(tri, ox, oy)
+    W = oracle.bounce_walk(tri, ox, oy, dx, dy, st, 2)
+    _equal_paths(W, oracle.bounce_bruteforce(tri, ox, oy, dx, dy, 2))
+    right = 1 if split_top else 2
+    assert W["hit"][0, 0] == right and W["t"][0, 0] == np.float32(199_999)
+    # snapped on the edge (U1 -> UM): a = U1 (right of the upward ray), b = UM on its line: mu = 1 -> i = 2^32 - 1
+    X, Y = int(W["org_x"][1, 0]), int(W["org_y"][1, 0])
+    assert Y == 500_000 * Q and X == 900_000 * Q + (Q - 1) * (500_000 - 900_000)
+    assert X > 500_000 * Q  # just right of the vertex
+    assert W["dir_x"][1, 0] == 0 and W["dir_y"][1, 0] == -1.0
+    assert W["hit"][1, 0] == 0 and W["t"][1, 0] == np.float32(400_000)
