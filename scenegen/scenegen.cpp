@@ -1315,16 +1315,46 @@ struct FuzzyLocal {
   const VertexClasses& vc;
   const FuzzyParams& fp;
   // open-addressing tables keyed by edge (cleared per evaluation through a generation stamp):
-  // the memoised c of an edge, and the edges already summed
-  static constexpr int kBits = 12, kSize = 1 << kBits;
+  // the memoised c of an edge, and the edges already summed; each grows (rehashing its live
+  // entries) before it is half full, so a probe always ends at a free slot
+  int bits = 12;
+  uint32_t mask = (1u << 12) - 1;
   std::vector<uint64_t> key_c, key_s;
   std::vector<uint32_t> gen_c, gen_s;
   std::vector<double> val_c;
   uint32_t gen = 0;
+  size_t used_c = 0, used_s = 0;
 
   FuzzyLocal(const Triangulation& t, const VertexClasses& v, const FuzzyParams& f)
-      : tr(t), vc(v), fp(f), key_c(kSize), key_s(kSize), gen_c(kSize, 0), gen_s(kSize, 0), val_c(kSize) {}
-  static uint32_t slot(uint64_t k) { return (uint32_t)((k * 0x9E3779B97F4A7C15ull) >> (64 - kBits)); }
+      : tr(t), vc(v), fp(f), key_c(4096), key_s(4096), gen_c(4096, 0), gen_s(4096, 0), val_c(4096) {}
+  uint32_t slot(uint64_t k) const { return (uint32_t)((k * 0x9E3779B97F4A7C15ull) >> (64 - bits)); }
+  void grow() {
+    std::vector<uint64_t> kc = key_c, ks = key_s;
+    std::vector<uint32_t> gc = gen_c, gs = gen_s;
+    std::vector<double> vcv = val_c;
+    ++bits;
+    mask = (1u << bits) - 1;
+    key_c.assign((size_t)1 << bits, 0);
+    key_s.assign((size_t)1 << bits, 0);
+    gen_c.assign((size_t)1 << bits, 0);
+    gen_s.assign((size_t)1 << bits, 0);
+    val_c.assign((size_t)1 << bits, 0.0);
+    for (size_t j = 0; j < kc.size(); ++j)
+      if (gc[j] == gen) {
+        uint32_t h = slot(kc[j]);
+        while (gen_c[h] == gen) h = (h + 1) & mask;
+        gen_c[h] = gen;
+        key_c[h] = kc[j];
+        val_c[h] = vcv[j];
+      }
+    for (size_t j = 0; j < ks.size(); ++j)
+      if (gs[j] == gen) {
+        uint32_t h = slot(ks[j]);
+        while (gen_s[h] == gen) h = (h + 1) & mask;
+        gen_s[h] = gen;
+        key_s[h] = ks[j];
+      }
+  }
   static uint64_t key(int p, int q) {
     return p < q ? ((uint64_t)(uint32_t)p << 32) | (uint32_t)q : ((uint64_t)(uint32_t)q << 32) | (uint32_t)p;
   }
@@ -1339,11 +1369,17 @@ struct FuzzyLocal {
     uint32_t h = slot(k);
     while (gen_c[h] == gen) {
       if (key_c[h] == k) return val_c[h];
-      h = (h + 1) & (kSize - 1);
+      h = (h + 1) & mask;
     }
     const double v = fuzzy_contractible(tr, vc, fp.eps * (double)tr.D, t, i)
                          ? 0.5 + std::min(1.0, len(t, i) / fp.eps) / 2.0
                          : 1.0;
+    if (2 * (used_c + 1) > key_c.size()) {
+      grow();
+      h = slot(k);
+      while (gen_c[h] == gen) h = (h + 1) & mask;
+    }
+    ++used_c;
     gen_c[h] = gen;
     key_c[h] = k;
     val_c[h] = v;
@@ -1354,8 +1390,14 @@ struct FuzzyLocal {
     uint32_t h = slot(k);
     while (gen_s[h] == gen) {
       if (key_s[h] == k) return true;
-      h = (h + 1) & (kSize - 1);
+      h = (h + 1) & mask;
     }
+    if (2 * (used_s + 1) > key_s.size()) {
+      grow();
+      h = slot(k);
+      while (gen_s[h] == gen) h = (h + 1) & mask;
+    }
+    ++used_s;
     gen_s[h] = gen;
     key_s[h] = k;
     return false;
@@ -1376,6 +1418,7 @@ struct FuzzyLocal {
       std::fill(gen_s.begin(), gen_s.end(), 0);
       gen = 1;
     }
+    used_c = used_s = 0;
     double E = 0.0;
     for (int t : tris)
       for (int i = 0; i < 3; ++i) {
@@ -1462,7 +1505,8 @@ static bool has_neighbour_within(const Triangulation& tr, int v, const Pt& q, do
 // neighbour closer than l ~ U[0.2 eps, 2 eps] resampled in the disk of radius l about a random
 // neighbour) and the contraction to a neighbour (Sec. 3.2.6: an uncontracted vertex resampled within
 // eps of a random neighbour, a contracted one by the resampling of Sec. 3.2.4 kept only if it leaves
-// every neighbour),
+// every neighbour), and, in 2 % of the vertex proposals, the perturbation of 2 % of the movable
+// vertices at once (Sec. 3.2.2's second variant, one Metropolis decision),
 // with Metropolis acceptance on the exact change of f over a region that holds every edge whose
 // weight the proposal can change: for a vertex move the triangles of the stars of the vertex and of
 // its neighbours (lengths and contractibility distances change at the vertex; an edge's weight reads
@@ -1491,7 +1535,9 @@ static void anneal_fuzzy(Triangulation& tr, uint64_t seed, double sweeps, double
     if (p_move > 0 && rng.uni() < p_move) {
       const int v = movable[rng.below((uint32_t)movable.size())];
       const double eps_lat = fp.eps * (double)tr.D;
-      const int kind = (int)rng.below(5);  // 3.2.2, 3.2.3, 3.2.4, 3.2.5, 3.2.6
+      // 3.2.2, 3.2.3, 3.2.4, 3.2.5, 3.2.6 in equal shares; 3.2.2 on 2 % of the vertices at once
+      // in 2 % of the proposals (each costs as much as up to 64 single moves)
+      const int kind = rng.uni() < 0.02 ? 5 : (int)rng.below(5);
       // the vertices that move and their new positions
       group.clear();
       newpos.clear();
@@ -1511,6 +1557,19 @@ static void anneal_fuzzy(Triangulation& tr, uint64_t seed, double sweeps, double
           ok = propose_to_neighbour(tr, vc, v, eps_lat, rng, q) && has_neighbour_within(tr, v, q, eps_lat);
         else
           ok = mover.resample(tr, vc, v, rng, q) && !has_neighbour_within(tr, v, q, eps_lat);
+      } else if (kind == 5) {
+        // Sec. 3.2.2's second variant: 2 % of the movable vertices perturbed at once (one decision)
+        const size_t m = std::min<size_t>(64, std::max<size_t>(1, (size_t)std::llround(0.02 * (double)movable.size())));
+        ok = true;
+        for (size_t g = 0; g < m && ok; ++g) {
+          const int u = movable[rng.below((uint32_t)movable.size())];
+          if (std::find(group.begin(), group.end(), u) != group.end()) continue;
+          Pt pu;
+          if (!mover.propose(tr, vc, u, rng, pu)) continue;
+          group.push_back(u);
+          newpos.push_back(pu);
+        }
+        ok = !group.empty();
       } else if (vc.kind[v] == 1) {
         // the group: free vertices within d of v, found through the triangulation's edges
         const double d = eps_lat * (0.5 + 4.5 * rng.uni()), d2 = d * d;
