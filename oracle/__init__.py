@@ -25,9 +25,11 @@ _libs: dict[int, ctypes.CDLL] = {}
 # failure bits of check_triangulation
 BAD_INDEX, NOT_CCW, AREA, NB_ASYM, HULL, EULER, CONSTRAINT_ASYM, COVERAGE, NOT_DELAUNAY = (
     1, 2, 4, 8, 16, 32, 64, 128, 256)
-N_MUTANTS = 7
+N_MUTANTS = 11
 PRIMARY_MUTANTS = (1, 2, 3, 4)  # planted in the primary-ray predicates and walk
 BOUNCE_MUTANTS = (5, 6, 7)  # planted in the secondary-ray construction
+KD_MUTANTS = (8, 9)  # planted in the kd-tree's rope-search count
+BVH_MUTANTS = (10, 11)  # planted in the BVH's traversal order and pruning
 BOUNCE_NONE = -3  # steps of a path entry with no ray
 
 
@@ -71,7 +73,7 @@ def _load(mutant: int = 0) -> ctypes.CDLL:
     L.oracle_bvh_trace.restype = ctypes.c_int
     L.oracle_bvh_trace.argtypes = [i32, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, i32]
     L.oracle_kd_trace.restype = ctypes.c_int
-    L.oracle_kd_trace.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, i32]
+    L.oracle_kd_trace.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, i32]
     L.oracle_bounce_walk.restype = ctypes.c_int
     L.oracle_bounce_walk.argtypes = [i64, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp,
                                      vp, i64, vp, i32]
@@ -266,9 +268,9 @@ def crofton_lines(n, seed, D):
     return cx, cy, p
 
 
-def bvh_trace(b, ox, oy, dx, dy, n_threads=None):
+def bvh_trace(b, ox, oy, dx, dy, n_threads=None, mutant=0):
     """BVH traversal of Sec. 5.3.1: (hit, t, ops (n,2): AABB tests, segment tests)."""
-    L = _load()
+    L = _load(mutant)
     box, c0, c1, pr = (_c(x, np.int32) for x in (b.box, b.child0, b.child1, b.prims))
     segs = _c(b.segs, np.int32)
     ox, oy, dx, dy = _c(ox, np.int32), _c(oy, np.int32), _c(dx, np.float32), _c(dy, np.float32)
@@ -279,12 +281,13 @@ def bvh_trace(b, ox, oy, dx, dy, n_threads=None):
     return hit, t, ops
 
 
-def kd_trace(k, ox, oy, dx, dy, n_threads=None):
+def kd_trace(k, ox, oy, dx, dy, n_threads=None, mutant=0):
     """Roped kd-tree traversal of Sec. 5.3.2: (hit, t, ops (n,6)): leaves,
-    descent nodes, segment tests, distinct segments, log2 rope sum, 0."""
-    L = _load()
-    arrs = [_c(x, np.int32) for x in (k.axis, k.split, k.child, k.count, k.box, k.rope, k.rope_log2, k.refs,
-                                      k.segs)]
+    descent nodes, segment tests, distinct segments, rope search steps of an
+    ideal rope tree (the rope counts found from the node boxes, not read from
+    the tree's own table), 0."""
+    L = _load(mutant)
+    arrs = [_c(x, np.int32) for x in (k.axis, k.split, k.child, k.count, k.box, k.rope, k.refs, k.segs)]
     ox, oy, dx, dy = _c(ox, np.int32), _c(oy, np.int32), _c(dx, np.float32), _c(dy, np.float32)
     n = ox.size
     hit, t, ops = np.empty(n, np.int32), np.empty(n, np.float32), np.empty((n, 6), np.int32)

@@ -737,7 +737,9 @@ static void bvh_range(void* p, int64_t lo, int64_t hi) {
       --sp;
       int32_t N = stack[sp];
       q64 bt = {b.t.num, b.t.den};
+#if ORACLE_MUTANT != 10 /* planted (10): nodes entered beyond the best hit are still opened */
       if (b.seg >= 0 && q_cmp(st_t[sp], bt) > 0) continue; /* entered beyond the best hit */
+#endif
       int32_t c0 = c->c0[N], c1 = c->c1[N];
       if (c0 < 0) { /* leaf: test every segment */
         for (int32_t k = 0; k < c1; ++k) {
@@ -755,7 +757,11 @@ static void bvh_range(void* p, int64_t lo, int64_t hi) {
       if (h0 && b.seg >= 0 && q_cmp(t0, bt) > 0) h0 = 0;
       if (h1 && b.seg >= 0 && q_cmp(t1, bt) > 0) h1 = 0;
       if (h0 && h1) { /* the nearer child is visited first; the left one on equal entry */
+#if ORACLE_MUTANT == 11 /* planted: the left child first whatever the entry parameters */
+        int left_first = 1;
+#else
         int left_first = q_cmp(t0, t1) <= 0;
+#endif
         stack[sp] = left_first ? c1 : c0;
         st_t[sp++] = left_first ? t1 : t0;
         stack[sp] = left_first ? c0 : c1;
@@ -787,12 +793,56 @@ int oracle_bvh_trace(int32_t n_nodes, const int32_t* box, const int32_t* c0, con
 
 typedef struct {
   int32_t n_nodes;
-  const int32_t *axis, *split, *child, *count, *box, *rope, *rope_log2, *refs, *seg;
+  const int32_t *axis, *split, *child, *count, *box, *rope, *refs, *seg;
   const int32_t *ox, *oy;
   const float *dx, *dy;
   int32_t *hit, *ops;
   float* t;
 } kd_ctx;
+
+/* The number of ropes of a leaf's face (Sec. 5.3.2: a leaf has one rope per
+ * neighbour cell along each of its boundary segments): the leaves on the far
+ * side of the face's plane whose boxes share a piece of positive length with
+ * the face.  Found by a plain spatial query from the root, independent of the
+ * ropes stored in the tree: a node is entered only if its box contains the
+ * plane's coordinate and overlaps the face's extent on the other axis (every
+ * qualifying leaf lies inside all its ancestors' boxes). */
+static int32_t kd_face_neighbours(const kd_ctx* c, int32_t L, int face, int32_t* stack) {
+  const int32_t* B = c->box + 4 * (int64_t)L;
+  int fa = face / 2, fmax = face & 1;
+  int64_t plane = fmax ? B[2 + fa] : B[fa];
+  int64_t f0 = B[1 - fa], f1 = B[3 - fa];
+  int32_t n = 0, sp = 0; /* stack: room for n_nodes + 1 entries */
+  stack[sp++] = 0;
+  while (sp > 0) {
+    int32_t N = stack[--sp];
+    const int32_t* nb = c->box + 4 * (int64_t)N;
+    if (nb[fa] > plane || nb[2 + fa] < plane) continue;
+    int64_t lo = nb[1 - fa] > f0 ? nb[1 - fa] : f0, hi = nb[3 - fa] < f1 ? nb[3 - fa] : f1;
+    if (hi <= lo) continue; /* shares a point at most with the face */
+    if (c->axis[N] != 2) {
+      stack[sp++] = c->child[N];
+      stack[sp++] = c->child[N] + 1;
+      continue;
+    }
+    if (N == L) continue;
+    /* a leaf on the far side touches the plane with its near boundary */
+    if (fmax ? nb[fa] == plane : nb[2 + fa] == plane) ++n;
+  }
+  return n;
+}
+
+/* Rope search steps of an ideal rope tree over n ropes (Sec. 5.3.2 counts
+ * log n steps for a boundary with n ropes): ceil(log2 n), 0 for one rope. */
+static int32_t ideal_rope_steps(int32_t n) {
+  int32_t s = 0;
+#if ORACLE_MUTANT == 9 /* planted: floor(log2 n) */
+  while ((2 << s) <= n) ++s;
+#else
+  while ((1 << s) < n) ++s;
+#endif
+  return s;
+}
 
 static int i32_cmp(const void* a, const void* b) {
   int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
@@ -811,6 +861,7 @@ static int plane_side(int a, int64_t kx, int64_t ky) {
 static void kd_range(void* p, int64_t lo, int64_t hi) {
   kd_ctx* c = (kd_ctx*)p;
   int32_t cap = 1024, *tested = (int32_t*)malloc(sizeof(int32_t) * cap);
+  int32_t* nstack = (int32_t*)malloc(sizeof(int32_t) * ((size_t)c->n_nodes + 1));
   for (int64_t i = lo; i < hi; ++i) {
     int32_t* o = c->ops + 6 * i;
     int64_t kx, ky, ox = c->ox[i], oy = c->oy[i];
@@ -855,10 +906,15 @@ static void kd_range(void* p, int64_t lo, int64_t hi) {
         tested[n_tested++] = sid;
         consider(&b, c->seg + 4 * (int64_t)sid, sid, ox, oy, kx, ky, &te);
       }
+#if ORACLE_MUTANT == 8 /* planted: a rope search counted for every leaf, the last one included */
+      ropes += ideal_rope_steps(kd_face_neighbours(c, L, face, nstack));
+#endif
       if (b.seg >= 0) break;
       int32_t nxt = c->rope[4 * (int64_t)L + face];
       if (nxt < 0) break;
-      ropes += c->rope_log2[4 * (int64_t)L + face];
+#if ORACLE_MUTANT != 8
+      ropes += ideal_rope_steps(kd_face_neighbours(c, L, face, nstack));
+#endif
       int fa = face / 2;
       int64_t plane = face == 0 ? B[0] : (face == 1 ? B[2] : (face == 2 ? B[1] : B[3]));
       int32_t N = nxt;
@@ -893,16 +949,19 @@ static void kd_range(void* p, int64_t lo, int64_t hi) {
     n_tested = 0;
   }
   free(tested);
+  free(nstack);
 }
 
 /* Roped kd-tree traversal (Sec. 5.3.2) from the leaf holding the origin.
  * ops per ray: leaves visited, nodes passed in rope descents, segment tests,
- * distinct segments tested, sum of log2 rope counts, 0. */
+ * distinct segments tested (an ideal mailbox), rope search steps of an ideal
+ * rope tree (sum over the faces crossed of ceil(log2 of the face's rope
+ * count), the count found by kd_face_neighbours), 0. */
 int oracle_kd_trace(int32_t n_nodes, const int32_t* axis, const int32_t* split, const int32_t* child,
-                    const int32_t* count, const int32_t* box, const int32_t* rope, const int32_t* rope_log2,
-                    const int32_t* refs, const int32_t* seg, int64_t n, const int32_t* ox, const int32_t* oy,
-                    const float* dx, const float* dy, int32_t* hit, float* t, int32_t* ops, int32_t n_threads) {
-  kd_ctx c = {n_nodes, axis, split, child, count, box, rope, rope_log2, refs, seg, ox, oy, dx, dy, hit, ops, t};
+                    const int32_t* count, const int32_t* box, const int32_t* rope, const int32_t* refs,
+                    const int32_t* seg, int64_t n, const int32_t* ox, const int32_t* oy, const float* dx,
+                    const float* dy, int32_t* hit, float* t, int32_t* ops, int32_t n_threads) {
+  kd_ctx c = {n_nodes, axis, split, child, count, box, rope, refs, seg, ox, oy, dx, dy, hit, ops, t};
   run_parallel(kd_range, &c, n, n_threads);
   return 0;
 }

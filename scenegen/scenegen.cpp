@@ -2131,7 +2131,9 @@ struct KdBuild {
   }
   int adjacent_leaves(int leaf, int f, int32_t N) const {
     const int fa = f / 2;
+    const bool fmax = (f & 1) != 0;
     const int32_t* lb = &box[4 * leaf];
+    const int32_t plane = fmax ? lb[2 + fa] : lb[fa];
     const int32_t f0 = lb[1 - fa], f1 = lb[3 - fa];
     int cnt = 0;
     std::vector<int32_t> st{N};
@@ -2141,6 +2143,9 @@ struct KdBuild {
       const int32_t* xb = &box[4 * x];
       const int32_t o0 = std::max(f0, xb[1 - fa]), o1 = std::min(f1, xb[3 - fa]);
       if (o1 <= o0) continue;  // touches the face in a point at most
+      // the node must reach the face's plane: cells beyond a split on the
+      // face's own axis are not adjacent across the face
+      if (fmax ? xb[fa] != plane : xb[2 + fa] != plane) continue;
       if (axis[x] == 2) {
         ++cnt;
       } else {
