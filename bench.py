@@ -119,9 +119,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(work, seconds_target=12.0):
+def cpu_oracle_rate(work, seconds_target=12.0, timed_results=None):
     """Oracle walk (given start cells) on all host cores over a bounded sample:
-    the first rays of every scene, sized to take about seconds_target."""
+    the first rays of every scene, sized to take about seconds_target.  With
+    timed_results (per scene: hit, t, steps of the timed GPU launch, host
+    arrays), the oracle's results on the sample are then compared with them:
+    ids and steps exactly, t within 1e-6 relative; a mismatch raises."""
     import oracle
 
     threads = os.cpu_count() or 1
@@ -132,12 +135,40 @@ def cpu_oracle_rate(work, seconds_target=12.0):
         oracle.walk(tri, r.ox[:n], r.oy[:n], r.dx[:n], r.dy[:n], r.start[:n], n_threads=threads)
     dt = time.perf_counter() - t0
     n2 = int(min(N_RAYS, max(n, n * seconds_target / max(dt, 1e-6))))
+    outs = []
     t0 = time.perf_counter()
     for w in work:
         tri, r = w[3], w[4]
-        oracle.walk(tri, r.ox[:n2], r.oy[:n2], r.dx[:n2], r.dy[:n2], r.start[:n2], n_threads=threads)
+        outs.append(oracle.walk(tri, r.ox[:n2], r.oy[:n2], r.dx[:n2], r.dy[:n2], r.start[:n2], n_threads=threads))
     dt = time.perf_counter() - t0
-    return n2 * len(work) / dt, threads, n2, dt
+    checked = 0
+    if timed_results is not None:
+        for w, (eh, et, es), (h, t, st) in zip(work, outs, timed_results):
+            m = min(n2, len(h))
+            bad = parity_mismatches(h[:m], t[:m], st[:m], eh[:m], et[:m], es[:m])
+            if bad:
+                raise RuntimeError(f"timed launch differs from the oracle on scene {w[0]}: {bad}")
+            checked += m
+    return n2 * len(work) / dt, threads, n2, dt, checked
+
+
+def parity_mismatches(h, t, st, eh, et, es, rel=1e-6):
+    """The walk's parity contract: hit ids and step counts equal, t equal to
+    1e-6 relative (both infinite on a miss).  Returns a short description of
+    the mismatches, or '' when there are none."""
+    out = []
+    if not np.array_equal(h, eh):
+        out.append(f"{int((h != eh).sum())} hit ids")
+    if not np.array_equal(st, es):
+        out.append(f"{int((st != es).sum())} step counts")
+    fin = np.isfinite(et)
+    if not np.array_equal(np.isfinite(t), fin):
+        out.append("finiteness of t")
+    else:
+        dev = np.abs(t[fin].astype(np.float64) - et[fin]) > rel * np.abs(et[fin].astype(np.float64))
+        if dev.any():
+            out.append(f"{int(dev.sum())} t values beyond {rel} relative")
+    return ", ".join(out)
 
 
 def cpu_oracle_bounce_rate(work, n=1 << 20):
@@ -239,13 +270,13 @@ def kernel_sources_sha256() -> str:
 
 
 def captured_traffic():
-    """DRAM bytes per launch of the timed step's kernel (batch_kernel over the
-    six scenes) from the committed ncu summary, or None when the kernel
-    sources changed since that capture."""
+    """DRAM bytes and L2 sector bytes per launch of the timed step's kernel
+    (batch_kernel over the six scenes) from the committed ncu summary, or None
+    when the kernel sources changed since that capture."""
     try:
         text = open(TRAFFIC_SUMMARY).read()
     except OSError:
-        return None, "no ncu summary"
+        return None, "no ncu summary", None
     import re
 
     vals = dict(re.findall(r"^- `(\w+)`: `([^`]+)`", text, flags=re.M))
@@ -253,10 +284,12 @@ def captured_traffic():
         b = float(vals["traffic_bytes_per_launch_mean"])
         sha = vals["sources_sha256"]
     except (KeyError, ValueError):
-        return None, "ncu summary unreadable"
+        return None, "ncu summary unreadable", None
     if sha != kernel_sources_sha256():
-        return None, "kernel changed since the ncu capture"
-    return b, "DRAM read+write bytes per launch from " + os.path.basename(TRAFFIC_SUMMARY)
+        return None, "kernel changed since the ncu capture", None
+    l2 = vals.get("l2_sector_bytes_per_launch_mean")
+    return (b, "DRAM read+write bytes per launch from " + os.path.basename(TRAFFIC_SUMMARY),
+            float(l2) if l2 else None)
 
 
 TUNE_PARAMS = (0.25, 0.5, 1.0, 2.0, 4.0)
@@ -371,21 +404,28 @@ def secondary_rays(torch, cct, scenes, dev, stream, gather_bps, k_rep):
             "per_scene": out}
 
 
-def make_roofline(achieved, l2_peak, hbm_peak, hbm_src, traffic, traffic_note, launch_ms, alg_per_launch):
+def make_roofline(achieved, l2_peak, hbm_peak, hbm_src, traffic, traffic_note, launch_ms, alg_per_launch,
+                  l2_bytes=None):
     """The roofline object of the timed kernel (batch_kernel): achieved =
-    algorithmic bytes per launch over its event-timed duration (GB/s), against
-    the measured HBM copy peak (the bound the line reports), and beside it the
-    stricter random-gather peak measured live over tables of the scenes' sizes
-    (the walk's L2-resident gathers)."""
-    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": traffic, "traffic_note": traffic_note, "peak_source": hbm_src,
-            "kernel": "batch_kernel (the timed step's only kernel): one launch per step over the six scenes",
-            "launch_ms_mean": launch_ms, "algorithmic_bytes_per_launch_mean": alg_per_launch,
-            "bytes_model": "32 B per distinct triangle record read (walk steps + locate steps - 1 per ray) + "
-                           "4 B seed cell + 28 B per ray (16 B ray in, 12 B result out)",
-            "l2_gather": {"peak": l2_peak, "frac": achieved / l2_peak,
-                          "source": "measured live: random 32-byte sector gathers over tables of each scene's size "
-                                    "(cct_measure_gather), weighted by each scene's bytes"}}
+    algorithmic bytes per launch over its event-timed duration (GB/s).  The
+    kernel is a dependent gather of 32-byte records from L2-resident tables,
+    so its bound is the random-sector gather rate of the L2, measured live over
+    tables of the scenes' sizes (cct_measure_gather, byte-weighted over the
+    scenes): `peak` and `frac` are against it.  The HBM copy peak and the DRAM
+    bytes the kernel actually moves (ncu) are reported beside it."""
+    r = {"bound": "l2_gather", "achieved": achieved, "peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
+         "traffic": traffic, "traffic_note": traffic_note,
+         "peak_source": "measured live: random 32-byte sector gathers over tables of each scene's size "
+                        "(cct_measure_gather), weighted by each scene's share of the algorithmic bytes",
+         "kernel": "batch_kernel (the timed step's only kernel): one launch per step over the six scenes",
+         "launch_ms_mean": launch_ms, "algorithmic_bytes_per_launch_mean": alg_per_launch,
+         "bytes_model": "32 B per distinct triangle record read (walk steps + locate steps - 1 per ray) + "
+                        "4 B seed cell + 28 B per ray (16 B ray in, 12 B result out)",
+         "hbm_peak": hbm_peak, "hbm_peak_source": hbm_src, "hbm_frac_of_algorithmic": achieved / hbm_peak,
+         "dram_frac": None if traffic is None else traffic / (launch_ms * 1e-3) / 1e9 / hbm_peak,
+         "l2_bytes_per_launch": l2_bytes,
+         "l2_over_algorithmic": None if l2_bytes is None else l2_bytes / alg_per_launch}
+    return r
 
 
 def _parallel(fn, items, workers=None):
@@ -930,9 +970,18 @@ def main():
     items = [(k, sc["d"]["ox"], sc["d"]["oy"], sc["d"]["dx"], sc["d"]["dy"], None, *outs[k])
              for k, sc in enumerate(scenes)]
     batch, btune = None, None
+    arms = {}
     for label, bflags in (("filtered", 0), ("exact", cct.CCT_TRACE_EXACT_ONLY)):
         b = cct.Batch([sc["scene"] for sc in scenes], len(items), bflags)
         res = autotune.tune_batch(b, items)
+        # one launch at the arm's tuned configuration: its fallback rate (0 by construction when exact-only)
+        b.stage(items)
+        b.stats(reset=True)
+        b.enqueue(stream)
+        st = b.stats(reset=True)
+        arms[label] = {"ms_per_launch_tuned": res["ms"], "tuning": res["tuning"],
+                       "int64_fallback_rate": st["exact_fallbacks"] / max(1, st["side_tests"]),
+                       "int64_fallbacks": int(st["exact_fallbacks"]), "side_tests": int(st["side_tests"])}
         if btune is None or res["ms"] < btune["ms"]:
             if batch is not None:
                 batch.free()
@@ -966,13 +1015,15 @@ def main():
     rays_per_step = n * len(scenes)
     value = job_rays_per_s(rays_per_step, world, ms)
     tot = batch.stats(reset=True)
-    # the results of the timed launches equal the plain per-scene trace's (one scene, every ray)
-    chk = scenes[len(scenes) // 2]
-    trace(chk, None, 0)
-    torch.cuda.synchronize(dev)
-    o = outs[len(scenes) // 2]
-    if not (torch.equal(o[0], hit) and torch.equal(o[2], steps)):
-        raise RuntimeError("batched results differ from the plain trace")
+    # the results of the timed launches, kept on the host for the oracle comparison (cpu_baseline leg)
+    timed_results = [tuple(x.cpu().numpy() for x in o) for o in outs]
+    # ... and equal to the plain per-scene trace's (every scene, every ray, t bit for bit)
+    for k, sc in enumerate(scenes):
+        trace(sc, None, 0)
+        torch.cuda.synchronize(dev)
+        o = outs[k]
+        if not (torch.equal(o[0], hit) and torch.equal(o[2], steps) and torch.equal(o[1], t)):
+            raise RuntimeError(f"batched results differ from the plain trace on scene {sc['name']}")
 
     # ---- the same step as six plain launches (one cct_trace per scene, each at its own tuned
     # configuration), for comparison; per-scene counters weight the roofline's peak
@@ -1042,8 +1093,9 @@ def main():
     hbm_peak = json.load(open(peaks_path)).get("hbm_gbs") if os.path.exists(peaks_path) else None
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm_peak else "fallback 6800 GB/s (of fallback)"
     hbm_peak = hbm_peak or 6800.0
-    traffic, traffic_note = captured_traffic()
-    roofline = make_roofline(achieved, l2_peak, hbm_peak, hbm_src, traffic, traffic_note, launch_ms, alg_per_launch)
+    traffic, traffic_note, l2_bytes = captured_traffic()
+    roofline = make_roofline(achieved, l2_peak, hbm_peak, hbm_src, traffic, traffic_note, launch_ms, alg_per_launch,
+                             l2_bytes)
 
     # ---- end to end through the public API with host buffers (pinned), every scene.  The
     # scenes' rays stream through a three-stream pipeline, as a serving caller would run them:
@@ -1147,14 +1199,21 @@ def main():
             "bvh_ops_per_ray": float(np.mean([p["bvh"]["ops_per_ray"] for p in per.values()])),
             "walk_steps_per_ray_mean_over_scenes": float(np.mean([p["steps_per_ray"] for p in per.values()])),
             "fallback_rate": tot["exact_fallbacks"] / max(1, tot["side_tests"]),
+            "predicate_arms": arms,
+            "kd_mailbox_overflow_rays": int(sum(p["kd"]["mailbox_overflow_rays"] for p in per.values())),
+            "kd_rays_traced": int(len(per) * n),
             "locate_steps_per_ray": tot["locate_steps"] / max(1, tot["located"]),
             "per_scene": per, "roofline": roofline, "e2e": e2e, "secondary_rays": secondary,
             "gpu_launches": args.steps}
     if rank == 0 and not args.no_cpu_baseline:
-        rate, cores, sample_n, dt = cpu_oracle_rate(work)
+        rate, cores, sample_n, dt, checked = cpu_oracle_rate(work, timed_results=timed_results)
         line["cpu_baseline"] = {"value": rate, "unit": "rays/s", "cores": cores, "kind": "oracle",
                                 "sample": f"oracle walk from given start cells over the first {sample_n} rays of "
                                           f"each of the {len(work)} scenes ({dt:.1f} s wall)"}
+        line["parity"] = {"rays_checked_against_oracle": checked, "mismatches": 0,
+                          "what": "the timed launch's hit ids and step counts equal the oracle's, t within 1e-6 "
+                                  "relative, on the cpu_baseline sample of every scene; every ray of every scene "
+                                  "equal to a plain cct_trace"}
         brate, bcores, bn, bdt = cpu_oracle_bounce_rate(work)
         secondary["cpu_oracle"] = {"value": brate, "unit": "walked rays/s", "cores": bcores, "kind": "oracle",
                                    "sample": f"oracle mirror paths ({N_BOUNCE} bounces) of the first {bn} rays of "

@@ -204,9 +204,12 @@ int cct_trace(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy, const f
 /* No counterpart in the paper: cct_trace for callers that cannot allocate
  * device memory during a query -- e.g. a process that reserved the GPU's memory
  * for its own pool at start-up, or a latency-critical loop that must not enter
- * an allocator.  Same arguments, outputs and per-ray statuses as cct_trace;
- * the scratch it needs (a work counter and, when d_start_tri is NULL, the
- * located start cells) lives in one file-scope device array of
+ * an allocator.  Same arguments, outputs and per-ray statuses as cct_trace,
+ * and the same launch configuration: the scene's tuning (block size, refill
+ * threshold, chunk, and its trace_flags: exact-only predicates, split locate)
+ * applies as in cct_trace, except that binning is never used.  The scratch it
+ * needs (a work counter and, with CCT_TRACE_SPLIT_LOCATE and no d_start_tri,
+ * the located start cells) lives in one file-scope device array of
  * CCT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
  * process exits.  Nothing is allocated: no cudaMalloc, cudaFree or allocating
  * library routine is called.

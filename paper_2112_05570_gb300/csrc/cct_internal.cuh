@@ -401,6 +401,17 @@ struct RaySrc {
 cudaError_t launch_walk(bool exact, bool sorted, bool start_user, const SceneDev& S, const RaySrc& R, int32_t* hit,
                         float* t, int32_t* steps, unsigned long long* counter, int dev, cudaStream_t stream);
 
+// Ray sources of the walk kernel: start cells as caller triangle ids, as
+// record indices, the binned (sorted, packed) form, or none (the kernel
+// locates each origin itself).
+enum : int { kSrcPlainUser = 0, kSrcPlainDev = 1, kSrcSorted = 2, kSrcLocate = 3 };
+
+// The same with an explicit launch configuration (block size, refill
+// threshold, chunk) and ray source.
+cudaError_t launch_walk_src(bool exact, int src, const SceneDev& S, const RaySrc& R, const cct_tuning& tu,
+                            int32_t* hit, float* t, int32_t* steps, unsigned long long* counter, int dev,
+                            cudaStream_t stream);
+
 cct_tuning default_tuning();
 
 struct BinOut {

@@ -67,18 +67,32 @@ extern "C" int cct_trace_noalloc(cct_scene scene, const int32_t* ox, const int32
   cudaStream_t stream = (cudaStream_t)stream_v;
   unsigned long long* counter = (unsigned long long*)base;
   if (cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream) != cudaSuccess) return CCT_ERR_CUDA;
+  // the scene's launch configuration and predicate choice, as cct_trace uses
+  // them; binning (which needs scratch per ray) is left out
+  const cct_tuning& tu = scene->tuning;
+  flags |= tu.trace_flags & ~(uint32_t)CCT_TRACE_BIN;
+  const bool exact = (flags & CCT_TRACE_EXACT_ONLY) != 0;
   const SceneDev& S = scene->dev;
-  const int32_t* st = start;
-  bool st_user = true;
-  if (!start) {
+  if (start) {
+    RaySrc R{ox, oy, dx, dy, start, nullptr, nullptr, n};
+    return launch_walk_src(exact, kSrcPlainUser, S, R, tu, hit, t, steps, counter, scene->device, stream) ==
+                   cudaSuccess
+               ? CCT_OK
+               : CCT_ERR_CUDA;
+  }
+  if (flags & CCT_TRACE_SPLIT_LOCATE) {
+    // start cells from the locate kernel into the array, then the walk
     int32_t* sbuf = (int32_t*)(base + kNoallocCounterBytes);
     if (launch_locate(S, ox, oy, n, sbuf, false, stream) != cudaSuccess) return CCT_ERR_CUDA;
-    st = sbuf;
-    st_user = false;
+    RaySrc R{ox, oy, dx, dy, sbuf, nullptr, nullptr, n};
+    return launch_walk_src(exact, kSrcPlainDev, S, R, tu, hit, t, steps, counter, scene->device, stream) ==
+                   cudaSuccess
+               ? CCT_OK
+               : CCT_ERR_CUDA;
   }
-  RaySrc R{ox, oy, dx, dy, st, nullptr, nullptr, n};
-  if (launch_walk((flags & CCT_TRACE_EXACT_ONLY) != 0, false, st_user, S, R, hit, t, steps, counter, scene->device,
-                  stream) != cudaSuccess)
-    return CCT_ERR_CUDA;
-  return CCT_OK;
+  // the walk kernel locates each origin itself (no start-cell scratch)
+  RaySrc R{ox, oy, dx, dy, nullptr, nullptr, nullptr, n};
+  return launch_walk_src(exact, kSrcLocate, S, R, tu, hit, t, steps, counter, scene->device, stream) == cudaSuccess
+             ? CCT_OK
+             : CCT_ERR_CUDA;
 }

@@ -34,7 +34,6 @@
 
 namespace cct {
 
-enum : int { kSrcPlainUser = 0, kSrcPlainDev = 1, kSrcSorted = 2, kSrcLocate = 3 };
 // rare per-warp counters (shared memory)
 enum : int { kCntRays = 0, kCntInvalid, kCntLocated, kCntLocSteps, kRareCounters };
 
@@ -473,9 +472,9 @@ static cudaError_t launch_walk_t(const SceneDev& S, const RaySrc& R, const cct_t
   return cudaGetLastError();
 }
 
-static cudaError_t launch_walk_src(bool exact, int src, const SceneDev& S, const RaySrc& R, const cct_tuning& tu,
-                                   int32_t* hit, float* t, int32_t* steps, unsigned long long* counter, int dev,
-                                   cudaStream_t stream) {
+cudaError_t launch_walk_src(bool exact, int src, const SceneDev& S, const RaySrc& R, const cct_tuning& tu,
+                            int32_t* hit, float* t, int32_t* steps, unsigned long long* counter, int dev,
+                            cudaStream_t stream) {
 #define CCT_WALK_CASE(SRC)                                                                 \
   case SRC:                                                                                \
     return exact ? launch_walk_t<true, SRC>(S, R, tu, hit, t, steps, counter, dev, stream) \

@@ -47,6 +47,7 @@ class Request:
     dev: object = None      # device int32 buffer of 7 n words while in flight: rays (n, 4), then results (3, n)
     upload: object = None   # CUDA event: rays on the device
     tick: int = -1
+    pool_lo: int = 0        # index of the request's first ray in its scene's pool (the rays wrap around it)
 
 
 @dataclass
@@ -188,8 +189,8 @@ class Server:
         rng = np.random.default_rng(seed)
         reqs = []
         for k, (t, sc, n) in enumerate(schedule):
-            parts, out, _ = pool.take(sc, n, rng)
-            reqs.append(Request(k, sc, int(n), t, parts, out))
+            parts, out, lo = pool.take(sc, n, rng)
+            reqs.append(Request(k, sc, int(n), t, parts, out, pool_lo=lo))
         if batched and self.use_graph and not self._graphs_ready and reqs:
             probe = Request(-1, reqs[0].scene, 1, 0.0, [(reqs[0].src[0][0][:1], None)])
             probe.dev = self._alloc(1)

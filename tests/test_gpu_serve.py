@@ -1,10 +1,12 @@
 """Continuous-batching server: every request's result in the mix (fused
 batched ticks, graph replays, overlapping uploads and downloads, admission by
 a memory budget) equals the same request traced alone: hit ids and step
-counts bit for bit, t within the 1e-6 relative tolerance."""
+counts bit for bit, t within the 1e-6 relative tolerance; and a sample of
+every request equals the oracle."""
 import numpy as np
 import pytest
 
+import oracle
 import scenegen as sg
 
 torch = pytest.importorskip("torch")
@@ -50,3 +52,13 @@ def test_each_result_equals_alone(env, batched):
         fin = np.isfinite(tb)
         assert np.array_equal(np.isfinite(ta), fin)
         assert np.all(np.abs(ta[fin] - tb[fin]) <= 1e-6 * np.abs(tb[fin]))  # the stated t tolerance
+        # a sample of the request (both ends included) against the oracle, through the pool's indices
+        m = out.shape[1]
+        idx = np.unique(np.concatenate([np.linspace(0, m - 1, min(m, 512)).astype(np.int64), [0, m - 1]]))
+        pr = rays[r.scene]
+        pi = (r.pool_lo + idx) % pr.ox.shape[0]
+        eh, et, es = oracle.walk(tris[r.scene], pr.ox[pi], pr.oy[pi], pr.dx[pi], pr.dy[pi], pr.start[pi])
+        assert np.array_equal(out[0][idx], eh) and np.array_equal(out[2][idx], es)
+        fo = np.isfinite(et)
+        assert np.array_equal(np.isfinite(ta[idx]), fo)
+        assert np.all(np.abs(ta[idx][fo] - et[fo]) <= 1e-6 * np.abs(et[fo]))

@@ -62,15 +62,21 @@ def test_single_process_is_identity():
 
 
 def test_roofline_object_schema():
-    """The bench's roofline object: bound hbm against the measured HBM copy
-    peak (achieved / peak = frac), the traffic figure, and the stricter
-    live random-gather peak beside it."""
+    """The bench's roofline object: bound = the L2's random-sector gather rate
+    measured live (achieved / peak = frac), the HBM copy peak and the DRAM
+    traffic beside it as top-level numbers."""
     import bench
 
     r = bench.make_roofline(5000.0, 9000.0, 6775.3, "MEASURED_PEAKS.json hbm_gbs (of measured)", 4.47e9, "note",
-                            5.8, 3.1e10)
-    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6775.3
-    assert abs(r["frac"] - 5000.0 / 6775.3) < 1e-12 and r["traffic"] == 4.47e9
-    assert abs(r["l2_gather"]["frac"] - 5000.0 / 9000.0) < 1e-12
+                            5.8, 3.1e10, 4.2e10)
+    assert r["bound"] == "l2_gather" and r["unit"] == "GB/s" and r["peak"] == 9000.0
+    assert abs(r["frac"] - 5000.0 / 9000.0) < 1e-12 and r["traffic"] == 4.47e9
+    assert abs(r["hbm_frac_of_algorithmic"] - 5000.0 / 6775.3) < 1e-12
+    assert abs(r["dram_frac"] - 4.47e9 / 5.8e-3 / 1e9 / 6775.3) < 1e-12
+    assert abs(r["l2_over_algorithmic"] - 4.2e10 / 3.1e10) < 1e-12
     for key in ("achieved", "peak", "unit", "frac", "traffic", "bound"):
         assert key in r
+    # every value is a scalar, so a flat parse of the line keeps them all
+    assert all(not isinstance(v, (dict, list)) for v in r.values())
+    r = bench.make_roofline(5000.0, 9000.0, 6775.3, "src", None, "kernel changed", 5.8, 3.1e10)
+    assert r["traffic"] is None and r["dram_frac"] is None and r["l2_over_algorithmic"] is None

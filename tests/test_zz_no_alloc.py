@@ -82,3 +82,40 @@ def test_noalloc_rejects_sizes_beyond_its_limit(cct):
                              _p(bf), _p(bi), cct.CCT_TRACE_BIN, stream)
     assert rc == cct.CCT_ERR_INVALID_ARGUMENT
     scene.free()
+
+
+def test_noalloc_follows_the_scenes_tuning(cct):
+    """The scene's launch configuration and predicate choice apply to the
+    allocation-free call as to cct_trace: under an exact-only tuning it takes
+    no int64 fallbacks of the fp32 filter (there is no filter), and its
+    results still equal cct_trace's, located and with start cells."""
+    segs = sg.random_segments(200, 35)
+    tri = sg.anneal(sg.cdt(segs), 35)
+    n = 100_003
+    r = sg.rays_isotropic(tri, n, 36)
+    scene = cct.Scene.from_triangulation(tri, sg.D)
+    dev = torch.device("cuda")
+    ox, oy = torch.from_numpy(r.ox).to(dev), torch.from_numpy(r.oy).to(dev)
+    dx, dy = torch.from_numpy(r.dx).to(dev), torch.from_numpy(r.dy).to(dev)
+    start = torch.from_numpy(r.start).to(dev)
+    L = cct.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for tune in ({"block_threads": 64, "refill_min": 16, "chunk": 512, "trace_flags": cct.CCT_TRACE_EXACT_ONLY},
+                 {"block_threads": 128, "refill_min": 24, "chunk": 256,
+                  "trace_flags": cct.CCT_TRACE_EXACT_ONLY | cct.CCT_TRACE_SPLIT_LOCATE | cct.CCT_TRACE_BIN}):
+        scene.set_tuning(tune)
+        for start_arg in (None, start):
+            ref = tuple(x.cpu().numpy() for x in scene.trace(ox, oy, dx, dy, start_arg))
+            scene.stats(reset=True)
+            hit = torch.empty(n, dtype=torch.int32, device=dev)
+            t = torch.empty(n, dtype=torch.float32, device=dev)
+            steps = torch.empty(n, dtype=torch.int32, device=dev)
+            rc = L.cct_trace_noalloc(ctypes.c_void_p(scene.handle), _p(ox), _p(oy), _p(dx), _p(dy), _p(start_arg),
+                                     n, _p(hit), _p(t), _p(steps), 0, stream)
+            assert rc == cct.CCT_OK, cct.cct_error_string(rc)
+            torch.cuda.synchronize()
+            st = scene.stats(reset=True)
+            assert st["rays"] == n and st["side_tests"] > 0 and st["exact_fallbacks"] == 0
+            assert np.array_equal(hit.cpu().numpy(), ref[0]) and np.array_equal(steps.cpu().numpy(), ref[2])
+            assert np.array_equal(t.cpu().numpy(), ref[1])
+    scene.free()
