@@ -37,28 +37,84 @@ WORKLOAD = "config2-families-30k-annealed-6x2^24-isotropic"
 FAMILIES = ("circles", "dash0", "dash1", "dash22.5", "dash45", "clustered")
 
 
-def family_segments(name):
+def family_segments(name, n=N_SEGMENTS):
     import scenegen as sg
 
     if name == "circles":
-        return sg.circles(N_SEGMENTS, SCENE_SEED)
+        return sg.circles(n, SCENE_SEED)
     if name == "clustered":
-        return sg.clustered(N_SEGMENTS, SCENE_SEED)
-    return sg.dash_grid(N_SEGMENTS, float(name[4:]))
+        return sg.clustered(n, SCENE_SEED)
+    return sg.dash_grid(n, float(name[4:]))
 
 
 def build_workload(n_rays=N_RAYS, families=FAMILIES, with_refined=False):
     """[(name, segs, cdt, annealed, rays)] for the scene families (annealed =
-    optimally refined CDT polished with edge flips); with_refined appends the
-    refined CDT to each tuple."""
+    the optimally refined CDT optimised, and optimised again after a 1 -> 4
+    subdivision, the shorter kept: scenegen.pipeline); with_refined appends the
+    refined CDT to each tuple.  The scenes are built in parallel."""
     import scenegen as sg
 
-    out = []
-    for k, name in enumerate(families):
+    def one(k):
+        name = families[k]
         segs = family_segments(name)
-        cdt, ref, tri = sg.pipeline(segs, SCENE_SEED + k, sweeps=4)
-        rays = sg.rays_isotropic(tri, n_rays, 100 + k)
-        out.append((name, segs, cdt, tri, rays) + ((ref,) if with_refined else ()))
+        cdt, ref, tri = sg.pipeline(segs, SCENE_SEED + FAMILIES.index(name), sweeps=4)
+        rays = sg.rays_isotropic(tri, n_rays, 100 + FAMILIES.index(name))
+        return (name, segs, cdt, tri, rays) + ((ref,) if with_refined else ())
+
+    return _parallel(one, range(len(families)), workers=len(families))
+
+
+FUZZY_SEGMENTS = 3000
+
+
+def fuzzy_family(k):
+    """One scene family at 3000 segments through both optimisers: the bench's
+    discrete route (scenegen.pipeline) and the paper's fuzzy contraction
+    (Sec. 2.2, 3.3-3.5: scenegen.fuzzy_pipeline, with its 1 -> 4 subdivision
+    round).  Returns the triangulations and the CPU seconds of each route."""
+    import scenegen as sg
+
+    name = FAMILIES[k]
+    segs = family_segments(name, FUZZY_SEGMENTS)
+    t0 = time.perf_counter()
+    cdt, ref, ann = sg.pipeline(segs, SCENE_SEED + k, sweeps=4)
+    t1 = time.perf_counter()
+    _, fz = sg.fuzzy_pipeline(segs, SCENE_SEED + k, sweeps=10, polish_sweeps=4, subdivisions=1)
+    t2 = time.perf_counter()
+    return {"name": name, "segs": segs, "cdt": cdt, "refined": ref, "annealed": ann, "fuzzy": fz,
+            "annealed_s": t1 - t0, "fuzzy_s": t2 - t1}
+
+
+def fuzzy_comparison(torch, cct, sg, built, dev, stream, n_rays=1 << 20):
+    """Per family (3000 segments): total interior edge length against the CDT
+    and walk steps per ray on the GPU for the CDT, the optimally refined CDT,
+    the discrete route and the fuzzy route; the walk's rate on the fuzzy
+    triangulation (start cells given, event-timed)."""
+    out = {}
+    for b in built:
+        L = b["cdt"].length(True)
+        row = {"segments": int(b["segs"].shape[0]), "annealed_build_s": b["annealed_s"],
+               "fuzzy_build_s": b["fuzzy_s"], "annealed_route": getattr(b["annealed"], "route", ""),
+               "length_over_cdt": {}, "steps_per_ray": {}, "vertices": {}}
+        for kind in ("cdt", "refined", "annealed", "fuzzy"):
+            tri = b[kind]
+            row["length_over_cdt"][kind] = tri.length(True) / L
+            row["vertices"][kind] = int(tri.n_vert)
+            r = sg.rays_isotropic(tri, n_rays, 500)
+            d = [torch.from_numpy(getattr(r, a)).to(dev) for a in ("ox", "oy", "dx", "dy", "start")]
+            sc = cct.Scene.from_triangulation(tri, sg.D)
+            sc.trace(*d, stream=stream)
+            torch.cuda.synchronize(dev)
+            sc.stats(reset=True)
+            res = sc.trace(*d, stream=stream)
+            torch.cuda.synchronize(dev)
+            st = sc.stats(reset=True)
+            row["steps_per_ray"][kind] = st["steps"] / max(1, st["rays"])
+            if kind == "fuzzy":
+                ms = _time_loop(torch, dev, stream, lambda: sc.trace(*d, stream=stream, out=res), 5)
+                row["walk_rays_per_s_fuzzy"] = n_rays / (ms * 1e-3)
+            sc.free()
+        out[b["name"]] = row
     return out
 
 
@@ -798,6 +854,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--flags", default="auto", help="auto | plain | bin")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fuzzy", action="store_true",
+                    help="leave out the optimiser comparison (discrete vs fuzzy contraction, 3000-segment scenes)")
     ap.add_argument("--config", default="2", choices=["1", "2", "3", "4", "5", "lines"],
                     help="2 (default): the six config-2 scene families; 1: the tiny plain case (200 segments, "
                          "65,536 rays, with the oracle's rates); 3: scaling in N; 4: 512 scenes in one "
@@ -854,6 +912,13 @@ def main():
         return 0
     fams = tuple(f for f in args.families.split(",") if f) if args.profile else FAMILIES
     n_build = min(N_RAYS, 1 << args.profile_rays) if args.profile_step else N_RAYS
+    fz_pool, fz_futs = None, []
+    if not (args.profile or args.profile_step or args.no_fuzzy):
+        # the optimiser comparison's scenes (CPU only) build while the GPU work runs
+        from concurrent.futures import ThreadPoolExecutor
+
+        fz_pool = ThreadPoolExecutor(max_workers=len(FAMILIES))
+        fz_futs = [fz_pool.submit(fuzzy_family, k) for k in range(len(FAMILIES))]
     work = build_workload(n_rays=n_build, families=fams, with_refined=True)
     stream = torch.cuda.current_stream(dev)
     n = N_RAYS
@@ -1083,10 +1148,22 @@ def main():
                            "steps_per_ray_cdt": cst["steps"] / max(1, cst["rays"]),
                            "steps_per_ray_refined_cdt": other["ref"]["steps"] / max(1, other["ref"]["rays"]),
                            "refine_params": list(getattr(sc["ref"], "refine_params", (0.0, 0.0))),
+                           "annealed_route": getattr(sc["tri"], "route", ""),
                            "length_annealed_over_cdt": sc["tri"].length(True) / sc["cdt"].length(True),
                            "length_refined_over_cdt": sc["ref"].length(True) / sc["cdt"].length(True),
                            "walk_l2_frac": (alg / (wms * 1e-3)) / bps, "gather_peak_gbs": bps / 1e9}
     secondary = secondary_rays(torch, cct, scenes, dev, stream, gather_bps, max(3, args.steps // 10))
+    optimisers = None
+    if fz_pool is not None:
+        built = [f.result() for f in fz_futs]
+        fz_pool.shutdown()
+        optimisers = {"segments_per_scene": FUZZY_SEGMENTS,
+                      "routes": "cdt; refined = optimally refined CDT (Sec. 3.5.1); annealed = the bench's route "
+                                "(scenegen.pipeline: discrete optimisation, again after a 1 -> 4 subdivision, the "
+                                "shorter kept); fuzzy = fuzzy contraction (Sec. 2.2, 3.3-3.5.3, "
+                                "scenegen.fuzzy_pipeline: 10 sweeps, contract-and-polish, one subdivision round)",
+                      "per_scene": fuzzy_comparison(torch, cct, sg, built, dev, stream)}
+        del built
     achieved = alg_per_launch / (launch_ms * 1e-3) / 1e9
     l2_peak = 1.0 / share_over_peak / 1e9  # byte-weighted gather peak over the scenes' table sizes
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -1204,6 +1281,7 @@ def main():
             "kd_rays_traced": int(len(per) * n),
             "locate_steps_per_ray": tot["locate_steps"] / max(1, tot["located"]),
             "per_scene": per, "roofline": roofline, "e2e": e2e, "secondary_rays": secondary,
+            "optimisers": optimisers,
             "gpu_launches": args.steps}
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample_n, dt, checked = cpu_oracle_rate(work, timed_results=timed_results)

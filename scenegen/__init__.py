@@ -88,6 +88,8 @@ def _load():
     L.sg_anneal_fuzzy.argtypes = [vp, ctypes.c_uint64, dbl, dbl, dbl, dbl, dbl, dbl]
     L.sg_contract_short_edges.restype = i64
     L.sg_contract_short_edges.argtypes = [vp, dbl]
+    L.sg_fuzzy_check_group_deltas.restype = i64
+    L.sg_fuzzy_check_group_deltas.argtypes = [vp, ctypes.c_uint64, i64, dbl, i32, dbl, P(dbl), P(i64)]
     L.sg_fuzzy_objective.restype = None
     L.sg_fuzzy_objective.argtypes = [vp, dbl, dbl, dbl, dbl, dbl, ctypes.c_int32, vp, vp]
     L.sg_refine_optimal.restype = vp
@@ -403,6 +405,20 @@ def _optimise_and_contract(tri: Triangulation, seed: int, sweeps: float, polish_
     return best
 
 
+def fuzzy_check_group_deltas(tri: Triangulation, seed: int, n: int, eps: float, init_bits: int = 12,
+                             step: float = 0.01):
+    """Test hook: n multi-vertex perturbations (Sec. 3.2.2's second variant) of
+    a copy of ``tri`` at contraction length eps and vertex-move step factor
+    ``step``, the annealer's region tables starting at 2^init_bits slots;
+    returns (proposals compared, largest |region energy change - whole fuzzy
+    objective change|, table growths)."""
+    L = _load()
+    err, grows = ctypes.c_double(), ctypes.c_int64()
+    n_cmp = L.sg_fuzzy_check_group_deltas(tri._h, int(seed), int(n), float(eps), int(init_bits), float(step),
+                                          ctypes.byref(err), ctypes.byref(grows))
+    return int(n_cmp), float(err.value), int(grows.value)
+
+
 def fuzzy_pipeline(segs: np.ndarray, seed: int, sweeps: float = 20.0, polish_sweeps: float = 10.0,
                    eps_a: float = 0.05, eps_b: float = 1e-4, T0: float = 0.02, T1: float = 1e-4,
                    max_rounds: int = 6, subdivisions: int = 0):
@@ -469,13 +485,23 @@ def refine_optimal(tri: Triangulation, angles=OPT_ANGLES, area_fractions=OPT_ARE
     return out
 
 
-def pipeline(segs: np.ndarray, seed: int, sweeps: float = 4.0):
+def pipeline(segs: np.ndarray, seed: int, sweeps: float = 4.0, subdivisions: int = 1):
     """The offline build of the paper's triangulations: (unrefined CDT, optimally
-    refined CDT (Sec. 3.5.1), annealed = the refined CDT polished with greedy and
-    simulated-annealing edge flips (Sec. 3.2.7, 3.3))."""
+    refined CDT (Sec. 3.5.1), annealed).  Annealed = the refined CDT optimised
+    (greedy and simulated-annealing flips, Sec. 3.2.7, 3.3; vertex moves and
+    contraction as discrete collapses), then, ``subdivisions`` times, the 1 -> 4
+    subdivision of the result optimised again (the full pipeline of Sec. 3.5.3),
+    keeping the shortest; its .route says which round won."""
     c = cdt(segs)
     r = refine_optimal(c)
-    return c, r, anneal(r, seed, sweeps=sweeps)
+    best = anneal(r, seed, sweeps=sweeps)
+    best.route = "annealed"
+    for k in range(subdivisions):
+        nxt = anneal(subdivide(best), seed + 100 * (k + 1), sweeps=sweeps)
+        if nxt.length(True) < best.length(True):
+            best = nxt
+            best.route = f"annealed after {k + 1} subdivision(s)"
+    return c, r, best
 
 
 def from_arrays(vx, vy, tri_v, tri_nb, tri_seg, segs, kind="given") -> Triangulation:

@@ -1317,18 +1317,22 @@ struct FuzzyLocal {
   // open-addressing tables keyed by edge (cleared per evaluation through a generation stamp):
   // the memoised c of an edge, and the edges already summed; each grows (rehashing its live
   // entries) before it is half full, so a probe always ends at a free slot
-  int bits = 12;
-  uint32_t mask = (1u << 12) - 1;
+  int bits;
+  uint32_t mask;
   std::vector<uint64_t> key_c, key_s;
   std::vector<uint32_t> gen_c, gen_s;
   std::vector<double> val_c;
   uint32_t gen = 0;
   size_t used_c = 0, used_s = 0;
+  int64_t grows = 0;  // table growths so far
 
-  FuzzyLocal(const Triangulation& t, const VertexClasses& v, const FuzzyParams& f)
-      : tr(t), vc(v), fp(f), key_c(4096), key_s(4096), gen_c(4096, 0), gen_s(4096, 0), val_c(4096) {}
+  FuzzyLocal(const Triangulation& t, const VertexClasses& v, const FuzzyParams& f, int init_bits = 12)
+      : tr(t), vc(v), fp(f), bits(init_bits), mask((1u << init_bits) - 1), key_c((size_t)1 << init_bits),
+        key_s((size_t)1 << init_bits), gen_c((size_t)1 << init_bits, 0), gen_s((size_t)1 << init_bits, 0),
+        val_c((size_t)1 << init_bits) {}
   uint32_t slot(uint64_t k) const { return (uint32_t)((k * 0x9E3779B97F4A7C15ull) >> (64 - bits)); }
   void grow() {
+    ++grows;
     std::vector<uint64_t> kc = key_c, ks = key_s;
     std::vector<uint32_t> gc = gen_c, gs = gen_s;
     std::vector<double> vcv = val_c;
@@ -1496,6 +1500,36 @@ static bool has_neighbour_within(const Triangulation& tr, int v, const Pt& q, do
   return tr.for_fan(v, [&](int t, int k) { return (double)len2(q, tr.P[tr.T[t].v[(k + 1) % 3]]) < r2; });
 }
 
+// Sec. 3.2.2's second variant: 2 % of the movable vertices (at least one, at most 64) each get the
+// vertex perturbation, decided together.  Fills group / newpos; false when no vertex got a move.
+static bool propose_many(const Triangulation& tr, const VertexClasses& vc, const std::vector<int32_t>& movable,
+                         VertexMover& mover, Rng& rng, std::vector<int>& group, std::vector<Pt>& newpos) {
+  const size_t m = std::min<size_t>(64, std::max<size_t>(1, (size_t)std::llround(0.02 * (double)movable.size())));
+  for (size_t g = 0; g < m; ++g) {
+    const int u = movable[rng.below((uint32_t)movable.size())];
+    if (std::find(group.begin(), group.end(), u) != group.end()) continue;
+    Pt pu;
+    if (!mover.propose(tr, vc, u, rng, pu)) continue;
+    group.push_back(u);
+    newpos.push_back(pu);
+  }
+  return !group.empty();
+}
+
+// The region of a move of `group`: the triangles of the stars of the moved vertices and of their
+// neighbours (every edge whose weight the move can change lies in it).
+static void group_region(const Triangulation& tr, const std::vector<int>& group, std::vector<int>& region) {
+  region.clear();
+  for (int u : group) {
+    add_star(tr, u, region);
+    tr.for_fan(u, [&](int t, int kk) {
+      add_star(tr, tr.T[t].v[(kk + 1) % 3], region);
+      return false;
+    });
+  }
+  sort_unique(region);
+}
+
 // Simulated annealing on the fuzzy objective f (Sec. 2.2, 3.1-3.3): T and eps decrease
 // exponentially together (T0 -> T1, eps_a -> eps_b, unit-square units); proposals are edge flips
 // and, in equal shares, the vertex perturbation (Sec. 3.2.2), the perturbation of a group of
@@ -1558,18 +1592,7 @@ static void anneal_fuzzy(Triangulation& tr, uint64_t seed, double sweeps, double
         else
           ok = mover.resample(tr, vc, v, rng, q) && !has_neighbour_within(tr, v, q, eps_lat);
       } else if (kind == 5) {
-        // Sec. 3.2.2's second variant: 2 % of the movable vertices perturbed at once (one decision)
-        const size_t m = std::min<size_t>(64, std::max<size_t>(1, (size_t)std::llround(0.02 * (double)movable.size())));
-        ok = true;
-        for (size_t g = 0; g < m && ok; ++g) {
-          const int u = movable[rng.below((uint32_t)movable.size())];
-          if (std::find(group.begin(), group.end(), u) != group.end()) continue;
-          Pt pu;
-          if (!mover.propose(tr, vc, u, rng, pu)) continue;
-          group.push_back(u);
-          newpos.push_back(pu);
-        }
-        ok = !group.empty();
+        ok = propose_many(tr, vc, movable, mover, rng, group, newpos);
       } else if (vc.kind[v] == 1) {
         // the group: free vertices within d of v, found through the triangulation's edges
         const double d = eps_lat * (0.5 + 4.5 * rng.uni()), d2 = d * d;
@@ -1603,15 +1626,7 @@ static void anneal_fuzzy(Triangulation& tr, uint64_t seed, double sweeps, double
       }
       bool acc = false;
       if (ok) {
-        region.clear();
-        for (int u : group) {
-          add_star(tr, u, region);
-          tr.for_fan(u, [&](int t, int kk) {
-            add_star(tr, tr.T[t].v[(kk + 1) % 3], region);
-            return false;
-          });
-        }
-        sort_unique(region);
+        group_region(tr, group, region);
         const double e0 = loc.energy(region);
         oldpos.clear();
         for (size_t g = 0; g < group.size(); ++g) {
@@ -2387,6 +2402,62 @@ int64_t sg_anneal_fuzzy(void* h, uint64_t seed, double sweeps, double T0, double
 
 // Contraction alone (contract_short_edges).
 int64_t sg_contract_short_edges(void* h, double eps) { return contract_short_edges(*(Triangulation*)h, eps); }
+
+// Check of the fuzzy annealer's local energy change (for tests): n multi-vertex perturbations
+// (propose_many) on a copy of the triangulation at contraction length eps, the region tables
+// starting at 2^init_bits slots; for every proposal that keeps the triangulation valid, the
+// region's energy change (what the annealer decides on) is compared with the change of the whole
+// fuzzy objective.  Half of the proposals are kept, so the state moves.  lambda = the vertex
+// move's step factor (the annealer adapts it; small steps keep most proposals valid).  Returns the
+// number of proposals compared; *max_err = the largest |local - whole| difference, *grows = table
+// growths.
+int64_t sg_fuzzy_check_group_deltas(void* h, uint64_t seed, int64_t n, double eps, int32_t init_bits,
+                                    double lambda, double* max_err, int64_t* grows) {
+  Triangulation tr = *(Triangulation*)h;
+  Rng rng(seed, 0xC4EC);
+  VertexClasses vc;
+  classify_vertices(tr, vc);
+  std::vector<int32_t> movable;
+  for (int v = 0; v < (int)vc.kind.size(); ++v)
+    if (vc.kind[v]) movable.push_back(v);
+  FuzzyParams fp{eps, 1.0 + std::cos(179.0 * 3.14159265358979323846 / 180.0), 1e-10, 1.0, 10.0, 0};
+  FuzzyLocal loc(tr, vc, fp, init_bits);
+  VertexMover mover;
+  mover.lambda[1] = mover.lambda[2] = lambda;
+  std::vector<int> group, region;
+  std::vector<Pt> newpos, oldpos;
+  double worst = 0.0, f0[4], f1[4];
+  int64_t compared = 0;
+  for (int64_t k = 0; k < n && !movable.empty(); ++k) {
+    group.clear();
+    newpos.clear();
+    if (!propose_many(tr, vc, movable, mover, rng, group, newpos)) continue;
+    group_region(tr, group, region);
+    const double e0 = loc.energy(region);
+    fuzzy_objective(tr, fp, f0, nullptr);
+    oldpos.clear();
+    for (size_t g = 0; g < group.size(); ++g) {
+      oldpos.push_back(tr.P[group[g]]);
+      tr.P[group[g]] = newpos[g];
+    }
+    bool valid = true;
+    for (int u : group)
+      valid = valid && !tr.for_fan(u, [&](int t, int) {
+        return orient(tr.P[tr.T[t].v[0]], tr.P[tr.T[t].v[1]], tr.P[tr.T[t].v[2]]) <= 0;
+      });
+    if (valid) {
+      const double local = loc.energy(region) - e0;
+      fuzzy_objective(tr, fp, f1, nullptr);
+      worst = std::max(worst, std::fabs(local - (f1[0] - f0[0])));
+      ++compared;
+    }
+    if (!valid || rng.uni() < 0.5)
+      for (size_t g = 0; g < group.size(); ++g) tr.P[group[g]] = oldpos[g];
+  }
+  *max_err = worst;
+  *grows = loc.grows;
+  return compared;
+}
 
 int64_t sg_anneal(void* h, uint64_t seed, double sweeps, double T0, double T1, double moves, double collapse) {
   auto* tr = (Triangulation*)h;

@@ -228,3 +228,37 @@ def test_contraction_along_a_segment_and_fixed_vertices():
     hb, tb = oracle.closest_bruteforce(np.asarray(segs, np.int32), r.ox, r.oy, r.dx, r.dy)
     hw, tw, _ = oracle.walk(out, r.ox, r.oy, r.dx, r.dy, r.start)
     assert np.array_equal(hb, hw) and np.array_equal(tb, tw)
+
+
+@pytest.mark.parametrize("init_bits", [3, 12])
+def test_group_move_region_delta_equals_whole_objective(init_bits):
+    """The annealer decides a multi-vertex perturbation (Sec. 3.2.2's second
+    variant) on the energy change of a region (the stars of the moved vertices
+    and of their neighbours).  For every proposal that change equals the change
+    of the whole fuzzy objective -- also when the region's hash tables start at
+    8 slots and must grow (rehash) during the evaluation."""
+    segs = sg.circles(400, 5)
+    tri = sg.refine_optimal(sg.cdt(segs))
+    for eps in (0.02, 0.002):
+        n, err, grows = sg.fuzzy_check_group_deltas(tri, 7, 300, eps, init_bits, step=0.003)
+        assert n >= 100
+        assert err <= 1e-9, (eps, err)
+        if init_bits == 3:
+            assert grows > 0
+
+
+def test_pipeline_subdivision_round_keeps_the_shorter():
+    """scenegen.pipeline: the optimised refined CDT, optimised again after a
+    1 -> 4 subdivision (Sec. 3.5.3); the shorter is kept and is valid.  On the
+    45-degree dash grid the subdivided round wins."""
+    import oracle
+
+    segs = sg.dash_grid(3000, 45.0)
+    c, r, best = sg.pipeline(segs, 3, sweeps=4)
+    plain = sg.anneal(r, 3, sweeps=4)
+    assert oracle.check_triangulation(best, sg.D) == 0
+    assert best.length(True) <= plain.length(True)
+    assert best.route.startswith("annealed after 1 subdivision")
+    assert best.length(True) < 0.97 * c.length(True)
+    _, _, once = sg.pipeline(segs, 3, sweeps=4, subdivisions=0)
+    assert once.route == "annealed" and once.length(True) == plain.length(True)
