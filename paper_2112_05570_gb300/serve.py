@@ -6,17 +6,20 @@ counterpart in the paper, whose Sec. 5 traces rays one query at a time.
 Requests (scene, n rays) arrive on an open-loop schedule.  Each tick:
   1. arrivals join the pending queue;
   2. admission: pending requests are admitted in arrival order while the
-     device-memory budget (28 bytes per ray: rays in, results out) has room;
-     an admitted request's rays are copied to the device on the copy stream;
-  3. every admitted request whose upload has finished and that is not yet on
-     the GPU joins this tick's work list; the list is staged into one of two
-     alternating cct_batch objects and launched by replaying that batch's
-     captured CUDA graph on the compute stream -- requests that arrive while
-     others are on the GPU are admitted into the next tick, so work from
+     device-memory budget (28 bytes per ray: rays in, results out) has room --
+     the budget is one device buffer handed out as a ring (DeviceArena), so
+     admitting a request calls no allocator; admitted rays are copied to the
+     device on the upload stream, in rounds of up to 2^24 rays that share one
+     completion event;
+  3. uploaded rounds (up to 2^25 rays) form this tick's work list, staged
+     into a free one of three cct_batch objects and launched by replaying that
+     batch's captured CUDA graph on the compute stream -- requests that arrive
+     while others are on the GPU are admitted into later ticks, so work from
      different ticks overlaps on the device;
-  4. finished ticks copy their results back on the copy stream; a request is
-     done when its results are on the host, and its memory returns to the
-     budget.
+  4. finished ticks copy their results back on the download stream (uploads
+     and downloads run on separate copy engines, both overlapping the walks);
+     a request is done when its results are on the host, and its block returns
+     to the arena.
 Latency of a request = its results on the host - its arrival.  The same loop
 with one plain cct_trace launch per request gives the unbatched comparison.
 """
@@ -45,6 +48,7 @@ class Request:
     admitted: float = -1.0
     done: float = -1.0
     dev: object = None      # device int32 buffer of 7 n words while in flight: rays (n, 4), then results (3, n)
+    blk: object = None      # its block of the server's memory arena while in flight
     upload: object = None   # CUDA event: rays on the device
     tick: int = -1
     pool_lo: int = 0        # index of the request's first ray in its scene's pool (the rays wrap around it)
@@ -133,11 +137,61 @@ class RayPool:
         return parts, out, lo
 
 
+class DeviceArena:
+    """The memory budget as one device buffer of int32 words, handed out as a
+    ring: blocks are taken in admission order and come back in (nearly)
+    completion order, so a request needs no allocator call.  A block that is
+    freed out of order is reclaimed when the blocks before it are."""
+
+    ALIGN = 64  # words: 256-byte aligned blocks
+
+    def __init__(self, torch, words: int):
+        self.buf = torch.empty(max(self.ALIGN, int(words)), dtype=torch.int32, device="cuda")
+        self.cap = int(self.buf.numel())
+        self.head = 0                    # next free word
+        self.live = collections.deque()  # [start, size, freed] in allocation order
+
+    def alloc(self, words: int):
+        """A block of `words` words (a tensor view), or None while the ring is full."""
+        n = -(-int(words) // self.ALIGN) * self.ALIGN
+        if n > self.cap:
+            raise ValueError(f"a request of {words} words exceeds the memory budget ({self.cap} words)")
+        if not self.live:
+            self.head = 0
+            start = 0
+        else:
+            tail = self.live[0][0]
+            if self.head > tail:  # free: [head, cap) and [0, tail)
+                start = self.head if self.cap - self.head >= n else (0 if tail >= n else -1)
+            else:  # free: [head, tail)
+                start = self.head if tail - self.head >= n else -1
+        if start < 0:
+            return None
+        blk = [start, n, False]
+        self.live.append(blk)
+        self.head = start + n
+        return blk, self.buf[start:start + int(words)]
+
+    def free(self, blk):
+        blk[2] = True
+        while self.live and self.live[0][2]:
+            self.live.popleft()
+
+    def reset(self):
+        """Every block back (the caller has synchronised: nothing on the GPU uses them)."""
+        self.live.clear()
+        self.head = 0
+
+
 class Server:
     """The continuous-batching loop over loaded cct.Scene objects."""
 
+    ROUND_RAYS = 1 << 24  # rays uploaded between two upload events (one tick takes whole rounds)
+    STALL_S = 60.0        # no admission, tick or completion for this long: the loop raises
+    TICK_RAYS = 1 << 25   # rays per tick (a burst is cut into ticks that overlap each other's copies)
+
     def __init__(self, scenes, budget_bytes: int, max_items: int = 4096, flags: int = 0, use_graph: bool = True,
-                 tuning: dict | None = None):
+                 tuning: dict | None = None, n_batches: int = 3):
         import torch
 
         self.torch = torch
@@ -145,12 +199,16 @@ class Server:
         self.budget = int(budget_bytes)
         self.flags = flags
         self.max_items = max_items
-        self.batches = [cct.Batch(scenes, max_items, flags) for _ in range(2)]
+        self.batches = [cct.Batch(scenes, max_items, flags) for _ in range(n_batches)]
         if tuning:
             for b in self.batches:
                 b.set_tuning(tuning)
+        # uploads, walks and downloads on three streams: the copy engines move rays in and
+        # results out at the same time, both overlapping the walks
         self.compute = torch.cuda.Stream()
-        self.copy = torch.cuda.Stream()
+        self.h2d = torch.cuda.Stream()
+        self.d2h = torch.cuda.Stream()
+        self.arena = DeviceArena(torch, self.budget // 4)
         self.use_graph = use_graph
         self._graphs_ready = False
 
@@ -169,7 +227,7 @@ class Server:
         self._graphs_ready = True
 
     def _alloc(self, n: int):
-        return self.torch.empty(7 * n, dtype=self.torch.int32, device="cuda")
+        return self.torch.empty(7 * n, dtype=self.torch.int32, device="cuda")  # the capture probe only
 
     @staticmethod
     def _item(r, interleaved: bool = True):
@@ -198,43 +256,58 @@ class Server:
             self._capture_item = self._item(probe)
             self._capture(self._capture_item)
             self._probe = probe
+        for r in reqs:  # a request larger than the whole budget could never be admitted
+            if -(-7 * r.n // DeviceArena.ALIGN) * DeviceArena.ALIGN > self.arena.cap:
+                raise ValueError(f"request {r.rid}: {r.n} rays exceed the memory budget")
+        arena = self.arena
         pending = collections.deque()
-        admitted = collections.deque()   # uploading
+        admitted = collections.deque()  # upload rounds: (event, requests)
         ticks_in_flight = collections.deque()  # (event, batch index, requests)
         downloads = collections.deque()  # (event, requests)
-        used = 0
         nxt = 0
         done_lat, done_rays = [], 0
-        free_batch = [True, True]
+        free_batch = [True] * len(self.batches)
         tick = 0
         start = time.perf_counter()
         deadline = None if max_wall_s is None else start + max_wall_s
         horizon = schedule[-1][0] if schedule else 0.0
+        last_progress = start
         while True:
             now = time.perf_counter() - start
+            rounds_before, done_before = len(admitted), len(done_lat)
             while nxt < len(reqs) and reqs[nxt].arrival <= now:
                 pending.append(reqs[nxt])
                 nxt += 1
-            # admission by memory budget, in arrival order
-            while pending and used + BYTES_PER_RAY * pending[0].n <= self.budget:
-                r = pending.popleft()
-                used += BYTES_PER_RAY * r.n
-                r.admitted = now
-                r.dev = self._alloc(r.n)
-                with torch.cuda.stream(self.copy):
-                    off = 0
-                    for aos, soa in r.src:
-                        k = int(aos.shape[0])
-                        if batched:  # interleaved records: one contiguous copy
-                            r.dev[4 * off:4 * (off + k)].copy_(aos.reshape(-1), non_blocking=True)
-                        else:  # four arrays
-                            for q in range(4):
-                                r.dev[q * r.n + off:q * r.n + off + k].copy_(soa[q], non_blocking=True)
-                        off += k
-                    r.upload = torch.cuda.Event()
-                    r.upload.record(self.copy)
-                admitted.append(r)
-            # completed downloads
+            # admission by memory budget, in arrival order: blocks of the arena, uploads in rounds
+            if pending:
+                with torch.cuda.stream(self.h2d):
+                    while pending:
+                        rnd, rays = [], 0
+                        while pending and len(rnd) < self.max_items and rays < self.ROUND_RAYS:
+                            r = pending[0]
+                            got = arena.alloc(7 * r.n)
+                            if got is None:
+                                break
+                            pending.popleft()
+                            r.blk, r.dev = got
+                            r.admitted = now
+                            off = 0
+                            for aos, soa in r.src:
+                                k = int(aos.shape[0])
+                                if batched:  # interleaved records: one contiguous copy
+                                    r.dev[4 * off:4 * (off + k)].copy_(aos.reshape(-1), non_blocking=True)
+                                else:  # four arrays
+                                    for q in range(4):
+                                        r.dev[q * r.n + off:q * r.n + off + k].copy_(soa[q], non_blocking=True)
+                                off += k
+                            rnd.append(r)
+                            rays += r.n
+                        if not rnd:
+                            break
+                        ev = torch.cuda.Event()
+                        ev.record(self.h2d)
+                        admitted.append((ev, rnd))
+            # completed downloads: the requests are done, their blocks return to the arena
             while downloads and downloads[0][0].query():
                 _, rs = downloads.popleft()
                 t_done = time.perf_counter() - start
@@ -242,48 +315,47 @@ class Server:
                     r.done = t_done
                     done_lat.append(t_done - r.arrival)
                     done_rays += r.n
-                    used -= BYTES_PER_RAY * r.n
-                    r.dev = None
+                    arena.free(r.blk)
+                    r.dev = r.blk = None
             # finished ticks -> download their results
             while ticks_in_flight and ticks_in_flight[0][0].query():
                 ev, bi, rs = ticks_in_flight.popleft()
                 free_batch[bi] = True
-                with torch.cuda.stream(self.copy):
-                    self.copy.wait_event(ev)
+                with torch.cuda.stream(self.d2h):
+                    self.d2h.wait_event(ev)
                     for r in rs:
                         m = r.out.shape[1]
-                        res = r.dev[4 * r.n:].view(3, r.n)
                         if m == r.n:
                             r.out.view(-1).copy_(r.dev[4 * r.n:], non_blocking=True)
                         else:
-                            r.out.copy_(res[:, :m], non_blocking=True)
+                            r.out.copy_(r.dev[4 * r.n:].view(3, r.n)[:, :m], non_blocking=True)
                     dev = torch.cuda.Event()
-                    dev.record(self.copy)
+                    dev.record(self.d2h)
                 downloads.append((dev, rs))
-            # a tick: every uploaded request
+            # a tick: uploaded rounds, on a free batch
             ready = []
-            while admitted and admitted[0].upload.query() and len(ready) < self.max_items:
-                ready.append(admitted.popleft())
+            bi = free_batch.index(True) if (batched and True in free_batch) else (0 if not batched else -1)
+            if bi >= 0:
+                rays = 0
+                while (admitted and admitted[0][0].query() and len(ready) + len(admitted[0][1]) <= self.max_items
+                       and rays < self.TICK_RAYS):
+                    rnd = admitted.popleft()[1]
+                    ready.extend(rnd)
+                    rays += sum(r.n for r in rnd)
             if ready:
                 if batched:
-                    bi = 0 if free_batch[0] else (1 if free_batch[1] else -1)
-                    if bi < 0:
-                        for r in reversed(ready):
-                            admitted.appendleft(r)
-                        ready = []
-                    else:
-                        b = self.batches[bi]
-                        b.stage_raw([self._item(r) for r in ready], ray_stride=4)
-                        with torch.cuda.stream(self.compute):
-                            if self.use_graph:
-                                b.graph.replay()
-                            else:
-                                b.enqueue(self.compute)
-                            ev = torch.cuda.Event()
-                            ev.record(self.compute)
-                        free_batch[bi] = False
-                        ticks_in_flight.append((ev, bi, ready))
-                        tick += 1
+                    b = self.batches[bi]
+                    b.stage_raw([self._item(r) for r in ready], ray_stride=4)
+                    with torch.cuda.stream(self.compute):
+                        if self.use_graph:
+                            b.graph.replay()
+                        else:
+                            b.enqueue(self.compute)
+                        ev = torch.cuda.Event()
+                        ev.record(self.compute)
+                    free_batch[bi] = False
+                    ticks_in_flight.append((ev, bi, ready))
+                    tick += 1
                 else:
                     L = cct.lib()
                     sp = cct._stream_ptr(self.compute)
@@ -297,7 +369,6 @@ class Server:
                         ev = torch.cuda.Event()
                         ev.record(self.compute)
                     ticks_in_flight.append((ev, 0, ready))
-                    free_batch[0] = True
                     tick += 1
             finished = nxt >= len(reqs) and not pending and not admitted and not ticks_in_flight and not downloads
             if finished:
@@ -307,9 +378,21 @@ class Server:
                 break
             if deadline is not None and t_now > deadline:
                 break
+            busy = pending or admitted or ticks_in_flight or downloads
+            if not busy or ready or rounds_before != len(admitted) or done_before != len(done_lat):
+                last_progress = t_now
+            elif t_now - last_progress > self.STALL_S:
+                torch.cuda.synchronize()
+                arena.reset()
+                raise RuntimeError(f"serving loop made no progress for {self.STALL_S} s "
+                                   f"({len(pending)} pending, {len(admitted)} upload rounds, "
+                                   f"{len(ticks_in_flight)} ticks, {len(downloads)} downloads)")
             if not ready and not (downloads and downloads[0][0].query()):
                 time.sleep(0.0002)
         torch.cuda.synchronize()
+        # requests still in flight when the run stopped early (drain=False, max_wall_s) are
+        # abandoned: their blocks go back to the arena for the next run
+        arena.reset()
         wall = time.perf_counter() - start
         res = ServeResult(len(done_lat), len(reqs), done_rays, wall, np.asarray(done_lat),
                           len(pending) + len(admitted), tick)
