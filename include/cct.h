@@ -79,6 +79,11 @@ extern "C" {
 #define CCT_TRACE_BIN 2u        /* sort rays by start cell before walking (ray binning) */
 #define CCT_TRACE_SPLIT_LOCATE 4u /* without start cells: locate all origins in a separate kernel
                                      first (default: inside the walk kernel) */
+#define CCT_TRACE_STAGE 8u      /* each block first copies the scene's half-edge table (48 bytes per
+                                   triangle) into shared memory and walks from there; used only when
+                                   it fits beside the block's stacks (about 3,500 triangles at 64
+                                   threads per block, fewer for larger blocks) and the rays are not
+                                   binned, ignored otherwise.  Pays on small scenes only */
 
 /* ------------------------------------------------------------------ types */
 typedef struct cct_scene_s* cct_scene; /* opaque; the library owns all device memory of a scene */

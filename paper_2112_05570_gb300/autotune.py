@@ -4,8 +4,8 @@ No counterpart in the paper.  Knobs: threads per block, the refill threshold
 (idle lanes a warp collects before serving new rays), the chunk of rays a warp
 takes from the work counter ("rays per warp"), ray binning and its
 granularity, where start cells are found when none are given (inside the walk
-kernel, or by a separate locate kernel first), and the side test
-(fp32-filtered vs exact int64).  Coordinate
+kernel, or by a separate locate kernel first), the side test (fp32-filtered vs
+exact int64), and on small scenes the half-edge table staged in shared memory.  Coordinate
 descent from the defaults: each knob in turn takes the value with the lowest
 median CUDA-event time on a ray sample, others fixed; two passes.  Results are
 cached per (GPU, triangle-count class, ray-count class, start cells given)
@@ -28,6 +28,8 @@ KNOBS = {
     "path": ("plain", "split", "bin", "bin-coarse", "bin-fine"),
     "exact": (0, 1),
 }
+# the half-edge table staged in shared memory (CCT_TRACE_STAGE) is tried on scenes up to this size
+STAGE_MAX_TRI = 1000
 
 
 def _key(n_tri: int, n_rays: int, has_start: bool) -> str:
@@ -54,6 +56,8 @@ def _save_cache(c: dict) -> None:
 
 def _to_tuning(cfg: dict, n_tri: int, n_rays: int) -> dict:
     flags = cct.CCT_TRACE_EXACT_ONLY if cfg["exact"] else 0
+    if cfg.get("stage"):
+        flags |= cct.CCT_TRACE_STAGE
     shift = -1
     if cfg["path"] == "split":
         flags |= cct.CCT_TRACE_SPLIT_LOCATE
@@ -100,12 +104,13 @@ def tune_scene(scene: "cct.Scene", ox, oy, dx, dy, start=None, reps: int = 3, pa
             times.append(e0.elapsed_time(e1))
         return sorted(times)[len(times) // 2]
 
-    cfg = {"block_threads": 256, "refill_min": 8, "chunk": 128, "path": "plain", "exact": 0}
+    cfg = {"block_threads": 256, "refill_min": 8, "chunk": 128, "path": "plain", "exact": 0, "stage": 0}
+    knobs = dict(KNOBS, stage=(0, 1)) if scene.n_tri <= STAGE_MAX_TRI else KNOBS
     tried = {}
     best_ms = time_cfg(cfg)
     tried[json.dumps(cfg, sort_keys=True)] = best_ms
     for _ in range(passes):
-        for knob, values in KNOBS.items():
+        for knob, values in knobs.items():
             for v in values:
                 if v == cfg[knob]:
                     continue

@@ -36,6 +36,7 @@ def CCT_LOAD_SEED_DENSITY(k: int) -> int:
 CCT_TRACE_EXACT_ONLY = 1
 CCT_TRACE_BIN = 2
 CCT_TRACE_SPLIT_LOCATE = 4
+CCT_TRACE_STAGE = 8
 CCT_NOALLOC_MAX_RAYS = 1 << 20
 
 

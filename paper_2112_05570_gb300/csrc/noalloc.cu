@@ -69,8 +69,9 @@ extern "C" int cct_trace_noalloc(cct_scene scene, const int32_t* ox, const int32
   if (cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream) != cudaSuccess) return CCT_ERR_CUDA;
   // the scene's launch configuration and predicate choice, as cct_trace uses
   // them; binning (which needs scratch per ray) is left out
-  const cct_tuning& tu = scene->tuning;
+  cct_tuning tu = scene->tuning;
   flags |= tu.trace_flags & ~(uint32_t)CCT_TRACE_BIN;
+  tu.trace_flags = flags;
   const bool exact = (flags & CCT_TRACE_EXACT_ONLY) != 0;
   const SceneDev& S = scene->dev;
   if (start) {

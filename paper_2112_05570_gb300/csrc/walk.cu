@@ -79,7 +79,10 @@ struct Slot {
   bool dn;   // finished, not yet parked
 };
 
-template <bool kExact, int kSrc>
+// kStage: the block first copies the scene's half-edge table into shared
+// memory (after its warps' stacks) and the walk steps read it there: for
+// tables small enough to share the SM with the stacks (CCT_TRACE_STAGE).
+template <bool kExact, int kSrc, bool kStage>
 __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySrc R, WalkParams P,
                                                                int32_t* __restrict__ hit_out,
                                                                float* __restrict__ t_out,
@@ -94,6 +97,11 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
   const unsigned lt = lanemask_lt();
   const int n = (int)R.n;
   const int4* __restrict__ he_tab = S.he;
+  int4* const sm_he = reinterpret_cast<int4*>(smem_raw + sizeof(Stacks) * (blockDim.x >> 5));
+  if (kStage) {
+    for (int k = threadIdx.x; k < 3 * S.n_tri; k += blockDim.x) sm_he[k] = load_he(S.he + k);
+    __syncthreads();
+  }
   const int max_steps = S.max_steps;
   int pool_next = 0, pool_end = 0;  // the warp's current range of ray indices
   int pf_base = 0, pf_end = 0;      // the batch in `pf` ([pf_base, pf_end)); pf_base < 0: none left
@@ -409,8 +417,13 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     // ---------------------------------------------------------------- one step per walking slot
     // both slots' loads first: two independent rays, two loads in flight
     int4 q0 = make_int4(0, 0, 0, 0), q1 = make_int4(0, 0, 0, 0);
-    if (sl[0].act) q0 = load_he(he_tab + sl[0].h);
-    if (sl[1].act) q1 = load_he(he_tab + sl[1].h);
+    if (kStage) {
+      if (sl[0].act) q0 = sm_he[sl[0].h];
+      if (sl[1].act) q1 = sm_he[sl[1].h];
+    } else {
+      if (sl[0].act) q0 = load_he(he_tab + sl[0].h);
+      if (sl[1].act) q1 = load_he(he_tab + sl[1].h);
+    }
     if (sl[0].act) step(sl[0], q0);
     if (sl[1].act) step(sl[1], q1);
   }
@@ -438,24 +451,32 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
   }
 }
 
-template <bool kExact, int kSrc>
+template <int kSrc>
+static size_t stacks_bytes(int threads) {
+  return sizeof(WarpStacks<pf_rows<kSrc>()>) * (size_t)(threads / 32);
+}
+
+// Shared memory a block may use (the GB300 per-block maximum).
+constexpr size_t kMaxBlockSmem = 227 * 1024;
+
+template <bool kExact, int kSrc, bool kStage>
 static cudaError_t launch_walk_t(const SceneDev& S, const RaySrc& R, const cct_tuning& tu, int32_t* hit, float* t,
                                  int32_t* steps, unsigned long long* counter, int dev, cudaStream_t stream) {
-  auto k = walk_kernel<kExact, kSrc>;
+  auto k = walk_kernel<kExact, kSrc, kStage>;
   const int threads = tu.block_threads;
-  const size_t smem = sizeof(WarpStacks<pf_rows<kSrc>()>) * (size_t)(threads / 32);
+  const size_t smem = stacks_bytes<kSrc>(threads) + (kStage ? sizeof(int4) * 3 * (size_t)S.n_tri : 0);
   {
     // once per instantiation and device (function attributes belong to each
-    // device's context; `dev` is current): the stacks of 16 warps exceed the
-    // default 48 KB of dynamic shared memory.  The shared/L1 split is left to
-    // the CUDA runtime's choice: a maximal shared carveout measured 1.5x
-    // slower (the L1 also holds the loads in flight).
+    // device's context; `dev` is current): the stacks of 16 warps (and a
+    // staged table) exceed the default 48 KB of dynamic shared memory.  The
+    // shared/L1 split is left to the CUDA runtime's choice: a maximal shared
+    // carveout measured 1.5x slower (the L1 also holds the loads in flight).
     static std::mutex mu;
     static uint64_t configured = 0;  // bit d: done on device d (d < 64; others every call)
     std::lock_guard<std::mutex> lk(mu);
     if (dev < 0 || dev >= 64 || !((configured >> dev) & 1u)) {
-      const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(sizeof(WarpStacks<pf_rows<kSrc>()>) * (kWalkMaxThreads / 32)));
+      const size_t cap = kStage ? kMaxBlockSmem : stacks_bytes<kSrc>(kWalkMaxThreads);
+      const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
       if (e != cudaSuccess) return e;
       if (dev >= 0 && dev < 64) configured |= 1ull << dev;
     }
@@ -472,18 +493,30 @@ static cudaError_t launch_walk_t(const SceneDev& S, const RaySrc& R, const cct_t
   return cudaGetLastError();
 }
 
+bool walk_stage_fits(int32_t n_tri, int block_threads) {
+  return stacks_bytes<kSrcPlainUser>(block_threads) + sizeof(int4) * 3 * (size_t)n_tri <= kMaxBlockSmem;
+}
+
 cudaError_t launch_walk_src(bool exact, int src, const SceneDev& S, const RaySrc& R, const cct_tuning& tu,
                             int32_t* hit, float* t, int32_t* steps, unsigned long long* counter, int dev,
                             cudaStream_t stream) {
-#define CCT_WALK_CASE(SRC)                                                                 \
-  case SRC:                                                                                \
-    return exact ? launch_walk_t<true, SRC>(S, R, tu, hit, t, steps, counter, dev, stream) \
-                 : launch_walk_t<false, SRC>(S, R, tu, hit, t, steps, counter, dev, stream);
+  // the staged table only for unsorted rays, and only when it fits beside the stacks
+  const bool stage = (tu.trace_flags & CCT_TRACE_STAGE) != 0 && src != kSrcSorted &&
+                     walk_stage_fits(S.n_tri, tu.block_threads);
+#define CCT_WALK_CASE(SRC)                                                                                  \
+  case SRC:                                                                                                 \
+    if (stage)                                                                                              \
+      return exact ? launch_walk_t<true, SRC, true>(S, R, tu, hit, t, steps, counter, dev, stream)          \
+                   : launch_walk_t<false, SRC, true>(S, R, tu, hit, t, steps, counter, dev, stream);        \
+    return exact ? launch_walk_t<true, SRC, false>(S, R, tu, hit, t, steps, counter, dev, stream)           \
+                 : launch_walk_t<false, SRC, false>(S, R, tu, hit, t, steps, counter, dev, stream);
   switch (src) {
     CCT_WALK_CASE(kSrcPlainUser)
     CCT_WALK_CASE(kSrcPlainDev)
-    CCT_WALK_CASE(kSrcSorted)
     CCT_WALK_CASE(kSrcLocate)
+    case kSrcSorted:
+      return exact ? launch_walk_t<true, kSrcSorted, false>(S, R, tu, hit, t, steps, counter, dev, stream)
+                   : launch_walk_t<false, kSrcSorted, false>(S, R, tu, hit, t, steps, counter, dev, stream);
     default:
       return cudaErrorInvalidValue;
   }
@@ -520,8 +553,9 @@ static int trace_impl(cct_scene scene, const int32_t* ox, const int32_t* oy, con
                       const int32_t* start, int64_t n, int32_t* hit, float* t, int32_t* steps, uint32_t flags,
                       cudaStream_t stream) {
   const SceneDev& S = scene->dev;
-  const cct_tuning& tu = scene->tuning;
+  cct_tuning tu = scene->tuning;
   flags |= tu.trace_flags;
+  tu.trace_flags = flags;  // the launch sees the call's flags too
   const bool exact = (flags & CCT_TRACE_EXACT_ONLY) != 0;
   const bool bin = (flags & CCT_TRACE_BIN) != 0;
   const bool split = !start && !bin && (flags & CCT_TRACE_SPLIT_LOCATE) != 0;
@@ -609,7 +643,7 @@ extern "C" int cct_scene_set_tuning(cct_scene scene, const cct_tuning* tu) {
   }
   if (tu->block_threads < 32 || tu->block_threads > kWalkMaxThreads || tu->block_threads % 32 != 0 ||
       tu->refill_min < 1 || tu->refill_min > 32 || tu->chunk < 32 || tu->chunk > (1 << 20) || tu->bin_shift > 30 ||
-      (tu->trace_flags & ~(CCT_TRACE_EXACT_ONLY | CCT_TRACE_BIN | CCT_TRACE_SPLIT_LOCATE)) != 0)
+      (tu->trace_flags & ~(CCT_TRACE_EXACT_ONLY | CCT_TRACE_BIN | CCT_TRACE_SPLIT_LOCATE | CCT_TRACE_STAGE)) != 0)
     return CCT_ERR_INVALID_ARGUMENT;
   scene->tuning = *tu;
   return CCT_OK;

@@ -340,3 +340,42 @@ def test_config3_ring_of_circles_sampled(cct, N):
                 _assert_parity((h[idx], t[idx], s[idx]), exp)
     finally:
         scene.free()
+
+
+@pytest.mark.parametrize("block", [64, 512])
+@pytest.mark.parametrize("exact", [0, 1])
+def test_staged_half_edge_table_bit_exact(cct, scenes, block, exact):
+    """CCT_TRACE_STAGE (the half-edge table copied into each block's shared
+    memory): start cells given, located in the walk kernel, and located by the
+    split locate kernel, on the config-1 scenes with a ragged ray count and
+    degenerate rays; every output equals the oracle."""
+    from test_oracle import _degenerate_rays
+
+    fl = cct.CCT_TRACE_STAGE | (cct.CCT_TRACE_EXACT_ONLY if exact else 0)
+    for kind, seed, tri in scenes:
+        r = sg.rays_isotropic(tri, 65536 + 77, 30 + seed)
+        ox, oy, dx, dy, _ = _degenerate_rays(tri, 300, 40 + seed)
+        st = oracle.locate_bruteforce(tri, ox, oy)
+        ok = st >= 0
+        cat = lambda a, b: np.ascontiguousarray(np.concatenate([a, b[ok]]))
+        ox, oy, dx, dy, st = cat(r.ox, ox), cat(r.oy, oy), cat(r.dx, dx), cat(r.dy, dy), cat(r.start, st)
+        exp = oracle.walk(tri, ox, oy, dx, dy, st)
+        scene = cct.Scene.from_triangulation(tri, sg.D)
+        scene.set_tuning({"block_threads": block, "refill_min": 16, "chunk": 256})
+        for start, extra in ((st, 0), (None, 0), (None, cct.CCT_TRACE_SPLIT_LOCATE)):
+            _assert_parity(_trace(scene, ox, oy, dx, dy, start, fl | extra), exp)
+        scene.free()
+
+
+def test_stage_flag_ignored_where_the_table_does_not_fit(cct):
+    """A scene whose half-edge table does not fit in shared memory beside the
+    stacks walks from global memory under CCT_TRACE_STAGE: same results."""
+    segs = sg.random_segments(3000, 9)
+    tri = sg.cdt(segs)
+    assert tri.n_tri * 48 > 227 * 1024
+    r = sg.rays_isotropic(tri, 100_000, 11)
+    exp = oracle.walk(tri, r.ox, r.oy, r.dx, r.dy, r.start)
+    scene = cct.Scene.from_triangulation(tri, sg.D)
+    _assert_parity(_trace(scene, r.ox, r.oy, r.dx, r.dy, r.start, cct.CCT_TRACE_STAGE), exp)
+    _assert_parity(_trace(scene, r.ox, r.oy, r.dx, r.dy, None, cct.CCT_TRACE_STAGE), exp)
+    scene.free()
