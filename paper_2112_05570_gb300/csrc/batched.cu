@@ -278,13 +278,16 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
       if (!locate)
         ok = orient_i(x1, y1, x2, y2, pox, poy) > 0 && orient_i(x2, y2, x0, y0, pox, poy) > 0 &&
              orient_i(x0, y0, x1, y1, pox, poy) > 0;
+      // the exit is the CCW edge (a -> b) with s(a) = R, s(b) = L.  The origin
+      // lies strictly inside, so the three vertices are not all on one side:
+      // vertex 0 left leaves edge 0 (s2 = L) or edge 1 (s2 = R); vertex 0
+      // right leaves edge 2 (s1 = L) or edge 0 (s1 = R).  Two side tests.
       const bool s0 = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(x0), coord_word(y0), n_fb);
-      const bool s1 = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(x1), coord_word(y1), n_fb);
-      const bool s2 = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(x2), coord_word(y2), n_fb);
-      e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
+      const bool sv = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(s0 ? x2 : x1), coord_word(s0 ? y2 : y1),
+                                        n_fb);
+      e = s0 ? (sv ? 0 : 1) : (sv ? 2 : 0);
       w = nb_of(r, e);
     }
-    const unsigned m_first = __ballot_sync(FULL, ok);
     const bool to_ready = ok && w >= 0;
     const bool to_done = v && !to_ready;
     const unsigned mr = __ballot_sync(FULL, to_ready), md = __ballot_sync(FULL, to_done);
@@ -299,7 +302,6 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
     if (lane == 0) {
       W.cnt[kBRays] += __popc(mv);
       W.cnt[kBInvalid] += __popc(minv);
-      W.sides += 3ull * (unsigned)__popc(m_first);
     }
     if (to_ready) {
       const int k = n_ready + __popc(mr & lt);
@@ -406,8 +408,9 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
   }
   __syncwarp();
   const unsigned w_fb = __reduce_add_sync(FULL, n_fb), w_limit = __reduce_add_sync(FULL, n_lim);
-  const unsigned long long w_steps = W.steps, w_side = W.sides;
+  // two side tests in the first triangle of every ray that reached it (the valid ones)
   const unsigned long long w_rays = W.cnt[kBRays], w_inv = W.cnt[kBInvalid];
+  const unsigned long long w_steps = W.steps, w_side = W.sides + 2ull * (w_rays - w_inv);
   const unsigned long long w_loc = W.cnt[kBLocated], w_lst = W.cnt[kBLocSteps];
   if (lane == 0) {
     if (w_rays) atomicAdd(&bstats->rays, w_rays);

@@ -168,16 +168,18 @@ __device__ __forceinline__ bool side_L_w(int kxw, int kyw, int ox, int oy, int v
   return e >= 0;
 }
 
-// Origin word of a ray in the walk state: the fp32 bits of 2^23 + o in the
-// filtered variant (so that apex - origin is one exact fp32 subtraction of two
-// numbers in [2^23, 2^24)), the integer o in the exact-only variant.
+// Origin word of a ray in the walk state: the fp32 bits of 2^23 + o, as the
+// apex words of the half-edge records.  Filtered, apex - origin is one exact
+// fp32 subtraction of two numbers in [2^23, 2^24); exact-only, it is one
+// integer subtraction of the two words (the bias bits are equal, so the
+// difference is v - o).  Both variants use the same words.
 template <bool kExactOnly>
 __device__ __forceinline__ int o_word(int o) {
-  return kExactOnly ? o : coord_word(o);
+  return coord_word(o);
 }
 template <bool kExactOnly>
 __device__ __forceinline__ int o_of_word(int w) {
-  return kExactOnly ? w : coord_of_word(w);
+  return coord_of_word(w);
 }
 
 // Side (true = L) of a vertex given by its coordinate words (coord_word)
@@ -194,8 +196,8 @@ __device__ __forceinline__ bool side_L_cw(int kxw, int kyw, int oxw, int oyw, in
     if (fabsf(r) >= kFilterBound * kDirScale) return r > 0.0f;
     ++fallbacks;
   }
-  const int ddx = coord_of_word(vxw) - o_of_word<kExactOnly>(oxw);
-  const int ddy = coord_of_word(vyw) - o_of_word<kExactOnly>(oyw);
+  const int ddx = vxw - oxw;  // both words carry the same bias
+  const int ddy = vyw - oyw;
   return (long long)k_of_word<kExactOnly>(kxw) * ddy - (long long)k_of_word<kExactOnly>(kyw) * ddx >= 0;
 }
 

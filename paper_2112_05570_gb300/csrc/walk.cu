@@ -1,7 +1,8 @@
 // The stackless walk (Sec. 5.1) and cct_trace.
 //
-// Per ray: in the start triangle decide the side (L/R) of all three vertices
-// and leave through the CCW edge (a -> b) with s(a) = R, s(b) = L.  Across an
+// Per ray: in the start triangle leave through the CCW edge (a -> b) with
+// s(a) = R, s(b) = L (two side tests: the origin lies strictly inside, so the
+// three vertices are not all on one side).  Across an
 // interior edge the neighbour shares the two decided vertices, so each later
 // step decides only the new apex c: s(c) = L -> leave through (R-vertex, c),
 // else through (c, L-vertex) -- the two remaining candidates of Sec. 7.2.  A
@@ -280,8 +281,8 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
         }
       }
     }
-    // first step (Sec. 5.1): sides of all three vertices, leave through the
-    // CCW edge (a -> b) with s(a) = R, s(b) = L
+    // first step (Sec. 5.1): leave the start triangle through the CCW edge
+    // (a -> b) with s(a) = R, s(b) = L
     const int oxw = o_word<kExact>(pox), oyw = o_word<kExact>(poy);
     int e = 0;
     int32_t w = -1;
@@ -291,14 +292,16 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
       if (!kLocate)
         ok = orient_i(x1, y1, x2, y2, pox, poy) > 0 && orient_i(x2, y2, x0, y0, pox, poy) > 0 &&
              orient_i(x0, y0, x1, y1, pox, poy) > 0;
+      // the exit is the CCW edge (a -> b) with s(a) = R, s(b) = L.  The origin
+      // lies strictly inside, so the three vertices are not all on one side:
+      // vertex 0 left leaves edge 0 (s2 = L) or edge 1 (s2 = R); vertex 0
+      // right leaves edge 2 (s1 = L) or edge 0 (s1 = R).  Two side tests.
       const bool s0 = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(x0), coord_word(y0), n_fb);
-      const bool s1 = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(x1), coord_word(y1), n_fb);
-      const bool s2 = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(x2), coord_word(y2), n_fb);
-      e = (!s1 && s2) ? 0 : ((!s2 && s0) ? 1 : 2);
+      const bool sv = side_L_cw<kExact>(pkx, pky, oxw, oyw, coord_word(s0 ? x2 : x1), coord_word(s0 ? y2 : y1),
+                                        n_fb);
+      e = s0 ? (sv ? 0 : 1) : (sv ? 2 : 0);
       w = nb_of(r, e);
     }
-    // three side tests per ray that reached its first step
-    const unsigned m_first = __ballot_sync(FULL, ok);
     const bool to_ready = ok && w >= 0;
     const bool to_done = v && !to_ready;
     const unsigned mr = __ballot_sync(FULL, to_ready), md = __ballot_sync(FULL, to_done);
@@ -313,7 +316,6 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     if (lane == 0) {
       W.cnt[kCntRays] += __popc(mv);
       W.cnt[kCntInvalid] += __popc(minv);
-      W.sides += 3ull * (unsigned)__popc(m_first);
     }
     if (to_ready) {
       const int k = n_ready + __popc(mr & lt);
@@ -436,8 +438,9 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
   // ---------------------------------------------------------------- counters: one atomic per warp and counter
   __syncwarp();
   const unsigned w_fb = __reduce_add_sync(FULL, n_fb), w_limit = __reduce_add_sync(FULL, n_lim);
-  const unsigned long long w_steps = W.steps, w_side = W.sides;
+  // two side tests in the first triangle of every ray that reached it (the valid ones)
   const unsigned long long w_rays = W.cnt[kCntRays], w_inv = W.cnt[kCntInvalid];
+  const unsigned long long w_steps = W.steps, w_side = W.sides + 2ull * (w_rays - w_inv);
   const unsigned long long w_loc = W.cnt[kCntLocated], w_lst = W.cnt[kCntLocSteps];
   if (lane == 0) {
     if (w_rays) atomicAdd(&S.stats->rays, w_rays);

@@ -241,7 +241,7 @@ def test_stats_counters(cct, scenes):
     h, t, s = _trace(scene, r.ox, r.oy, r.dx, r.dy, r.start)
     st = scene.stats(reset=True)
     assert st["rays"] == len(r) and st["steps"] == int(s.sum())
-    assert st["side_tests"] == int(s.sum()) + 2 * len(r)  # 3 in the first triangle, 1 per later step
+    assert st["side_tests"] == int(s.sum()) + len(r)  # 2 in the first triangle, 1 per later step
     assert st["exact_fallbacks"] < st["side_tests"] * 1e-3
     h, t, s = _trace(scene, r.ox, r.oy, r.dx, r.dy, r.start, cct.CCT_TRACE_EXACT_ONLY)
     st2 = scene.stats()
