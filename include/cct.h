@@ -309,7 +309,8 @@ typedef struct cct_batch_s* cct_batch;
 
 /* A reusable batch over n_scenes loaded scenes (all on one device) for up to
  * max_items items; flags: 0 or CCT_TRACE_EXACT_ONLY.  Holds a device work table
- * and a pinned host staging copy of it.  The scenes must outlive the batch. */
+ * and a pinned, device-mapped host staging copy of it.  The scenes must outlive
+ * the batch. */
 int cct_batch_create(const cct_scene* scenes, int32_t n_scenes, int32_t max_items, uint32_t flags, cct_batch* out);
 int cct_batch_free(cct_batch batch);
 
@@ -323,10 +324,12 @@ int cct_batch_set_tuning(cct_batch batch, const cct_tuning* tuning);
  * null arrays, more than max_items). */
 int cct_batch_stage(cct_batch batch, const cct_batch_item* items, int32_t n_items);
 
-/* Enqueues on `stream`: the copy of the staged table to the device (its full
- * fixed size), the work-counter reset and the persistent kernel.  Its three
- * operations have fixed arguments, so one stream capture of this call can be
- * replayed after every cct_batch_stage. */
+/* Enqueues on `stream` two kernels: one that copies the staged table (its full
+ * fixed size, read by the GPU from the mapped staging buffer) to the device and
+ * resets the work counter, then the persistent walk.  No copy engine is used,
+ * so the launch does not queue behind the caller's bulk transfers on other
+ * streams.  Both have fixed arguments, so one stream capture of this call can
+ * be replayed after every cct_batch_stage. */
 int cct_batch_enqueue(cct_batch batch, void* stream);
 
 /* Counters accumulated by this batch's launches (per-scene counters of
@@ -427,6 +430,18 @@ int cct_kdtree_free(cct_kdtree kd);
  * from the stream-ordered allocator on `stream`. */
 int cct_trace_kdtree(cct_kdtree kd, const int32_t* d_ox, const int32_t* d_oy, const float* d_dx, const float* d_dy,
                      int64_t n, int32_t* d_hit_seg, float* d_t, int32_t* d_ops, void* stream);
+
+/* No counterpart in the paper: a host utility for a serving loop that moves
+ * many requests' rays and results at once.  Enqueues n asynchronous copies on
+ * `stream`, in order, one runtime copy call each: copy k moves bytes[k] bytes
+ * from src[k] to dst[k] (host or device addresses, resolved by the CUDA
+ * runtime's unified addressing; host memory should be pinned for the copies to
+ * overlap other work).  The three arrays are host arrays, read before the call
+ * returns; the memory they point to must stay valid until the copies have run
+ * on the stream.  n = 0 is a no-op.  Errors: CCT_ERR_INVALID_ARGUMENT (n < 0,
+ * or a NULL array with n > 0), CCT_ERR_CUDA (a copy could not be enqueued; the
+ * copies before it stay enqueued). */
+int cct_copies_async(int32_t n, void* const* dst, const void* const* src, const size_t* bytes, void* stream);
 
 /* Static text for a status code. */
 const char* cct_error_string(int code);

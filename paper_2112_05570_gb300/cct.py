@@ -97,6 +97,8 @@ def lib() -> ctypes.CDLL:
                            "(there is no CPU fallback)")
     L = ctypes.CDLL(_build.LIB)
     vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    L.cct_copies_async.restype = ctypes.c_int
+    L.cct_copies_async.argtypes = [i32, vp, vp, vp, vp]
     L.cct_scene_load.restype = ctypes.c_int
     L.cct_scene_load.argtypes = [ctypes.POINTER(_TriDesc), u32, vp, ctypes.POINTER(vp)]
     L.cct_scene_free.restype = ctypes.c_int
@@ -157,6 +159,21 @@ def lib() -> ctypes.CDLL:
 
 def cct_error_string(code: int) -> str:
     return lib().cct_error_string(int(code)).decode()
+
+
+def cct_copies_async(dst, src, nbytes, stream=None) -> None:
+    """Enqueues len(dst) copies on `stream` in one call (include/cct.h): dst,
+    src and nbytes are equal-length sequences of addresses and byte counts."""
+    n = len(dst)
+    if n == 0:
+        return
+    d = np.ascontiguousarray(dst, dtype=np.uint64)
+    s_ = np.ascontiguousarray(src, dtype=np.uint64)
+    b = np.ascontiguousarray(nbytes, dtype=np.uint64)
+    if not (d.size == s_.size == b.size == n):
+        raise ValueError("cct_copies_async: dst, src and nbytes differ in length")
+    _check(lib().cct_copies_async(n, d.ctypes.data, s_.ctypes.data, b.ctypes.data, _stream_ptr(stream)),
+           "cct_copies_async")
 
 
 def _check(code: int, what: str):

@@ -10,10 +10,11 @@
 // (and the seed locate of Sec. 5.2 when an item has no start cells), exactly
 // as in walk.cu.
 //
-// The table is filled from a pinned host staging buffer by
-// cct_batch_enqueue (a fixed-size copy, a counter reset, one kernel), so the
-// enqueue can be captured once in a CUDA graph and replayed after each
-// cct_batch_stage.
+// The table is filled from a pinned, device-mapped host staging buffer by
+// cct_batch_enqueue (a small kernel that copies it and resets the work
+// counter, then the walk), so the enqueue can be captured once in a CUDA graph
+// and replayed after each cct_batch_stage.  No copy engine is involved: a
+// launch does not wait behind the caller's bulk transfers.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -426,6 +427,17 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
 
 static size_t al256d(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// The staged work list into device memory, read by the GPU straight from the
+// pinned (device-mapped) host staging buffer, and the work counter reset.  A
+// kernel rather than a copy: a copy would queue on a copy engine behind the
+// caller's bulk ray transfers (measured: a serving tick's launch waited
+// 22 ms behind 16 queued uploads).
+__global__ void stage_table_kernel(int4* __restrict__ dst, const int4* __restrict__ src, int n16,
+                                   unsigned long long* __restrict__ counter) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n16; k += gridDim.x * blockDim.x) dst[k] = src[k];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0ull;
+}
+
 }  // namespace cct
 
 using namespace cct;
@@ -441,7 +453,8 @@ struct cct_batch_s {
   BatchHeader* d_hdr;    // followed by max_items BatchItemDev
   unsigned long long* d_counter;
   DevStats* d_stats;
-  char* h_staging;       // pinned copy of header + items
+  char* h_staging;       // pinned copy of header + items, mapped into the device's address space
+  const int4* h_staging_dev;  // its device address
   size_t table_bytes;
   int grid;
   int staged;
@@ -481,6 +494,7 @@ extern "C" int cct_batch_create(const cct_scene* scenes, int32_t n_scenes, int32
   b->flags = flags;
   b->tuning = default_tuning();
   b->table_bytes = sizeof(BatchHeader) + sizeof(BatchItemDev) * (size_t)max_items;
+  static_assert(sizeof(BatchHeader) % 16 == 0 && sizeof(BatchItemDev) % 16 == 0, "the table is copied as int4");
   const size_t o_scenes = 0, o_table = al256d(sizeof(SceneDev) * n_scenes);
   const size_t o_counter = o_table + al256d(b->table_bytes), o_stats = o_counter + 256;
   const size_t total = o_stats + al256d(sizeof(DevStats));
@@ -489,13 +503,18 @@ extern "C" int cct_batch_create(const cct_scene* scenes, int32_t n_scenes, int32
     delete b;
     return CCT_ERR_OUT_OF_MEMORY;
   }
-  if (cudaMallocHost(&b->h_staging, b->table_bytes) != cudaSuccess) {
+  void* staging_dev = nullptr;
+  b->h_staging = nullptr;
+  if (cudaHostAlloc(&b->h_staging, b->table_bytes, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(&staging_dev, b->h_staging, 0) != cudaSuccess) {
     cudaGetLastError();
+    if (b->h_staging) cudaFreeHost(b->h_staging);
     cudaFree(b->d_base);
     delete b;
     return CCT_ERR_OUT_OF_MEMORY;
   }
   std::memset(b->h_staging, 0, b->table_bytes);
+  b->h_staging_dev = (const int4*)staging_dev;
   b->d_scenes = (SceneDev*)(b->d_base + o_scenes);
   b->d_hdr = (BatchHeader*)(b->d_base + o_table);
   b->d_counter = (unsigned long long*)(b->d_base + o_counter);
@@ -578,9 +597,10 @@ extern "C" int cct_batch_enqueue(cct_batch b, void* stream_v) {
   if (!b || !b->staged) return CCT_ERR_INVALID_ARGUMENT;
   DeviceGuard g(b->device);
   cudaStream_t stream = (cudaStream_t)stream_v;
-  if (cudaMemcpyAsync(b->d_hdr, b->h_staging, b->table_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
-    return CCT_ERR_CUDA;
-  if (cudaMemsetAsync(b->d_counter, 0, 8, stream) != cudaSuccess) return CCT_ERR_CUDA;
+  const int n16 = (int)(b->table_bytes / 16);
+  stage_table_kernel<<<std::min(152, (n16 + 255) / 256), 256, 0, stream>>>((int4*)b->d_hdr, b->h_staging_dev, n16,
+                                                                          b->d_counter);
+  if (cudaGetLastError() != cudaSuccess) return CCT_ERR_CUDA;
   const auto* items = (const BatchItemDev*)((const char*)b->d_hdr + sizeof(BatchHeader));
   const size_t smem = batch_smem(b->tuning.block_threads);
   if (b->flags & CCT_TRACE_EXACT_ONLY)

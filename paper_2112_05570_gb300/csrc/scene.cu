@@ -418,3 +418,17 @@ extern "C" const char* cct_error_string(int code) {
 }
 
 extern "C" int cct_version(void) { return (0 << 16) | 1; }
+
+extern "C" int cct_copies_async(int32_t n, void* const* dst, const void* const* src, const size_t* bytes,
+                                void* stream_v) {
+  if (n < 0 || (n > 0 && (!dst || !src || !bytes))) return CCT_ERR_INVALID_ARGUMENT;
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  for (int32_t k = 0; k < n; ++k) {
+    if (bytes[k] == 0) continue;
+    if (cudaMemcpyAsync(dst[k], src[k], bytes[k], cudaMemcpyDefault, stream) != cudaSuccess) {
+      cudaGetLastError();
+      return CCT_ERR_CUDA;
+    }
+  }
+  return CCT_OK;
+}

@@ -52,6 +52,7 @@ class Request:
     upload: object = None   # CUDA event: rays on the device
     tick: int = -1
     pool_lo: int = 0        # index of the request's first ray in its scene's pool (the rays wrap around it)
+    ranges: list = None     # its pieces of the pool: (first ray, count), wrapping around
 
 
 @dataclass
@@ -113,20 +114,24 @@ class RayPool:
             # the same rays as four separate arrays (the layout cct_trace takes)
             self.soa.append(torch.from_numpy(np.ascontiguousarray(a.T)).pin_memory())
         self.n = [int(r.ox.shape[0]) for r in rays_per_scene]
+        self.src_ptr = [t.data_ptr() for t in self.src]  # 16 bytes per ray
+        self.soa_ptr = [t.data_ptr() for t in self.soa]  # 4 rows of n[scene] words
         self.out = torch.empty(3 * capacity_out, dtype=torch.int32).pin_memory()
         self.out_cap = capacity_out
         self.out_pos = 0
 
     def take(self, scene: int, n: int, rng):
         """n rays of `scene`: a list of (k, 4) pool slices (wrapping around the
-        pool when n exceeds it), and a (3, n') view of the result ring (n' = n,
-        or the ring's capacity if smaller)."""
+        pool when n exceeds it), a (3, n') view of the result ring (n' = n, or
+        the ring's capacity if smaller), the first ray's pool index, and the
+        pieces as (first ray, count)."""
         m = self.n[scene]
         lo = int(rng.integers(0, m))
-        parts, left, pos = [], n, lo
+        parts, ranges, left, pos = [], [], n, lo
         while left > 0:
             k = min(left, m - pos)
             parts.append((self.src[scene][pos:pos + k], self.soa[scene][:, pos:pos + k]))
+            ranges.append((pos, k))
             left -= k
             pos = 0
         n_out = min(n, self.out_cap)
@@ -134,7 +139,7 @@ class RayPool:
             self.out_pos = 0
         out = self.out[3 * self.out_pos:3 * (self.out_pos + n_out)].view(3, n_out)
         self.out_pos += n_out
-        return parts, out, lo
+        return parts, out, lo, ranges
 
 
 class DeviceArena:
@@ -189,6 +194,8 @@ class Server:
     ROUND_RAYS = 1 << 24  # rays uploaded between two upload events (one tick takes whole rounds)
     STALL_S = 60.0        # no admission, tick or completion for this long: the loop raises
     TICK_RAYS = 1 << 25   # rays per tick (a burst is cut into ticks that overlap each other's copies)
+    TICK_MIN_RAYS = 1 << 22  # while a tick runs, the next starts only with this many rays ready: a
+                             # launch has a fixed ramp-up and drain, so many small ticks waste the GPU
 
     def __init__(self, scenes, budget_bytes: int, max_items: int = 4096, flags: int = 0, use_graph: bool = True,
                  tuning: dict | None = None, n_batches: int = 3):
@@ -247,8 +254,8 @@ class Server:
         rng = np.random.default_rng(seed)
         reqs = []
         for k, (t, sc, n) in enumerate(schedule):
-            parts, out, lo = pool.take(sc, n, rng)
-            reqs.append(Request(k, sc, int(n), t, parts, out, pool_lo=lo))
+            parts, out, lo, ranges = pool.take(sc, n, rng)
+            reqs.append(Request(k, sc, int(n), t, parts, out, pool_lo=lo, ranges=ranges))
         if batched and self.use_graph and not self._graphs_ready and reqs:
             probe = Request(-1, reqs[0].scene, 1, 0.0, [(reqs[0].src[0][0][:1], None)])
             probe.dev = self._alloc(1)
@@ -280,33 +287,38 @@ class Server:
                 nxt += 1
             # admission by memory budget, in arrival order: blocks of the arena, uploads in rounds
             if pending:
-                with torch.cuda.stream(self.h2d):
-                    while pending:
-                        rnd, rays = [], 0
-                        while pending and len(rnd) < self.max_items and rays < self.ROUND_RAYS:
-                            r = pending[0]
-                            got = arena.alloc(7 * r.n)
-                            if got is None:
-                                break
-                            pending.popleft()
-                            r.blk, r.dev = got
-                            r.admitted = now
-                            off = 0
-                            for aos, soa in r.src:
-                                k = int(aos.shape[0])
-                                if batched:  # interleaved records: one contiguous copy
-                                    r.dev[4 * off:4 * (off + k)].copy_(aos.reshape(-1), non_blocking=True)
-                                else:  # four arrays
-                                    for q in range(4):
-                                        r.dev[q * r.n + off:q * r.n + off + k].copy_(soa[q], non_blocking=True)
-                                off += k
-                            rnd.append(r)
-                            rays += r.n
-                        if not rnd:
+                while pending:
+                    rnd, rays, dst, src, nb = [], 0, [], [], []
+                    while pending and len(rnd) < self.max_items and rays < self.ROUND_RAYS:
+                        r = pending[0]
+                        got = arena.alloc(7 * r.n)
+                        if got is None:
                             break
-                        ev = torch.cuda.Event()
-                        ev.record(self.h2d)
-                        admitted.append((ev, rnd))
+                        pending.popleft()
+                        r.blk, r.dev = got
+                        r.admitted = now
+                        base, off = r.dev.data_ptr(), 0
+                        for pos, k in r.ranges:
+                            if batched:  # interleaved records: one contiguous piece
+                                dst.append(base + 16 * off)
+                                src.append(pool.src_ptr[r.scene] + 16 * pos)
+                                nb.append(16 * k)
+                            else:  # four arrays
+                                m = pool.n[r.scene]
+                                for q in range(4):
+                                    dst.append(base + 4 * (q * r.n + off))
+                                    src.append(pool.soa_ptr[r.scene] + 4 * (q * m + pos))
+                                    nb.append(4 * k)
+                            off += k
+                        rnd.append(r)
+                        rays += r.n
+                    if not rnd:
+                        break
+                    # the round's copies in one call, then one event for all of them
+                    cct.cct_copies_async(dst, src, nb, self.h2d)
+                    ev = torch.cuda.Event()
+                    ev.record(self.h2d)
+                    admitted.append((ev, rnd))
             # completed downloads: the requests are done, their blocks return to the arena
             while downloads and downloads[0][0].query():
                 _, rs = downloads.popleft()
@@ -321,27 +333,37 @@ class Server:
             while ticks_in_flight and ticks_in_flight[0][0].query():
                 ev, bi, rs = ticks_in_flight.popleft()
                 free_batch[bi] = True
-                with torch.cuda.stream(self.d2h):
-                    self.d2h.wait_event(ev)
-                    for r in rs:
-                        m = r.out.shape[1]
-                        if m == r.n:
-                            r.out.view(-1).copy_(r.dev[4 * r.n:], non_blocking=True)
-                        else:
-                            r.out.copy_(r.dev[4 * r.n:].view(3, r.n)[:, :m], non_blocking=True)
-                    dev = torch.cuda.Event()
-                    dev.record(self.d2h)
+                self.d2h.wait_event(ev)
+                dst, src, nb = [], [], []
+                for r in rs:
+                    m, res, out = r.out.shape[1], r.dev.data_ptr() + 16 * r.n, r.out.data_ptr()
+                    if m == r.n:  # the three result rows in one piece
+                        dst.append(out)
+                        src.append(res)
+                        nb.append(12 * m)
+                    else:  # the ring holds only the first m results of each row
+                        for q in range(3):
+                            dst.append(out + 4 * q * m)
+                            src.append(res + 4 * q * r.n)
+                            nb.append(4 * m)
+                cct.cct_copies_async(dst, src, nb, self.d2h)
+                dev = torch.cuda.Event()
+                dev.record(self.d2h)
                 downloads.append((dev, rs))
             # a tick: uploaded rounds, on a free batch
             ready = []
             bi = free_batch.index(True) if (batched and True in free_batch) else (0 if not batched else -1)
             if bi >= 0:
-                rays = 0
-                while (admitted and admitted[0][0].query() and len(ready) + len(admitted[0][1]) <= self.max_items
+                # the uploaded rounds at the front, up to a tick's size
+                k, rays, items = 0, 0, 0
+                while (k < len(admitted) and admitted[k][0].query() and items + len(admitted[k][1]) <= self.max_items
                        and rays < self.TICK_RAYS):
-                    rnd = admitted.popleft()[1]
-                    ready.extend(rnd)
-                    rays += sum(r.n for r in rnd)
+                    items += len(admitted[k][1])
+                    rays += sum(r.n for r in admitted[k][1])
+                    k += 1
+                if k and (not ticks_in_flight or rays >= self.TICK_MIN_RAYS):
+                    for _ in range(k):
+                        ready.extend(admitted.popleft()[1])
             if ready:
                 if batched:
                     b = self.batches[bi]
@@ -387,7 +409,9 @@ class Server:
                 raise RuntimeError(f"serving loop made no progress for {self.STALL_S} s "
                                    f"({len(pending)} pending, {len(admitted)} upload rounds, "
                                    f"{len(ticks_in_flight)} ticks, {len(downloads)} downloads)")
-            if not ready and not (downloads and downloads[0][0].query()):
+            if not busy:
+                # nothing in flight: wait for the next arrival (a short sleep); with work on the
+                # GPU the loop keeps polling, so a finished tick is followed at once by the next
                 time.sleep(0.0002)
         torch.cuda.synchronize()
         # requests still in flight when the run stopped early (drain=False, max_wall_s) are

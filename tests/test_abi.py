@@ -99,6 +99,12 @@ def test_load_argument_errors():
     a = list(args)
     a[0] = fake
     assert L.cct_trace_bounces(*a) == cct.CCT_OK  # n = 0: a no-op before any pointer is read
+    # cct_copies_async: n < 0 or missing arrays; n = 0 is a no-op
+    assert L.cct_copies_async(-1, None, None, None, None) == cct.CCT_ERR_INVALID_ARGUMENT
+    assert L.cct_copies_async(2, None, None, None, None) == cct.CCT_ERR_INVALID_ARGUMENT
+    assert L.cct_copies_async(0, None, None, None, None) == cct.CCT_OK
+    with pytest.raises(ValueError):
+        cct.cct_copies_async([1, 2], [3], [4, 5])
 
 
 def test_valid_triangulation_passes_validation_without_gpu():

@@ -62,3 +62,26 @@ def test_each_result_equals_alone(env, batched):
         fo = np.isfinite(et)
         assert np.array_equal(np.isfinite(ta[idx]), fo)
         assert np.all(np.abs(ta[idx][fo] - et[fo]) <= 1e-6 * np.abs(et[fo]))
+
+
+def test_copies_async_moves_every_piece():
+    """cct_copies_async: pieces of a pinned host buffer to scattered device
+    offsets and back, on one stream, in order (the later copy into a range wins)."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2112_05570_gb300 import _build, cct
+
+    _build.build()
+    src = torch.arange(1 << 16, dtype=torch.int32).pin_memory()
+    dev = torch.full((1 << 17,), -1, dtype=torch.int32, device="cuda")
+    back = torch.zeros(1 << 17, dtype=torch.int32).pin_memory()
+    s = torch.cuda.Stream()
+    pieces = [(0, 100, 7), (100, 5000, 3), (60000, 70000, 5536), (10, 10, 0), (0, 100, 20)]  # (src, dst, n) words
+    cct.cct_copies_async([dev.data_ptr() + 4 * d for _, d, _ in pieces], [src.data_ptr() + 4 * a for a, _, _ in pieces],
+                         [4 * n for *_, n in pieces], s)
+    cct.cct_copies_async([back.data_ptr()], [dev.data_ptr()], [4 * (1 << 17)], s)
+    s.synchronize()
+    exp = np.full(1 << 17, -1, np.int32)
+    for a, d, n in pieces:
+        exp[d:d + n] = np.arange(a, a + n)
+    assert np.array_equal(back.numpy(), exp)
