@@ -149,9 +149,10 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
         f_sides = (unsigned)S.max_steps - 1u;
         ++n_lim;
       }
-      it.hit[id] = h;
-      it.t[id] = tv;
-      it.steps[id] = st;
+      const unsigned long long pol = l2_evict_first();
+      st_stream(it.hit + id, h, pol);
+      st_stream(it.t + id, __float_as_int(tv), pol);
+      st_stream(it.steps + id, st, pol);
     }
     f_steps = __reduce_add_sync(FULL, f_steps);
     f_sides = __reduce_add_sync(FULL, f_sides);
@@ -186,11 +187,12 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
     if (i < pf_end) {
       const BatchItemDev& it = items[pf_item];
       const long long ri = (long long)i * it.stride;
-      cp_async4(&W.pf[0][lane], it.ox + ri);
-      cp_async4(&W.pf[1][lane], it.oy + ri);
-      cp_async4(&W.pf[2][lane], it.dx + ri);
-      cp_async4(&W.pf[3][lane], it.dy + ri);
-      if (it.start) cp_async4(&W.pf[4][lane], it.start + i);
+      const unsigned long long pol = l2_evict_first();
+      cp_async4_stream(&W.pf[0][lane], it.ox + ri, pol);
+      cp_async4_stream(&W.pf[1][lane], it.oy + ri, pol);
+      cp_async4_stream(&W.pf[2][lane], it.dx + ri, pol);
+      cp_async4_stream(&W.pf[3][lane], it.dy + ri, pol);
+      if (it.start) cp_async4_stream(&W.pf[4][lane], it.start + i, pol);
     }
     cp_async_commit();
   };

@@ -147,9 +147,10 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
       } else if (st == CCT_RAY_WALK_LIMIT) {
         f_sides = (unsigned)S.max_steps - 1u;
       }
-      hit_out[id] = h;
-      t_out[id] = tv;
-      steps_out[id] = st;
+      const unsigned long long pol = l2_evict_first();
+      st_stream(hit_out + id, h, pol);
+      st_stream(t_out + id, __float_as_int(tv), pol);
+      st_stream(steps_out + id, st, pol);
     }
     f_steps = __reduce_add_sync(FULL, f_steps);
     f_sides = __reduce_add_sync(FULL, f_sides);
@@ -179,16 +180,17 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     pool_next = pf_end;
     const int i = pf_base + lane;
     if (i < pf_end) {
+      const unsigned long long pol = l2_evict_first();
       if (kSrc == kSrcSorted) {
-        cp_async16(&W.pf[0][4 * lane], R.rays + i);  // rows 0..3 hold 32 int4
-        cp_async4(&W.pf[4][lane], R.start + i);
-        cp_async4(&W.pf[5][lane], R.orig + i);
+        cp_async16_stream(&W.pf[0][4 * lane], R.rays + i, pol);  // rows 0..3 hold 32 int4
+        cp_async4_stream(&W.pf[4][lane], R.start + i, pol);
+        cp_async4_stream(&W.pf[5][lane], R.orig + i, pol);
       } else {
-        cp_async4(&W.pf[0][lane], R.ox + i);
-        cp_async4(&W.pf[1][lane], R.oy + i);
-        cp_async4(&W.pf[2][lane], R.dx + i);
-        cp_async4(&W.pf[3][lane], R.dy + i);
-        if (!kLocate) cp_async4(&W.pf[4][lane], R.start + i);
+        cp_async4_stream(&W.pf[0][lane], R.ox + i, pol);
+        cp_async4_stream(&W.pf[1][lane], R.oy + i, pol);
+        cp_async4_stream(&W.pf[2][lane], R.dx + i, pol);
+        cp_async4_stream(&W.pf[3][lane], R.dy + i, pol);
+        if (!kLocate) cp_async4_stream(&W.pf[4][lane], R.start + i, pol);
       }
     }
     cp_async_commit();
