@@ -55,12 +55,15 @@ extern "C" {
 #define CCT_ERR_WALK_LIMIT -5          /* reported by cct_get_stats' counters only */
 #define CCT_ERR_NO_DEVICE -6           /* no usable CUDA device */
 #define CCT_ERR_IO -7                  /* cct_scene_load_file: file missing, unreadable or malformed */
+#define CCT_ERR_UNSUPPORTED -8         /* the call needs the checked build (libcct_checked.so) */
 
 /* Per-ray status, written to d_steps instead of a step count. */
 #define CCT_RAY_INVALID -1    /* direction off the 2^-22 grid, |component| > 1, zero, or the
                                  start triangle does not strictly contain the origin */
 #define CCT_RAY_WALK_LIMIT -2 /* more than n_tri + 8 steps (only on a corrupt triangulation) */
 #define CCT_RAY_NONE -3       /* cct_trace_bounces: no ray at this bounce (the path ended before it) */
+#define CCT_RAY_BAD_INDEX -4  /* checked build only: the ray met an out-of-range index in a device
+                                 table (a corrupted table), which was not read */
 
 /* ------------------------------------------------------------------ flags */
 /* cct_scene_load */
@@ -198,7 +201,8 @@ int cct_locate(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy, int64_
  * n entries written): d_hit_seg = segment id of the closest hit or -1 (miss
  * or invalid ray); d_t = hit parameter (o + t d), +inf on a miss, NaN on an
  * invalid ray; d_steps = triangles visited including the start triangle
- * (Sec. 5.4), or CCT_RAY_INVALID / CCT_RAY_WALK_LIMIT.  flags: CCT_TRACE_*.
+ * (Sec. 5.4), or CCT_RAY_INVALID / CCT_RAY_WALK_LIMIT (CCT_RAY_BAD_INDEX in the checked
+ * build).  flags: CCT_TRACE_*.
  * Scratch memory (ray binning, start cells) is taken from the stream-ordered
  * allocator on `stream` and released on it.  n = 0 is a no-op.
  * Errors: CCT_ERR_INVALID_ARGUMENT, CCT_ERR_OUT_OF_MEMORY, CCT_ERR_CUDA. */
@@ -430,6 +434,68 @@ int cct_kdtree_free(cct_kdtree kd);
  * from the stream-ordered allocator on `stream`. */
 int cct_trace_kdtree(cct_kdtree kd, const int32_t* d_ox, const int32_t* d_oy, const float* d_dx, const float* d_dy,
                      int64_t n, int32_t* d_hit_seg, float* d_t, int32_t* d_ops, void* stream);
+
+/* ------------------------------------------------------------------ checked build */
+/* No counterpart in the paper: a checked build and fault injection for it.
+ *
+ * libcct_checked.so is this library compiled with -DCCT_CHECKED: every index
+ * its kernels read out of a device table (a seed cell's triangle, a neighbour
+ * or half-edge exit word, a constrained-edge neighbour, the caller-id map, the
+ * kd-tree's and BVH's child, rope, reference and primitive entries) is
+ * range-checked before it addresses memory.  A ray that meets an index out of
+ * range -- possible only in a corrupted table -- ends with CCT_RAY_BAD_INDEX
+ * in d_steps (hit -1, t NaN; in every op count of cct_trace_kdtree and
+ * cct_trace_bvh) instead of reading outside the table, and cct_locate reports
+ * CCT_RAY_BAD_INDEX for its origin.  Every other result equals libcct.so's.
+ * libcct.so leaves the checks out: its loaders validate every table, so its
+ * indices are in range by construction.  The checked kernels are slower; the
+ * build exists to test that claim and to run suspect data. */
+
+/* 1 in libcct_checked.so, 0 in libcct.so. */
+int cct_is_checked(void);
+
+/* Device tables the poke calls may overwrite, one 32-bit word at a time:
+ *   CCT_TABLE_NEIGHBOUR       scene: neighbour word of edge e of triangle
+ *                             record r, index 3 r + e (records in the scene's
+ *                             device order, which need not be the caller's)
+ *   CCT_TABLE_HALF_EDGE_EXIT  scene: exit word c of half-edge record h (c = 0:
+ *                             the exit when the apex is left, 1: right),
+ *                             index 2 h + c, h in [0, 3 n_tri)
+ *   CCT_TABLE_CONSTRAINED     scene: neighbour across constrained edge e of
+ *                             record r (read by the locate walk), index 3 r + e
+ *   CCT_TABLE_SEED            scene: the triangle record of locate seed cell c
+ *   CCT_TABLE_USER_TO_RECORD  scene: the record of caller triangle id u
+ *   CCT_TABLE_KD_CHILD        kd-tree: child of inner node v, first ref of
+ *                             leaf v, index v
+ *   CCT_TABLE_KD_ROPE         kd-tree: rope across face f of node v, index 4 v + f
+ *   CCT_TABLE_KD_REF          kd-tree: ref k
+ *   CCT_TABLE_BVH_CHILD0      BVH: child0 of node v
+ *   CCT_TABLE_BVH_CHILD1      BVH: child1 of node v
+ *   CCT_TABLE_BVH_PRIM        BVH: primitive k */
+#define CCT_TABLE_NEIGHBOUR 1
+#define CCT_TABLE_HALF_EDGE_EXIT 2
+#define CCT_TABLE_CONSTRAINED 3
+#define CCT_TABLE_SEED 4
+#define CCT_TABLE_USER_TO_RECORD 5
+#define CCT_TABLE_KD_CHILD 6
+#define CCT_TABLE_KD_ROPE 7
+#define CCT_TABLE_KD_REF 8
+#define CCT_TABLE_BVH_CHILD0 9
+#define CCT_TABLE_BVH_CHILD1 10
+#define CCT_TABLE_BVH_PRIM 11
+
+/* Fault injection (checked build only): writes `value` at `index` of one of
+ * the object's tables, after reading the word it replaces into *old (when old
+ * is not NULL).  With index < 0 nothing is written and the table's length is
+ * reported in *len (when len is not NULL).  Synchronous: waits for the whole
+ * device before and after.  Any value may be written: the checked kernels
+ * report each ray that reads an out-of-range one.
+ * Errors: CCT_ERR_UNSUPPORTED in libcct.so (its kernels do not check, so it
+ * refuses to corrupt a table); CCT_ERR_INVALID_ARGUMENT (NULL object, a table
+ * of another kind of object, index beyond the table); CCT_ERR_CUDA. */
+int cct_scene_poke(cct_scene scene, int32_t table, int64_t index, int32_t value, int32_t* old, int64_t* len);
+int cct_kdtree_poke(cct_kdtree kd, int32_t table, int64_t index, int32_t value, int32_t* old, int64_t* len);
+int cct_bvh_poke(cct_bvh bvh, int32_t table, int64_t index, int32_t value, int32_t* old, int64_t* len);
 
 /* No counterpart in the paper: a host utility for a serving loop that moves
  * many requests' rays and results at once.  Enqueues n asynchronous copies on

@@ -2,6 +2,11 @@
 torch CUDA tensors for device buffers and torch streams.  Argument marshalling
 only -- every step of the ray query runs in the library's CUDA kernels.  There
 is no CPU fallback: if libcct.so is missing or no GPU is present, calls raise.
+
+With the environment variable CCT_LIBRARY=checked set before the first call,
+the process binds libcct_checked.so instead: the same entry points with every
+device-table index range-checked in the kernels, and the poke calls of the
+fault-injection tests enabled.
 """
 from __future__ import annotations
 
@@ -20,9 +25,11 @@ CCT_ERR_CUDA = -4
 CCT_ERR_WALK_LIMIT = -5
 CCT_ERR_NO_DEVICE = -6
 CCT_ERR_IO = -7
+CCT_ERR_UNSUPPORTED = -8
 CCT_RAY_INVALID = -1
 CCT_RAY_WALK_LIMIT = -2
 CCT_RAY_NONE = -3
+CCT_RAY_BAD_INDEX = -4
 CCT_MAX_BOUNCES = 1024
 CCT_LOAD_NO_REORDER = 1
 CCT_LOAD_NO_VALIDATE = 2
@@ -38,6 +45,17 @@ CCT_TRACE_BIN = 2
 CCT_TRACE_SPLIT_LOCATE = 4
 CCT_TRACE_STAGE = 8
 CCT_NOALLOC_MAX_RAYS = 1 << 20
+CCT_TABLE_NEIGHBOUR = 1
+CCT_TABLE_HALF_EDGE_EXIT = 2
+CCT_TABLE_CONSTRAINED = 3
+CCT_TABLE_SEED = 4
+CCT_TABLE_USER_TO_RECORD = 5
+CCT_TABLE_KD_CHILD = 6
+CCT_TABLE_KD_ROPE = 7
+CCT_TABLE_KD_REF = 8
+CCT_TABLE_BVH_CHILD0 = 9
+CCT_TABLE_BVH_CHILD1 = 10
+CCT_TABLE_BVH_PRIM = 11
 
 
 class CctError(RuntimeError):
@@ -87,15 +105,24 @@ class _Stats(ctypes.Structure):
 _lib = None
 
 
+def library_path() -> str:
+    """libcct.so, or libcct_checked.so when CCT_LIBRARY=checked."""
+    which = os.environ.get("CCT_LIBRARY", "")
+    if which not in ("", "checked"):
+        raise RuntimeError(f"CCT_LIBRARY={which!r}: expected 'checked' or unset")
+    return _build.LIB_CHECKED if which == "checked" else _build.LIB
+
+
 def lib() -> ctypes.CDLL:
-    """The loaded libcct.so; raises if it has not been built."""
+    """The loaded library (library_path()); raises if it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError(f"libcct.so not built at {_build.LIB}: call __graft_entry__.build() "
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{os.path.basename(path)} not built at {path}: call __graft_entry__.build() "
                            "(there is no CPU fallback)")
-    L = ctypes.CDLL(_build.LIB)
+    L = ctypes.CDLL(path)
     vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
     L.cct_copies_async.restype = ctypes.c_int
     L.cct_copies_async.argtypes = [i32, vp, vp, vp, vp]
@@ -150,6 +177,11 @@ def lib() -> ctypes.CDLL:
     L.cct_error_string.restype = ctypes.c_char_p
     L.cct_error_string.argtypes = [ctypes.c_int]
     L.cct_version.restype = ctypes.c_int
+    L.cct_is_checked.restype = ctypes.c_int
+    for name in ("cct_scene_poke", "cct_kdtree_poke", "cct_bvh_poke"):
+        f = getattr(L, name)
+        f.restype = ctypes.c_int
+        f.argtypes = [vp, i32, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(i64)]
     L.cct_measure_gather.restype = ctypes.c_int
     L.cct_measure_gather.argtypes = [ctypes.c_size_t, i64, i32, vp, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_double)]
@@ -425,6 +457,51 @@ class Scene:
             self.free()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------- checked build
+def cct_is_checked() -> bool:
+    """True when the bound library is libcct_checked.so."""
+    return bool(lib().cct_is_checked())
+
+
+def _poke(fn: str, handle: int, table: int, index: int, value: int) -> int:
+    old = ctypes.c_int32()
+    _check(getattr(lib(), fn)(ctypes.c_void_p(handle), int(table), int(index), int(value), ctypes.byref(old), None),
+           fn)
+    return int(old.value)
+
+
+def _table_len(fn: str, handle: int, table: int) -> int:
+    n = ctypes.c_int64()
+    _check(getattr(lib(), fn)(ctypes.c_void_p(handle), int(table), -1, 0, None, ctypes.byref(n)), fn)
+    return int(n.value)
+
+
+def cct_scene_poke(scene: int, table: int, index: int, value: int) -> int:
+    """Checked build only: overwrite entry `index` of a scene table
+    (CCT_TABLE_*), returning the old word (include/cct.h)."""
+    return _poke("cct_scene_poke", scene, table, index, value)
+
+
+def cct_scene_table_len(scene: int, table: int) -> int:
+    return _table_len("cct_scene_poke", scene, table)
+
+
+def cct_kdtree_poke(h: int, table: int, index: int, value: int) -> int:
+    return _poke("cct_kdtree_poke", h, table, index, value)
+
+
+def cct_kdtree_table_len(h: int, table: int) -> int:
+    return _table_len("cct_kdtree_poke", h, table)
+
+
+def cct_bvh_poke(h: int, table: int, index: int, value: int) -> int:
+    return _poke("cct_bvh_poke", h, table, index, value)
+
+
+def cct_bvh_table_len(h: int, table: int) -> int:
+    return _table_len("cct_bvh_poke", h, table)
 
 
 # ----------------------------------------------------------------------------- comparison structures (Sec. 5.3)

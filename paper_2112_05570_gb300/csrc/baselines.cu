@@ -33,6 +33,8 @@ struct BvhDev {
   const int32_t* prims;
   const int4* seg;
   int32_t n_nodes;
+  int32_t n_prims;  // the checked build's bounds
+  int32_t n_seg;
 };
 
 struct KdDev {
@@ -46,6 +48,8 @@ struct KdDev {
   const int32_t* refs;
   const int4* seg;
   int32_t n_nodes;
+  int32_t n_refs;  // the checked build's bounds
+  int32_t n_seg;
 };
 
 struct Frac {  // num / den, den > 0; den == 0 means +infinity
@@ -178,6 +182,7 @@ __global__ void __launch_bounds__(kBaseThreads) bvh_kernel(BvhDev B, const int32
     int st_node[kBvhStack];
     Frac st_t[kBvhStack];
     int sp = 0;
+    bool bad = false;  // the checked build met an out-of-range table index
     Frac tn;
     if (box_hit(B.box[0], ox, oy, kx, ky, tn)) {
       st_node[0] = 0;
@@ -191,14 +196,28 @@ __global__ void __launch_bounds__(kBaseThreads) bvh_kernel(BvhDev B, const int32
       const int c0 = B.c0[N];
       if (c0 < 0) {
         const int first = -1 - c0, cnt = B.c1[N];
+        if (kChecked && (cnt < 0 || first > B.n_prims - cnt)) {
+          bad = true;
+          break;
+        }
         for (int k = 0; k < cnt; ++k) {
           const int sid = B.prims[first + k];
+          if (idx_bad(sid, B.n_seg)) {
+            bad = true;
+            break;
+          }
           ++n_prim;
           seg_test(B.seg[sid], sid, ox, oy, kx, ky, b, nullptr);
         }
+        if (bad) break;
         continue;
       }
       const int c1 = B.c1[N];
+      // children after their parent (so the traversal ends) and room on the stack
+      if (kChecked && (c0 <= N || c1 <= N || c0 >= B.n_nodes || c1 >= B.n_nodes || sp + 2 > kBvhStack)) {
+        bad = true;
+        break;
+      }
       Frac t0, t1;
       n_aabb += 2;
       bool h0 = box_hit(B.box[c0], ox, oy, kx, ky, t0);
@@ -222,6 +241,13 @@ __global__ void __launch_bounds__(kBaseThreads) bvh_kernel(BvhDev B, const int32
         st_t[sp] = t1;
         ++sp;
       }
+    }
+    if (bad) {
+      hit[i] = -1;
+      tout[i] = __int_as_float(0x7fc00000);
+      ops[2 * i] = CCT_RAY_BAD_INDEX;
+      ops[2 * i + 1] = CCT_RAY_BAD_INDEX;
+      continue;
     }
     hit[i] = b.seg;
     tout[i] = best_t(b);
@@ -268,11 +294,17 @@ __global__ void __launch_bounds__(kBaseThreads) kd_kernel(KdDev K, const int32_t
     ++stamp;
     // start leaf: descend with the origin (not counted: known a priori, Sec. 5.4)
     int L = 0;
+    bool bad = false;  // the checked build met an out-of-range table index
     while (K.axis[L] != 2) {
       const int a = K.axis[L], s = K.split[L];
       const int c = (a == 0 ? ox : oy) - s;
       const bool right = c > 0 || (c == 0 && tie_side(a, kx, ky));
-      L = K.child[L] + (right ? 1 : 0);
+      const int ch = K.child[L];
+      if (kChecked && (ch <= L || ch >= K.n_nodes - 1)) {  // children follow their parent
+        bad = true;
+        break;
+      }
+      L = ch + (right ? 1 : 0);
     }
     Best b;
     b.seg = -1;
@@ -281,7 +313,7 @@ __global__ void __launch_bounds__(kBaseThreads) kd_kernel(KdDev K, const int32_t
     b.wx = b.wy = b.vx = b.vy = 0;
     int leaves = 0, desc = 0, tests = 0, uniq = 0, ropes = 0, overflow = 0;
     const int guard = K.n_nodes + 8;
-    while (true) {
+    while (!bad) {
       if (++leaves > guard) {
         b.seg = -1;
         overflow = 2;  // corrupt ropes: reported as a mailbox/traversal fault
@@ -294,8 +326,16 @@ __global__ void __launch_bounds__(kBaseThreads) kd_kernel(KdDev K, const int32_t
       const Frac te = xface ? tx : ty;
       const int face = xface ? (kx > 0 ? 1 : 0) : (ky > 0 ? 3 : 2);
       const int first = K.child[L], cnt = K.count[L];
+      if (kChecked && (first < 0 || cnt < 0 || first > K.n_refs - cnt)) {
+        bad = true;
+        break;
+      }
       for (int q = 0; q < cnt; ++q) {
         const int sid = K.refs[first + q];
+        if (idx_bad(sid, K.n_seg)) {
+          bad = true;
+          break;
+        }
         ++tests;
         // ideal mailbox: count each segment once per ray
         unsigned h = ((unsigned)sid * 2654435761u) >> 24;
@@ -317,10 +357,14 @@ __global__ void __launch_bounds__(kBaseThreads) kd_kernel(KdDev K, const int32_t
         if (!seen && !placed) overflow = 1;
         seg_test(K.seg[sid], sid, ox, oy, kx, ky, b, &te);
       }
-      if (b.seg >= 0) break;
+      if (bad || b.seg >= 0) break;
       const int4 R = K.rope[L];
       const int nxt = face == 0 ? R.x : (face == 1 ? R.y : (face == 2 ? R.z : R.w));
       if (nxt < 0) break;  // left the domain: a miss
+      if (idx_bad(nxt, K.n_nodes)) {
+        bad = true;
+        break;
+      }
       ropes += (K.rope_log2[L] >> (8 * face)) & 0xff;
       // descend to the leaf holding the exit point P = o + te * k
       int N = nxt;
@@ -336,10 +380,21 @@ __global__ void __launch_bounds__(kBaseThreads) kd_kernel(KdDev K, const int32_t
           const long long v = (long long)(oa - s) * te.den + (long long)te.num * ka;  // (P_a - s) * den
           right = v > 0 || (v == 0 && tie_side(a, kx, ky));
         }
-        N = K.child[N] + (right ? 1 : 0);
+        const int ch = K.child[N];
+        if (kChecked && (ch <= N || ch >= K.n_nodes - 1)) {
+          bad = true;
+          break;
+        }
+        N = ch + (right ? 1 : 0);
         ++desc;
       }
       L = N;
+    }
+    if (bad) {
+      hit[i] = -1;
+      tout[i] = __int_as_float(0x7fc00000);
+      for (int q = 0; q < 6; ++q) o[q] = CCT_RAY_BAD_INDEX;
+      continue;
     }
     hit[i] = b.seg;
     tout[i] = best_t(b);
@@ -425,9 +480,25 @@ extern "C" int cct_bvh_load(const cct_bvh_desc* d, void* stream_v, cct_bvh* out)
   b->base = base;
   b->device = dev;
   b->dev = BvhDev{(const int4*)(base + o_box), (const int32_t*)(base + o_c0), (const int32_t*)(base + o_c1),
-                  (const int32_t*)(base + o_pr), (const int4*)(base + o_seg), d->n_nodes};
+                  (const int32_t*)(base + o_pr), (const int4*)(base + o_seg), d->n_nodes, d->n_prims, d->n_seg};
   *out = b;
   return CCT_OK;
+}
+
+extern "C" int cct_bvh_poke(cct_bvh b, int32_t table, int64_t index, int32_t value, int32_t* old, int64_t* len) {
+  if (!b) return CCT_ERR_INVALID_ARGUMENT;
+  if (!kChecked) return CCT_ERR_UNSUPPORTED;
+  const BvhDev& B = b->dev;
+  switch (table) {
+    case CCT_TABLE_BVH_CHILD0:
+      return poke_word(b->device, B.c0, B.n_nodes, index, index, value, old, len);
+    case CCT_TABLE_BVH_CHILD1:
+      return poke_word(b->device, B.c1, B.n_nodes, index, index, value, old, len);
+    case CCT_TABLE_BVH_PRIM:
+      return poke_word(b->device, B.prims, B.n_prims, index, index, value, old, len);
+    default:
+      return CCT_ERR_INVALID_ARGUMENT;
+  }
 }
 
 extern "C" int cct_bvh_free(cct_bvh b) {
@@ -528,9 +599,26 @@ extern "C" int cct_kdtree_load(const cct_kdtree_desc* d, void* stream_v, cct_kdt
   k->dev = KdDev{(const int32_t*)(base + o_axis), (const int32_t*)(base + o_split), (const int32_t*)(base + o_child),
                  (const int32_t*)(base + o_count), (const int4*)(base + o_box),     (const int4*)(base + o_rope),
                  (const int32_t*)(base + o_lg),    (const int32_t*)(base + o_refs), (const int4*)(base + o_seg),
-                 nn};
+                 nn,                               d->n_refs,                       d->n_seg};
   *out = k;
   return CCT_OK;
+}
+
+extern "C" int cct_kdtree_poke(cct_kdtree k, int32_t table, int64_t index, int32_t value, int32_t* old,
+                               int64_t* len) {
+  if (!k) return CCT_ERR_INVALID_ARGUMENT;
+  if (!kChecked) return CCT_ERR_UNSUPPORTED;
+  const KdDev& K = k->dev;
+  switch (table) {
+    case CCT_TABLE_KD_CHILD:
+      return poke_word(k->device, K.child, K.n_nodes, index, index, value, old, len);
+    case CCT_TABLE_KD_ROPE:
+      return poke_word(k->device, K.rope, 4ll * K.n_nodes, index, index, value, old, len);
+    case CCT_TABLE_KD_REF:
+      return poke_word(k->device, K.refs, K.n_refs, index, index, value, old, len);
+    default:
+      return CCT_ERR_INVALID_ARGUMENT;
+  }
 }
 
 extern "C" int cct_kdtree_free(cct_kdtree k) {

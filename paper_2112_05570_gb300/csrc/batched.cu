@@ -80,6 +80,7 @@ struct BatchStacks {
 struct BSlot {
   const int4* he;
   int ox, oy, kx, ky, h, ns;
+  int n_he;  // the checked build's bound on h (unused otherwise)
   bool act, dn;
 };
 
@@ -111,7 +112,7 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
   unsigned n_fb = 0;  // this lane's int64 fallbacks
   BSlot sl[2];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) sl[q] = BSlot{nullptr, 0, 0, 0, 0, 0, 0, false, false};
+  for (int q = 0; q < 2; ++q) sl[q] = BSlot{nullptr, 0, 0, 0, 0, 0, 0, 0, false, false};
   if (lane < kBCounters) W.cnt[lane] = 0;
   if (lane == 0) W.steps = W.sides = 0;
   __syncwarp();
@@ -136,7 +137,9 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
         const TriRec r = load_rec(S.rec + (te >> 2));
         const int e = te & 3;
         const int32_t w = nb_of(r, e);
-        if (w <= -2) {
+        if (w >= 0 && idx_bad(w, 3 * S.n_tri)) {
+          st = CCT_RAY_BAD_INDEX;  // the exit word of the final triangle is out of range
+        } else if (w <= -2) {
           h = -2 - w;
           const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
           const int4 o = W.d_a[k];
@@ -223,17 +226,28 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
     }
     __syncwarp();
     prefetch();  // the next batch arrives while this one is prepared and walked
-    bool ok = false;
+    bool ok = false, bad = false;  // bad: the checked build met an out-of-range table index
     if (v) {
       ok = dir_to_k(pdx, pkx) && dir_to_k(pdy, pky) && (pkx | pky) != 0 && pox >= 0 && poy >= 0 && pox <= S.D &&
            poy <= S.D;
       pkx = k_word<kExact>(pkx);
       pky = k_word<kExact>(pky);
       if (locate) {
-        if (ok) T0 = S.seeds[seed_cell(S, pox, poy)];
+        if (ok) {
+          T0 = S.seeds[seed_cell(S, pox, poy)];
+          if (idx_bad(T0, S.n_tri)) {
+            ok = false;
+            bad = true;
+          }
+        }
       } else {
-        T0 = (T0 >= 0 && T0 < S.n_tri) ? S.user2dev[T0] : -1;
-        ok = ok && T0 >= 0;
+        if (T0 >= 0 && T0 < S.n_tri) {
+          T0 = S.user2dev[T0];
+          bad = idx_bad(T0, S.n_tri);
+        } else {
+          T0 = -1;
+        }
+        ok = ok && !bad && T0 >= 0;
       }
     }
     const unsigned m_loc = locate ? __ballot_sync(FULL, ok) : 0u;
@@ -254,6 +268,7 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
           seed_point(S, pox, poy, cx, cy);
           locating = locate_hop(S, r, T0, jj, seed_exit(r, cx, cy, pox, poy));
           ok = locating;
+          if (kChecked && T0 < 0) bad = true;
         } else if (o0 == 0 || o1 == 0 || o2 == 0) {
           ok = false;
         }
@@ -268,6 +283,7 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
           if (res != 0 || lsteps > S.max_steps) {
             locating = false;
             ok = res > 0;
+            if (kChecked && T0 < 0) bad = true;
           }
         }
       }
@@ -290,11 +306,15 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
                                         n_fb);
       e = s0 ? (sv ? 0 : 1) : (sv ? 2 : 0);
       w = nb_of(r, e);
+      if (ok && w >= 0 && idx_bad(w, 3 * S.n_tri)) {
+        ok = false;
+        bad = true;
+      }
     }
     const bool to_ready = ok && w >= 0;
     const bool to_done = v && !to_ready;
     const unsigned mr = __ballot_sync(FULL, to_ready), md = __ballot_sync(FULL, to_done);
-    const unsigned mv = __ballot_sync(FULL, v), minv = __ballot_sync(FULL, v && !ok);
+    const unsigned mv = __ballot_sync(FULL, v), minv = __ballot_sync(FULL, v && !ok && !bad);
     if (locate) {
       const unsigned ls = __reduce_add_sync(FULL, (unsigned)lsteps);
       if (lane == 0) {
@@ -313,7 +333,7 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
     } else if (to_done) {
       const int k = n_done + __popc(md & lt);
       W.d_a[k] = make_int4(oxw, oyw, pkx, pky);
-      W.d_b[k] = make_int4(i, (T0 << 2) | e, ok ? 1 : CCT_RAY_INVALID, it_idx);
+      W.d_b[k] = make_int4(i, (T0 << 2) | e, ok ? 1 : (bad ? CCT_RAY_BAD_INDEX : CCT_RAY_INVALID), it_idx);
     }
     n_ready += __popc(mr);
     n_done += __popc(md);
@@ -325,11 +345,13 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
     const bool sc = side_L_cw<kExact>(s.kx, s.ky, s.ox, s.oy, q.x, q.y, n_fb);
     ++s.ns;
     const int32_t w = sc ? q.z : q.w;
-    if (w >= 0 && s.ns < max_steps) {
+    if (w >= 0 && s.ns < max_steps && !idx_bad(w, s.n_he)) {
       s.h = w;
       return;
     }
-    if (w >= 0) {
+    if (w >= 0 && idx_bad(w, s.n_he)) {
+      s.ns = CCT_RAY_BAD_INDEX;
+    } else if (w >= 0) {
       s.ns = CCT_RAY_WALK_LIMIT;
     } else {
       const int T = he_tri(s.h), j = s.h - 3 * T;
@@ -387,6 +409,7 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
           W.l_idx[q][lane] = b.y;
           W.l_item[q][lane] = b.z;
           sl[q].he = scenes[b.w].he;
+          if (kChecked) sl[q].n_he = 3 * scenes[b.w].n_tri;
           sl[q].ns = 1;
           sl[q].act = true;
         }

@@ -32,8 +32,11 @@ size_t bin_scratch_bytes(int64_t n, int32_t n_tri, int shift) {
 __device__ __forceinline__ int32_t start_rec(const SceneDev& S, const int32_t* start, bool start_is_user,
                                              long long i) {
   int32_t s = start[i];
+  if (kChecked && !start_is_user && s == CCT_RAY_BAD_INDEX) return s;  // marked by the locate kernel
   if (s < 0 || s >= S.n_tri) return -1;
-  return start_is_user ? S.user2dev[s] : s;
+  if (!start_is_user) return s;
+  const int32_t r = S.user2dev[s];
+  return idx_bad(r, S.n_tri) ? CCT_RAY_BAD_INDEX : r;
 }
 
 __device__ __forceinline__ int32_t bin_key(int32_t rec, int shift, int32_t nb) {

@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(kBounceThreads, kFrame ? 3 : 4) bounce_kernel(
   const unsigned lt = lanemask_lt();
   const int4* __restrict__ he_tab = S.he;
   const int max_steps = S.max_steps;
+  const int n_he = 3 * S.n_tri;  // half-edge records (the checked build's bound)
   const int nb_max = A.n_bounce;
 
   // the lane's path
@@ -192,7 +193,14 @@ __global__ void __launch_bounds__(kBounceThreads, kFrame ? 3 : 4) bounce_kernel(
     int T0 = A.start ? A.start[gi] : -1;
     bool ok = dir_to_k(A.dx[gi], kx) && dir_to_k(A.dy[gi], ky) && (kx | ky) != 0 && ox >= 0 && oy >= 0 &&
               ox <= S.D && oy <= S.D && T0 >= 0 && T0 < S.n_tri;
-    if (ok && A.start_user) T0 = S.user2dev[T0];
+    bool bad = false;  // the checked build met an out-of-range table index
+    if (ok && A.start_user) {
+      T0 = S.user2dev[T0];
+      if (idx_bad(T0, S.n_tri)) {
+        ok = false;
+        bad = true;
+      }
+    }
     TriRec r;
     if (ok) {
       r = load_rec(S.rec + T0);
@@ -204,7 +212,7 @@ __global__ void __launch_bounds__(kBounceThreads, kFrame ? 3 : 4) bounce_kernel(
     if (!ok) {
       ++c_inv;
       kx = ky = 0;
-      record(0, -1, __int_as_float(0x7fc00000), CCT_RAY_INVALID, false);
+      record(0, -1, __int_as_float(0x7fc00000), bad ? CCT_RAY_BAD_INDEX : CCT_RAY_INVALID, false);
       end_path(1);
       return;
     }
@@ -220,7 +228,11 @@ __global__ void __launch_bounds__(kBounceThreads, kFrame ? 3 : 4) bounce_kernel(
     const int32_t w = nb_of(r, e);
     ns = 1;
     act = true;
-    if (w >= 0) {
+    if (w >= 0 && idx_bad(w, n_he)) {
+      c_sides += 2u;
+      record(0, -1, __int_as_float(0x7fc00000), CCT_RAY_BAD_INDEX, true);
+      end_path(1);
+    } else if (w >= 0) {
       h = w;
     } else {
       finish(T0, e, w);
@@ -271,8 +283,12 @@ __global__ void __launch_bounds__(kBounceThreads, kFrame ? 3 : 4) bounce_kernel(
       const bool sc = (long long)kx * coord_of_word(q.y) - (long long)ky * coord_of_word(q.x) >= ch;
       ++ns;
       const int32_t w = sc ? q.z : q.w;
-      if (w >= 0 && ns < max_steps) {
+      if (w >= 0 && ns < max_steps && !idx_bad(w, n_he)) {
         h = w;
+      } else if (w >= 0 && idx_bad(w, n_he)) {
+        c_sides += (unsigned)ns + (b == 0 ? 2u : 0u);
+        record(b, -1, __int_as_float(0x7fc00000), CCT_RAY_BAD_INDEX, true);
+        end_path(b + 1);
       } else if (w >= 0) {
         ++c_lim;
         c_sides += (unsigned)ns + (b == 0 ? 2u : 0u);

@@ -61,6 +61,22 @@ __host__ __device__ __forceinline__ int coord_of_word(int w) { return w & kCoord
 // Triangle and edge of a half-edge index (3 T + j; T < 2^29).
 __device__ __forceinline__ int he_tri(int h) { return (int)((unsigned)h / 3u); }
 
+// Checked build.  Compiled with -DCCT_CHECKED (libcct_checked.so), every
+// index that a kernel reads out of a device table -- a seed cell's record, a
+// neighbour or half-edge exit word, a constrained-edge neighbour, the caller-id
+// map, the comparison structures' child, rope and reference entries -- is
+// range-checked before it addresses memory, and a ray that meets one out of
+// range ends with CCT_RAY_BAD_INDEX instead of reading it.  The normal build
+// compiles every check away: its loaders validate each table, so the indices
+// are in range by construction.
+#ifdef CCT_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+// True when the checked build finds i outside [0, n).
+__host__ __device__ __forceinline__ bool idx_bad(int i, int n) { return kChecked && (unsigned)i >= (unsigned)n; }
+
 struct DevStats {
   unsigned long long rays, steps, side_tests, exact_fallbacks, invalid_rays, walk_limit_rays, located,
       locate_steps;
@@ -278,11 +294,16 @@ __device__ __forceinline__ int seed_exit(const TriRec& r, int cx, int cy, int ox
 }
 
 // Moves the locate walk across edge e of record T (the walk crosses
-// constrained edges: their neighbours come from cnb).  False at the hull.
+// constrained edges: their neighbours come from cnb).  False at the hull, and
+// in the checked build on an out-of-range neighbour word, with T = -1.
 __device__ __forceinline__ bool locate_hop(const SceneDev& S, const TriRec& r, int& T, int& j, int e) {
   int32_t w = nb_of(r, e);
   if (w <= -2) w = S.cnb[3 * T + e];
   if (w < 0) return false;
+  if (idx_bad(w, 3 * S.n_tri)) {
+    T = -1;
+    return false;
+  }
   T = he_tri(w);
   j = w - 3 * T;
   return true;
@@ -314,7 +335,8 @@ __device__ __forceinline__ int locate_step_entered(const SceneDev& S, const TriR
 // perturbed) towards the origin o, in record r = triangle T entered through
 // its edge j (j = 3: T is the seed's own triangle).  Returns 1 when T holds o
 // strictly inside, -1 when o lies on an edge or a vertex (or the walk leaves
-// the domain), 0 after moving to the next triangle (T, j updated).
+// the domain; in the checked build also on a bad index, with T = -1), 0 after
+// moving to the next triangle (T, j updated).
 __device__ __forceinline__ int locate_step(const SceneDev& S, const TriRec& r, int& T, int& j, int ox, int oy,
                                            int cx, int cy) {
   if (j == 3) {
@@ -390,6 +412,12 @@ struct DeviceGuard {
 };
 
 int sm_count(int dev);
+
+// Fault injection of the checked build: entry `index` of a device table of n
+// entries is the 32-bit word `word` from `base`; reads the old word into *old
+// and writes `value` (index < 0: only reports n in *len).  Synchronous.
+int poke_word(int device, const void* base, int64_t n, int64_t index, int64_t word, int32_t value, int32_t* old,
+              int64_t* len);
 
 // Stream-ordered scratch for one call: one cudaMallocAsync, released with
 // cudaFreeAsync on the same stream.

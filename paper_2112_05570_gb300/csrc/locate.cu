@@ -28,7 +28,8 @@ __global__ void __launch_bounds__(kLocateThreads) locate_kernel(SceneDev S, cons
       int T = S.seeds[seed_cell(S, qx, qy)], j = 3, cx, cy;
       seed_point(S, qx, qy, cx, cy);
       int steps = 0;
-      while (true) {
+      if (idx_bad(T, S.n_tri)) res = CCT_RAY_BAD_INDEX;
+      while (res != CCT_RAY_BAD_INDEX) {
         if (++steps > S.max_steps) {
           res = -1;
           break;
@@ -36,7 +37,7 @@ __global__ void __launch_bounds__(kLocateThreads) locate_kernel(SceneDev S, cons
         const TriRec r = load_rec(S.rec + T);
         const int st = locate_step(S, r, T, j, qx, qy, cx, cy);
         if (st != 0) {
-          res = st > 0 ? T : -1;
+          res = st > 0 ? T : (kChecked && T < 0 ? CCT_RAY_BAD_INDEX : -1);
           break;
         }
       }

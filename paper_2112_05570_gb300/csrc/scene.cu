@@ -413,11 +413,55 @@ extern "C" const char* cct_error_string(int code) {
     case CCT_ERR_WALK_LIMIT: return "walk step limit exceeded";
     case CCT_ERR_NO_DEVICE: return "no CUDA device";
     case CCT_ERR_IO: return "scene file missing, unreadable or malformed";
+    case CCT_ERR_UNSUPPORTED: return "needs the checked build (libcct_checked.so)";
     default: return "unknown status";
   }
 }
 
 extern "C" int cct_version(void) { return (0 << 16) | 1; }
+
+extern "C" int cct_is_checked(void) { return kChecked ? 1 : 0; }
+
+namespace cct {
+
+int poke_word(int device, const void* base, int64_t n, int64_t index, int64_t word, int32_t value, int32_t* old,
+              int64_t* len) {
+  if (index < 0) {
+    if (len) *len = n;
+    return CCT_OK;
+  }
+  if (index >= n) return CCT_ERR_INVALID_ARGUMENT;
+  DeviceGuard g(device);
+  int32_t* p = (int32_t*)base + word;
+  if (cudaDeviceSynchronize() != cudaSuccess) return CCT_ERR_CUDA;
+  if (old && cudaMemcpy(old, p, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return CCT_ERR_CUDA;
+  if (cudaMemcpy(p, &value, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) return CCT_ERR_CUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? CCT_OK : CCT_ERR_CUDA;
+}
+
+}  // namespace cct
+
+extern "C" int cct_scene_poke(cct_scene scene, int32_t table, int64_t index, int32_t value, int32_t* old,
+                              int64_t* len) {
+  if (!scene) return CCT_ERR_INVALID_ARGUMENT;
+  if (!kChecked) return CCT_ERR_UNSUPPORTED;
+  const SceneDev& S = scene->dev;
+  const int64_t nt = S.n_tri;
+  switch (table) {
+    case CCT_TABLE_NEIGHBOUR:  // nb[e] is word 4 + e of the 8-word record
+      return poke_word(scene->device, S.rec, 3 * nt, index, 8 * (index / 3) + 4 + index % 3, value, old, len);
+    case CCT_TABLE_HALF_EDGE_EXIT:  // the exits are words 2 and 3 of the 4-word half-edge record
+      return poke_word(scene->device, S.he, 6 * nt, index, 4 * (index / 2) + 2 + index % 2, value, old, len);
+    case CCT_TABLE_CONSTRAINED:
+      return poke_word(scene->device, S.cnb, 3 * nt, index, index, value, old, len);
+    case CCT_TABLE_SEED:
+      return poke_word(scene->device, S.seeds, (int64_t)S.G * S.G, index, index, value, old, len);
+    case CCT_TABLE_USER_TO_RECORD:
+      return poke_word(scene->device, S.user2dev, nt, index, index, value, old, len);
+    default:
+      return CCT_ERR_INVALID_ARGUMENT;
+  }
+}
 
 extern "C" int cct_copies_async(int32_t n, void* const* dst, const void* const* src, const size_t* bytes,
                                 void* stream_v) {

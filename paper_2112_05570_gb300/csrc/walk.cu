@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     __syncthreads();
   }
   const int max_steps = S.max_steps;
+  const int n_he = 3 * S.n_tri;     // half-edge records (the checked build's bound)
   int pool_next = 0, pool_end = 0;  // the warp's current range of ray indices
   int pf_base = 0, pf_end = 0;      // the batch in `pf` ([pf_base, pf_end)); pf_base < 0: none left
   int n_ready = 0, n_done = 0;      // stack depths (warp-uniform)
@@ -126,7 +127,8 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     if (lane < m) {
       const int k = top - m + lane;
       const int2 b = W.d_b[k];
-      const int id = b.x, te = b.y, st = W.d_st[k];
+      const int id = b.x, te = b.y;
+      int st = W.d_st[k];
       int32_t h = -1;
       float tv = __int_as_float(0x7fc00000);  // NaN: invalid ray or step limit
       if (st > 0) {
@@ -135,7 +137,9 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
         const TriRec r = load_rec(S.rec + (te >> 2));
         const int e = te & 3;
         const int32_t w = nb_of(r, e);
-        if (w <= -2) {
+        if (w >= 0 && idx_bad(w, n_he)) {
+          st = CCT_RAY_BAD_INDEX;  // the exit word of the final triangle is out of range
+        } else if (w <= -2) {
           h = -2 - w;
           const int a = (e == 2) ? 0 : e + 1, b = (e == 0) ? 2 : e - 1;
           const int4 o = W.d_a[k];
@@ -230,9 +234,18 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     }
     __syncwarp();
     prefetch();  // the next batch arrives while this one is prepared and walked
-    bool ok = false;
+    bool ok = false, bad = false;  // bad: the checked build met an out-of-range table index
     if (v) {
-      if (kSrc == kSrcPlainUser) T0 = (T0 >= 0 && T0 < S.n_tri) ? S.user2dev[T0] : -1;
+      if (kSrc == kSrcPlainUser) {
+        if (T0 >= 0 && T0 < S.n_tri) {
+          T0 = S.user2dev[T0];
+          bad = idx_bad(T0, S.n_tri);
+        } else {
+          T0 = -1;
+        }
+      } else if (kChecked && kSrc != kSrcLocate) {
+        bad = T0 == CCT_RAY_BAD_INDEX;  // marked by the locate kernel or the binning pass
+      }
       // origins outside the domain lie in no triangle; rejecting them here
       // keeps every coordinate difference of the walk within int32
       ok = dir_to_k(pdx, pkx) && dir_to_k(pdy, pky) && (pkx | pky) != 0 && pox >= 0 && poy >= 0 && pox <= S.D &&
@@ -240,9 +253,15 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
       pkx = k_word<kExact>(pkx);
       pky = k_word<kExact>(pky);
       if (kLocate) {
-        if (ok) T0 = S.seeds[seed_cell(S, pox, poy)];
+        if (ok) {
+          T0 = S.seeds[seed_cell(S, pox, poy)];
+          if (idx_bad(T0, S.n_tri)) {
+            ok = false;
+            bad = true;
+          }
+        }
       } else {
-        ok = ok && T0 >= 0 && T0 < S.n_tri;
+        ok = ok && !bad && T0 >= 0 && T0 < S.n_tri;
       }
     }
     const unsigned m_loc = kLocate ? __ballot_sync(FULL, ok) : 0u;
@@ -265,6 +284,7 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
           seed_point(S, pox, poy, cx, cy);
           locating = locate_hop(S, r, T0, jj, seed_exit(r, cx, cy, pox, poy));
           ok = locating;
+          if (kChecked && T0 < 0) bad = true;
         } else if (o0 == 0 || o1 == 0 || o2 == 0) {
           ok = false;  // origin on an edge or a vertex: not a valid ray origin
         }
@@ -279,6 +299,7 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
           if (res != 0 || lsteps > S.max_steps) {
             locating = false;
             ok = res > 0;
+            if (kChecked && T0 < 0) bad = true;
           }
         }
       }
@@ -303,11 +324,15 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
                                         n_fb);
       e = s0 ? (sv ? 0 : 1) : (sv ? 2 : 0);
       w = nb_of(r, e);
+      if (ok && w >= 0 && idx_bad(w, n_he)) {
+        ok = false;
+        bad = true;
+      }
     }
     const bool to_ready = ok && w >= 0;
     const bool to_done = v && !to_ready;
     const unsigned mr = __ballot_sync(FULL, to_ready), md = __ballot_sync(FULL, to_done);
-    const unsigned mv = __ballot_sync(FULL, v), minv = __ballot_sync(FULL, v && !ok);
+    const unsigned mv = __ballot_sync(FULL, v), minv = __ballot_sync(FULL, v && !ok && !bad);
     if (kLocate) {
       const unsigned ls = __reduce_add_sync(FULL, (unsigned)lsteps);
       if (lane == 0) {
@@ -327,7 +352,7 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
       const int k = n_done + __popc(md & lt);
       W.d_a[k] = make_int4(oxw, oyw, pkx, pky);
       W.d_b[k] = make_int2(pid, (T0 << 2) | e);
-      W.d_st[k] = ok ? 1 : CCT_RAY_INVALID;
+      W.d_st[k] = ok ? 1 : (bad ? CCT_RAY_BAD_INDEX : CCT_RAY_INVALID);
     }
     n_ready += __popc(mr);
     n_done += __popc(md);
@@ -340,11 +365,13 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     const bool sc = side_L_cw<kExact>(s.kx, s.ky, s.ox, s.oy, q.x, q.y, n_fb);
     ++s.ns;
     const int32_t w = sc ? q.z : q.w;
-    if (w >= 0 && s.ns < max_steps) {
+    if (w >= 0 && s.ns < max_steps && !idx_bad(w, n_he)) {
       s.h = w;
       return;
     }
-    if (w >= 0) {
+    if (w >= 0 && idx_bad(w, n_he)) {
+      s.ns = CCT_RAY_BAD_INDEX;
+    } else if (w >= 0) {
       s.ns = CCT_RAY_WALK_LIMIT;
       ++n_lim;
     } else {

@@ -1,5 +1,6 @@
-"""C-ABI library checks that need no GPU: libcct.so loads, exports every symbol
-include/cct.h declares, and its host-side validation returns status codes."""
+"""C-ABI library checks that need no GPU: libcct.so (and its checked build,
+libcct_checked.so) loads, exports every symbol include/ declares, and its
+host-side validation returns status codes."""
 import ctypes
 import json
 import os
@@ -29,11 +30,47 @@ def lib():
     return ctypes.CDLL(_build.LIB)
 
 
-def test_every_declared_symbol_is_exported(lib):
+@pytest.fixture(scope="module")
+def checked_lib():
+    _build.build()
+    return ctypes.CDLL(_build.LIB_CHECKED)
+
+
+def test_every_declared_symbol_is_exported(lib, checked_lib):
     names = _declared()
     assert "cct_trace" in names and "cct_scene_load" in names and len(names) >= 8
-    for n in names:
-        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+    assert {"cct_is_checked", "cct_scene_poke", "cct_kdtree_poke", "cct_bvh_poke"} <= set(names)
+    for L in (lib, checked_lib):
+        for n in names:
+            assert hasattr(L, n), f"{n} declared in include/ but not exported"
+
+
+def test_checked_build_identifies_itself(lib, checked_lib):
+    """libcct.so is the unchecked build and libcct_checked.so the checked one;
+    both refuse a poke of no object, and the binding picks the library from
+    CCT_LIBRARY."""
+    assert lib.cct_is_checked() == 0 and checked_lib.cct_is_checked() == 1
+    for L in (lib, checked_lib):
+        for fn in ("cct_scene_poke", "cct_kdtree_poke", "cct_bvh_poke"):
+            f = getattr(L, fn)
+            f.restype = ctypes.c_int
+            f.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                          ctypes.c_void_p]
+            assert f(None, cct.CCT_TABLE_SEED, 0, 0, None, None) == cct.CCT_ERR_INVALID_ARGUMENT
+    assert "checked" in cct.cct_error_string(cct.CCT_ERR_UNSUPPORTED)
+    old = os.environ.get("CCT_LIBRARY")
+    try:
+        os.environ["CCT_LIBRARY"] = "checked"
+        assert cct.library_path() == _build.LIB_CHECKED
+        os.environ["CCT_LIBRARY"] = "other"
+        with pytest.raises(RuntimeError):
+            cct.library_path()
+    finally:
+        if old is None:
+            os.environ.pop("CCT_LIBRARY", None)
+        else:
+            os.environ["CCT_LIBRARY"] = old
+    assert cct.library_path() == (_build.LIB_CHECKED if old == "checked" else _build.LIB)
 
 
 def test_status_strings_and_version():
