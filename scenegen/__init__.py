@@ -15,6 +15,7 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
+import threading
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -25,17 +26,19 @@ _SRC = os.path.join(_HERE, "scenegen.cpp")
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "libscenegen.so")
 _lib = None
+_lock = threading.Lock()  # the first use may come from several threads at once
 
 
 def build(force: bool = False) -> str:
     """Compile the generator library in-tree with g++ (host code, any arch)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    with _lock:
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+            return _LIB
+        os.makedirs(_LIBDIR, exist_ok=True)
+        tmp = _LIB + f".tmp{os.getpid()}.{threading.get_ident()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
         return _LIB
-    os.makedirs(_LIBDIR, exist_ok=True)
-    tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp])
-    os.replace(tmp, _LIB)
-    return _LIB
 
 
 def _load():
@@ -43,6 +46,14 @@ def _load():
     if _lib is not None:
         return _lib
     build()
+    with _lock:
+        if _lib is not None:
+            return _lib
+        return _bind()
+
+
+def _bind():
+    global _lib
     L = ctypes.CDLL(_LIB)
     i64, i32, u64, dbl, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
     P = ctypes.POINTER
