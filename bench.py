@@ -944,7 +944,7 @@ def main():
     for name, segs, cdt, tri, r, ref in work:
         d = {k: torch.from_numpy(getattr(r, k)).to(dev) for k in ("ox", "oy", "dx", "dy", "start")}
         scenes.append(dict(name=name, segs=segs, cdt=cdt, ref=ref, tri=tri, rays=r, d=d,
-                           scene=cct.Scene.from_triangulation(tri, sg.D)))
+                           scene=cct.Scene.from_triangulation(tri, sg.D, flags=cct.CCT_LOAD_TWO_STEP)))
 
     def trace(sc, start, flags, s=None):
         d = sc["d"]
@@ -1051,7 +1051,9 @@ def main():
              for k, sc in enumerate(scenes)]
     batch, btune = None, None
     arms = {}
-    for label, bflags in (("filtered", 0), ("exact", cct.CCT_TRACE_EXACT_ONLY)):
+    # predicate arms on the two-step records (CCT_LOAD_TWO_STEP), and exact-only on the 16-byte records
+    for label, bflags in (("filtered", 0), ("exact", cct.CCT_TRACE_EXACT_ONLY),
+                          ("exact_one_step", cct.CCT_TRACE_EXACT_ONLY | cct.CCT_TRACE_ONE_STEP)):
         b = cct.Batch([sc["scene"] for sc in scenes], len(items), bflags)
         res = autotune.tune_batch(b, items)
         # one launch at the arm's tuned configuration: its fallback rate (0 by construction when exact-only)
@@ -1275,12 +1277,14 @@ def main():
 
     line = {"metric": "closest-hit rays/s", "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64" if btune["predicates"] == "exact" else "int64+fp32-filter",
+            "vs_baseline": None, "dtype": "int64" if btune["predicates"].startswith("exact") else "int64+fp32-filter",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "families": list(FAMILIES), "segments_per_scene": N_SEGMENTS,
                        "rays_per_step": rays_per_step,
                        "launch": "one batched launch per step over the six scenes (CUDA-graph replay)",
                        "batch_tuning": dict(btune["tuning"], predicates=btune["predicates"]),
+                       "records": ("16-byte half-edge records" if btune["predicates"].endswith("one_step") else
+                                   "two-step records (CCT_LOAD_TWO_STEP: two triangles per dependent load)"),
                        "l2": "inputs larger than L2 (6 x 2^24 rays + results, 2 GB); triangle tables L2-resident",
                        "parallelism": f"replicas x{world}"},
             "plain_per_scene": {"rays_per_s": rays_per_step * world / (plain_ms * 1e-3), "ms_per_step": plain_ms,

@@ -33,6 +33,7 @@ CCT_RAY_BAD_INDEX = -4
 CCT_MAX_BOUNCES = 1024
 CCT_LOAD_NO_REORDER = 1
 CCT_LOAD_NO_VALIDATE = 2
+CCT_LOAD_TWO_STEP = 4
 
 
 def CCT_LOAD_SEED_DENSITY(k: int) -> int:
@@ -44,6 +45,7 @@ CCT_TRACE_EXACT_ONLY = 1
 CCT_TRACE_BIN = 2
 CCT_TRACE_SPLIT_LOCATE = 4
 CCT_TRACE_STAGE = 8
+CCT_TRACE_ONE_STEP = 16
 CCT_NOALLOC_MAX_RAYS = 1 << 20
 CCT_TABLE_NEIGHBOUR = 1
 CCT_TABLE_HALF_EDGE_EXIT = 2
@@ -56,6 +58,7 @@ CCT_TABLE_KD_REF = 8
 CCT_TABLE_BVH_CHILD0 = 9
 CCT_TABLE_BVH_CHILD1 = 10
 CCT_TABLE_BVH_PRIM = 11
+CCT_TABLE_TWO_STEP_EXIT = 12
 
 
 class CctError(RuntimeError):
@@ -379,6 +382,7 @@ class Scene:
     def __init__(self, vx, vy, tri_v, tri_nb, tri_seg, n_seg: int, domain: int, flags: int = 0, stream=None):
         self.handle = cct_scene_load(vx, vy, tri_v, tri_nb, tri_seg, n_seg, domain, flags, stream)
         self.n_tri = int(np.asarray(tri_v).size // 3)
+        self.load_flags = int(flags)
 
     @classmethod
     def from_triangulation(cls, tri, domain: int, flags: int = 0, stream=None) -> "Scene":
@@ -391,6 +395,7 @@ class Scene:
         self = cls.__new__(cls)
         self.handle = cct_scene_load_file(path, flags, stream)
         self.n_tri = cct_scene_info(self.handle)[1]
+        self.load_flags = int(flags)
         return self
 
     def trace(self, ox, oy, dx, dy, start=None, flags: int = 0, stream=None, out=None):

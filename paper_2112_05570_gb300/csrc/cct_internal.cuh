@@ -10,6 +10,13 @@
 //                               step after the first needs and nothing else
 //                               (the apex of the entry edge and the two
 //                               candidate exit words), one L2 sector per step
+//   he2       int4[4*3*n_tri]   (CCT_LOAD_TWO_STEP only) two-step records, 64
+//                               bytes per half-edge h: he[h], he[he[h].z] (the
+//                               record behind its L exit), he[he[h].w] (behind
+//                               its R exit), 16 unused bytes.  The first 32
+//                               bytes are one sector: a left exit needs no
+//                               second load; a right exit reads 16 more bytes
+//                               of the same record
 //   cnb       int32[3*n_tri]    neighbour word across constrained edges (read
 //                               only by the locate walk, which crosses them)
 //   user2dev  int32[n_tri]      caller triangle id -> record index
@@ -85,6 +92,7 @@ struct DevStats {
 struct SceneDev {
   const TriRec* rec;
   const int4* he;
+  const int4* he2;  // two-step records, or NULL
   const int32_t* cnb;
   const int32_t* user2dev;
   const int32_t* dev2user;
@@ -109,6 +117,14 @@ __device__ __forceinline__ TriRec load_rec(const TriRec* p) {
   r.nb[2] = (int32_t)(uint32_t)d;
   r.pad = (int32_t)(uint32_t)(d >> 32);
   return r;
+}
+
+// One 32-byte sector as two int4 (the first half of a two-step record).
+__device__ __forceinline__ void load_sector(const int4* p, int4& lo, int4& hi) {
+  unsigned long long a, b, c, d;
+  asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+  lo = make_int4((int)(uint32_t)a, (int)(uint32_t)(a >> 32), (int)(uint32_t)b, (int)(uint32_t)(b >> 32));
+  hi = make_int4((int)(uint32_t)c, (int)(uint32_t)(c >> 32), (int)(uint32_t)d, (int)(uint32_t)(d >> 32));
 }
 
 __device__ __forceinline__ int4 load_he(const int4* p) {

@@ -275,7 +275,9 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
     size_t o_u2d = o_cnb + align256(sizeof(int32_t) * 3 * (size_t)nt);
     size_t o_d2u = o_u2d + align256(sizeof(int32_t) * (size_t)nt);
     size_t o_seed = o_d2u + align256(sizeof(int32_t) * (size_t)nt);
-    size_t o_stats = o_seed + align256(sizeof(int32_t) * (size_t)G * G);
+    const bool two = (flags & CCT_LOAD_TWO_STEP) != 0;
+    size_t o_he2 = o_seed + align256(sizeof(int32_t) * (size_t)G * G);
+    size_t o_stats = o_he2 + (two ? align256(sizeof(int4) * 12 * (size_t)nt) : 0);
     size_t total = o_stats + align256(sizeof(DevStats));
     char* base = nullptr;
     if (cudaMalloc(&base, total) != cudaSuccess) {
@@ -292,6 +294,18 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
     up(o_u2d, user2dev.data(), sizeof(int32_t) * (size_t)nt);
     up(o_d2u, dev2user.data(), sizeof(int32_t) * (size_t)nt);
     up(o_seed, seeds.data(), sizeof(int32_t) * (size_t)G * G);
+    std::vector<int4> he2;
+    if (two) {
+      // two-step records: he[h], then the records behind its L and R exits
+      he2.assign(12 * (size_t)nt, make_int4(0, 0, 0, 0));
+      for (size_t h = 0; h < 3 * (size_t)nt; ++h) {
+        const int4 q = he[h];
+        he2[4 * h] = q;
+        if (q.z >= 0) he2[4 * h + 1] = he[q.z];
+        if (q.w >= 0) he2[4 * h + 2] = he[q.w];
+      }
+      up(o_he2, he2.data(), sizeof(int4) * 12 * (size_t)nt);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_stats, 0, sizeof(DevStats), stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
@@ -304,6 +318,7 @@ extern "C" int cct_scene_load(const cct_tri_desc* desc, uint32_t flags, void* st
     s->device = dev;
     s->dev.rec = (const TriRec*)(base + o_rec);
     s->dev.he = (const int4*)(base + o_he);
+    s->dev.he2 = two ? (const int4*)(base + o_he2) : nullptr;
     s->dev.cnb = (const int32_t*)(base + o_cnb);
     s->dev.user2dev = (const int32_t*)(base + o_u2d);
     s->dev.dev2user = (const int32_t*)(base + o_d2u);
@@ -458,6 +473,10 @@ extern "C" int cct_scene_poke(cct_scene scene, int32_t table, int64_t index, int
       return poke_word(scene->device, S.seeds, (int64_t)S.G * S.G, index, index, value, old, len);
     case CCT_TABLE_USER_TO_RECORD:
       return poke_word(scene->device, S.user2dev, nt, index, index, value, old, len);
+    case CCT_TABLE_TWO_STEP_EXIT:  // exit c of sub-record k of half-edge h: word 16 h + 4 k + 2 + c
+      if (!S.he2) return CCT_ERR_INVALID_ARGUMENT;
+      return poke_word(scene->device, S.he2, 18 * nt, index, 16 * (index / 6) + 4 * (index % 6 / 2) + 2 + index % 2,
+                       value, old, len);
     default:
       return CCT_ERR_INVALID_ARGUMENT;
   }

@@ -96,6 +96,33 @@ def test_batch_tunings_and_graph_replay(setup):
     b.free()
 
 
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batched_two_step_records(setup, mixed):
+    """Scenes loaded with two-step records: the batched launch walks them two
+    triangles per load when every scene has them, and falls back to the
+    16-byte records when one does not or CCT_TRACE_ONE_STEP is given; every
+    item equals the oracle either way."""
+    cct, tris, _, items = setup
+    scenes2 = [cct.Scene.from_triangulation(t, sg.D, flags=0 if (mixed and k == 1) else cct.CCT_LOAD_TWO_STEP)
+               for k, t in enumerate(tris)]
+    for flags in (0, cct.CCT_TRACE_EXACT_ONLY, cct.CCT_TRACE_EXACT_ONLY | cct.CCT_TRACE_ONE_STEP):
+        dev_items = _make(items, with_start=True)
+        cct.cct_trace_batched(scenes2, dev_items, flags=flags)
+        torch.cuda.synchronize()
+        _check((cct, tris, scenes2, items), dev_items)
+    b = cct.Batch(scenes2, max_items=64, flags=cct.CCT_TRACE_EXACT_ONLY)
+    b.set_tuning({"block_threads": 64, "refill_min": 16, "chunk": 512})
+    dev_items = _make(items, with_start=False)
+    b.stage(dev_items)
+    b.capture()
+    b.replay()
+    torch.cuda.synchronize()
+    _check((cct, tris, scenes2, items), dev_items)
+    b.free()
+    for sc in scenes2:
+        sc.free()
+
+
 def test_batch_rejects_bad_items(setup):
     cct, tris, scenes, items = setup
     b = cct.Batch(scenes, max_items=2)

@@ -104,15 +104,15 @@ def base():
     return segs, tri, r, (eh, et, es)
 
 
-def _plant(cct, handle, poke, table_len, table, bound, frac, seed, lo=0):
-    """Writes bound + (k % 61) at a random `frac` of the table's entries from
-    `lo` on (all when frac >= 1); returns how many."""
+def _plant(cct, handle, poke, table_len, table, bound, frac, seed, lo=0, spread=61):
+    """Writes bound + (k % spread) at a random `frac` of the table's entries
+    from `lo` on (all when frac >= 1); returns how many."""
     n = table_len(handle, table)
     rng = np.random.default_rng(seed)
     idx = np.arange(lo, n) if frac >= 1 else lo + rng.choice(n - lo, size=max(1, int((n - lo) * frac)),
                                                               replace=False)
     for k, i in enumerate(idx):
-        poke(handle, table, int(i), int(bound + k % 61))
+        poke(handle, table, int(i), int(bound + k % spread))
     return len(idx)
 
 
@@ -165,6 +165,32 @@ def test_planted_scene_indices_are_reported(cct, base, table, frac, reads):
         bad = st == cct.CCT_RAY_BAD_INDEX
         assert 0 < bad.sum() < len(st)
         assert (st[~bad] == r.start[~bad]).all()
+    scene.free()
+
+
+def test_planted_two_step_exits_are_reported(cct, base):
+    """A scene with two-step records, 10 % of their exit words planted: the
+    two-step walks (single-scene and batched) report the rays that read one;
+    the paths on the 16-byte records (CCT_TRACE_ONE_STEP, binned rays) never
+    read them and equal the oracle."""
+    _only_checked()
+    segs, tri, r, ref = base
+    scene = cct.Scene.from_triangulation(tri, sg.D, flags=cct.CCT_LOAD_TWO_STEP)
+    # the two-step table ends just before the scene's counters: plant exactly one past its end
+    _plant(cct, scene.handle, cct.cct_scene_poke, cct.cct_scene_table_len, cct.CCT_TABLE_TWO_STEP_EXIT,
+           3 * tri.n_tri, 0.1, 11, spread=1)
+    d = [torch.from_numpy(a).cuda() for a in (r.ox, r.oy, r.dx, r.dy, r.start)]
+    for given in (True, False):
+        for flags, affected in ((0, True), (1, True), (4, True), (16, False), (2, False)):
+            h, t, s = scene.trace(*d[:4], d[4] if given else None, flags=flags)
+            torch.cuda.synchronize()
+            n_bad = _check_rays(cct, h.cpu().numpy(), t.cpu().numpy(), s.cpu().numpy(), ref)
+            assert (n_bad > 0) == affected, (given, flags, n_bad)
+    n = d[0].numel()
+    o = (torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, dtype=torch.float32, device="cuda"),
+         torch.empty(n, dtype=torch.int32, device="cuda"))
+    cct.cct_trace_batched([scene], [(0, *d[:4], None, *o)], cct.CCT_TRACE_EXACT_ONLY)
+    assert _check_rays(cct, o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy(), ref) > 0
     scene.free()
 
 
