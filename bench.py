@@ -959,7 +959,7 @@ def main():
                  torch.empty(m, dtype=torch.int32, device=dev)) for _ in scenes]
         items = [(k, sc["d"]["ox"][:m], sc["d"]["oy"][:m], sc["d"]["dx"][:m], sc["d"]["dy"][:m], None, *outs[k])
                  for k, sc in enumerate(scenes)]
-        b = cct.Batch([sc["scene"] for sc in scenes], len(items), cct.CCT_TRACE_EXACT_ONLY)
+        b = cct.Batch([sc["scene"] for sc in scenes], len(items), cct.CCT_TRACE_EXACT_ONLY | cct.CCT_TRACE_ONE_STEP)
         b.set_tuning({"block_threads": 64, "refill_min": 16, "chunk": 512})
         b.stage(items)
         b.enqueue(stream)
@@ -1140,13 +1140,21 @@ def main():
     per = {}
     for sc in scenes:
         tuned_cfg = sc["scene"].tuning()
-        sc["scene"].set_tuning(dict(tuned_cfg, trace_flags=tuned_cfg["trace_flags"] & ~cct.CCT_TRACE_BIN))
-        for _ in range(2):
-            trace(sc, sc["d"]["start"], 0)
-        sc["scene"].stats(reset=True)
         k_rep = max(3, args.steps // 4)
-        wms = _time_loop(torch, dev, stream, lambda sc=sc: trace(sc, sc["d"]["start"], 0), k_rep)
-        st = sc["scene"].stats(reset=True)
+        # the tuned configuration without binning, on the two-step and on the 16-byte records
+        # (the tuning was chosen for located start cells): the faster of the two
+        wms, records = None, None
+        for one in (0, cct.CCT_TRACE_ONE_STEP):
+            fl = (tuned_cfg["trace_flags"] & ~(cct.CCT_TRACE_BIN | cct.CCT_TRACE_ONE_STEP)) | one
+            sc["scene"].set_tuning(dict(tuned_cfg, trace_flags=fl))
+            for _ in range(2):
+                trace(sc, sc["d"]["start"], 0)
+            sc["scene"].stats(reset=True)
+            ms_one = _time_loop(torch, dev, stream, lambda sc=sc: trace(sc, sc["d"]["start"], 0), k_rep)
+            st_one = sc["scene"].stats(reset=True)
+            if wms is None or ms_one < wms:
+                wms, st, records, best_fl = ms_one, st_one, ("16-byte" if one else "two-step"), fl
+        sc["scene"].set_tuning(dict(tuned_cfg, trace_flags=best_fl))
         wsteps = st["steps"] / k_rep
         alg = wsteps * 32.0 + n * 32.0
         bps = gather_bps[sc["name"]]
@@ -1161,7 +1169,8 @@ def main():
         cmp = comparison_structures(torch, cct, sg, sc, dev, stream, 2)
         per[sc["name"]] = {"segments": int(sc["segs"].shape[0]), "triangles": sc["tri"].n_tri,
                            "kd": cmp["kd"], "bvh": cmp["bvh"],
-                           "walk_rays_per_s": n / (wms * 1e-3), "steps_per_ray": wsteps / n,
+                           "walk_rays_per_s": n / (wms * 1e-3), "walk_records": records,
+                           "steps_per_ray": wsteps / n,
                            "steps_per_ray_cdt": cst["steps"] / max(1, cst["rays"]),
                            "steps_per_ray_refined_cdt": other["ref"]["steps"] / max(1, other["ref"]["rays"]),
                            "refine_params": list(getattr(sc["ref"], "refine_params", (0.0, 0.0))),
