@@ -196,6 +196,11 @@ class Server:
     TICK_RAYS = 1 << 25   # rays per tick (a burst is cut into ticks that overlap each other's copies)
     TICK_MIN_RAYS = 1 << 22  # while a tick runs, the next starts only with this many rays ready: a
                              # launch has a fixed ramp-up and drain, so many small ticks waste the GPU
+    AHEAD_RAYS = 1 << 27     # admitted rays that no tick has taken yet, at most (None: up to the
+                             # memory budget).  With every request of a deep queue admitted at once
+                             # the upload stream holds gigabytes of copies ahead of the walks and the
+                             # whole burst ran at 5.9e9 rays/s (1024 requests of 2^20 rays); a window
+                             # of 2^26..2^28 rays: 8.4e9
 
     def __init__(self, scenes, budget_bytes: int, max_items: int = 4096, flags: int = 0, use_graph: bool = True,
                  tuning: dict | None = None, n_batches: int = 3):
@@ -274,6 +279,7 @@ class Server:
         nxt = 0
         done_lat, done_rays = [], 0
         free_batch = [True] * len(self.batches)
+        ahead = 0  # rays uploaded or uploading that no tick has taken yet
         tick = 0
         start = time.perf_counter()
         deadline = None if max_wall_s is None else start + max_wall_s
@@ -291,6 +297,8 @@ class Server:
                     rnd, rays, dst, src, nb = [], 0, [], [], []
                     while pending and len(rnd) < self.max_items and rays < self.ROUND_RAYS:
                         r = pending[0]
+                        if self.AHEAD_RAYS is not None and ahead + rays >= self.AHEAD_RAYS:
+                            break
                         got = arena.alloc(7 * r.n)
                         if got is None:
                             break
@@ -319,6 +327,7 @@ class Server:
                     ev = torch.cuda.Event()
                     ev.record(self.h2d)
                     admitted.append((ev, rnd))
+                    ahead += rays
             # completed downloads: the requests are done, their blocks return to the arena
             while downloads and downloads[0][0].query():
                 _, rs = downloads.popleft()
@@ -364,6 +373,7 @@ class Server:
                 if k and (not ticks_in_flight or rays >= self.TICK_MIN_RAYS):
                     for _ in range(k):
                         ready.extend(admitted.popleft()[1])
+                    ahead -= rays
             if ready:
                 if batched:
                     b = self.batches[bi]
