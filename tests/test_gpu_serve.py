@@ -29,13 +29,17 @@ def env():
     return cct, serve, tris, scenes, rays
 
 
-@pytest.mark.parametrize("batched", [True, False])
-def test_each_result_equals_alone(env, batched):
+@pytest.mark.parametrize("batched,ahead", [(True, None), (False, None), (True, 4096)])
+def test_each_result_equals_alone(env, batched, ahead):
+    """ahead: a small upload window (Server.AHEAD_RAYS), so that admission also
+    waits for the ticks to take what was uploaded."""
     cct, serve, tris, scenes, rays = env
     pool = serve.RayPool(rays, capacity_out=1 << 24)
     sched = serve.poisson_schedule(3000.0, 0.25, len(scenes), 50, 20000, seed=3)
     budget = 28 * 60_000  # small: forces admission to wait for memory
     srv = serve.Server(scenes, budget_bytes=budget, max_items=256)
+    if ahead is not None:
+        srv.AHEAD_RAYS = ahead
     res, reqs = srv.run(sched, pool, batched=batched, seed=4, keep_requests=True)
     assert res.completed == res.offered == len(sched) and res.queue_depth_end == 0
     assert np.isfinite(res.p50_ms) and res.p99_ms >= res.p50_ms
