@@ -286,7 +286,9 @@ int cct_trace_noalloc(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy,
  * units of 2^-32 (int64; 0 where there is no ray or the ray is invalid),
  * d_dir_x, d_dir_y = its direction (0 likewise).
  * Launch: blocks of 256 threads, one path per lane; the scene tuning's chunk
- * applies.  flags: 0 or CCT_TRACE_EXACT_ONLY (every decision is exact here).  Scratch
+ * applies.  flags: CCT_TRACE_EXACT_ONLY (every decision is exact here anyway) and
+ * CCT_TRACE_ONE_STEP (on a scene loaded with CCT_LOAD_TWO_STEP the paths walk
+ * the two-step records unless this flag is given; 5-6 % faster).  Scratch
  * (a work counter, located start cells) comes from the stream-ordered
  * allocator on `stream`.  n = 0 is a no-op.
  * Errors: CCT_ERR_INVALID_ARGUMENT (n < 0, n_bounce outside

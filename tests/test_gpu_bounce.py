@@ -82,6 +82,32 @@ def test_bounce_paths_equal_oracle(cct, name, gen):
             scene.free()
 
 
+@pytest.mark.parametrize("name,gen", _scene_cases(), ids=[c[0] for c in _scene_cases()])
+def test_bounce_paths_on_two_step_records(cct, name, gen):
+    """Scenes loaded with two-step records: mirror paths and paths of
+    caller-given directions (two triangles per iteration) equal the oracle's,
+    start cells given and located, and so do the paths that keep the 16-byte
+    records (CCT_TRACE_ONE_STEP)."""
+    segs = gen()
+    tri = sg.pipeline(segs, 24, sweeps=2)[2]
+    scene = cct.Scene.from_triangulation(tri, sg.D, flags=cct.CCT_LOAD_TWO_STEP)
+    try:
+        r = sg.rays_isotropic(tri, 20_000 + 77, 29)
+        nb = 8
+        exp = oracle.bounce_walk(tri, r.ox, r.oy, r.dx, r.dy, r.start, nb)
+        for flags in (0, cct.CCT_TRACE_ONE_STEP):
+            _assert_paths(_gpu_paths(scene, r, nb, flags=flags), exp)
+        _assert_paths(_gpu_paths(scene, r, nb, start=False), exp)
+        fr = _frames(30, r.ox.size, nb)
+        efr = oracle.bounce_walk(tri, r.ox, r.oy, r.dx, r.dy, r.start, nb, frame=fr)
+        out = scene.trace_bounces(_dev(r.ox), _dev(r.oy), _dev(r.dx), _dev(r.dy), nb, start=_dev(r.start),
+                                  frame=_dev(fr))
+        torch.cuda.synchronize()
+        _assert_paths({k: v.cpu().numpy() for k, v in out.items()}, efr)
+    finally:
+        scene.free()
+
+
 def test_zero_bounces_equal_cct_trace(cct):
     """n_bounce = 0: one record per ray, equal to cct_trace's results."""
     segs = sg.circles(3000, 26)

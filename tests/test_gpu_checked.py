@@ -191,6 +191,12 @@ def test_planted_two_step_exits_are_reported(cct, base):
          torch.empty(n, dtype=torch.int32, device="cuda"))
     cct.cct_trace_batched([scene], [(0, *d[:4], None, *o)], cct.CCT_TRACE_EXACT_ONLY)
     assert _check_rays(cct, o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy(), ref) > 0
+    # the mirror paths read the two-step records too: their primary rays are reported or equal the oracle
+    paths = scene.trace_bounces(*d[:4], 2, start=d[4])
+    torch.cuda.synchronize()
+    p0 = [paths[k][0].cpu().numpy() for k in ("hit", "t", "steps")]
+    assert _check_rays(cct, *p0, ref) > 0
+    assert (paths["steps"].cpu().numpy() == cct.CCT_RAY_BAD_INDEX).sum(axis=0).max() <= 1
     scene.free()
 
 
