@@ -544,8 +544,11 @@ def run_config4(args, torch, cct, sg, dev):
         b.free()
         return work, scenes, None
     out = {}
-    for name, flags in (("filtered", 0), ("exact", cct.CCT_TRACE_EXACT_ONLY)):
-        b = cct.Batch(scenes, len(items), flags)
+    # the same scenes with two-step records, for the third arm
+    scenes2 = [cct.Scene.from_triangulation(tri, sg.D, flags=cct.CCT_LOAD_TWO_STEP) for segs, tri, r, _ in work]
+    for name, flags, scs in (("filtered", 0, scenes), ("exact", cct.CCT_TRACE_EXACT_ONLY, scenes),
+                             ("exact_two_step", cct.CCT_TRACE_EXACT_ONLY, scenes2)):
+        b = cct.Batch(scs, len(items), flags)
         tune = autotune.tune_batch(b, items)
         b.capture()
         for _ in range(args.warmup):
@@ -557,6 +560,8 @@ def run_config4(args, torch, cct, sg, dev):
                      "steps_per_ray": st["steps"] / max(1, st["rays"]),
                      "fallback_rate": st["exact_fallbacks"] / max(1, st["side_tests"])}
         b.free()
+    for sc in scenes2:
+        sc.free()
 
     def plain():
         for it in items:
