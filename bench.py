@@ -810,9 +810,11 @@ def run_profile_kernels(args, torch, cct, sg, dev):
     kernel, the binned trace (locate, histogram, three scan passes, scatter,
     sorted walk), the split and fused walks, the kd-tree and BVH baselines,
     a four-item batched launch over the same scene, mirror and diffuse paths
-    of 2^21 of the rays with 8 bounces and the gather peak; each
-    twice (warm-up, then the launch a profiler captures).  Prints the
-    CUDA-event time of the second launch of each call."""
+    of 2^21 of the rays with 8 bounces, the fused and given-start walks and
+    the mirror paths again on two-step records (CCT_LOAD_TWO_STEP), and the
+    gather peak; each twice (warm-up, then the launch a profiler captures).
+    Prints the CUDA-event time of the second launch of each call and the
+    scene's steps per ray."""
     name = args.families.split(",")[0]
     segs = family_segments(name)
     cdt, ref, tri = sg.pipeline(segs, SCENE_SEED + FAMILIES.index(name), sweeps=4)
@@ -826,6 +828,7 @@ def run_profile_kernels(args, torch, cct, sg, dev):
     loc = torch.empty(n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     scene = cct.Scene.from_triangulation(tri, sg.D)
+    scene2 = cct.Scene.from_triangulation(tri, sg.D, flags=cct.CCT_LOAD_TWO_STEP)
     bvh = cct.Bvh(sg.bvh(segs, 1.0))
     kd = cct.KdTree(sg.kdtree(segs, 1.0), sg.D)
     q = n // 4
@@ -855,6 +858,11 @@ def run_profile_kernels(args, torch, cct, sg, dev):
         "bounce_8_diffuse": lambda: scene.trace_bounces(d[0][:nb_rays], d[1][:nb_rays], d[2][:nb_rays],
                                                         d[3][:nb_rays], N_BOUNCE, start=start[:nb_rays], stream=stream,
                                                         with_rays=False, frame=frame),
+        "fused_trace_two_step": lambda: cct.cct_trace(scene2.handle, *d, None, hit, t, steps, 0, stream),
+        "given_trace_two_step": lambda: cct.cct_trace(scene2.handle, *d, start, hit, t, steps, 0, stream),
+        "bounce_8_two_step": lambda: scene2.trace_bounces(d[0][:nb_rays], d[1][:nb_rays], d[2][:nb_rays],
+                                                          d[3][:nb_rays], N_BOUNCE, start=start[:nb_rays],
+                                                          stream=stream, with_rays=False),
     }
     out = {}
     for label, fn in calls.items():
@@ -862,9 +870,12 @@ def run_profile_kernels(args, torch, cct, sg, dev):
         out[label] = _time_loop(torch, dev, stream, fn, 1)
     ms, bps = cct.cct_measure_gather(tri.n_tri * 32, 1 << 27, 1, stream)
     out["gather_kernel"] = ms
+    scene.stats(reset=True)
+    cct.cct_trace(scene.handle, *d, start, hit, t, steps, 0, stream)
+    st = scene.stats(reset=True)
     print(json.dumps({"profile_kernels_ms": out, "scene": name, "rays": n, "triangles": tri.n_tri,
-                      "gather_peak_gbs": bps / 1e9}))
-    for o in (batch, bvh, kd, scene):
+                      "steps_per_ray": st["steps"] / max(1, st["rays"]), "gather_peak_gbs": bps / 1e9}))
+    for o in (batch, bvh, kd, scene, scene2):
         o.free()
     return 0
 
