@@ -119,3 +119,34 @@ def test_noalloc_follows_the_scenes_tuning(cct):
             assert np.array_equal(hit.cpu().numpy(), ref[0]) and np.array_equal(steps.cpu().numpy(), ref[2])
             assert np.array_equal(t.cpu().numpy(), ref[1])
     scene.free()
+
+
+def test_noalloc_on_two_step_records(cct):
+    """On a scene loaded with two-step records the allocation-free entry point
+    walks them as cct_trace does, with the same results (fused and split
+    locate, start cells given)."""
+    tri = sg.anneal(sg.cdt(sg.random_segments(300, 35)), 35)
+    n = 200_003
+    r = sg.rays_isotropic(tri, n, 36)
+    scene = cct.Scene.from_triangulation(tri, sg.D, flags=cct.CCT_LOAD_TWO_STEP)
+    dev = torch.device("cuda")
+    ox, oy = torch.from_numpy(r.ox).to(dev), torch.from_numpy(r.oy).to(dev)
+    dx, dy = torch.from_numpy(r.dx).to(dev), torch.from_numpy(r.dy).to(dev)
+    start = torch.from_numpy(r.start).to(dev)
+    L = cct.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    eh, et, es = oracle.walk(tri, r.ox, r.oy, r.dx, r.dy, r.start)
+    for start_arg, flags in ((None, 0), (None, cct.CCT_TRACE_SPLIT_LOCATE), (start, cct.CCT_TRACE_EXACT_ONLY)):
+        hit = torch.full((n,), -7, dtype=torch.int32, device=dev)
+        t = torch.full((n,), -7.0, dtype=torch.float32, device=dev)
+        steps = torch.full((n,), -7, dtype=torch.int32, device=dev)
+        rc = L.cct_trace_noalloc(ctypes.c_void_p(scene.handle), _p(ox), _p(oy), _p(dx), _p(dy), _p(start_arg), n,
+                                 _p(hit), _p(t), _p(steps), flags, stream)
+        assert rc == cct.CCT_OK, cct.cct_error_string(rc)
+        torch.cuda.synchronize()
+        h, tt, s = hit.cpu().numpy(), t.cpu().numpy(), steps.cpu().numpy()
+        assert np.array_equal(h, eh) and np.array_equal(s, es), flags
+        fin = np.isfinite(et)
+        assert np.array_equal(np.isfinite(tt), fin)
+        assert np.all(np.abs(tt[fin].astype(np.float64) - et[fin]) <= 1e-6 * np.abs(et[fin].astype(np.float64)))
+    scene.free()
