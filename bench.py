@@ -544,11 +544,8 @@ def run_config4(args, torch, cct, sg, dev):
         b.free()
         return work, scenes, None
     out = {}
-    # the same scenes with two-step records, for the third arm
-    scenes2 = [cct.Scene.from_triangulation(tri, sg.D, flags=cct.CCT_LOAD_TWO_STEP) for segs, tri, r, _ in work]
-    for name, flags, scs in (("filtered", 0, scenes), ("exact", cct.CCT_TRACE_EXACT_ONLY, scenes),
-                             ("exact_two_step", cct.CCT_TRACE_EXACT_ONLY, scenes2)):
-        b = cct.Batch(scs, len(items), flags)
+    for name, flags in (("filtered", 0), ("exact", cct.CCT_TRACE_EXACT_ONLY)):
+        b = cct.Batch(scenes, len(items), flags)
         tune = autotune.tune_batch(b, items)
         b.capture()
         for _ in range(args.warmup):
@@ -560,8 +557,6 @@ def run_config4(args, torch, cct, sg, dev):
                      "steps_per_ray": st["steps"] / max(1, st["rays"]),
                      "fallback_rate": st["exact_fallbacks"] / max(1, st["side_tests"])}
         b.free()
-    for sc in scenes2:
-        sc.free()
 
     def plain():
         for it in items:
@@ -810,9 +805,9 @@ def run_profile_kernels(args, torch, cct, sg, dev):
     kernel, the binned trace (locate, histogram, three scan passes, scatter,
     sorted walk), the split and fused walks, the kd-tree and BVH baselines,
     a four-item batched launch over the same scene, mirror and diffuse paths
-    of 2^21 of the rays with 8 bounces, the fused and given-start walks and
-    the mirror paths again on two-step records (CCT_LOAD_TWO_STEP), and the
-    gather peak; each twice (warm-up, then the launch a profiler captures).
+    of 2^21 of the rays with 8 bounces, the mirror paths again on two-step
+    records (CCT_LOAD_TWO_STEP), and the gather peak; each twice (warm-up,
+    then the launch a profiler captures).
     Prints the CUDA-event time of the second launch of each call and the
     scene's steps per ray."""
     name = args.families.split(",")[0]
@@ -858,8 +853,6 @@ def run_profile_kernels(args, torch, cct, sg, dev):
         "bounce_8_diffuse": lambda: scene.trace_bounces(d[0][:nb_rays], d[1][:nb_rays], d[2][:nb_rays],
                                                         d[3][:nb_rays], N_BOUNCE, start=start[:nb_rays], stream=stream,
                                                         with_rays=False, frame=frame),
-        "fused_trace_two_step": lambda: cct.cct_trace(scene2.handle, *d, None, hit, t, steps, 0, stream),
-        "given_trace_two_step": lambda: cct.cct_trace(scene2.handle, *d, start, hit, t, steps, 0, stream),
         "bounce_8_two_step": lambda: scene2.trace_bounces(d[0][:nb_rays], d[1][:nb_rays], d[2][:nb_rays],
                                                           d[3][:nb_rays], N_BOUNCE, start=start[:nb_rays],
                                                           stream=stream, with_rays=False),
@@ -978,7 +971,7 @@ def main():
                  torch.empty(m, dtype=torch.int32, device=dev)) for _ in scenes]
         items = [(k, sc["d"]["ox"][:m], sc["d"]["oy"][:m], sc["d"]["dx"][:m], sc["d"]["dy"][:m], None, *outs[k])
                  for k, sc in enumerate(scenes)]
-        b = cct.Batch([sc["scene"] for sc in scenes], len(items), cct.CCT_TRACE_EXACT_ONLY | cct.CCT_TRACE_ONE_STEP)
+        b = cct.Batch([sc["scene"] for sc in scenes], len(items), cct.CCT_TRACE_EXACT_ONLY)
         b.set_tuning({"block_threads": 64, "refill_min": 16, "chunk": 512})
         b.stage(items)
         b.enqueue(stream)
@@ -1070,9 +1063,7 @@ def main():
              for k, sc in enumerate(scenes)]
     batch, btune = None, None
     arms = {}
-    # predicate arms on the two-step records (CCT_LOAD_TWO_STEP), and exact-only on the 16-byte records
-    for label, bflags in (("filtered", 0), ("exact", cct.CCT_TRACE_EXACT_ONLY),
-                          ("exact_one_step", cct.CCT_TRACE_EXACT_ONLY | cct.CCT_TRACE_ONE_STEP)):
+    for label, bflags in (("filtered", 0), ("exact", cct.CCT_TRACE_EXACT_ONLY)):
         b = cct.Batch([sc["scene"] for sc in scenes], len(items), bflags)
         res = autotune.tune_batch(b, items)
         # one launch at the arm's tuned configuration: its fallback rate (0 by construction when exact-only)
@@ -1159,21 +1150,13 @@ def main():
     per = {}
     for sc in scenes:
         tuned_cfg = sc["scene"].tuning()
+        sc["scene"].set_tuning(dict(tuned_cfg, trace_flags=tuned_cfg["trace_flags"] & ~cct.CCT_TRACE_BIN))
+        for _ in range(2):
+            trace(sc, sc["d"]["start"], 0)
+        sc["scene"].stats(reset=True)
         k_rep = max(3, args.steps // 4)
-        # the tuned configuration without binning, on the two-step and on the 16-byte records
-        # (the tuning was chosen for located start cells): the faster of the two
-        wms, records = None, None
-        for one in (0, cct.CCT_TRACE_ONE_STEP):
-            fl = (tuned_cfg["trace_flags"] & ~(cct.CCT_TRACE_BIN | cct.CCT_TRACE_ONE_STEP)) | one
-            sc["scene"].set_tuning(dict(tuned_cfg, trace_flags=fl))
-            for _ in range(2):
-                trace(sc, sc["d"]["start"], 0)
-            sc["scene"].stats(reset=True)
-            ms_one = _time_loop(torch, dev, stream, lambda sc=sc: trace(sc, sc["d"]["start"], 0), k_rep)
-            st_one = sc["scene"].stats(reset=True)
-            if wms is None or ms_one < wms:
-                wms, st, records, best_fl = ms_one, st_one, ("16-byte" if one else "two-step"), fl
-        sc["scene"].set_tuning(dict(tuned_cfg, trace_flags=best_fl))
+        wms = _time_loop(torch, dev, stream, lambda sc=sc: trace(sc, sc["d"]["start"], 0), k_rep)
+        st = sc["scene"].stats(reset=True)
         wsteps = st["steps"] / k_rep
         alg = wsteps * 32.0 + n * 32.0
         bps = gather_bps[sc["name"]]
@@ -1188,8 +1171,7 @@ def main():
         cmp = comparison_structures(torch, cct, sg, sc, dev, stream, 2)
         per[sc["name"]] = {"segments": int(sc["segs"].shape[0]), "triangles": sc["tri"].n_tri,
                            "kd": cmp["kd"], "bvh": cmp["bvh"],
-                           "walk_rays_per_s": n / (wms * 1e-3), "walk_records": records,
-                           "steps_per_ray": wsteps / n,
+                           "walk_rays_per_s": n / (wms * 1e-3), "steps_per_ray": wsteps / n,
                            "steps_per_ray_cdt": cst["steps"] / max(1, cst["rays"]),
                            "steps_per_ray_refined_cdt": other["ref"]["steps"] / max(1, other["ref"]["rays"]),
                            "refine_params": list(getattr(sc["ref"], "refine_params", (0.0, 0.0))),
@@ -1305,14 +1287,12 @@ def main():
 
     line = {"metric": "closest-hit rays/s", "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64" if btune["predicates"].startswith("exact") else "int64+fp32-filter",
+            "vs_baseline": None, "dtype": "int64" if btune["predicates"] == "exact" else "int64+fp32-filter",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "families": list(FAMILIES), "segments_per_scene": N_SEGMENTS,
                        "rays_per_step": rays_per_step,
                        "launch": "one batched launch per step over the six scenes (CUDA-graph replay)",
                        "batch_tuning": dict(btune["tuning"], predicates=btune["predicates"]),
-                       "records": ("16-byte half-edge records" if btune["predicates"].endswith("one_step") else
-                                   "two-step records (CCT_LOAD_TWO_STEP: two triangles per dependent load)"),
                        "l2": "inputs larger than L2 (6 x 2^24 rays + results, 2 GB); triangle tables L2-resident",
                        "parallelism": f"replicas x{world}"},
             "plain_per_scene": {"rays_per_s": rays_per_step * world / (plain_ms * 1e-3), "ms_per_step": plain_ms,

@@ -72,8 +72,8 @@ extern "C" {
                                    index ranges are always checked */
 #define CCT_LOAD_TWO_STEP 4u    /* also build two-step half-edge records (64 bytes per half-edge, 192
                                    per triangle): the record of a half-edge together with the records
-                                   behind its two exits, so that the walk decides two triangles per
-                                   dependent load (see cct_trace) */
+                                   behind its two exits, so that the paths of cct_trace_bounces decide
+                                   two triangles per dependent load (see there) */
 
 /* Density of the locate seed grid (Sec. 5.2): square cells of side 2^s with
  * about 2^k cells per triangle, k in [0, 8] (at most 8192 cells per side; 4
@@ -91,8 +91,8 @@ extern "C" {
                                    it fits beside the block's stacks (about 3,500 triangles at 64
                                    threads per block, fewer for larger blocks) and the rays are not
                                    binned, ignored otherwise.  Pays on small scenes only */
-#define CCT_TRACE_ONE_STEP 16u  /* on a scene loaded with CCT_LOAD_TWO_STEP, walk one triangle per
-                                   load on the 16-byte records anyway */
+#define CCT_TRACE_ONE_STEP 16u  /* cct_trace_bounces on a scene loaded with CCT_LOAD_TWO_STEP: walk one
+                                   triangle per load on the 16-byte records anyway */
 
 /* ------------------------------------------------------------------ types */
 typedef struct cct_scene_s* cct_scene; /* opaque; the library owns all device memory of a scene */
@@ -209,15 +209,6 @@ int cct_locate(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy, int64_
  * invalid ray; d_steps = triangles visited including the start triangle
  * (Sec. 5.4), or CCT_RAY_INVALID / CCT_RAY_WALK_LIMIT (CCT_RAY_BAD_INDEX in the checked
  * build).  flags: CCT_TRACE_*.
- * On a scene loaded with CCT_LOAD_TWO_STEP the walk reads the two-step
- * records: after deciding the exit of a triangle it already holds the next
- * triangle's apex and exits (in the same 32-byte sector after a left exit; 16
- * more bytes of the same record after a right one), so each record serves two
- * triangles; not with CCT_TRACE_ONE_STEP, binned rays or a staged table.
- * Results are identical either way.  Measured on GB300 (2^24 rays per
- * scene): 10-12 % faster on scenes with short walks, equal on long walks; in
- * a batched launch over several large scenes the larger tables crowd L2 and
- * the 16-byte records are faster (CCT_TRACE_ONE_STEP at cct_batch_create).
  * Scratch memory (ray binning, start cells) is taken from the stream-ordered
  * allocator on `stream` and released on it.  n = 0 is a no-op.
  * Errors: CCT_ERR_INVALID_ARGUMENT, CCT_ERR_OUT_OF_MEMORY, CCT_ERR_CUDA. */
@@ -288,7 +279,10 @@ int cct_trace_noalloc(cct_scene scene, const int32_t* d_ox, const int32_t* d_oy,
  * Launch: blocks of 256 threads, one path per lane; the scene tuning's chunk
  * applies.  flags: CCT_TRACE_EXACT_ONLY (every decision is exact here anyway) and
  * CCT_TRACE_ONE_STEP (on a scene loaded with CCT_LOAD_TWO_STEP the paths walk
- * the two-step records unless this flag is given; 5-6 % faster).  Scratch
+ * the two-step records unless this flag is given: after deciding the exit of
+ * a triangle a lane already holds the next triangle's apex and exits, in the
+ * same 32-byte sector after a left exit, 16 more bytes of the same record
+ * after a right one; 7-12 % faster, identical results).  Scratch
  * (a work counter, located start cells) comes from the stream-ordered
  * allocator on `stream`.  n = 0 is a no-op.
  * Errors: CCT_ERR_INVALID_ARGUMENT (n < 0, n_bounce outside
@@ -329,9 +323,7 @@ typedef struct {
 typedef struct cct_batch_s* cct_batch;
 
 /* A reusable batch over n_scenes loaded scenes (all on one device) for up to
- * max_items items; flags: CCT_TRACE_EXACT_ONLY and CCT_TRACE_ONE_STEP (the
- * batch walks two-step records when every scene has them and this flag is
- * absent, the 16-byte records otherwise).  Holds a device work table
+ * max_items items; flags: 0 or CCT_TRACE_EXACT_ONLY.  Holds a device work table
  * and a pinned, device-mapped host staging copy of it.  The scenes must outlive
  * the batch. */
 int cct_batch_create(const cct_scene* scenes, int32_t n_scenes, int32_t max_items, uint32_t flags, cct_batch* out);

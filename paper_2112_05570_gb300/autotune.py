@@ -5,8 +5,7 @@ No counterpart in the paper.  Knobs: threads per block, the refill threshold
 takes from the work counter ("rays per warp"), ray binning and its
 granularity, where start cells are found when none are given (inside the walk
 kernel, or by a separate locate kernel first), the side test (fp32-filtered vs
-exact int64), on small scenes the half-edge table staged in shared memory, and
-on scenes loaded with two-step records whether the walk reads them.  Coordinate
+exact int64), and on small scenes the half-edge table staged in shared memory.  Coordinate
 descent from the defaults: each knob in turn takes the value with the lowest
 median CUDA-event time on a ray sample, others fixed; two passes.  Results are
 cached per (GPU, triangle-count class, ray-count class, start cells given)
@@ -59,8 +58,6 @@ def _to_tuning(cfg: dict, n_tri: int, n_rays: int) -> dict:
     flags = cct.CCT_TRACE_EXACT_ONLY if cfg["exact"] else 0
     if cfg.get("stage"):
         flags |= cct.CCT_TRACE_STAGE
-    if cfg.get("one_step"):
-        flags |= cct.CCT_TRACE_ONE_STEP
     shift = -1
     if cfg["path"] == "split":
         flags |= cct.CCT_TRACE_SPLIT_LOCATE
@@ -83,7 +80,7 @@ def tune_scene(scene: "cct.Scene", ox, oy, dx, dy, start=None, reps: int = 3, pa
     import torch
 
     n = ox.numel()
-    key = _key(scene.n_tri, n, start is not None) + f"|two{int(bool(getattr(scene, 'load_flags', 0) & cct.CCT_LOAD_TWO_STEP))}"
+    key = _key(scene.n_tri, n, start is not None)
     cache = _load_cache() if use_cache else {}
     if key in cache:
         if apply:
@@ -108,10 +105,7 @@ def tune_scene(scene: "cct.Scene", ox, oy, dx, dy, start=None, reps: int = 3, pa
         return sorted(times)[len(times) // 2]
 
     cfg = {"block_threads": 256, "refill_min": 8, "chunk": 128, "path": "plain", "exact": 0, "stage": 0}
-    knobs = dict(KNOBS, stage=(0, 1)) if scene.n_tri <= STAGE_MAX_TRI else dict(KNOBS)
-    if getattr(scene, "load_flags", 0) & cct.CCT_LOAD_TWO_STEP:
-        knobs["one_step"] = (0, 1)
-        cfg["one_step"] = 0
+    knobs = dict(KNOBS, stage=(0, 1)) if scene.n_tri <= STAGE_MAX_TRI else KNOBS
     tried = {}
     best_ms = time_cfg(cfg)
     tried[json.dumps(cfg, sort_keys=True)] = best_ms

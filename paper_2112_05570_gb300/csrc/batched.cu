@@ -75,9 +75,8 @@ struct BatchStacks {
   unsigned long long steps, sides;
 };
 
-// One walk slot (see walk.cu), plus its scene's half-edge table (the
-// two-step records in the two-step kernel); its ray index and item wait in
-// shared memory until it parks.
+// One walk slot (see walk.cu), plus its scene's half-edge table; its ray
+// index and item wait in shared memory until it parks.
 struct BSlot {
   const int4* he;
   int ox, oy, kx, ky, h, ns;
@@ -92,9 +91,7 @@ struct BSlot {
 // 72 registers per thread (no spills): at the compiler's own choice (83) the
 // kernel holds 24 warps per SM and ran 13 % slower on 512 scenes; at 64 it
 // spills and ran 13 % slower.  72 x 512 threads still fits one block per SM.
-// kTwo: every scene of the batch has two-step records (CCT_LOAD_TWO_STEP) and
-// the walk reads them, two triangles per dependent load (see walk.cu).
-template <bool kExact, bool kTwo>
+template <bool kExact>
 __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes,
                                                                  const BatchHeader* __restrict__ hdr,
                                                                  const BatchItemDev* __restrict__ items,
@@ -365,37 +362,6 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
     s.dn = true;
   };
 
-  // Two steps on a two-step record (as in walk.cu): al = he[h]; across an L
-  // exit the sector's high half ah, across an R exit the record's third
-  // quarter, loaded now.
-  auto step2 = [&](BSlot& s, const int4& al, const int4& ah) {
-    bool sc = side_L_cw<kExact>(s.kx, s.ky, s.ox, s.oy, al.x, al.y, n_fb);
-    ++s.ns;
-    int32_t w = sc ? al.z : al.w;
-    if (w >= 0 && s.ns < max_steps && !idx_bad(w, s.n_he)) {
-      const int4 q = sc ? ah : load_he(s.he + 4 * s.h + 2);
-      s.h = w;
-      sc = side_L_cw<kExact>(s.kx, s.ky, s.ox, s.oy, q.x, q.y, n_fb);
-      ++s.ns;
-      w = sc ? q.z : q.w;
-      if (w >= 0 && s.ns < max_steps && !idx_bad(w, s.n_he)) {
-        s.h = w;
-        return;
-      }
-    }
-    if (w >= 0 && idx_bad(w, s.n_he)) {
-      s.ns = CCT_RAY_BAD_INDEX;
-    } else if (w >= 0) {
-      s.ns = CCT_RAY_WALK_LIMIT;
-    } else {
-      const int T = he_tri(s.h), j = s.h - 3 * T;
-      const int e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
-      s.h = (T << 2) | e;
-    }
-    s.act = false;
-    s.dn = true;
-  };
-
   if (!exhausted) prefetch();
   while (true) {
     const unsigned idle0 = __ballot_sync(FULL, !sl[0].act), idle1 = __ballot_sync(FULL, !sl[1].act);
@@ -442,7 +408,7 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
           sl[q].h = b.x;
           W.l_idx[q][lane] = b.y;
           W.l_item[q][lane] = b.z;
-          sl[q].he = kTwo ? scenes[b.w].he2 : scenes[b.w].he;
+          sl[q].he = scenes[b.w].he;
           if (kChecked) sl[q].n_he = 3 * scenes[b.w].n_tri;
           sl[q].ns = 1;
           sl[q].act = true;
@@ -455,19 +421,15 @@ __global__ void __maxnreg__(72) batch_kernel(const SceneDev* __restrict__ scenes
       if (exhausted && n_ready == 0) break;
       continue;
     }
-    if (kTwo) {
-      int4 a0 = make_int4(0, 0, 0, 0), b0 = a0, a1 = a0, b1 = a0;
-      if (sl[0].act) load_sector(sl[0].he + 4 * sl[0].h, a0, b0);
-      if (sl[1].act) load_sector(sl[1].he + 4 * sl[1].h, a1, b1);
-      if (sl[0].act) step2(sl[0], a0, b0);
-      if (sl[1].act) step2(sl[1], a1, b1);
-      continue;
+    // kStepsPerServe steps per slot before the next serve check (see cct_internal.cuh)
+#pragma unroll
+    for (int rep = 0; rep < kStepsPerServe; ++rep) {
+      int4 q0 = make_int4(0, 0, 0, 0), q1 = make_int4(0, 0, 0, 0);
+      if (sl[0].act) q0 = load_he(sl[0].he + sl[0].h);
+      if (sl[1].act) q1 = load_he(sl[1].he + sl[1].h);
+      if (sl[0].act) step(sl[0], q0);
+      if (sl[1].act) step(sl[1], q1);
     }
-    int4 q0 = make_int4(0, 0, 0, 0), q1 = make_int4(0, 0, 0, 0);
-    if (sl[0].act) q0 = load_he(sl[0].he + sl[0].h);
-    if (sl[1].act) q1 = load_he(sl[1].he + sl[1].h);
-    if (sl[0].act) step(sl[0], q0);
-    if (sl[1].act) step(sl[1], q1);
   }
   while (n_done > 0) {
     const int m = min(32, n_done);
@@ -526,7 +488,6 @@ struct cct_batch_s {
   int grid;
   int staged;
   int max_steps;  // the largest step limit of the batch's scenes
-  bool two;       // every scene has two-step records and the flags allow them
 };
 
 static size_t batch_smem(int threads) { return sizeof(BatchStacks) * (size_t)(threads / 32); }
@@ -534,9 +495,7 @@ static size_t batch_smem(int threads) { return sizeof(BatchStacks) * (size_t)(th
 static int batch_grid(cct_batch b) {
   int per_sm = 0;
   const int threads = b->tuning.block_threads;
-  const bool exact = (b->flags & CCT_TRACE_EXACT_ONLY) != 0;
-  auto k = exact ? (b->two ? batch_kernel<true, true> : batch_kernel<true, false>)
-                 : (b->two ? batch_kernel<false, true> : batch_kernel<false, false>);
+  auto k = (b->flags & CCT_TRACE_EXACT_ONLY) ? batch_kernel<true> : batch_kernel<false>;
   // the stacks of 16 warps exceed the default 48 KB of dynamic shared memory
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem(kBatchMaxThreads)) !=
       cudaSuccess)
@@ -550,7 +509,7 @@ static int batch_grid(cct_batch b) {
 extern "C" int cct_batch_create(const cct_scene* scenes, int32_t n_scenes, int32_t max_items, uint32_t flags,
                                 cct_batch* out) {
   if (!scenes || !out || n_scenes < 1 || max_items < 1 || max_items > (1 << 20) ||
-      (flags & ~(uint32_t)(CCT_TRACE_EXACT_ONLY | CCT_TRACE_ONE_STEP)) != 0)
+      (flags & ~(uint32_t)CCT_TRACE_EXACT_ONLY) != 0)
     return CCT_ERR_INVALID_ARGUMENT;
   *out = nullptr;
   const int dev = scenes[0] ? scenes[0]->device : -1;
@@ -591,11 +550,9 @@ extern "C" int cct_batch_create(const cct_scene* scenes, int32_t n_scenes, int32
   b->d_stats = (DevStats*)(b->d_base + o_stats);
   std::vector<SceneDev> sd(n_scenes);
   b->max_steps = 1;
-  b->two = (flags & CCT_TRACE_ONE_STEP) == 0;
   for (int k = 0; k < n_scenes; ++k) {
     sd[k] = scenes[k]->dev;
     b->max_steps = std::max(b->max_steps, sd[k].max_steps);
-    if (!sd[k].he2) b->two = false;
   }
   cudaError_t e = cudaMemcpy(b->d_scenes, sd.data(), sizeof(SceneDev) * n_scenes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->d_hdr, 0, b->table_bytes);
@@ -675,9 +632,7 @@ extern "C" int cct_batch_enqueue(cct_batch b, void* stream_v) {
   if (cudaGetLastError() != cudaSuccess) return CCT_ERR_CUDA;
   const auto* items = (const BatchItemDev*)((const char*)b->d_hdr + sizeof(BatchHeader));
   const size_t smem = batch_smem(b->tuning.block_threads);
-  const bool exact = (b->flags & CCT_TRACE_EXACT_ONLY) != 0;
-  auto k = exact ? (b->two ? batch_kernel<true, true> : batch_kernel<true, false>)
-                 : (b->two ? batch_kernel<false, true> : batch_kernel<false, false>);
+  auto k = (b->flags & CCT_TRACE_EXACT_ONLY) ? batch_kernel<true> : batch_kernel<false>;
   k<<<b->grid, b->tuning.block_threads, smem, stream>>>(b->d_scenes, b->d_hdr, items, b->tuning.refill_min,
                                                         b->max_steps, b->d_counter, b->d_stats);
   return cudaGetLastError() == cudaSuccess ? CCT_OK : CCT_ERR_CUDA;

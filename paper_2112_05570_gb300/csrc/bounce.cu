@@ -88,7 +88,11 @@ __device__ __forceinline__ float i128_to_float(i128 v) {
 // spilled and ran 1.14-1.28x slower.
 // kTwo: the walk reads the scene's two-step records (CCT_LOAD_TWO_STEP): after
 // an L exit the next triangle's record is already in the loaded sector, after
-// an R exit 16 more bytes of the same record; two triangles per iteration.
+// an R exit 16 more bytes of the same record; two triangles per iteration.  A
+// lane walks one path, so its chain of dependent loads bounds it: the records
+// halve the chain's length after an L exit (7-12 % faster on the bench's
+// scenes).  Steps per serve check do not pay here (1, 2, 3, 4: the serve
+// check is one ballot).
 template <bool kFrame, bool kTwo>
 __global__ void __launch_bounds__(kBounceThreads, kFrame ? 3 : 4) bounce_kernel(SceneDev S, BounceArgs A,
                                                                 unsigned long long* __restrict__ counter) {
@@ -373,7 +377,7 @@ extern "C" int cct_trace_bounces(cct_scene scene, const int32_t* ox, const int32
     return CCT_ERR_OUT_OF_MEMORY;
   }
   unsigned long long* counter = (unsigned long long*)sc.base;
-  // the two-step records whenever the scene has them (5-6 % faster on every bench scene, long
+  // the two-step records whenever the scene has them (7-12 % faster on every bench scene, long
   // walks included), unless the call asks for the 16-byte records
   const bool two = S.he2 && (flags & CCT_TRACE_ONE_STEP) == 0;
   auto kern = frame ? (two ? bounce_kernel<true, true> : bounce_kernel<true, false>)

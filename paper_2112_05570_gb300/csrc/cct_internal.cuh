@@ -10,7 +10,8 @@
 //                               step after the first needs and nothing else
 //                               (the apex of the entry edge and the two
 //                               candidate exit words), one L2 sector per step
-//   he2       int4[4*3*n_tri]   (CCT_LOAD_TWO_STEP only) two-step records, 64
+//   he2       int4[4*3*n_tri]   (CCT_LOAD_TWO_STEP only; read by the path
+//                               kernel of cct_trace_bounces) two-step records, 64
 //                               bytes per half-edge h: he[h], he[he[h].z] (the
 //                               record behind its L exit), he[he[h].w] (behind
 //                               its R exit), 16 unused bytes.  The first 32
@@ -83,6 +84,14 @@ constexpr bool kChecked = false;
 #endif
 // True when the checked build finds i outside [0, n).
 __host__ __device__ __forceinline__ bool idx_bad(int i, int n) { return kChecked && (unsigned)i >= (unsigned)n; }
+
+// Walk steps each slot of the walk and batched kernels takes between two serve
+// checks (the warp's ballots and counts of idle slots): measured on the bench's
+// scenes at 2^24 rays, 1 -> 2 -> 3 took the walk from 1.00/1.05/1.17 ms to
+// 0.96/0.94/1.12 and 0.94/0.92/1.11 ms (circles / dash grid / clusters) and
+// the six-scene batched step from 5.62 to 5.50 and 5.44 ms; 4, 6 and 8 were
+// slower again (the slots that finish early idle longer).
+constexpr int kStepsPerServe = 3;
 
 struct DevStats {
   unsigned long long rays, steps, side_tests, exact_fallbacks, invalid_rays, walk_limit_rays, located,

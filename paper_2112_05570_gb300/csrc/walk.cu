@@ -83,9 +83,7 @@ struct Slot {
 // kStage: the block first copies the scene's half-edge table into shared
 // memory (after its warps' stacks) and the walk steps read it there: for
 // tables small enough to share the SM with the stacks (CCT_TRACE_STAGE).
-// kTwo: the walk reads the scene's two-step records (CCT_LOAD_TWO_STEP), two
-// triangles per dependent load.
-template <bool kExact, int kSrc, bool kStage, bool kTwo>
+template <bool kExact, int kSrc, bool kStage>
 __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySrc R, WalkParams P,
                                                                int32_t* __restrict__ hit_out,
                                                                float* __restrict__ t_out,
@@ -100,7 +98,6 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
   const unsigned lt = lanemask_lt();
   const int n = (int)R.n;
   const int4* __restrict__ he_tab = S.he;
-  const int4* __restrict__ he2_tab = S.he2;
   int4* const sm_he = reinterpret_cast<int4*>(smem_raw + sizeof(Stacks) * (blockDim.x >> 5));
   if (kStage) {
     for (int k = threadIdx.x; k < 3 * S.n_tri; k += blockDim.x) sm_he[k] = load_he(S.he + k);
@@ -387,38 +384,6 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
     s.dn = true;
   };
 
-  // Two steps on a two-step record: the first on he[h] (al); across an L exit
-  // the next record is the sector's high half (ah), across an R exit the
-  // record's third quarter, loaded now (16 bytes of the same 64-byte record).
-  auto step2 = [&](Slot& s, const int4& al, const int4& ah) {
-    bool sc = side_L_cw<kExact>(s.kx, s.ky, s.ox, s.oy, al.x, al.y, n_fb);
-    ++s.ns;
-    int32_t w = sc ? al.z : al.w;
-    if (w >= 0 && s.ns < max_steps && !idx_bad(w, n_he)) {
-      const int4 q = sc ? ah : load_he(he2_tab + 4 * s.h + 2);
-      s.h = w;
-      sc = side_L_cw<kExact>(s.kx, s.ky, s.ox, s.oy, q.x, q.y, n_fb);
-      ++s.ns;
-      w = sc ? q.z : q.w;
-      if (w >= 0 && s.ns < max_steps && !idx_bad(w, n_he)) {
-        s.h = w;
-        return;
-      }
-    }
-    if (w >= 0 && idx_bad(w, n_he)) {
-      s.ns = CCT_RAY_BAD_INDEX;
-    } else if (w >= 0) {
-      s.ns = CCT_RAY_WALK_LIMIT;
-      ++n_lim;
-    } else {
-      const int T = he_tri(s.h), j = s.h - 3 * T;
-      const int e = sc ? (j == 2 ? 0 : j + 1) : (j == 0 ? 2 : j - 1);
-      s.h = (T << 2) | e;
-    }
-    s.act = false;
-    s.dn = true;
-  };
-
   prefetch();
   while (true) {
     // ---------------------------------------------------------------- serve idle slots
@@ -482,24 +447,22 @@ __global__ void __launch_bounds__(kWalkMaxThreads) walk_kernel(SceneDev S, RaySr
 
     // ---------------------------------------------------------------- one step per walking slot
     // both slots' loads first: two independent rays, two loads in flight
-    if (kTwo) {
-      int4 a0 = make_int4(0, 0, 0, 0), b0 = a0, a1 = a0, b1 = a0;
-      if (sl[0].act) load_sector(he2_tab + 4 * sl[0].h, a0, b0);
-      if (sl[1].act) load_sector(he2_tab + 4 * sl[1].h, a1, b1);
-      if (sl[0].act) step2(sl[0], a0, b0);
-      if (sl[1].act) step2(sl[1], a1, b1);
-      continue;
+    // kStepsPerServe steps per slot before the next serve check: a slot that
+    // finishes in one of them idles until then, but the warp runs a third of
+    // the checks (ballots, counts, branch) it would otherwise
+#pragma unroll
+    for (int rep = 0; rep < kStepsPerServe; ++rep) {
+      int4 q0 = make_int4(0, 0, 0, 0), q1 = make_int4(0, 0, 0, 0);
+      if (kStage) {
+        if (sl[0].act) q0 = sm_he[sl[0].h];
+        if (sl[1].act) q1 = sm_he[sl[1].h];
+      } else {
+        if (sl[0].act) q0 = load_he(he_tab + sl[0].h);
+        if (sl[1].act) q1 = load_he(he_tab + sl[1].h);
+      }
+      if (sl[0].act) step(sl[0], q0);
+      if (sl[1].act) step(sl[1], q1);
     }
-    int4 q0 = make_int4(0, 0, 0, 0), q1 = make_int4(0, 0, 0, 0);
-    if (kStage) {
-      if (sl[0].act) q0 = sm_he[sl[0].h];
-      if (sl[1].act) q1 = sm_he[sl[1].h];
-    } else {
-      if (sl[0].act) q0 = load_he(he_tab + sl[0].h);
-      if (sl[1].act) q1 = load_he(he_tab + sl[1].h);
-    }
-    if (sl[0].act) step(sl[0], q0);
-    if (sl[1].act) step(sl[1], q1);
   }
   // the last parked rays (the final serve round parked every finished slot)
   while (n_done > 0) {
@@ -534,10 +497,10 @@ static size_t stacks_bytes(int threads) {
 // Shared memory a block may use (the GB300 per-block maximum).
 constexpr size_t kMaxBlockSmem = 227 * 1024;
 
-template <bool kExact, int kSrc, bool kStage, bool kTwo = false>
+template <bool kExact, int kSrc, bool kStage>
 static cudaError_t launch_walk_t(const SceneDev& S, const RaySrc& R, const cct_tuning& tu, int32_t* hit, float* t,
                                  int32_t* steps, unsigned long long* counter, int dev, cudaStream_t stream) {
-  auto k = walk_kernel<kExact, kSrc, kStage, kTwo>;
+  auto k = walk_kernel<kExact, kSrc, kStage>;
   const int threads = tu.block_threads;
   const size_t smem = stacks_bytes<kSrc>(threads) + (kStage ? sizeof(int4) * 3 * (size_t)S.n_tri : 0);
   {
@@ -575,19 +538,14 @@ bool walk_stage_fits(int32_t n_tri, int block_threads) {
 cudaError_t launch_walk_src(bool exact, int src, const SceneDev& S, const RaySrc& R, const cct_tuning& tu,
                             int32_t* hit, float* t, int32_t* steps, unsigned long long* counter, int dev,
                             cudaStream_t stream) {
-  // the staged table only for unsorted rays, and only when it fits beside the stacks; the
-  // two-step records for unsorted rays on a scene that has them, unless staged or refused
+  // the staged table only for unsorted rays, and only when it fits beside the stacks
   const bool stage = (tu.trace_flags & CCT_TRACE_STAGE) != 0 && src != kSrcSorted &&
                      walk_stage_fits(S.n_tri, tu.block_threads);
-  const bool two = S.he2 && !stage && src != kSrcSorted && (tu.trace_flags & CCT_TRACE_ONE_STEP) == 0;
 #define CCT_WALK_CASE(SRC)                                                                                  \
   case SRC:                                                                                                 \
     if (stage)                                                                                              \
       return exact ? launch_walk_t<true, SRC, true>(S, R, tu, hit, t, steps, counter, dev, stream)          \
                    : launch_walk_t<false, SRC, true>(S, R, tu, hit, t, steps, counter, dev, stream);        \
-    if (two)                                                                                                \
-      return exact ? launch_walk_t<true, SRC, false, true>(S, R, tu, hit, t, steps, counter, dev, stream)   \
-                   : launch_walk_t<false, SRC, false, true>(S, R, tu, hit, t, steps, counter, dev, stream); \
     return exact ? launch_walk_t<true, SRC, false>(S, R, tu, hit, t, steps, counter, dev, stream)           \
                  : launch_walk_t<false, SRC, false>(S, R, tu, hit, t, steps, counter, dev, stream);
   switch (src) {
@@ -723,8 +681,7 @@ extern "C" int cct_scene_set_tuning(cct_scene scene, const cct_tuning* tu) {
   }
   if (tu->block_threads < 32 || tu->block_threads > kWalkMaxThreads || tu->block_threads % 32 != 0 ||
       tu->refill_min < 1 || tu->refill_min > 32 || tu->chunk < 32 || tu->chunk > (1 << 20) || tu->bin_shift > 30 ||
-      (tu->trace_flags & ~(CCT_TRACE_EXACT_ONLY | CCT_TRACE_BIN | CCT_TRACE_SPLIT_LOCATE | CCT_TRACE_STAGE |
-                           CCT_TRACE_ONE_STEP)) != 0)
+      (tu->trace_flags & ~(CCT_TRACE_EXACT_ONLY | CCT_TRACE_BIN | CCT_TRACE_SPLIT_LOCATE | CCT_TRACE_STAGE)) != 0)
     return CCT_ERR_INVALID_ARGUMENT;
   scene->tuning = *tu;
   return CCT_OK;

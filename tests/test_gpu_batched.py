@@ -96,21 +96,20 @@ def test_batch_tunings_and_graph_replay(setup):
     b.free()
 
 
-@pytest.mark.parametrize("mixed", [False, True])
-def test_batched_two_step_records(setup, mixed):
-    """Scenes loaded with two-step records: the batched launch walks them two
-    triangles per load when every scene has them, and falls back to the
-    16-byte records when one does not or CCT_TRACE_ONE_STEP is given; every
-    item equals the oracle either way."""
+def test_batched_scenes_with_two_step_records(setup):
+    """Scenes loaded with two-step records (for the path kernel), some of them,
+    in one batch: every item equals the oracle, graph replay included."""
     cct, tris, _, items = setup
-    scenes2 = [cct.Scene.from_triangulation(t, sg.D, flags=0 if (mixed and k == 1) else cct.CCT_LOAD_TWO_STEP)
+    scenes2 = [cct.Scene.from_triangulation(t, sg.D, flags=0 if k == 1 else cct.CCT_LOAD_TWO_STEP)
                for k, t in enumerate(tris)]
-    for flags in (0, cct.CCT_TRACE_EXACT_ONLY, cct.CCT_TRACE_EXACT_ONLY | cct.CCT_TRACE_ONE_STEP):
+    for flags in (0, cct.CCT_TRACE_EXACT_ONLY):
         dev_items = _make(items, with_start=True)
         cct.cct_trace_batched(scenes2, dev_items, flags=flags)
         torch.cuda.synchronize()
         _check((cct, tris, scenes2, items), dev_items)
     b = cct.Batch(scenes2, max_items=64, flags=cct.CCT_TRACE_EXACT_ONLY)
+    with pytest.raises(cct.CctError):
+        cct.Batch(scenes2, max_items=64, flags=cct.CCT_TRACE_ONE_STEP)  # a path-kernel flag
     b.set_tuning({"block_threads": 64, "refill_min": 16, "chunk": 512})
     dev_items = _make(items, with_start=False)
     b.stage(dev_items)

@@ -274,7 +274,8 @@ def test_frame_direction_paths_equal_oracle(cct, name, gen):
         scene.free()
 
 
-def test_walk_limit_on_corrupt_triangulation(cct):
+@pytest.mark.parametrize("load_flags", [0, 4])  # 4: CCT_LOAD_TWO_STEP
+def test_walk_limit_on_corrupt_triangulation(cct, load_flags):
     """Mirror paths in a triangulation whose triangle 0 names itself as every
     neighbour (loaded without validation): the primary rays starting in it stop
     at the step limit with CCT_RAY_WALK_LIMIT, the rest of each path is 'no
@@ -295,7 +296,7 @@ def test_walk_limit_on_corrupt_triangulation(cct):
     dx = (np.rint(np.cos(th) * K) / K).astype(np.float32)
     dy = (np.rint(np.sin(th) * K) / K).astype(np.float32)
     scene = cct.Scene(tri.vx, tri.vy, tri.tri_v, tn, ts, tri.segs.shape[0], sg.D,
-                      flags=cct.CCT_LOAD_NO_VALIDATE | cct.CCT_LOAD_NO_REORDER)
+                      flags=cct.CCT_LOAD_NO_VALIDATE | cct.CCT_LOAD_NO_REORDER | load_flags)
     try:
         r = sg.Rays(ox=ox, oy=oy, dx=dx, dy=dy, start=np.zeros(n, np.int32))
         got = _gpu_paths(scene, r, 3)

@@ -122,9 +122,9 @@ def test_noalloc_follows_the_scenes_tuning(cct):
 
 
 def test_noalloc_on_two_step_records(cct):
-    """On a scene loaded with two-step records the allocation-free entry point
-    walks them as cct_trace does, with the same results (fused and split
-    locate, start cells given)."""
+    """On a scene loaded with two-step records (which only the path kernel
+    reads) the allocation-free entry point gives the oracle's results as
+    cct_trace does (fused and split locate, start cells given)."""
     tri = sg.anneal(sg.cdt(sg.random_segments(300, 35)), 35)
     n = 200_003
     r = sg.rays_isotropic(tri, n, 36)
