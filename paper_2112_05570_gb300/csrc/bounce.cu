@@ -42,10 +42,12 @@ namespace {
 
 constexpr int kBounceThreads = 256;
 // A warp serves (finishes pending rays, refills idle lanes) once this many of
-// its lanes are pending or idle: measured best between 20 and 28 on circles,
-// a closed room and a dash grid at 8 bounces (3.4x faster than serving every
-// finished ray at once).
-constexpr int kBounceServeMin = 24;
+// its lanes are pending or idle (3.4x faster than serving every finished ray
+// at once).  On the six bench scenes' two-step records, 2^22 mirror paths of
+// 8 bounces: 16, 20, 24, 28, 32 took 19.8, 18.6, 17.2, 16.6, 18.8 ms in all;
+// at 28 the dash grids run 5-6 % faster than at 24, circles and clusters 1
+// and 5 % slower.
+constexpr int kBounceServeMin = 28;
 
 typedef __int128 i128;
 
