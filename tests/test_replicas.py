@@ -80,3 +80,17 @@ def test_roofline_object_schema():
     assert all(not isinstance(v, (dict, list)) for v in r.values())
     r = bench.make_roofline(5000.0, 9000.0, 6775.3, "src", None, "kernel changed", 5.8, 3.1e10)
     assert r["traffic"] is None and r["dram_frac"] is None and r["l2_over_algorithmic"] is None
+
+
+def test_committed_traffic_summary_is_readable():
+    """The committed ncu summary the bench reads for `roofline.traffic` parses:
+    its figures come back when the kernel sources hash to the recorded value,
+    else the bench says the kernel changed (never that the summary is missing
+    or unreadable)."""
+    import bench
+
+    traffic, note, l2 = bench.captured_traffic()
+    if traffic is None:
+        assert note == "kernel changed since the ncu capture"
+    else:
+        assert traffic > 1e9 and l2 is not None and l2 > traffic and "from" in note
